@@ -1,0 +1,271 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+Worked examples (tests/golden/*.json, each citing its passage), Theorem 1 in
+exact rationals by brute force on tiny vertices, the ITS sampler by exhaustive
+enumeration of r, closed forms (truncated geometric PPR lengths, node2vec on a
+tiny graph), special cases and the invariant sum_k 2^k |G_k| = sum w.
+"""
+import itertools
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.conftest import golden
+from tests.stats import chisq_p, tv
+
+KIND = {"empty": O.EMPTY, "dense": O.DENSE, "one": O.ONE, "sparse": O.SPARSE, "regular": O.REGULAR}
+
+
+def _groups_by_dst(g, v):
+    """{k: sorted dst list} for vertex v through the oracle's membership export."""
+    offs, dst, w, eid = g.edges()
+    eid2dst = {int(e): int(d) for e, d in zip(eid, dst)}
+    moffs, meids = g.members_all()
+    out = {}
+    for k in range(32):
+        a, b = int(moffs[32 * v + k]), int(moffs[32 * v + k + 1])
+        if b > a:
+            out[k] = sorted(eid2dst[int(e)] for e in meids[a:b])
+    return out
+
+
+def test_running_example_groups_totals_insert_delete():
+    gd = golden("running_example.json")
+    n = 6
+    g = O.Graph.from_edges(n, [tuple(e) for e in gd["edges"]])
+    v = gd["vertex"]
+    grp = _groups_by_dst(g, v)
+    assert grp == {int(k): sorted(x) for k, x in gd["groups"].items()}
+    Wk = g.group_totals(v)
+    for k, t in gd["totals"].items():
+        assert int(Wk[int(k)]) == t
+    cnt, _, sw = g.factor(v)
+    assert sum(int(cnt[k]) << k for k in range(32)) == sw == 12
+    # insertion example
+    s, d, b = gd["insert"]["edge"]
+    rc, st = g.apply(np.array([[s, d, b, 0]]))
+    assert rc == 0 and st == (1, 0, 0)
+    assert _groups_by_dst(g, v) == {int(k): sorted(x) for k, x in gd["insert"]["groups_after"].items()}
+    # deletion example: the deleted edge is neighbour index 0 and touches groups 2^0 and 2^2
+    offs, dst, w, eid = g.edges()
+    s, d, b = gd["delete"]["edge"]
+    row = list(zip(dst[offs[v]:offs[v + 1]], w[offs[v]:offs[v + 1]]))
+    assert row.index((d, b)) == gd["delete"]["neighbor_index"]
+    assert [k for k in range(32) if b & (1 << k)] == gd["delete"]["groups_touched"]
+    rc, st = g.apply(np.array([[s, d, 0, 1]]))
+    assert rc == 0 and st == (0, 1, 0)
+    assert _groups_by_dst(g, v) == {int(k): sorted(x) for k, x in gd["delete"]["groups_after"].items()}
+
+
+def test_float_example():
+    gd = golden("float_example.json")
+    cnt, ndec, wi, wd = O.float_factor(gd["biases"], gd["lambda"])
+    for k, members in gd["groups"].items():
+        assert int(cnt[int(k)]) == len(members)
+    assert ndec == len(gd["decimal_group"])
+    assert abs(wd / (wi + wd) - gd["decimal_share"]) < 1e-12
+    # membership: neighbour j is in group k iff bit k of floor(lambda * b_j) is set
+    ip = [int(np.floor(gd["lambda"] * b)) for b in gd["biases"]]
+    assert ip == [5, 7, 3]
+
+
+def test_adaption_example():
+    gd = golden("adaption_example.json")
+    g = O.Graph.from_edges(1 + gd["d"], [(0, 1 + j, b) for j, b in enumerate(gd["biases"])])
+    cnt, kd, sw = g.factor(0, gd["alpha"], gd["beta"])
+    for k, c in gd["counts"].items():
+        assert int(cnt[int(k)]) == c
+    for k, name in gd["kinds"].items():
+        assert int(kd[int(k)]) == KIND[name], k
+    # the neighbour rejected for group 2^0 is not a member of it, and Theorem 1 still holds for it
+    grp = _groups_by_dst(g, 0)
+    for j in gd["rejected_for_group0"]:
+        assert (1 + j) not in grp[0]
+    for i, b in enumerate(gd["biases"]):
+        assert Fraction(*g.factored_prob(0, i, gd["alpha"], gd["beta"])) == Fraction(b, sw)
+
+
+def test_kind_boundaries():
+    for case in golden("kind_boundaries.json")["cases"]:
+        assert O.kind(case["cnt"], case["d"]) == KIND[case["kind"]], case
+
+
+def test_update_semantics():
+    gd = golden("update_semantics.json")
+    g = O.Graph.from_edges(gd["n"], [tuple(e) for e in gd["initial"]])
+    for b in gd["batches"]:
+        rc, st = g.apply(np.array(b["records"], dtype=np.uint32), max_bits=32)
+        if b.get("status") == "invalid":
+            assert rc == 1, b["why"]
+        else:
+            assert rc == 0 and list(st) == b["stats"], b["why"]
+        offs, dst, w, eid = g.edges()
+        for v in range(gd["n"]):
+            got = [[int(dst[j]), int(w[j]), int(eid[j])] for j in range(int(offs[v]), int(offs[v + 1]))]
+            exp = b["edges_after"].get(str(v), [])
+            assert got == exp, (b["why"], v)
+
+
+def test_philox_known_answers():
+    for vec in golden("philox_kat.json")["vectors"]:
+        out = W.philox4x32_10([int(x, 16) for x in vec["ctr"]], [int(x, 16) for x in vec["key"]])
+        assert [int(x) for x in out] == [int(x, 16) for x in vec["out"]]
+
+
+def test_node2vec_tiny_closed_form():
+    gd = golden("node2vec_tiny.json")
+    g = O.Graph.from_edges(gd["n"], [tuple(e) for e in gd["edges"]])
+    ss = gd["second_step"]
+    wts = g.n2v_weights(ss["prev"], ss["u"], gd["accept_u32"])
+    offs, dst, _, _ = g.edges()
+    nb = [int(x) for x in dst[offs[ss["u"]]:offs[ss["u"] + 1]]]
+    assert nb == ss["neighbors"]
+    tot = int(wts.sum())
+    assert [Fraction(int(x), tot) for x in wts] == [Fraction(a, ss["prob_den"]) for a in ss["prob_num"]]
+    # walk frequencies of 2-step node2vec paths from vertex 0
+    tp = gd["two_step_paths_from_0"]
+    pol = O.policy(O.NODE2VEC, 2, 0, gd["accept_u32"])
+    N = 200_000
+    paths, plen = g.walk(np.zeros(N, dtype=np.uint32), [pol], seed=11)
+    assert (plen == 3).all()
+    keys = [tuple(p) for p in tp["paths"]]
+    idx = {k: i for i, k in enumerate(keys)}
+    counts = np.zeros(len(keys))
+    for row in paths:
+        counts[idx[tuple(int(x) for x in row)]] += 1
+    probs = np.array(tp["prob_num"], dtype=np.float64) / tp["prob_den"]
+    assert tv(counts, probs) < 0.01
+    assert chisq_p(counts, probs) > 1e-3
+
+
+def _vertex_graph(configs):
+    """One vertex per bias configuration; vertex v's edges go to arbitrary targets."""
+    edges = []
+    n = len(configs) + 8
+    for v, ws in enumerate(configs):
+        for j, w in enumerate(ws):
+            edges.append((v, (v + j + 1) % n, w))
+    return O.Graph.from_edges(n, edges)
+
+
+def test_theorem1_exact_exhaustive_small():
+    configs = [c for d in (1, 2, 3) for c in itertools.product(range(1, 16), repeat=d)]
+    g = _vertex_graph(configs)
+    for v, ws in enumerate(configs):
+        s = sum(ws)
+        for i, w in enumerate(ws):
+            assert Fraction(*g.factored_prob(v, i)) == Fraction(w, s), (ws, i)
+
+
+def test_theorem1_exact_random_up_to_d6():
+    rng = np.random.default_rng(5)
+    configs = [tuple(int(x) for x in rng.integers(1, 64, size=int(rng.integers(4, 7)))) for _ in range(1500)]
+    # plus vertices whose groups cover all four kinds
+    configs += [tuple([1] * 9 + [2, 6]), tuple([1] * 30 + [3, 3]), tuple([7] * 3 + [1] * 40 + [64, 128])]
+    g = _vertex_graph(configs)
+    kinds_seen = set()
+    for v, ws in enumerate(configs):
+        _, kd, _ = g.factor(v)
+        kinds_seen |= set(int(x) for x in kd)
+        s = sum(ws)
+        for i, w in enumerate(ws):
+            assert Fraction(*g.factored_prob(v, i)) == Fraction(w, s)
+    assert {O.DENSE, O.ONE, O.SPARSE, O.REGULAR} <= kinds_seen
+
+
+def test_its_exhaustive_enumeration():
+    rng = np.random.default_rng(7)
+    configs = [tuple(int(x) for x in rng.integers(1, 40, size=int(rng.integers(1, 7)))) for _ in range(120)]
+    g = _vertex_graph(configs)
+    for v, ws in enumerate(configs):
+        hits = [0] * len(ws)
+        for r in range(sum(ws)):
+            hits[g.its_pick(v, r)] += 1
+        assert hits == list(ws)
+
+
+def test_special_cases_uniform_and_powers_of_two():
+    # all biases 1: one group (k = 0) holding every edge -> uniform sampling
+    g = O.Graph.from_edges(12, [(0, j + 1, 1) for j in range(10)])
+    cnt, kd, sw = g.factor(0)
+    assert int(cnt[0]) == 10 and int(cnt[1:].sum()) == 0 and kd[0] == O.DENSE
+    assert all(Fraction(*g.factored_prob(0, i)) == Fraction(1, 10) for i in range(10))
+    # distinct powers of two: every edge alone in its own group
+    g = O.Graph.from_edges(12, [(0, j + 1, 1 << j) for j in range(10)])
+    cnt, kd, sw = g.factor(0)
+    assert [int(x) for x in cnt[:10]] == [1] * 10 and int(cnt[10:].sum()) == 0
+    assert all(kd[k] == O.ONE for k in range(10))
+    assert sw == (1 << 10) - 1
+
+
+def test_invariants_after_random_batches():
+    wl = W.make_workload("c1")
+    G = wl.graph
+    g = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    m0 = g.m
+    for b in wl.batches:
+        rc, (ins, dele, nf) = g.apply(b.records(), G.max_bits)
+        assert rc == 0
+        assert g.m == m0 + ins - dele
+        m0 = g.m
+    cnt, kd, sw = g.factor_all()
+    offs, dst, w, eid = g.edges()
+    deg = np.diff(offs.astype(np.int64))
+    tot = (cnt.astype(np.uint64) << np.arange(32, dtype=np.uint64)[None, :]).sum(axis=1)
+    assert (tot == sw).all()
+    for v in range(0, G.n, 97):
+        Wk = g.group_totals(v)
+        assert all(int(Wk[k]) == int(cnt[v, k]) << k for k in range(32))
+        assert all(int(kd[v, k]) == O.kind(int(cnt[v, k]), int(deg[v])) for k in range(32))
+    assert len(np.unique(eid)) == len(eid)
+
+
+def test_oracle_sampler_statistics():
+    wl = W.make_workload("c1")
+    G = wl.graph
+    g = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    offs, dst, w, eid = g.edges()
+    for v in (0, 17, 511):
+        a, b = int(offs[v]), int(offs[v + 1])
+        s = g.sample_many(v, 1_000_000, seed=v + 1)
+        counts = np.bincount(s.astype(np.int64), minlength=b - a)
+        probs = w[a:b].astype(np.float64)
+        assert tv(counts, probs) < 0.01
+        assert chisq_p(counts, probs) > 1e-3
+
+
+def test_ppr_length_truncated_geometric():
+    # a ring with chords: every vertex has out-edges, so only the stop rule ends walks
+    n = 64
+    edges = [(v, (v + 1) % n, 1 + v % 5) for v in range(n)] + [(v, (v * 7 + 3) % n, 2) for v in range(n)]
+    g = O.Graph.from_edges(n, edges)
+    s_u32 = 644245094  # round(0.15 * 2^32)
+    cap = 30
+    pol = O.policy(O.PPR, cap, s_u32)
+    N = 400_000
+    starts = W.walk_starts(n, N, 3)
+    _, plen = g.walk(starts, [pol], seed=5)
+    steps = plen.astype(np.int64) - 1
+    counts = np.bincount(steps, minlength=cap + 1)
+    s = s_u32 / 2 ** 32
+    probs = np.array([(1 - s) ** l * s for l in range(cap)] + [(1 - s) ** cap])
+    assert abs(probs.sum() - 1) < 1e-12
+    assert chisq_p(counts, probs) > 1e-3
+    assert tv(counts, probs) < 0.01
+
+
+def test_oracle_walk_steps_are_live_edges_and_padding():
+    wl = W.make_workload("c1")
+    G = wl.graph
+    g = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    starts = W.walk_starts(G.n, 256, 0)
+    paths, plen = g.walk(starts, [O.policy(O.DEEPWALK, 80)], seed=1)
+    for i in range(256):
+        L = int(plen[i])
+        assert paths[i, 0] == starts[i]
+        for t in range(L - 1):
+            assert g.has_edge(int(paths[i, t]), int(paths[i, t + 1]))
+        assert (paths[i, L:] == O.PAD).all()
