@@ -1,0 +1,286 @@
+/*
+ * bingo.h — C ABI of a GB300 (sm_103a) library for biased random walks on
+ * dynamic graphs with radix-factorised sampling (Bingo, arXiv 2504.10233).
+ *
+ * Method (Section 4.1): each integer edge bias w is split into its binary
+ * digits, D(w) = {2^k : w AND 2^k != 0} (Eq. dwi).  Every vertex keeps one
+ * neighbour group G_k per bit position k, with total W(p_k) = 2^k |G_k|
+ * (Eq. wpk).  Sampling picks a group with probability W(p_k) / sum_j W(p_j)
+ * (Eq. group_prob), then a member uniformly (Eq. pvp), which draws neighbour i
+ * with probability w_i / sum w (Theorem 1).  Groups are stored as dense,
+ * one-element, sparse or regular by Eq. group (Section 5.1); edge insertions
+ * and deletions update the groups in place, batched per source vertex with a
+ * two-phase delete-and-swap (Section 5.2).
+ *
+ * Conventions for every entry point:
+ *  - Pointer arguments may be device pointers or host pointers; the library
+ *    detects which (cudaPointerGetAttributes).  Host inputs are copied to the
+ *    device and host outputs are copied back before the call returns.  Device
+ *    pointers are used in place, in stream order on `stream`.
+ *  - The caller owns all inputs and outputs; the library owns bingo_graph and
+ *    bingo_server and everything they allocate.
+ *  - No call throws.  Every call returns a bingo_status; bingo_last_error()
+ *    returns a thread-local message for the last failure on this thread.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.
+ *  - Vertex ids are < n < 2^31.  Biases are 1 <= w < 2^max_bits (max_bits <= 32).
+ *  - Calls on one graph must not run concurrently from several host threads.
+ */
+#ifndef BINGO_H
+#define BINGO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bingo_graph bingo_graph;
+typedef struct bingo_server bingo_server;
+
+typedef enum {
+    BINGO_OK = 0,
+    BINGO_E_INVALID = 1, /* bad argument or malformed batch; state unchanged */
+    BINGO_E_OOM = 2,     /* device memory or the graph's pool is exhausted; state unchanged */
+    BINGO_E_CUDA = 3,    /* a CUDA call failed (message in bingo_last_error) */
+    BINGO_E_TIMEOUT = 4, /* a bounded wait expired (device or host side) */
+    BINGO_E_STATE = 5    /* call not valid in the object's current state */
+} bingo_status;
+
+/* Group kinds of Eq. group (Section 5.1). */
+enum { BINGO_KIND_EMPTY = 0, BINGO_KIND_DENSE = 1, BINGO_KIND_ONE = 2, BINGO_KIND_SPARSE = 3, BINGO_KIND_REGULAR = 4 };
+
+/* Walk applications (Section 2.2; Section 6.1 evaluation settings). */
+enum { BINGO_DEEPWALK = 0, BINGO_PPR = 1, BINGO_NODE2VEC = 2 };
+
+/* Update operations (Section 4.2): insertion, deletion, and a bias change
+ * built from one insertion plus one deletion of the same (src, dst). */
+enum { BINGO_OP_INSERT = 0, BINGO_OP_DELETE = 1, BINGO_OP_SET_BIAS = 2 };
+
+/* Walk execution forms (low byte of `mode`), plus flags. */
+enum {
+    BINGO_WALK_PERSISTENT = 0, /* one persistent launch; warps pull walkers from a device queue */
+    BINGO_WALK_STEPWISE = 1,   /* one launch per step over all walkers (the paper's step-by-step form, Section 6) */
+    BINGO_WALK_NO_PAD = 0x100  /* flag: leave path entries beyond path_len untouched instead of writing 0xFFFFFFFF */
+};
+
+typedef struct {
+    uint32_t alpha_pct;        /* Eq. group alpha, percent (paper: 40) */
+    uint32_t beta_pct;         /* Eq. group beta, percent (paper: 10) */
+    uint32_t max_bits;         /* K: bias bits, 1..32; biases must be < 2^max_bits */
+    uint32_t lanes_per_walker; /* group-selection team width: 1, 4 or 32; 0 = tuned default */
+    uint32_t warps_per_block;  /* walker kernel block size in warps; 0 = tuned default */
+    uint32_t blocks_per_sm;    /* walker kernel persistent blocks per SM; 0 = tuned default */
+    uint32_t update_chunk;     /* segments above this many adjacency slots use a whole block; 0 = default */
+    uint32_t reserved;
+    uint64_t pool_words;       /* device pool for adjacency and group blocks, in 4-byte words; 0 = auto */
+} bingo_config;
+
+/* One update record, 16 bytes. */
+typedef struct {
+    uint32_t src, dst, bias; /* bias ignored for BINGO_OP_DELETE */
+    uint32_t op;             /* BINGO_OP_* */
+} bingo_update;
+
+typedef struct {
+    uint64_t inserted;          /* insertion records applied (op 0 and op 2) */
+    uint64_t deleted;           /* deletions that removed an edge (op 1 and op 2) */
+    uint64_t not_found;         /* deletions whose (src, dst) had no live copy */
+    uint64_t conversions[5][5]; /* [old kind][new kind] group-kind changes of touched vertices (Table trans) */
+    uint64_t vertices_touched;
+    uint64_t groups_rebuilt;    /* groups rebuilt from the adjacency after a kind change or a capacity change */
+} bingo_update_stats;
+
+typedef struct {
+    uint32_t kind;           /* BINGO_DEEPWALK | BINGO_PPR | BINGO_NODE2VEC */
+    uint32_t max_len;        /* steps; the path holds at most max_len + 1 vertices */
+    uint32_t ppr_stop_u32;   /* PPR: before every step, stop iff a uniform u32 < ppr_stop_u32 */
+    uint32_t reserved;
+    uint64_t n2v_accept[3];  /* node2vec: accept a candidate at distance 0/1/2 from the previous vertex iff a
+                                uniform u32 < n2v_accept[dist]; values in [0, 2^32] = f(dist) / max f * 2^32 */
+} bingo_policy;
+
+/* Library and build info. */
+const char* bingo_version(void);
+/* Thread-local message describing the last non-OK status on this thread. */
+const char* bingo_last_error(void);
+/* Default configuration: alpha 40, beta 10 (Section 5.1), max_bits 32, everything else tuned. */
+void bingo_default_config(bingo_config* cfg);
+
+/*
+ * Build the factorised sampling state from a CSR graph (Section 4.1, sampling
+ * space construction; Section 5.1, adaptive group representation).
+ *   n        number of vertices (< 2^31)
+ *   m        number of edges
+ *   row_ptr  uint64[n+1], row_ptr[0] = 0, row_ptr[n] = m
+ *   col      uint32[m]  destination of each edge
+ *   bias     uint32[m]  1 <= bias < 2^cfg->max_bits
+ *   cfg      nullable: defaults of bingo_default_config
+ * Edge ids are assigned 0..m-1 in CSR order; later insertions continue the count.
+ * Errors: BINGO_E_INVALID (bad ids or biases; nothing allocated), BINGO_E_OOM, BINGO_E_CUDA.
+ * Synchronises `stream` before returning.  *out receives the new graph.
+ */
+bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t* col,
+                          const uint32_t* bias, const bingo_config* cfg, void* stream, bingo_graph** out);
+
+/* Free the graph and everything it owns.  NULL is allowed. */
+bingo_status bingo_destroy(bingo_graph* g);
+
+/*
+ * Apply one batch of updates in place (Section 5.2, parallel batched graph
+ * updates; Section 4.2 for single-edge insertion and deletion).
+ *   ups    bingo_update[count]
+ *   stats  nullable host pointer; filled when given
+ * Semantics: all insertions of the batch in batch order (new edge ids continue
+ * after the largest id ever assigned), then all deletions in batch order, each
+ * removing the live copy of (src, dst) with the smallest edge id (the earliest
+ * version of a duplicated edge).  A deletion of a missing edge is counted in
+ * not_found and is not an error.  BINGO_OP_SET_BIAS is an insertion of
+ * (src, dst, bias) plus a deletion of (src, dst) under these rules.  Group
+ * kinds are re-evaluated for every touched vertex after the batch.
+ * Errors: BINGO_E_INVALID if any record has src or dst >= n, op > 2, or an
+ * inserted bias outside [1, 2^max_bits): the whole batch is rejected before any
+ * change.  BINGO_E_OOM if the pool cannot hold the batch's growth: the batch
+ * is rejected before any change.  Synchronises `stream` before returning.
+ */
+bingo_status bingo_apply_updates(bingo_graph* g, const bingo_update* ups, uint64_t count, void* stream,
+                                 bingo_update_stats* stats);
+
+/*
+ * Streaming updates (Section 4.2): apply the records one at a time, in order,
+ * each as a batch of size one (so kinds are re-evaluated after every record),
+ * inside a single launch.  Same validation, errors and stats as
+ * bingo_apply_updates.  Synchronises `stream` before returning.
+ */
+bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint64_t count, void* stream,
+                                  bingo_update_stats* stats);
+
+/*
+ * Random walks (Section 2.2; sampling by Eqs. group_prob and pvp, dense groups
+ * by rejection on the neighbour list, Section 5.1; node2vec by rejection
+ * against f(prev, x) of Eq. node2vec, first step first-order).
+ *   nwalkers    number of walkers; walker i starts at starts[i]
+ *   starts      uint32[nwalkers]
+ *   lengths     nullable uint32[nwalkers]: step limit per walker (default: its policy's max_len)
+ *   policy_ids  nullable uint8[nwalkers]: index into policies (default 0)
+ *   policies    host array of npolicies bingo_policy (npolicies 1..16)
+ *   seed        Philox4x32-10 key; walker i draws from counters (i, 0, step, j)
+ *   stride      row length of paths (>= longest step limit + 1)
+ *   paths       uint32[nwalkers][stride]: vertex sequence including the start, padded with 0xFFFFFFFF
+ *   path_len    uint32[nwalkers]: vertices written (steps taken + 1)
+ *   mode        BINGO_WALK_PERSISTENT or BINGO_WALK_STEPWISE
+ * A vertex without out-edges ends the walk.  Results depend only on (graph
+ * state, seed, walker index) — not on the launch shape or the mode.
+ * Asynchronous on `stream` when every pointer is a device pointer.
+ */
+bingo_status bingo_walk(bingo_graph* g, uint64_t nwalkers, const uint32_t* starts, const uint32_t* lengths,
+                        const uint8_t* policy_ids, const bingo_policy* policies, uint32_t npolicies, uint64_t seed,
+                        uint32_t stride, uint32_t* paths, uint32_t* path_len, uint32_t mode, void* stream);
+
+/*
+ * Synchronise `stream` and return the device status latched by earlier
+ * asynchronous calls on this graph (BINGO_E_INVALID for a bad start vertex,
+ * policy id or length; BINGO_E_TIMEOUT if a bounded rejection loop gave up),
+ * then clear it.
+ */
+bingo_status bingo_check(bingo_graph* g, void* stream);
+
+/* Sizes needed by bingo_export_state (host pointer). */
+typedef struct {
+    uint64_t n;            /* vertices */
+    uint64_t m;            /* live edges */
+    uint64_t list_entries; /* member entries of all regular and sparse groups */
+    uint64_t sparse_entries; /* entries of all sparse neighbour lists */
+    uint64_t pool_words_used;
+    uint64_t pool_words_total;
+    uint64_t next_edge_id;
+} bingo_state_sizes;
+
+bingo_status bingo_state_sizes_get(bingo_graph* g, bingo_state_sizes* out);
+
+/*
+ * Copy the whole sampling state to host buffers (checkpoint and parity checks).
+ * All pointers are host pointers sized from bingo_state_sizes_get:
+ *   deg[n]; dst[m], bias[m], eid[m]: adjacency of each vertex in slot order,
+ *     vertices concatenated in id order (offsets = prefix sum of deg);
+ *   cnt[32n]: |G_k|; kind[32n]: BINGO_KIND_*;
+ *   one_slot[32n]: slot of the single member of one-element groups (else 0xFFFFFFFF);
+ *   glen[32n]: stored member-list length of regular and sparse groups (else 0);
+ *   members[list_entries]: member lists in (vertex, k) order — slots for
+ *     regular groups, positions in the vertex's sparse list for sparse groups;
+ *   member_inv[list_entries]: the group's inverted index read at each member
+ *     (must equal the member's own position);
+ *   sp_len[n]; sp_list[sparse_entries]: each vertex's sparse neighbour list (slots);
+ *   sp_inv[sparse_entries]: the sparse list's inverted index read at each entry.
+ * Synchronises the graph's internal stream.
+ */
+bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, uint32_t* bias, uint64_t* eid,
+                                uint32_t* cnt, uint8_t* kind, uint32_t* one_slot, uint32_t* glen, uint32_t* members,
+                                uint32_t* member_inv, uint32_t* sp_len, uint32_t* sp_list, uint32_t* sp_inv);
+
+/* Bytes of device state by structure: [0] adjacency, [1] counts+headers+group refs,
+ * [2] regular groups, [3] sparse groups + sparse lists, [4] edge index, [5] pool capacity. */
+bingo_status bingo_memory_report(bingo_graph* g, uint64_t out[6]);
+
+/*
+ * Autotune the walker launch (lanes per walker, warps per block, blocks per SM)
+ * on this graph with a trial walk of `nwalkers` DeepWalk walkers of `length`
+ * steps from the given device/host starts; the best setting is stored in the
+ * graph's config.  out_cfg (nullable) receives it.  Synchronises `stream`.
+ */
+bingo_status bingo_autotune(bingo_graph* g, uint64_t nwalkers, const uint32_t* starts, uint32_t length, void* stream,
+                            bingo_config* out_cfg);
+
+/* Current configuration of the graph (host pointer). */
+bingo_status bingo_get_config(bingo_graph* g, bingo_config* out);
+bingo_status bingo_set_walk_config(bingo_graph* g, uint32_t lanes_per_walker, uint32_t warps_per_block,
+                                   uint32_t blocks_per_sm);
+
+/* Kernel launches issued by this graph so far (walk, update and build kernels). */
+uint64_t bingo_kernel_launches(bingo_graph* g);
+
+/* ---------------------------------------------------------------------------------------------- serving
+ * Continuous-batching request loop (the paper's "integrate all updates before
+ * each walk", Section 6 (ii)): a host thread owns the graph; streaming updates
+ * are queued and applied at epoch boundaries; walk requests are admitted while
+ * device memory and walker slots allow, merged into shared launches, and
+ * complete independently.  A request binds to the epoch current at admission,
+ * and its paths depend only on (that epoch's state, its seed, walker index).
+ */
+typedef struct {
+    uint64_t max_inflight_walkers; /* walker slots; 0 = 4M */
+    uint64_t hbm_reserve_bytes;    /* admission keeps this much device memory free; 0 = 1 GiB */
+    uint32_t max_update_batch;     /* updates applied per epoch at most; 0 = 65536 */
+    uint32_t concurrent_launches;  /* walk launches in flight at once; 0 = 4 */
+    uint32_t max_len_cap;          /* longest step limit a request may ask for; 0 = 128 */
+    uint32_t flags;                /* BINGO_SERVER_NO_MERGE: one request per launch (the plain form) */
+} bingo_server_config;
+
+enum { BINGO_SERVER_NO_MERGE = 1 };
+
+typedef struct {
+    uint64_t requests_done, walkers_done, steps_done, updates_applied, epochs;
+    double p50_ms, p99_ms, mean_ms; /* arrival to completion, completed requests */
+} bingo_server_stats;
+
+/* The server takes over the graph until bingo_server_destroy; no other call may use it meanwhile. */
+bingo_status bingo_server_create(bingo_graph* g, const bingo_server_config* cfg, bingo_server** out);
+bingo_status bingo_server_destroy(bingo_server* s);
+/* Queue updates (host records, copied); *epoch (nullable) receives the epoch that will include them. */
+bingo_status bingo_server_submit_updates(bingo_server* s, const bingo_update* ups, uint64_t n, uint64_t* epoch);
+/* Queue a walk request (host starts, copied).  Returns a ticket. */
+bingo_status bingo_server_submit_walk(bingo_server* s, const uint32_t* starts, uint64_t nwalkers,
+                                      const bingo_policy* policy, uint64_t seed, uint64_t* ticket);
+/* Wait up to timeout_ms for a request; copies paths ([nwalkers][policy max_len+1]) and lengths to host
+ * buffers, and the epoch it ran at.  BINGO_E_TIMEOUT if not done in time (it stays queued). */
+bingo_status bingo_server_wait(bingo_server* s, uint64_t ticket, uint32_t timeout_ms, uint32_t* paths,
+                               uint32_t* path_len, uint64_t* epoch);
+/* Block until every queued update and request has been processed (bounded by timeout_ms). */
+bingo_status bingo_server_drain(bingo_server* s, uint32_t timeout_ms);
+bingo_status bingo_server_stats_get(bingo_server* s, bingo_server_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BINGO_H */

@@ -10,7 +10,7 @@
  *     (dst, bias, edge id), kept in ascending edge-id order;
  *   - batched updates with the paper's per-batch order: all insertions, then
  *     all deletions, where deleting a duplicated edge removes the earliest
- *     copy (Section 4.4, parallel batched updates);
+ *     copy (Section 5.2, parallel batched updates);
  *   - the radix factorisation recomputed from scratch from the adjacency:
  *     D(w) (Eq. dwi), group sizes |G_k| and totals W(p_k) = 2^k |G_k| (Eq. wpk),
  *     and the group kinds of Eq. group (alpha, beta in percent);
@@ -128,7 +128,7 @@ int o_has_edge(const o_graph* g, uint32_t u, uint32_t x) {
  * are built from insertions and deletions).
  * Order: all insertions in batch order (new edge ids continue after the
  * largest id ever assigned), then all deletions in batch order, each removing
- * the live copy of (src, dst) with the smallest edge id (Section 4.4).
+ * the live copy of (src, dst) with the smallest edge id (Section 5.2).
  * A deletion that finds no copy changes nothing and is counted in not_found.
  * Validation (src, dst < n; 1 <= bias < 2^max_bits for insertions; op <= 2)
  * runs over the whole batch first; any failure returns O_INVALID and leaves

@@ -1,0 +1,220 @@
+// C-ABI entry points for walks, the walker autotuner and device-status checks.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "bingo_host.h"
+
+using namespace bingo;
+
+#define CK(call, what)                                     \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+namespace bingo {
+bingo_status edge_index_build(bingo_graph* g, cudaStream_t s);
+}
+
+namespace {
+
+bingo_status check_policies(const bingo_policy* pols, uint32_t npol, uint32_t stride, bool have_lengths,
+                            bool* need_n2v, uint32_t* max_len) {
+    if (!pols || npol == 0 || npol > MAX_POL) {
+        set_error("policies: need 1..%u entries", MAX_POL);
+        return BINGO_E_INVALID;
+    }
+    *need_n2v = false;
+    *max_len = 0;
+    for (uint32_t i = 0; i < npol; i++) {
+        const bingo_policy& p = pols[i];
+        if (p.kind > BINGO_NODE2VEC) { set_error("policy %u: unknown kind %u", i, p.kind); return BINGO_E_INVALID; }
+        if (p.kind == BINGO_NODE2VEC) {
+            *need_n2v = true;
+            for (int d = 0; d < 3; d++)
+                if (p.n2v_accept[d] > (1ull << 32)) { set_error("policy %u: n2v_accept > 2^32", i); return BINGO_E_INVALID; }
+        }
+        if (!have_lengths && (uint64_t)p.max_len + 1 > stride) {
+            set_error("policy %u: max_len %u does not fit stride %u", i, p.max_len, stride);
+            return BINGO_E_INVALID;
+        }
+        *max_len = std::max(*max_len, p.max_len);
+    }
+    return BINGO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bingo_status bingo_walk(bingo_graph* g, uint64_t nwalkers, const uint32_t* starts, const uint32_t* lengths,
+                        const uint8_t* policy_ids, const bingo_policy* policies, uint32_t npolicies, uint64_t seed,
+                        uint32_t stride, uint32_t* paths, uint32_t* path_len, uint32_t mode, void* stream) {
+    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+    if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
+    const uint32_t base_mode = mode & 0xFF;
+    const bool pad = !(mode & 0x100);
+    if (base_mode > BINGO_WALK_STEPWISE) { set_error("unknown walk mode %u", mode); return BINGO_E_INVALID; }
+    if (nwalkers && (!starts || !paths || !path_len)) { set_error("NULL walk buffer"); return BINGO_E_INVALID; }
+    if (stride == 0) { set_error("stride must be >= 1"); return BINGO_E_INVALID; }
+    bool need_n2v = false;
+    uint32_t max_len = 0;
+    bingo_status st = check_policies(policies, npolicies, stride, lengths != nullptr, &need_n2v, &max_len);
+    if (st != BINGO_OK) return st;
+    if (nwalkers == 0) return BINGO_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (need_n2v && g->G.eh_mask == 0) {
+        st = edge_index_build(g, s);
+        if (st != BINGO_OK) return st;
+    }
+    bool host_io = false;
+    auto in = [&](const void* src, size_t bytes, Buf& b, const void** out) -> bingo_status {
+        if (!src || is_device_ptr(src)) { *out = src; return BINGO_OK; }
+        host_io = true;
+        CK(ensure(b, bytes), "walk staging");
+        CK(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, s), "walk upload");
+        *out = b.p;
+        return BINGO_OK;
+    };
+    const uint32_t *ds, *dl;
+    const uint8_t* dp;
+    if ((st = in(starts, 4 * nwalkers, g->w_starts, (const void**)&ds)) != BINGO_OK) return st;
+    if ((st = in(lengths, 4 * nwalkers, g->w_len, (const void**)&dl)) != BINGO_OK) return st;
+    if ((st = in(policy_ids, nwalkers, g->w_pid, (const void**)&dp)) != BINGO_OK) return st;
+    uint32_t* dpaths = paths;
+    uint32_t* dplen = path_len;
+    const bool host_paths = !is_device_ptr(paths), host_plen = !is_device_ptr(path_len);
+    if (host_paths) {
+        CK(ensure(g->w_paths, 4ull * nwalkers * stride), "walk output staging");
+        dpaths = (uint32_t*)g->w_paths.p;
+    }
+    if (host_plen) {
+        CK(ensure(g->w_plen, 4ull * nwalkers), "walk output staging");
+        dplen = (uint32_t*)g->w_plen.p;
+    }
+    CK(ensure(g->w_pols, sizeof(bingo_policy) * npolicies), "policy staging");
+    CK(cudaMemcpyAsync(g->w_pols.p, policies, sizeof(bingo_policy) * npolicies, cudaMemcpyHostToDevice, s),
+       "policy upload");
+    WalkReq q;
+    q.nwalkers = nwalkers;
+    q.starts = ds;
+    q.lengths = dl;
+    q.pids = dp;
+    q.dev_pols = (const bingo_policy*)g->w_pols.p;
+    q.npol = npolicies;
+    q.seed = seed;
+    q.stride = stride;
+    q.paths = dpaths;
+    q.plen = dplen;
+    q.mode = base_mode;
+    q.pad = pad;
+    q.max_steps = lengths ? stride - 1 : max_len;
+    q.queue = (unsigned long long*)((uint64_t*)g->d_ctl + CTL_QUEUE);
+    st = walk_launch(g, q, s);
+    if (st != BINGO_OK) return st;
+    if (host_paths) CK(cudaMemcpyAsync(paths, dpaths, 4ull * nwalkers * stride, cudaMemcpyDeviceToHost, s), "paths download");
+    if (host_plen) CK(cudaMemcpyAsync(path_len, dplen, 4ull * nwalkers, cudaMemcpyDeviceToHost, s), "lengths download");
+    if (host_io || host_paths || host_plen) {
+        CK(cudaStreamSynchronize(s), "walk");
+        uint32_t status = 0;
+        CK(cudaMemcpy(&status, (uint64_t*)g->d_ctl + CTL_STATUS, 4, cudaMemcpyDeviceToHost), "status read");
+        if (status & ST_STATE) { set_error("walk: inconsistent group structure"); return BINGO_E_STATE; }
+        if (status & ST_INVALID) { set_error("walk: a start vertex >= n, a policy id >= npolicies or a length > stride-1"); return BINGO_E_INVALID; }
+        if (status & ST_TIMEOUT) { set_error("walk: a bounded rejection loop gave up"); return BINGO_E_TIMEOUT; }
+    }
+    return BINGO_OK;
+}
+
+// Synchronise `stream` and return (and clear) the device status latched by asynchronous calls.
+bingo_status bingo_check(bingo_graph* g, void* stream) {
+    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "sync");
+    uint32_t status = 0;
+    uint64_t* word = (uint64_t*)g->d_ctl + CTL_STATUS;
+    CK(cudaMemcpy(&status, word, 4, cudaMemcpyDeviceToHost), "status read");
+    CK(cudaMemset(word, 0, 8), "status clear");
+    if (status & ST_STATE) { set_error("device found an inconsistent group structure"); return BINGO_E_STATE; }
+    if (status & ST_INVALID) { set_error("device reported an invalid argument"); return BINGO_E_INVALID; }
+    if (status & ST_OOM) { set_error("device pool exhausted"); return BINGO_E_OOM; }
+    if (status & ST_TIMEOUT) { set_error("a bounded device loop gave up"); return BINGO_E_TIMEOUT; }
+    return BINGO_OK;
+}
+
+bingo_status bingo_autotune(bingo_graph* g, uint64_t nwalkers, const uint32_t* starts, uint32_t length, void* stream,
+                            bingo_config* out_cfg) {
+    if (!g || !starts || nwalkers == 0 || length == 0) { set_error("autotune: bad arguments"); return BINGO_E_INVALID; }
+    cudaStream_t s = (cudaStream_t)stream;
+    Buf dstarts, dpaths, dplen;
+    const uint32_t* ds = starts;
+    auto cleanup = [&]() { release(dstarts); release(dpaths); release(dplen); };
+    if (!is_device_ptr(starts)) {
+        cudaError_t e = ensure(dstarts, 4 * nwalkers);
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "autotune"); }
+        cudaMemcpyAsync(dstarts.p, starts, 4 * nwalkers, cudaMemcpyHostToDevice, s);
+        ds = (const uint32_t*)dstarts.p;
+    }
+    const uint32_t stride = length + 1;
+    cudaError_t e = ensure(dpaths, 4ull * nwalkers * stride);
+    if (e == cudaSuccess) e = ensure(dplen, 4ull * nwalkers);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "autotune"); }
+    bingo_policy pol;
+    memset(&pol, 0, sizeof(pol));
+    pol.kind = BINGO_DEEPWALK;
+    pol.max_len = length;
+    e = ensure(g->w_pols, sizeof(bingo_policy));
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "autotune"); }
+    cudaMemcpyAsync(g->w_pols.p, &pol, sizeof(pol), cudaMemcpyHostToDevice, s);
+    WalkReq q;
+    q.nwalkers = nwalkers;
+    q.starts = ds;
+    q.dev_pols = (const bingo_policy*)g->w_pols.p;
+    q.npol = 1;
+    q.stride = stride;
+    q.paths = (uint32_t*)dpaths.p;
+    q.plen = (uint32_t*)dplen.p;
+    q.mode = BINGO_WALK_PERSISTENT;
+    q.pad = false;
+    q.max_steps = length;
+    q.queue = (unsigned long long*)((uint64_t*)g->d_ctl + CTL_QUEUE);
+    const WalkTune saved = g->tune;
+    const uint32_t lanes_c[3] = {1, 4, 32};
+    const uint32_t wpb_c[3] = {4, 8, 16};
+    float best = 1e30f;
+    WalkTune bestt = saved;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (uint32_t li = 0; li < 3; li++) {
+        for (uint32_t wi = 0; wi < 3; wi++) {
+            g->tune.lanes = lanes_c[li];
+            g->tune.warps_per_block = wpb_c[wi];
+            g->tune.blocks_per_sm = 0;
+            float tsum = 0;
+            bool ok = true;
+            for (int rep = 0; rep < 3 && ok; rep++) {
+                cudaEventRecord(e0, s);
+                q.seed = 1234 + rep;
+                ok = walk_launch(g, q, s) == BINGO_OK;
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tsum += ms;
+            }
+            if (ok && tsum < best) {
+                best = tsum;
+                bestt = g->tune;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cleanup();
+    g->tune = bestt;
+    if (out_cfg) bingo_get_config(g, out_cfg);
+    return best < 1e30f ? BINGO_OK : BINGO_E_CUDA;
+}
+
+}  // extern "C"

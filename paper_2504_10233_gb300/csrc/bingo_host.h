@@ -1,0 +1,103 @@
+// Host-side graph object and helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "bingo_internal.cuh"
+
+namespace bingo {
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// grow-only device buffer
+cudaError_t ensure(Buf& b, size_t bytes);
+void release(Buf& b);
+
+void set_error(const char* fmt, ...);
+bingo_status cuda_fail(cudaError_t e, const char* what);
+bool is_device_ptr(const void* p);
+
+// device-wide exclusive scan of u64 values; *total_dev (device) receives the sum
+cudaError_t scan_excl_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* total_dev, Buf& tmp,
+                          cudaStream_t s, uint64_t* launches);
+
+// stable LSD radix sort of (key u64, value u32) pairs on the low `bits` key bits
+cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, uint64_t n,
+                             uint32_t bits, Buf& tmp, cudaStream_t s, bool* result_in_alt, uint64_t* launches);
+
+// One walk launch, all pointers on the device.
+struct WalkReq {
+    uint64_t nwalkers = 0;
+    const uint32_t* starts = nullptr;
+    const uint32_t* lengths = nullptr;   // nullable
+    const uint8_t* pids = nullptr;       // nullable
+    const bingo_policy* dev_pols = nullptr;
+    uint32_t npol = 0;
+    uint64_t seed = 0;
+    uint32_t stride = 0;
+    uint32_t* paths = nullptr;
+    uint32_t* plen = nullptr;
+    uint32_t mode = 0;                   // BINGO_WALK_PERSISTENT / STEPWISE
+    bool pad = true;
+    uint32_t max_steps = 0;              // step launches of the stepwise form
+    unsigned long long* queue = nullptr; // device work counter of this launch
+    const uint64_t* req_off = nullptr;   // request mode
+    const uint64_t* req_key = nullptr;
+    uint32_t nreq = 0;
+};
+
+bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s);
+
+struct WalkTune {
+    uint32_t lanes = 1;         // lanes per walker: 1, 4, 32
+    uint32_t warps_per_block = 8;
+    uint32_t blocks_per_sm = 0; // 0 = occupancy maximum
+};
+
+}  // namespace bingo
+
+struct bingo_graph {
+    bingo_config cfg;
+    int device = 0;
+    int num_sms = 0;
+    uint32_t n = 0;
+    uint64_t m_live = 0;
+    uint64_t next_eid = 0;
+    bingo::DevGraph G{};
+    // owned device allocations
+    void* d_hdr = nullptr;
+    void* d_cnt = nullptr;
+    void* d_gref = nullptr;
+    void* d_pool = nullptr;
+    void* d_ctl = nullptr;      // control words: top, npending, leaked, status, queue, counters
+    void* d_fcount = nullptr;
+    void* d_fstack = nullptr;
+    void* d_pending = nullptr;
+    void* d_eh = nullptr;       // edge index keys + counts
+    uint64_t eh_distinct = 0;   // keys ever placed in the edge index (tombstones included)
+    // scratch
+    bingo::Buf s_in, s_keys, s_keys2, s_vals, s_vals2, s_tmp, s_seg, s_rank, s_best, s_aux, s_walk, s_stage;
+    bingo::Buf w_starts, w_len, w_pid, w_paths, w_plen, w_pols;
+    // walk tuning
+    bingo::WalkTune tune;
+    uint64_t launches = 0;
+    bool broken = false;        // a device-side failure left the state unusable
+};
+
+// control-word layout inside d_ctl (u64 words)
+enum CtlSlot : int {
+    CTL_TOP = 0,
+    CTL_NPENDING = 1,
+    CTL_LEAKED = 2,
+    CTL_STATUS = 3,     // u32 in the low half
+    CTL_QUEUE = 4,
+    CTL_STATS = 8,      // 30 u64: inserted, deleted, not_found, touched, rebuilt, conv[5][5]
+    CTL_SCR = 40,       // scratch words of the update pipeline
+    CTL_WORDS = 64
+};

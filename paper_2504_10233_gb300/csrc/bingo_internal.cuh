@@ -1,0 +1,369 @@
+// Internal device structures and primitives of the radix-factorised sampler.
+//
+// Device state of a graph (all in HBM, indexed by vertex v):
+//   hdr[v]      VHdr, one 32-byte sector: adjacency block, degree d, nonempty-group mask,
+//               sparse-list block, |S|, log2 capacities.
+//   cnt[v][32]  |G_k| for k < 32, one 128-byte line per vertex (Eq. wpk: W(p_k) = 2^k |G_k|).
+//   gref[v][32] per-group reference: one-element -> slot of its member; regular/sparse ->
+//               word offset of the group block; dense/empty -> 0.
+//   pool        u32 words holding every variable-size block, in power-of-two sizes:
+//                 adjacency   4*capA words: capA x {dst, bias} (8 B, AoS) then capA x u64 edge id
+//                 regular k   2*capA words: member slots [capA] then inverted index [capA] (by slot)
+//                 sparse list 2*capA words: S = slots of edges in any sparse group [capA], then
+//                             S_inv [capA] (by slot)
+//                 sparse k    2*capS words: member positions in S [capS] then inverted index [capS]
+// A group's kind is never stored: it is the pure function of (|G_k|, d) given by Eq. group.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bingo.h"
+
+namespace bingo {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr uint32_t NONE32 = 0xFFFFFFFFu;
+constexpr uint64_t DEAD_BIT = 1ull << 63;      // set in an adjacency edge id while its slot is being deleted
+constexpr uint64_t GOFF_MASK = (1ull << 56) - 1;
+constexpr uint32_t MIN_CAPA = 4;               // smallest adjacency capacity of a vertex with edges
+constexpr uint32_t MIN_CAPS = 4;
+constexpr int NCLASS = 48;                     // pool size classes: block of 8 << c words
+constexpr uint32_t MAX_POL = 16;
+
+enum : uint32_t { K_EMPTY = 0, K_DENSE = 1, K_ONE = 2, K_SPARSE = 3, K_REGULAR = 4 };
+
+// status bits accumulated on the device
+enum : uint32_t {
+    ST_INVALID = 1u,
+    ST_OOM = 2u,
+    ST_TIMEOUT = 4u,   // a bounded loop gave up (corrupt state or an impossible rejection)
+    ST_STATE = 8u,
+};
+
+struct __align__(32) VHdr {
+    uint64_t adj;   // word offset of the adjacency block (0 = none)
+    uint32_t deg;   // live edges d
+    uint32_t mask;  // bit k set iff |G_k| > 0
+    uint64_t sref;  // word offset of the sparse-list block (0 = none)
+    uint32_t nsp;   // |S|
+    uint8_t lcapa;  // log2(capA) + 1, 0 = no adjacency block
+    uint8_t lcaps;  // log2(capS) + 1, 0 = no sparse groups
+    uint16_t pad;
+};
+static_assert(sizeof(VHdr) == 32, "VHdr must be one sector");
+
+__host__ __device__ __forceinline__ uint32_t capa_of(const VHdr& h) { return h.lcapa ? (1u << (h.lcapa - 1)) : 0u; }
+__host__ __device__ __forceinline__ uint32_t caps_of(const VHdr& h) { return h.lcaps ? (1u << (h.lcaps - 1)) : 0u; }
+
+// Eq. group (Section 5.1), in its printed order with strict percent comparisons.
+__host__ __device__ __forceinline__ uint32_t kind_of(uint32_t c, uint32_t d, uint32_t alpha, uint32_t beta) {
+    if (c == 0) return K_EMPTY;
+    const uint64_t c100 = 100ull * c;
+    if (c100 > (uint64_t)alpha * d) return K_DENSE;
+    if (c == 1) return K_ONE;
+    if (c100 < (uint64_t)beta * d) return K_SPARSE;
+    return K_REGULAR;
+}
+__host__ __device__ __forceinline__ bool is_list(uint32_t k) { return k == K_REGULAR || k == K_SPARSE; }
+
+__host__ __device__ __forceinline__ uint32_t next_pow2_u32(uint32_t x) {
+    if (x <= 1) return 1;
+#ifdef __CUDA_ARCH__
+    return 1u << (32 - __clz(x - 1));
+#else
+    return 1u << (32 - __builtin_clz(x - 1));
+#endif
+}
+__host__ __device__ __forceinline__ uint32_t log2_u32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return 31 - __clz(x);
+#else
+    return 31 - __builtin_clz(x);
+#endif
+}
+__host__ __device__ __forceinline__ uint32_t capa_for(uint32_t d) {
+    if (d == 0) return 0;
+    uint32_t c = next_pow2_u32(d);
+    return c < MIN_CAPA ? MIN_CAPA : c;
+}
+__host__ __device__ __forceinline__ uint32_t caps_for(uint32_t s) {
+    uint32_t c = next_pow2_u32(s);
+    return c < MIN_CAPS ? MIN_CAPS : c;
+}
+// size class of a power-of-two block of `words` (>= 8) words
+__host__ __device__ __forceinline__ uint32_t class_of(uint64_t words) {
+    uint32_t c = 0;
+    while ((8ull << c) < words) c++;
+    return c;
+}
+
+// ---------------------------------------------------------------------------------------------- pool
+
+struct Pool {
+    uint32_t* base;                  // words
+    uint64_t words;                  // capacity
+    unsigned long long* top;         // device: bump pointer (words)
+    long long* fcount;               // device [NCLASS]: free blocks available per class
+    uint64_t* fstack;                // device [NCLASS][fcap]
+    uint64_t fcap;                   // entries per class stack
+    unsigned long long* npending;    // device: frees made during the current batch
+    uint64_t* pending;               // device [pcap]: (offset << 8) | class
+    uint64_t pcap;
+    unsigned long long* leaked;      // device: words dropped because a free list was full
+    uint32_t* status;                // device status word
+};
+
+#ifdef __CUDACC__
+// Allocate a power-of-two block (words >= 8).  Free blocks of the class are
+// popped first; otherwise the bump pointer advances.  Frees made in the same
+// batch only become reusable at the batch's end, so pops never race pushes.
+__device__ __forceinline__ uint64_t pool_alloc(const Pool& P, uint64_t words) {
+    const uint32_t c = class_of(words);
+    const uint64_t sz = 8ull << c;
+    const long long i = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&P.fcount[c]), ~0ull) - 1;
+    if (i >= 0 && (uint64_t)i < P.fcap) return P.fstack[(uint64_t)c * P.fcap + (uint64_t)i];
+    unsigned long long off = atomicAdd(P.top, (unsigned long long)sz);
+    if (off + sz > P.words) {
+        atomicOr(P.status, ST_OOM);
+        return 0;
+    }
+    return off;
+}
+__device__ __forceinline__ void pool_free(const Pool& P, uint64_t off, uint64_t words) {
+    if (off == 0) return;
+    const uint32_t c = class_of(words);
+    unsigned long long i = atomicAdd(P.npending, 1ull);
+    if (i < P.pcap) P.pending[i] = (off << 8) | c;
+    else atomicAdd(P.leaked, (unsigned long long)(8ull << c));
+}
+#endif
+
+// ---------------------------------------------------------------------------------------------- graph view
+
+struct DevGraph {
+    uint32_t n;
+    uint32_t max_bits;
+    uint32_t alpha, beta;
+    VHdr* hdr;
+    uint32_t* cnt;
+    uint64_t* gref;
+    Pool pool;
+    // edge index (node2vec distance probe): open addressing over (src << 32 | dst) -> live copies
+    unsigned long long* eh_key;  // EH_EMPTY = empty
+    uint32_t* eh_cnt;
+    uint64_t eh_mask;            // capacity - 1, 0 = absent
+};
+constexpr unsigned long long EH_EMPTY = 0xFFFFFFFFFFFFFFFFull;
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint2* adj_pairs(const DevGraph& G, uint64_t adj) { return reinterpret_cast<uint2*>(G.pool.base + adj); }
+__device__ __forceinline__ uint64_t* adj_eids(const DevGraph& G, uint64_t adj, uint32_t capa) {
+    return reinterpret_cast<uint64_t*>(G.pool.base + adj + 2ull * capa);
+}
+
+__device__ __forceinline__ uint64_t eh_hash(uint64_t key) {
+    key ^= key >> 33;
+    key *= 0xff51afd7ed558ccdull;
+    key ^= key >> 33;
+    key *= 0xc4ceb9fe1a85ec53ull;
+    key ^= key >> 33;
+    return key;
+}
+// live copies of (u, x) in the edge index; bounded probe
+__device__ __forceinline__ uint32_t eh_lookup(const DevGraph& G, uint32_t u, uint32_t x) {
+    const unsigned long long key = ((unsigned long long)u << 32) | x;
+    uint64_t h = eh_hash(key) & G.eh_mask;
+    for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
+        unsigned long long k = __ldg(G.eh_key + h);
+        if (k == key) return __ldg(G.eh_cnt + h);
+        if (k == EH_EMPTY) return 0;
+        h = (h + 1) & G.eh_mask;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11):
+// ten rounds of two 32x32 -> 64 multiplies with a Weyl-sequence key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Per walker-step stream: counter (walker lo, walker hi, step, j) with j = 0, 1, ...;
+// the four outputs of each call are consumed in order.
+struct StepRng {
+    uint2 key;
+    uint32_t c0, c1, step, j;
+    uint4 buf;
+    uint32_t left;
+    __device__ __forceinline__ void init(uint2 k, uint64_t walker, uint32_t s) {
+        key = k;
+        c0 = (uint32_t)walker;
+        c1 = (uint32_t)(walker >> 32);
+        step = s;
+        j = 0;
+        left = 0;
+    }
+    __device__ __forceinline__ uint32_t next() {
+        if (left == 0) {
+            buf = philox4x32_10(make_uint4(c0, c1, step, j++), key);
+            left = 4;
+        }
+        const uint32_t r = buf.x;
+        buf.x = buf.y;
+        buf.y = buf.z;
+        buf.z = buf.w;
+        left--;
+        return r;
+    }
+};
+
+// Exact uniform integer in [0, range), range >= 1: Lemire's multiply-shift with
+// rejection ("Fast random integer generation in an interval", ACM TOMACS 2019).
+// A draw is rejected iff the low word of x * range is below 2^32 mod range.
+// The retry loop is bounded; running out (probability < 2^-60) flags ST_TIMEOUT.
+__device__ __forceinline__ uint32_t below32(StepRng& R, uint32_t range, uint32_t* status) {
+    uint32_t x = R.next();
+    uint64_t m = (uint64_t)x * range;
+    uint32_t l = (uint32_t)m;
+    if (l < range) {
+        const uint32_t t = (0u - range) % range;
+        int guard = 0;
+        while (l < t) {
+            if (++guard > 64) { atomicOr(status, ST_TIMEOUT); break; }
+            x = R.next();
+            m = (uint64_t)x * range;
+            l = (uint32_t)m;
+        }
+    }
+    return (uint32_t)(m >> 32);
+}
+__device__ __forceinline__ uint64_t below64(StepRng& R, uint64_t range, uint32_t* status) {
+    if (range <= 0xFFFFFFFFull) return below32(R, (uint32_t)range, status);
+    uint64_t x = ((uint64_t)R.next() << 32) | R.next();
+    uint64_t lo = x * range, hi = __umul64hi(x, range);
+    if (lo < range) {
+        const uint64_t t = (0ull - range) % range;
+        int guard = 0;
+        while (lo < t) {
+            if (++guard > 64) { atomicOr(status, ST_TIMEOUT); break; }
+            x = ((uint64_t)R.next() << 32) | R.next();
+            lo = x * range;
+            hi = __umul64hi(x, range);
+        }
+    }
+    return hi;
+}
+
+// ---------------------------------------------------------------------------------------------- teams
+// A team is the set of threads that cooperates on one vertex: a warp or a block.
+// Every member must reach every team call (loops run a team-uniform trip count).
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+struct WarpTeam {
+    __device__ __forceinline__ uint32_t size() const { return 32; }
+    __device__ __forceinline__ uint32_t rank() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    // exclusive prefix count of a predicate, in rank order
+    __device__ __forceinline__ uint32_t scan_pred(bool p, uint32_t& total) const {
+        const uint32_t b = __ballot_sync(FULL, p);
+        total = __popc(b);
+        return __popc(b & lanemask_lt());
+    }
+    __device__ __forceinline__ uint32_t scan_excl(uint32_t x, uint32_t& total) const {
+        uint32_t v = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, v, d);
+            if ((threadIdx.x & 31) >= (uint32_t)d) v += y;
+        }
+        total = __shfl_sync(FULL, v, 31);
+        return v - x;
+    }
+    __device__ __forceinline__ uint32_t sum(uint32_t x) const {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(FULL, x, d);
+        return x;
+    }
+    __device__ __forceinline__ uint32_t max(uint32_t x) const {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) x = ::max(x, __shfl_xor_sync(FULL, x, d));
+        return x;
+    }
+    __device__ __forceinline__ bool any(bool p) const { return __any_sync(FULL, p); }
+};
+
+// Block team; needs `sm` = shared scratch of at least 40 words, private to the team.
+struct BlockTeam {
+    uint32_t* sm;
+    __device__ __forceinline__ uint32_t size() const { return blockDim.x; }
+    __device__ __forceinline__ uint32_t rank() const { return threadIdx.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ uint32_t scan_excl(uint32_t x, uint32_t& total) const {
+        const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+        uint32_t v = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, v, d);
+            if (lane >= (uint32_t)d) v += y;
+        }
+        if (lane == 31) sm[w] = v;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t t = lane < nw ? sm[lane] : 0, s = t;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                uint32_t y = __shfl_up_sync(FULL, s, d);
+                if (lane >= (uint32_t)d) s += y;
+            }
+            if (lane < nw) sm[lane] = s - t;
+            if (lane == 31) sm[32] = s;
+        }
+        __syncthreads();
+        const uint32_t r = sm[w] + v - x;
+        total = sm[32];
+        __syncthreads();
+        return r;
+    }
+    __device__ __forceinline__ uint32_t scan_pred(bool p, uint32_t& total) const { return scan_excl(p ? 1u : 0u, total); }
+    __device__ __forceinline__ uint32_t sum(uint32_t x) const {
+        uint32_t t;
+        scan_excl(x, t);
+        return t;
+    }
+    __device__ __forceinline__ uint32_t max(uint32_t x) const {
+        const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) x = ::max(x, __shfl_xor_sync(FULL, x, d));
+        if (lane == 0) sm[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t t = lane < nw ? sm[lane] : 0;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) t = ::max(t, __shfl_xor_sync(FULL, t, d));
+            if (lane == 0) sm[32] = t;
+        }
+        __syncthreads();
+        const uint32_t r = sm[32];
+        __syncthreads();
+        return r;
+    }
+    __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
+};
+#endif  // __CUDACC__
+
+}  // namespace bingo

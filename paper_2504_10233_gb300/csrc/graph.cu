@@ -1,0 +1,584 @@
+// Graph creation from CSR (Section 4.1, sampling space construction; Section 5.1,
+// adaptive group representation), destruction, state export and reports.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "bingo_host.h"
+#include "groups.cuh"
+
+using namespace bingo;
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+namespace bingo {
+const char* last_error_cstr();
+}
+
+// ------------------------------------------------------------------------------------------- kernels
+
+__global__ void k_validate_csr(uint32_t n, uint64_t m, const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                               const uint32_t* __restrict__ bias, uint32_t max_bits, uint32_t* status) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (uint64_t j = tid; j < m; j += nt) {
+        const uint32_t w = bias[j];
+        bad |= col[j] >= n || w == 0 || (max_bits < 32 && (w >> max_bits) != 0);
+    }
+    for (uint64_t v = tid; v < n; v += nt) {
+        const uint64_t a = rp[v], b = rp[v + 1];
+        bad |= b < a || b - a >= 0xFFFFFFFFull;
+    }
+    if (tid == 0) bad |= rp[0] != 0 || rp[n] != m;
+    if (bad) atomicOr(status, ST_INVALID);
+}
+
+// Per vertex: d, |G_k| (Eq. dwi / wpk by ballot over 32-edge chunks), mask, kinds (Eq. group),
+// |S| and the words its blocks need.  One warp per vertex.
+__global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const uint32_t* __restrict__ bias,
+                              uint64_t* __restrict__ words) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = warp; v < G.n; v += nwarps) {
+        const uint64_t a = rp[v];
+        const uint32_t d = (uint32_t)(rp[v + 1] - a);
+        uint32_t c = 0;  // lane k: |G_k|
+        for (uint32_t b = 0; b < d; b += 32) {
+            const uint32_t w = (b + lane < d) ? bias[a + b + lane] : 0u;
+#pragma unroll
+            for (int k = 0; k < 32; k++) {
+                const uint32_t bb = __ballot_sync(FULL, (w >> k) & 1u);
+                if (lane == (uint32_t)k) c += __popc(bb);
+            }
+        }
+        G.cnt[v * 32 + lane] = c;
+        const uint32_t kd = kind_of(c, d, G.alpha, G.beta);
+        const uint32_t mask = __ballot_sync(FULL, c > 0);
+        const uint32_t regm = __ballot_sync(FULL, kd == K_REGULAR);
+        const uint32_t spm = __ballot_sync(FULL, kd == K_SPARSE);
+        uint32_t nsp = 0;
+        if (spm) {
+            for (uint32_t b = 0; b < d; b += 32) {
+                const uint32_t w = (b + lane < d) ? bias[a + b + lane] : 0u;
+                nsp += __popc(__ballot_sync(FULL, (w & spm) != 0u));
+            }
+        }
+        if (lane == 0) {
+            const uint32_t capa = capa_for(d);
+            const uint32_t caps = spm ? caps_for(nsp) : 0;
+            uint64_t wd = (uint64_t)4 * capa + (uint64_t)__popc(regm) * 2 * capa;
+            if (spm) wd += 2ull * capa + (uint64_t)__popc(spm) * 2 * caps;
+            words[v] = wd;
+            VHdr h;
+            h.adj = 0;
+            h.deg = d;
+            h.mask = mask;
+            h.sref = 0;
+            h.nsp = nsp;
+            h.lcapa = capa ? (uint8_t)(log2_u32(capa) + 1) : 0;
+            h.lcaps = caps ? (uint8_t)(log2_u32(caps) + 1) : 0;
+            h.pad = 0;
+            G.hdr[v] = h;
+        }
+    }
+}
+
+// Copy edges into the vertex's adjacency block and build its group structures.
+__global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
+                             const uint32_t* __restrict__ bias, const uint64_t* __restrict__ offs, uint64_t base) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    WarpTeam t;
+    for (uint64_t v = warp; v < G.n; v += nwarps) {
+        VHdr h = G.hdr[v];
+        const uint32_t d = h.deg, capa = capa_of(h), caps = caps_of(h);
+        const uint64_t a = rp[v];
+        uint64_t next = base + offs[v];
+        const uint32_t c = G.cnt[v * 32 + lane];
+        const uint32_t kd = kind_of(c, d, G.alpha, G.beta);
+        const uint32_t regm = __ballot_sync(FULL, kd == K_REGULAR);
+        const uint32_t spm = __ballot_sync(FULL, kd == K_SPARSE);
+        const uint32_t onem = __ballot_sync(FULL, kd == K_ONE);
+        uint64_t gref = 0;
+        if (d) {
+            h.adj = next;
+            uint2* pairs = adj_pairs(G, h.adj);
+            uint64_t* eids = adj_eids(G, h.adj, capa);
+            for (uint32_t j = lane; j < d; j += 32) {
+                pairs[j] = make_uint2(col[a + j], bias[a + j]);
+                eids[j] = a + j;
+            }
+            next += 4ull * capa;
+        }
+        __syncwarp();
+        for (uint32_t m = regm; m; m &= m - 1) {
+            const uint32_t k = __ffs(m) - 1;
+            build_regular(t, G, h.adj, d, k, next, capa);
+            if (lane == k) gref = next;
+            next += 2ull * capa;
+        }
+        if (spm) {
+            h.sref = next;
+            const uint32_t ns = build_slist(t, G, h.adj, d, spm, h.sref, capa);
+            next += 2ull * capa;
+            __syncwarp();
+            for (uint32_t m = spm; m; m &= m - 1) {
+                const uint32_t k = __ffs(m) - 1;
+                build_sparse(t, G, h.adj, h.sref, ns, k, next, caps);
+                if (lane == k) gref = next;
+                next += 2ull * caps;
+            }
+        }
+        for (uint32_t m = onem; m; m &= m - 1) {
+            const uint32_t k = __ffs(m) - 1;
+            const uint32_t s = find_one(t, G, h.adj, d, k);
+            if (lane == k) gref = s;
+        }
+        G.gref[v * 32 + lane] = gref;
+        if (lane == 0) G.hdr[v] = h;
+    }
+}
+
+// ---- export ----------------------------------------------------------------------------------------------
+
+__global__ void k_export_sizes(DevGraph G, uint64_t* __restrict__ deg64, uint64_t* __restrict__ glen64,
+                               uint64_t* __restrict__ nsp64) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = warp; v < G.n; v += nwarps) {
+        const VHdr h = G.hdr[v];
+        const uint32_t c = G.cnt[v * 32 + lane];
+        const uint32_t kd = kind_of(c, h.deg, G.alpha, G.beta);
+        glen64[v * 32 + lane] = is_list(kd) ? c : 0;
+        if (lane == 0) {
+            deg64[v] = h.deg;
+            nsp64[v] = h.sref ? h.nsp : 0;
+        }
+    }
+}
+
+__global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, const uint64_t* __restrict__ goff,
+                              const uint64_t* __restrict__ soff, uint32_t* __restrict__ odst,
+                              uint32_t* __restrict__ obias, uint64_t* __restrict__ oeid, uint8_t* __restrict__ okind,
+                              uint32_t* __restrict__ oone, uint32_t* __restrict__ omem, uint32_t* __restrict__ ominv,
+                              uint32_t* __restrict__ osp, uint32_t* __restrict__ ospinv) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = warp; v < G.n; v += nwarps) {
+        const VHdr h = G.hdr[v];
+        const uint32_t d = h.deg, capa = capa_of(h), caps = caps_of(h);
+        if (d) {
+            const uint2* pairs = adj_pairs(G, h.adj);
+            const uint64_t* eids = adj_eids(G, h.adj, capa);
+            for (uint32_t j = lane; j < d; j += 32) {
+                const uint2 e = pairs[j];
+                odst[eoff[v] + j] = e.x;
+                obias[eoff[v] + j] = e.y;
+                oeid[eoff[v] + j] = eids[j];
+            }
+        }
+        const uint32_t c = G.cnt[v * 32 + lane];
+        const uint32_t kd = kind_of(c, d, G.alpha, G.beta);
+        const uint64_t gr = G.gref[v * 32 + lane];
+        okind[v * 32 + lane] = (uint8_t)kd;
+        oone[v * 32 + lane] = kd == K_ONE ? (uint32_t)gr : NONE32;
+        const uint32_t listm = __ballot_sync(FULL, is_list(kd));
+        for (uint32_t m = listm; m; m &= m - 1) {
+            const uint32_t k = __ffs(m) - 1;
+            const uint64_t g = __shfl_sync(FULL, gr, k) & GOFF_MASK;
+            const uint32_t ck = __shfl_sync(FULL, c, k);
+            const uint32_t kk = __shfl_sync(FULL, kd, k);
+            const uint32_t icap = kk == K_REGULAR ? capa : caps;
+            const uint32_t* mem = G.pool.base + g;
+            const uint32_t* inv = mem + icap;
+            const uint64_t o = goff[v * 32 + k];
+            for (uint32_t i = lane; i < ck; i += 32) {
+                const uint32_t x = mem[i];
+                omem[o + i] = x;
+                ominv[o + i] = x < icap ? inv[x] : NONE32;
+            }
+        }
+        if (h.sref) {
+            const uint32_t* S = G.pool.base + h.sref;
+            const uint32_t* Sinv = S + capa;
+            for (uint32_t i = lane; i < h.nsp; i += 32) {
+                const uint32_t x = S[i];
+                osp[soff[v] + i] = x;
+                ospinv[soff[v] + i] = x < capa ? Sinv[x] : NONE32;
+            }
+        }
+    }
+}
+
+// memory by structure: [0] adjacency words, [1] regular group words, [2] sparse words
+__global__ void k_memory(DevGraph G, unsigned long long* out) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long a = 0, r = 0, s = 0;
+    for (uint64_t v = warp; v < G.n; v += nwarps) {
+        const VHdr h = G.hdr[v];
+        const uint32_t capa = capa_of(h), caps = caps_of(h);
+        const uint32_t kd = kind_of(G.cnt[v * 32 + lane], h.deg, G.alpha, G.beta);
+        const uint32_t regm = __ballot_sync(FULL, kd == K_REGULAR), spm = __ballot_sync(FULL, kd == K_SPARSE);
+        if (lane == 0) {
+            a += 4ull * capa;
+            r += (unsigned long long)__popc(regm) * 2 * capa;
+            if (h.sref) s += 2ull * capa + (unsigned long long)__popc(spm) * 2 * caps;
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(out + 0, a);
+        atomicAdd(out + 1, r);
+        atomicAdd(out + 2, s);
+    }
+}
+
+// ------------------------------------------------------------------------------------------- host
+
+static unsigned grid_for(const bingo_graph* g, uint64_t work_items, unsigned block) {
+    uint64_t b = (work_items + block - 1) / block;
+    uint64_t cap = (uint64_t)g->num_sms * 16;
+    if (b > cap) b = cap;
+    if (b == 0) b = 1;
+    return (unsigned)b;
+}
+
+static void free_graph(bingo_graph* g) {
+    if (!g) return;
+    void* ptrs[] = {g->d_hdr, g->d_cnt, g->d_gref, g->d_pool, g->d_ctl, g->d_fcount, g->d_fstack, g->d_pending, g->d_eh};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    Buf* bufs[] = {&g->s_in, &g->s_keys, &g->s_keys2, &g->s_vals, &g->s_vals2, &g->s_tmp, &g->s_seg,
+                   &g->s_rank, &g->s_best, &g->s_aux, &g->s_walk, &g->s_stage,
+                   &g->w_starts, &g->w_len, &g->w_pid, &g->w_paths, &g->w_plen};
+    for (Buf* b : bufs) release(*b);
+    delete g;
+}
+
+// stage a host or device array on the device; returns the device pointer (maybe the input)
+static bingo_status stage_in(const void* src, size_t bytes, Buf& buf, cudaStream_t s, const void** out) {
+    if (bytes == 0 || is_device_ptr(src)) {
+        *out = src;
+        return BINGO_OK;
+    }
+    CK(ensure(buf, bytes), "staging allocation");
+    CK(cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, s), "staging copy");
+    *out = buf.p;
+    return BINGO_OK;
+}
+
+extern "C" {
+
+const char* bingo_version(void) { return "bingo-gb300 0.1 (sm_103a)"; }
+
+const char* bingo_last_error(void) { return bingo::last_error_cstr(); }
+
+void bingo_default_config(bingo_config* c) {
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->alpha_pct = 40;
+    c->beta_pct = 10;
+    c->max_bits = 32;
+}
+
+bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* bias,
+                          const bingo_config* cfg, void* stream, bingo_graph** out) {
+    if (!out) { set_error("out is NULL"); return BINGO_E_INVALID; }
+    *out = nullptr;
+    if (n == 0 || n >= 0x80000000u || !row_ptr || (m && (!col || !bias))) {
+        set_error("invalid graph arguments (n=%u, m=%llu)", n, (unsigned long long)m);
+        return BINGO_E_INVALID;
+    }
+    bingo_config c;
+    bingo_default_config(&c);
+    if (cfg) c = *cfg;
+    if (c.max_bits == 0 || c.max_bits > 32 || c.alpha_pct > 100 || c.beta_pct > 100) {
+        set_error("invalid config (max_bits=%u alpha=%u beta=%u)", c.max_bits, c.alpha_pct, c.beta_pct);
+        return BINGO_E_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    bingo_graph* g = new bingo_graph();
+    g->cfg = c;
+    g->n = n;
+    cudaGetDevice(&g->device);
+    cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    bingo_status st = BINGO_OK;
+    auto fail = [&](bingo_status x) { free_graph(g); return x; };
+    const uint64_t* rp = nullptr;
+    const uint32_t *cl = nullptr, *bs = nullptr;
+    Buf brp, bcl, bbs;
+    auto release_stage = [&]() { release(brp); release(bcl); release(bbs); };
+    if ((st = stage_in(row_ptr, sizeof(uint64_t) * ((size_t)n + 1), brp, s, (const void**)&rp)) != BINGO_OK) { release_stage(); return fail(st); }
+    if ((st = stage_in(col, sizeof(uint32_t) * m, bcl, s, (const void**)&cl)) != BINGO_OK) { release_stage(); return fail(st); }
+    if ((st = stage_in(bias, sizeof(uint32_t) * m, bbs, s, (const void**)&bs)) != BINGO_OK) { release_stage(); return fail(st); }
+
+    auto cu = [&](cudaError_t e, const char* what) -> bool {
+        if (e != cudaSuccess) { st = cuda_fail(e, what); return false; }
+        return true;
+    };
+    if (!cu(cudaMalloc(&g->d_ctl, CTL_WORDS * sizeof(uint64_t)), "control words") ||
+        !cu(cudaMemsetAsync(g->d_ctl, 0, CTL_WORDS * sizeof(uint64_t), s), "control init")) { release_stage(); return fail(st); }
+    uint64_t* ctl = (uint64_t*)g->d_ctl;
+    uint32_t* status = (uint32_t*)(ctl + CTL_STATUS);
+    k_validate_csr<<<grid_for(g, (m > n ? m : n), 256), 256, 0, s>>>(n, m, rp, cl, bs, c.max_bits, status);
+    g->launches++;
+    uint32_t hst = 0;
+    if (!cu(cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, s), "status read") ||
+        !cu(cudaStreamSynchronize(s), "validate")) { release_stage(); return fail(st); }
+    if (hst & ST_INVALID) {
+        set_error("invalid CSR: ids >= n, zero or too-wide biases, or malformed row_ptr");
+        release_stage();
+        return fail(BINGO_E_INVALID);
+    }
+    if (!cu(cudaMalloc(&g->d_hdr, sizeof(VHdr) * (size_t)n), "vertex headers") ||
+        !cu(cudaMalloc(&g->d_cnt, sizeof(uint32_t) * 32 * (size_t)n), "group counts") ||
+        !cu(cudaMalloc(&g->d_gref, sizeof(uint64_t) * 32 * (size_t)n), "group refs")) { release_stage(); return fail(st); }
+    DevGraph& G = g->G;
+    G.n = n;
+    G.max_bits = c.max_bits;
+    G.alpha = c.alpha_pct;
+    G.beta = c.beta_pct;
+    G.hdr = (VHdr*)g->d_hdr;
+    G.cnt = (uint32_t*)g->d_cnt;
+    G.gref = (uint64_t*)g->d_gref;
+    G.pool.status = status;
+    G.pool.top = (unsigned long long*)(ctl + CTL_TOP);
+    G.pool.npending = (unsigned long long*)(ctl + CTL_NPENDING);
+    G.pool.leaked = (unsigned long long*)(ctl + CTL_LEAKED);
+
+    Buf words, offs, tot;
+    auto release_all = [&]() { release(words); release(offs); release(tot); release_stage(); };
+    if (!cu(ensure(words, sizeof(uint64_t) * n), "build words") || !cu(ensure(offs, sizeof(uint64_t) * n), "build offsets") ||
+        !cu(ensure(tot, 64), "build total")) { release_all(); return fail(st); }
+    const unsigned wblocks = grid_for(g, (uint64_t)n * 32, 256);
+    k_build_count<<<wblocks, 256, 0, s>>>(G, rp, bs, (uint64_t*)words.p);
+    g->launches++;
+    if (!cu(scan_excl_u64((uint64_t*)words.p, (uint64_t*)offs.p, n, (uint64_t*)tot.p, g->s_tmp, s, &g->launches), "build scan")) {
+        release_all(); return fail(st);
+    }
+    uint64_t total = 0;
+    if (!cu(cudaMemcpyAsync(&total, tot.p, 8, cudaMemcpyDeviceToHost, s), "total read") ||
+        !cu(cudaStreamSynchronize(s), "build count")) { release_all(); return fail(st); }
+    const uint64_t base = 8;  // word 0..7 reserved: offset 0 means "no block"
+    uint64_t need = base + total;
+    uint64_t pool_words = c.pool_words;
+    size_t fr = 0, tt = 0;
+    cudaMemGetInfo(&fr, &tt);
+    if (pool_words == 0) {
+        pool_words = need + need / 2 + (64ull << 20);
+        const uint64_t avail = fr > (4ull << 30) ? (fr - (4ull << 30)) / 4 : 0;
+        if (pool_words > avail) pool_words = std::max<uint64_t>(need + (need >> 4), avail);
+    }
+    pool_words = (pool_words + 7) & ~7ull;
+    if (pool_words < need) {
+        set_error("pool too small: need %llu words, have %llu", (unsigned long long)need, (unsigned long long)pool_words);
+        release_all();
+        return fail(BINGO_E_OOM);
+    }
+    if (!cu(cudaMalloc(&g->d_pool, pool_words * 4), "pool")) { release_all(); return fail(st); }
+    G.pool.base = (uint32_t*)g->d_pool;
+    G.pool.words = pool_words;
+    // free lists
+    uint64_t fcap = pool_words / 256;
+    fcap = std::max<uint64_t>(4096, std::min<uint64_t>(fcap, 1ull << 19));
+    const uint64_t pcap = 1ull << 20;
+    if (!cu(cudaMalloc(&g->d_fcount, sizeof(long long) * NCLASS), "free counts") ||
+        !cu(cudaMalloc(&g->d_fstack, sizeof(uint64_t) * NCLASS * fcap), "free stacks") ||
+        !cu(cudaMalloc(&g->d_pending, sizeof(uint64_t) * pcap), "pending frees") ||
+        !cu(cudaMemsetAsync(g->d_fcount, 0, sizeof(long long) * NCLASS, s), "free init")) { release_all(); return fail(st); }
+    G.pool.fcount = (long long*)g->d_fcount;
+    G.pool.fstack = (uint64_t*)g->d_fstack;
+    G.pool.fcap = fcap;
+    G.pool.pending = (uint64_t*)g->d_pending;
+    G.pool.pcap = pcap;
+    G.eh_key = nullptr;
+    G.eh_cnt = nullptr;
+    G.eh_mask = 0;
+    if (!cu(cudaMemcpyAsync(G.pool.top, &need, 8, cudaMemcpyHostToDevice, s), "pool top")) { release_all(); return fail(st); }
+    k_build_fill<<<wblocks, 256, 0, s>>>(G, rp, cl, bs, (uint64_t*)offs.p, base);
+    g->launches++;
+    if (!cu(cudaGetLastError(), "build fill") || !cu(cudaStreamSynchronize(s), "build fill")) { release_all(); return fail(st); }
+    release_all();
+    g->m_live = m;
+    g->next_eid = m;
+    g->tune.lanes = c.lanes_per_walker ? c.lanes_per_walker : 1;
+    g->tune.warps_per_block = c.warps_per_block ? c.warps_per_block : 8;
+    g->tune.blocks_per_sm = c.blocks_per_sm;
+    *out = g;
+    return BINGO_OK;
+}
+
+bingo_status bingo_destroy(bingo_graph* g) {
+    if (!g) return BINGO_OK;
+    cudaDeviceSynchronize();
+    free_graph(g);
+    return BINGO_OK;
+}
+
+uint64_t bingo_kernel_launches(bingo_graph* g) { return g ? g->launches : 0; }
+
+bingo_status bingo_get_config(bingo_graph* g, bingo_config* out) {
+    if (!g || !out) { set_error("NULL argument"); return BINGO_E_INVALID; }
+    *out = g->cfg;
+    out->lanes_per_walker = g->tune.lanes;
+    out->warps_per_block = g->tune.warps_per_block;
+    out->blocks_per_sm = g->tune.blocks_per_sm;
+    out->pool_words = g->G.pool.words;
+    return BINGO_OK;
+}
+
+bingo_status bingo_set_walk_config(bingo_graph* g, uint32_t lanes, uint32_t wpb, uint32_t bps) {
+    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+    if (!(lanes == 1 || lanes == 4 || lanes == 32) || wpb == 0 || wpb > 32) {
+        set_error("invalid walk config (lanes %u, warps/block %u)", lanes, wpb);
+        return BINGO_E_INVALID;
+    }
+    g->tune.lanes = lanes;
+    g->tune.warps_per_block = wpb;
+    g->tune.blocks_per_sm = bps;
+    return BINGO_OK;
+}
+
+struct ExportPlan {
+    Buf deg64, eoff, glen, goff, nsp, soff, tot;
+    void release_all() {
+        release(deg64); release(eoff); release(glen); release(goff); release(nsp); release(soff); release(tot);
+    }
+};
+
+static bingo_status export_plan(bingo_graph* g, ExportPlan& P, uint64_t totals[3]) {
+    const uint64_t n = g->n;
+    CK(ensure(P.deg64, 8 * n), "export");
+    CK(ensure(P.eoff, 8 * n), "export");
+    CK(ensure(P.glen, 8 * 32 * n), "export");
+    CK(ensure(P.goff, 8 * 32 * n), "export");
+    CK(ensure(P.nsp, 8 * n), "export");
+    CK(ensure(P.soff, 8 * n), "export");
+    CK(ensure(P.tot, 64), "export");
+    cudaStream_t s = 0;
+    k_export_sizes<<<grid_for(g, n * 32, 256), 256, 0, s>>>(g->G, (uint64_t*)P.deg64.p, (uint64_t*)P.glen.p,
+                                                            (uint64_t*)P.nsp.p);
+    uint64_t* tot = (uint64_t*)P.tot.p;
+    CK(scan_excl_u64((uint64_t*)P.deg64.p, (uint64_t*)P.eoff.p, n, tot + 0, g->s_tmp, s, &g->launches), "export scan");
+    CK(scan_excl_u64((uint64_t*)P.glen.p, (uint64_t*)P.goff.p, 32 * n, tot + 1, g->s_tmp, s, &g->launches), "export scan");
+    CK(scan_excl_u64((uint64_t*)P.nsp.p, (uint64_t*)P.soff.p, n, tot + 2, g->s_tmp, s, &g->launches), "export scan");
+    CK(cudaMemcpy(totals, tot, 24, cudaMemcpyDeviceToHost), "export totals");
+    return BINGO_OK;
+}
+
+bingo_status bingo_state_sizes_get(bingo_graph* g, bingo_state_sizes* out) {
+    if (!g || !out) { set_error("NULL argument"); return BINGO_E_INVALID; }
+    CK(cudaDeviceSynchronize(), "sync");
+    ExportPlan P;
+    uint64_t t[3];
+    bingo_status st = export_plan(g, P, t);
+    P.release_all();
+    if (st != BINGO_OK) return st;
+    uint64_t top = 0;
+    CK(cudaMemcpy(&top, g->G.pool.top, 8, cudaMemcpyDeviceToHost), "pool top");
+    out->n = g->n;
+    out->m = t[0];
+    out->list_entries = t[1];
+    out->sparse_entries = t[2];
+    out->pool_words_used = top;
+    out->pool_words_total = g->G.pool.words;
+    out->next_edge_id = g->next_eid;
+    return BINGO_OK;
+}
+
+bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, uint32_t* bias, uint64_t* eid,
+                                uint32_t* cnt, uint8_t* kind, uint32_t* one_slot, uint32_t* glen, uint32_t* members,
+                                uint32_t* member_inv, uint32_t* sp_len, uint32_t* sp_list, uint32_t* sp_inv) {
+    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+    CK(cudaDeviceSynchronize(), "sync");
+    ExportPlan P;
+    uint64_t t[3];
+    bingo_status st = export_plan(g, P, t);
+    if (st != BINGO_OK) { P.release_all(); return st; }
+    const uint64_t n = g->n, m = t[0], L = t[1], S = t[2];
+    Buf o;
+    // device staging: dst, bias (u32 m each), eid (u64 m), kind (u8 32n), one (u32 32n), mem/minv (L), sp/spinv (S)
+    const size_t bytes = 8 * m + 8 * m + 32 * n + 4 * 32 * n + 8 * L + 8 * S + 64;
+    cudaError_t e = ensure(o, bytes);
+    if (e != cudaSuccess) { P.release_all(); return cuda_fail(e, "export staging"); }
+    char* p = (char*)o.p;
+    uint64_t* oeid = (uint64_t*)p; p += 8 * m;
+    uint32_t* odst = (uint32_t*)p; p += 4 * m;
+    uint32_t* obias = (uint32_t*)p; p += 4 * m;
+    uint32_t* oone = (uint32_t*)p; p += 4 * 32 * n;
+    uint32_t* omem = (uint32_t*)p; p += 4 * L;
+    uint32_t* ominv = (uint32_t*)p; p += 4 * L;
+    uint32_t* osp = (uint32_t*)p; p += 4 * S;
+    uint32_t* ospinv = (uint32_t*)p; p += 4 * S;
+    uint8_t* okind = (uint8_t*)p;
+    k_export_fill<<<grid_for(g, n * 32, 256), 256>>>(g->G, (uint64_t*)P.eoff.p, (uint64_t*)P.goff.p,
+                                                     (uint64_t*)P.soff.p, odst, obias, oeid, okind, oone, omem, ominv,
+                                                     osp, ospinv);
+    e = cudaDeviceSynchronize();
+    std::vector<uint64_t> tmp;
+    auto d2h32 = [&](uint32_t* dsth, const void* src, uint64_t cnt64) -> cudaError_t {
+        if (!dsth || cnt64 == 0) return cudaSuccess;
+        return cudaMemcpy(dsth, src, 4 * cnt64, cudaMemcpyDeviceToHost);
+    };
+    if (e == cudaSuccess && deg) {
+        tmp.resize(n);
+        e = cudaMemcpy(tmp.data(), P.deg64.p, 8 * n, cudaMemcpyDeviceToHost);
+        for (uint64_t v = 0; v < n && e == cudaSuccess; v++) deg[v] = (uint32_t)tmp[v];
+    }
+    if (e == cudaSuccess && sp_len) {
+        tmp.resize(n);
+        e = cudaMemcpy(tmp.data(), P.nsp.p, 8 * n, cudaMemcpyDeviceToHost);
+        for (uint64_t v = 0; v < n && e == cudaSuccess; v++) sp_len[v] = (uint32_t)tmp[v];
+    }
+    if (e == cudaSuccess && glen) {
+        tmp.resize(32 * n);
+        e = cudaMemcpy(tmp.data(), P.glen.p, 8 * 32 * n, cudaMemcpyDeviceToHost);
+        for (uint64_t i = 0; i < 32 * n && e == cudaSuccess; i++) glen[i] = (uint32_t)tmp[i];
+    }
+    if (e == cudaSuccess) e = d2h32(dst, odst, m);
+    if (e == cudaSuccess) e = d2h32(bias, obias, m);
+    if (e == cudaSuccess && eid && m) e = cudaMemcpy(eid, oeid, 8 * m, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = d2h32(cnt, g->G.cnt, 32 * n);
+    if (e == cudaSuccess && kind) e = cudaMemcpy(kind, okind, 32 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = d2h32(one_slot, oone, 32 * n);
+    if (e == cudaSuccess) e = d2h32(members, omem, L);
+    if (e == cudaSuccess) e = d2h32(member_inv, ominv, L);
+    if (e == cudaSuccess) e = d2h32(sp_list, osp, S);
+    if (e == cudaSuccess) e = d2h32(sp_inv, ospinv, S);
+    release(o);
+    P.release_all();
+    if (e != cudaSuccess) return cuda_fail(e, "export copy");
+    return BINGO_OK;
+}
+
+bingo_status bingo_memory_report(bingo_graph* g, uint64_t out[6]) {
+    if (!g || !out) { set_error("NULL argument"); return BINGO_E_INVALID; }
+    Buf b;
+    CK(ensure(b, 64), "memory report");
+    cudaMemset(b.p, 0, 64);
+    k_memory<<<grid_for(g, (uint64_t)g->n * 32, 256), 256>>>(g->G, (unsigned long long*)b.p);
+    unsigned long long w[3];
+    cudaError_t e = cudaMemcpy(w, b.p, 24, cudaMemcpyDeviceToHost);
+    release(b);
+    if (e != cudaSuccess) return cuda_fail(e, "memory report");
+    out[0] = 4ull * w[0];
+    out[1] = (uint64_t)g->n * (sizeof(VHdr) + 128 + 256);
+    out[2] = 4ull * w[1];
+    out[3] = 4ull * w[2];
+    out[4] = g->G.eh_mask ? (g->G.eh_mask + 1) * 12 : 0;
+    out[5] = 4ull * g->G.pool.words;
+    return BINGO_OK;
+}
+
+}  // extern "C"

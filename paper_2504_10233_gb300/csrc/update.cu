@@ -1,0 +1,1113 @@
+// Batched and streaming edge updates applied in place to the radix groups.
+//
+// Batch (Section 5.2, Fig. update): records are grouped by source vertex on the
+// GPU (stable radix sort on (src, is_delete, dst)); per vertex, insertions are
+// appended, deletions resolved to the earliest live copy of (src, dst), the
+// group counts updated by the bits of the inserted / deleted biases (Eq. dwi),
+// members removed from regular and sparse groups by two-phase delete-and-swap,
+// the adjacency compacted the same way (moved edges are renumbered in every
+// group through the inverted indexes, Section 4.2), new members appended, and
+// groups whose kind changed (Eq. group) rebuilt from the adjacency.
+// Streaming (Section 4.2): the same per-vertex procedure, one record at a time,
+// in order, inside one launch.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "bingo_host.h"
+#include "groups.cuh"
+
+using namespace bingo;
+
+#define CK(call, what)                                     \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+namespace {
+
+constexpr unsigned long long INF64 = 0xFFFFFFFFFFFFFFFFull;
+constexpr uint32_t APPLY_WARPS = 8;      // warp teams per block
+constexpr uint32_t BIG_THREADS = 512;    // block team size
+constexpr uint32_t ST_STOP = ST_INVALID | ST_OOM | ST_STATE;
+
+// stats layout inside CTL_STATS: 0 inserted, 1 deleted, 2 not_found, 3 touched, 4 rebuilt, 5.. conv[5][5]
+enum { S_INS = 0, S_DEL = 1, S_NF = 2, S_TOUCH = 3, S_REBUILT = 4, S_CONV = 5 };
+
+// Source of a segment's records: insertions (dst, bias, edge id) and deletions (dst, sorted ascending).
+struct BatchSrc {
+    const uint4* ups;
+    const uint64_t* keys;
+    const uint32_t* vals;
+    const uint64_t* rank;  // packed scan: high 32 bits = insert rank
+    uint64_t eid_base;
+    uint64_t dmask;
+    uint64_t start;  // first key of the segment
+    uint32_t ni;
+    __device__ __forceinline__ uint4 ins(uint32_t i) const { return ups[vals[start + i]]; }
+    __device__ __forceinline__ uint64_t ins_eid(uint32_t i) const { return eid_base + (rank[vals[start + i]] >> 32); }
+    __device__ __forceinline__ uint32_t del_dst(uint32_t j) const { return (uint32_t)(keys[start + ni + j] & dmask); }
+};
+
+struct OneSrc {
+    uint32_t dst, bias;
+    uint64_t eid;
+    __device__ __forceinline__ uint4 ins(uint32_t) const { return make_uint4(0, dst, bias, 0); }
+    __device__ __forceinline__ uint64_t ins_eid(uint32_t) const { return eid; }
+    __device__ __forceinline__ uint32_t del_dst(uint32_t) const { return dst; }
+};
+
+// team-shared state of one segment
+struct SegSh {
+    uint32_t cnt_old[32];
+    uint32_t cnt_new[32];
+    int32_t delta[32];
+    uint32_t removed[32];      // dead pre-existing edges with bit k
+    uint64_t gref_old[32];
+    uint64_t gref_new[32];
+    uint32_t tscratch[40];     // block-team scan scratch
+    uint64_t adj;
+    uint64_t alloc_off;
+    uint32_t nsp_del, nsp_add;
+    uint32_t rounds;
+    uint32_t found;
+};
+
+// equal range of x among the segment's (sorted) deletion destinations
+template <class Src>
+__device__ __forceinline__ void del_range(const Src& B, uint32_t nd, uint32_t x, uint32_t& lo_out, uint32_t& hi_out) {
+    uint32_t lo = 0, hi = nd;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (B.del_dst(mid) < x) lo = mid + 1; else hi = mid;
+    }
+    uint32_t a = lo;
+    hi = nd;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (B.del_dst(mid) <= x) lo = mid + 1; else hi = mid;
+    }
+    lo_out = a;
+    hi_out = lo;
+}
+
+// Two-phase parallel delete-and-swap (Section 5.2, Fig. update(b)) on a list L of length c.
+// cand(i), i < ncand, yields a position to delete or NONE32.  Phase 1 marks the N deleted
+// positions; the N tail positions [c-N, c) then hold gamma deleted entries and N-gamma survivors,
+// and phase 2 moves the survivors (ascending) into the N-gamma holes below c-N (in candidate
+// order).  move(value, from, to) patches the inverted index of each moved entry.
+template <class Team, class Cand, class Move>
+__device__ uint32_t dswap(const Team& t, uint32_t* L, uint32_t c, uint32_t ncand, Cand cand, Move move,
+                          uint32_t* holes, uint32_t* surv, uint32_t* status) {
+    uint32_t nrem = 0;
+    for (uint32_t b = 0; b < ncand; b += t.size()) {
+        const uint32_t i = b + t.rank();
+        uint32_t p = i < ncand ? cand(i) : NONE32;
+        if (p != NONE32 && p >= c) {  // inconsistent inverted index: record and skip
+            atomicOr(status, ST_STATE);
+            p = NONE32;
+        }
+        if (p != NONE32) L[p] = NONE32;
+        nrem += t.sum(p != NONE32 ? 1u : 0u);
+    }
+    t.sync();
+    if (nrem == 0) return c;
+    const uint32_t c1 = c - nrem;
+    uint32_t nh = 0;
+    for (uint32_t b = 0; b < ncand; b += t.size()) {
+        const uint32_t i = b + t.rank();
+        uint32_t p = i < ncand ? cand(i) : NONE32;
+        if (p != NONE32 && p >= c) p = NONE32;
+        const bool pred = p != NONE32 && p < c1;
+        uint32_t tot;
+        const uint32_t r = t.scan_pred(pred, tot);
+        if (pred) holes[nh + r] = p;
+        nh += tot;
+    }
+    uint32_t ns = 0;
+    for (uint32_t b = c1; b < c; b += t.size()) {
+        const uint32_t q = b + t.rank();
+        const bool pred = q < c && L[q] != NONE32;
+        uint32_t tot;
+        const uint32_t r = t.scan_pred(pred, tot);
+        if (pred) surv[ns + r] = q;
+        ns += tot;
+    }
+    t.sync();
+    for (uint32_t b = 0; b < nh; b += t.size()) {
+        const uint32_t r = b + t.rank();
+        if (r < nh) {
+            const uint32_t h = holes[r], s = (r < ns) ? surv[r] : NONE32;
+            if (s == NONE32) {
+                atomicOr(status, ST_STATE);
+            } else {
+                const uint32_t val = L[s];
+                L[h] = val;
+                move(val, s, h);
+            }
+        }
+    }
+    t.sync();
+    return c1;
+}
+
+struct SegScratch {
+    uint32_t* holes;          // >= nd entries
+    uint32_t* surv;           // >= nd entries
+    uint32_t* ins_final;      // [ni] final slot of each inserted edge (NONE32 if deleted in the batch)
+    uint32_t* del_slot;       // [nd] slot removed by each deletion (NONE32 if not found)
+    unsigned long long* best; // [nd]
+};
+
+// Apply one vertex's segment (ni insertions then nd deletions).  Returns false if the graph ran out of pool.
+template <class Team, class Src>
+__device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint32_t v, uint32_t ni, uint32_t nd,
+                              const Src& B, const SegScratch& X, unsigned long long* stats) {
+    const uint32_t rank = t.rank(), T = t.size();
+    const VHdr h0 = G.hdr[v];
+    const uint32_t d0 = h0.deg, capa0 = capa_of(h0), caps0 = caps_of(h0);
+    const uint32_t dtot = d0 + ni;
+    for (uint32_t k = rank; k < 32; k += T) {
+        sh.cnt_old[k] = G.cnt[(uint64_t)v * 32 + k];
+        sh.gref_old[k] = G.gref[(uint64_t)v * 32 + k];
+        sh.gref_new[k] = sh.gref_old[k];
+        sh.delta[k] = 0;
+        sh.removed[k] = 0;
+    }
+    if (rank == 0) {
+        sh.adj = h0.adj;
+        sh.nsp_del = 0;
+        sh.nsp_add = 0;
+        sh.found = 0;
+        sh.rounds = 0;
+    }
+    t.sync();
+    // old kinds
+    uint32_t SPo = 0, REGo = 0, ONEo = 0;
+    for (int k = 0; k < 32; k++) {
+        const uint32_t kd = kind_of(sh.cnt_old[k], d0, G.alpha, G.beta);
+        SPo |= (kd == K_SPARSE) << k;
+        REGo |= (kd == K_REGULAR) << k;
+        ONEo |= (kd == K_ONE) << k;
+    }
+
+    // ---- S1: adjacency capacity for the insertions
+    uint32_t capa1 = capa0;
+    bool full = false;
+    if (dtot > capa0) {
+        capa1 = capa_for(dtot);
+        full = true;
+        if (rank == 0) sh.alloc_off = pool_alloc(G.pool, 4ull * capa1);
+        t.sync();
+        const uint64_t noff = sh.alloc_off;
+        if (noff == 0) return;  // pool exhausted (flagged); the pre-check makes this unreachable
+        if (d0) {
+            const uint2* op = adj_pairs(G, h0.adj);
+            const uint64_t* oe = adj_eids(G, h0.adj, capa0);
+            uint2* np = adj_pairs(G, noff);
+            uint64_t* ne = adj_eids(G, noff, capa1);
+            for (uint32_t j = rank; j < d0; j += T) {
+                np[j] = op[j];
+                ne[j] = oe[j];
+            }
+        }
+        t.sync();
+        if (rank == 0) {
+            if (capa0) pool_free(G.pool, h0.adj, 4ull * capa0);
+            sh.adj = noff;
+        }
+        t.sync();
+    }
+    const uint64_t adj = sh.adj;
+    uint2* pairs = adj_pairs(G, adj);
+    uint64_t* eids = adj_eids(G, adj, capa1);
+
+    // ---- S2: append insertions at slots d0 .. d0+ni-1
+    for (uint32_t i = rank; i < ni; i += T) {
+        const uint4 u = B.ins(i);
+        pairs[d0 + i] = make_uint2(u.y, u.z);
+        eids[d0 + i] = B.ins_eid(i);
+    }
+    for (uint32_t j = rank; j < nd; j += T) {
+        X.del_slot[j] = NONE32;
+        X.best[j] = INF64;
+    }
+    t.sync();
+
+    // ---- S3: resolve each deletion to the earliest live copy (smallest edge id) of (v, dst);
+    // the r-th deletion of the same dst takes the r-th earliest copy (round r).
+    if (nd) {
+        uint32_t mr = 0;
+        for (uint32_t j = rank; j < nd; j += T) {
+            uint32_t lo, hi;
+            del_range(B, nd, B.del_dst(j), lo, hi);
+            mr = max(mr, j - lo + 1);
+        }
+        const uint32_t rounds = t.max(mr);
+        for (uint32_t r = 0; r < rounds; r++) {
+            for (uint32_t j = rank; j < dtot; j += T) {
+                const uint64_t e = eids[j];
+                if (e & DEAD_BIT) continue;
+                uint32_t lo, hi;
+                del_range(B, nd, pairs[j].x, lo, hi);
+                if (hi - lo > r) atomicMin(&X.best[lo + r], (unsigned long long)e);
+            }
+            t.sync();
+            for (uint32_t j = rank; j < dtot; j += T) {
+                const uint64_t e = eids[j];
+                if (e & DEAD_BIT) continue;
+                uint32_t lo, hi;
+                del_range(B, nd, pairs[j].x, lo, hi);
+                if (hi - lo > r && X.best[lo + r] == e) {
+                    eids[j] = e | DEAD_BIT;
+                    X.del_slot[lo + r] = j;
+                }
+            }
+            t.sync();
+        }
+    }
+    uint32_t found = 0;
+    for (uint32_t b = 0; b < nd; b += T) {
+        const uint32_t j = b + rank;
+        found += t.sum(j < nd && X.del_slot[j] != NONE32 ? 1u : 0u);
+    }
+    const uint32_t d1 = dtot - found;
+
+    // ---- S4: count deltas from the bits of deleted pre-existing and surviving new edges
+    uint32_t deadbits_local = 0;
+    for (uint32_t j = rank; j < nd; j += T) {
+        const uint32_t s = X.del_slot[j];
+        if (s != NONE32 && s < d0) {
+            const uint32_t w = pairs[s].y;
+            deadbits_local |= w;
+            for (uint32_t b = w; b; b &= b - 1) {
+                const int k = __ffs(b) - 1;
+                atomicAdd(&sh.delta[k], -1);
+                atomicAdd(&sh.removed[k], 1u);
+            }
+        }
+    }
+    for (uint32_t i = rank; i < ni; i += T) {
+        if (!(eids[d0 + i] & DEAD_BIT)) {
+            const uint32_t w = pairs[d0 + i].y;
+            for (uint32_t b = w; b; b &= b - 1) atomicAdd(&sh.delta[__ffs(b) - 1], 1);
+        }
+    }
+    t.sync();
+    for (uint32_t k = rank; k < 32; k += T) sh.cnt_new[k] = (uint32_t)((int32_t)sh.cnt_old[k] + sh.delta[k]);
+    t.sync();
+    uint32_t SPn = 0, REGn = 0, ONEn = 0, maskn = 0, deadbits = 0;
+    for (int k = 0; k < 32; k++) {
+        const uint32_t kd = kind_of(sh.cnt_new[k], d1, G.alpha, G.beta);
+        SPn |= (kd == K_SPARSE) << k;
+        REGn |= (kd == K_REGULAR) << k;
+        ONEn |= (kd == K_ONE) << k;
+        maskn |= (sh.cnt_new[k] > 0) << k;
+        deadbits |= (sh.removed[k] > 0) << k;
+    }
+    (void)deadbits_local;
+    const uint32_t REGk = full ? 0u : (REGo & REGn);              // regular groups updated in place
+    const uint32_t ONEk = full ? 0u : (ONEo & ONEn & ~deadbits);   // one-element groups whose member survives
+    bool keepS = !full && SPo == SPn && SPn != 0 && h0.sref != 0;
+    uint32_t nsp1 = 0;
+    if (keepS) {
+        uint32_t del_s = 0, add_s = 0;
+        for (uint32_t b = 0; b < nd; b += T) {
+            const uint32_t j = b + rank;
+            const uint32_t s = j < nd ? X.del_slot[j] : NONE32;
+            del_s += t.sum(s != NONE32 && s < d0 && (pairs[s].y & SPo) ? 1u : 0u);
+        }
+        for (uint32_t b = 0; b < ni; b += T) {
+            const uint32_t i = b + rank;
+            const bool live = i < ni && !(eids[d0 + i] & DEAD_BIT);
+            add_s += t.sum(live && (pairs[d0 + i].y & SPn) ? 1u : 0u);
+        }
+        nsp1 = h0.nsp - del_s + add_s;
+        if (nsp1 > caps0) keepS = false;  // sparse capacity outgrown: rebuild S and sparse groups
+    }
+
+    // ---- S6: remove deleted members from regular groups kept in place
+    for (uint32_t m = REGk & deadbits; m; m &= m - 1) {
+        const uint32_t k = __ffs(m) - 1;
+        uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+        uint32_t* inv = L + capa0;
+        const uint32_t icap_guard = capa0;
+        dswap(
+            t, L, sh.cnt_old[k], nd,
+            [&](uint32_t j) -> uint32_t {
+                const uint32_t s = X.del_slot[j];
+                return (s != NONE32 && s < d0 && ((pairs[s].y >> k) & 1u)) ? inv[s] : NONE32;
+            },
+            [&](uint32_t val, uint32_t, uint32_t to) { if (val < icap_guard) inv[val] = to; }, X.holes, X.surv, G.pool.status);
+    }
+    // ---- S7: sparse groups, then the sparse list itself
+    uint32_t nsp_after_del = h0.nsp;
+    if (keepS) {
+        uint32_t* S = G.pool.base + h0.sref;
+        uint32_t* Sinv = S + capa0;
+        for (uint32_t m = SPn & deadbits; m; m &= m - 1) {
+            const uint32_t k = __ffs(m) - 1;
+            uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+            uint32_t* inv = L + caps0;
+            const uint32_t icap_guard = caps0;
+            dswap(
+                t, L, sh.cnt_old[k], nd,
+                [&](uint32_t j) -> uint32_t {
+                    const uint32_t s = X.del_slot[j];
+                    if (!(s != NONE32 && s < d0 && ((pairs[s].y >> k) & 1u))) return NONE32;
+                    const uint32_t sp = Sinv[s];
+                    return sp < caps0 ? inv[sp] : NONE32;
+                },
+                [&](uint32_t val, uint32_t, uint32_t to) { if (val < icap_guard) inv[val] = to; }, X.holes, X.surv, G.pool.status);
+        }
+        nsp_after_del = dswap(
+            t, S, h0.nsp, nd,
+            [&](uint32_t j) -> uint32_t {
+                const uint32_t s = X.del_slot[j];
+                return (s != NONE32 && s < d0 && (pairs[s].y & SPo)) ? Sinv[s] : NONE32;
+            },
+            [&](uint32_t e, uint32_t from, uint32_t to) {
+                if (e >= capa0) { atomicOr(G.pool.status, ST_STATE); return; }
+                Sinv[e] = to;
+                const uint32_t w = pairs[e].y & SPn;
+                for (uint32_t b = w; b; b &= b - 1) {
+                    const uint32_t k = __ffs(b) - 1;
+                    uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+                    uint32_t* inv = L + caps0;
+                    const uint32_t mpos = inv[from];
+                    if (mpos < caps0) {
+                        L[mpos] = to;
+                        inv[to] = mpos;
+                    } else {
+                        atomicOr(G.pool.status, ST_STATE);
+                    }
+                }
+            },
+            X.holes, X.surv, G.pool.status);
+    }
+
+    // ---- S8: compact the adjacency: surviving edges of the tail [d1, dtot) fill the holes below d1
+    for (uint32_t i = rank; i < ni; i += T) X.ins_final[i] = (eids[d0 + i] & DEAD_BIT) ? NONE32 : d0 + i;
+    t.sync();
+    if (found) {
+        uint32_t nh = 0, ns = 0;
+        for (uint32_t b = 0; b < nd; b += T) {
+            const uint32_t j = b + rank;
+            const uint32_t s = j < nd ? X.del_slot[j] : NONE32;
+            const bool pred = s != NONE32 && s < d1;
+            uint32_t tot;
+            const uint32_t r = t.scan_pred(pred, tot);
+            if (pred) X.holes[nh + r] = s;
+            nh += tot;
+        }
+        for (uint32_t b = d1; b < dtot; b += T) {
+            const uint32_t q = b + rank;
+            const bool pred = q < dtot && !(eids[q] & DEAD_BIT);
+            uint32_t tot;
+            const uint32_t r = t.scan_pred(pred, tot);
+            if (pred) X.surv[ns + r] = q;
+            ns += tot;
+        }
+        t.sync();
+        uint32_t* S = h0.sref ? G.pool.base + h0.sref : nullptr;
+        uint32_t* Sinv = S ? S + capa0 : nullptr;
+        for (uint32_t b = 0; b < nh; b += T) {
+            const uint32_t r = b + rank;
+            if (r < nh) {
+                const uint32_t q = X.holes[r], p = X.surv[r];
+                const uint2 e = pairs[p];
+                pairs[q] = e;
+                eids[q] = eids[p];
+                if (p < d0) {
+                    for (uint32_t bb = e.y & REGk; bb; bb &= bb - 1) {
+                        const uint32_t k = __ffs(bb) - 1;
+                        uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+                        uint32_t* inv = L + capa0;
+                        const uint32_t mpos = inv[p];
+                        if (mpos < capa0) {
+                            L[mpos] = q;
+                            inv[q] = mpos;
+                        } else {
+                            atomicOr(G.pool.status, ST_STATE);
+                        }
+                    }
+                    if (keepS && (e.y & SPn)) {
+                        const uint32_t sp = Sinv[p];
+                        if (sp < capa0) {
+                            S[sp] = q;
+                            Sinv[q] = sp;
+                        } else {
+                            atomicOr(G.pool.status, ST_STATE);
+                        }
+                    }
+                    for (uint32_t bb = e.y & ONEk; bb; bb &= bb - 1) sh.gref_new[__ffs(bb) - 1] = q;
+                } else {
+                    X.ins_final[p - d0] = q;
+                }
+            }
+        }
+        t.sync();
+    }
+
+    // ---- S9: append surviving new edges to the groups kept in place
+    for (uint32_t m = REGk & REGn; m; m &= m - 1) {
+        const uint32_t k = __ffs(m) - 1;
+        uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+        uint32_t* inv = L + capa0;
+        uint32_t pos = sh.cnt_old[k] - sh.removed[k];
+        for (uint32_t b = 0; b < ni; b += T) {
+            const uint32_t i = b + rank;
+            const uint32_t s = i < ni ? X.ins_final[i] : NONE32;
+            const bool pred = s != NONE32 && ((pairs[s].y >> k) & 1u);
+            uint32_t tot;
+            const uint32_t r = t.scan_pred(pred, tot);
+            if (pred) {
+                L[pos + r] = s;
+                inv[s] = pos + r;
+            }
+            pos += tot;
+        }
+    }
+    if (keepS) {
+        uint32_t* S = G.pool.base + h0.sref;
+        uint32_t* Sinv = S + capa0;
+        uint32_t pos = nsp_after_del;
+        for (uint32_t b = 0; b < ni; b += T) {
+            const uint32_t i = b + rank;
+            const uint32_t s = i < ni ? X.ins_final[i] : NONE32;
+            const bool pred = s != NONE32 && (pairs[s].y & SPn);
+            uint32_t tot;
+            const uint32_t r = t.scan_pred(pred, tot);
+            if (pred) {
+                S[pos + r] = s;
+                Sinv[s] = pos + r;
+            }
+            pos += tot;
+        }
+        t.sync();
+        for (uint32_t m = SPn; m; m &= m - 1) {
+            const uint32_t k = __ffs(m) - 1;
+            uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+            uint32_t* inv = L + caps0;
+            uint32_t gpos = sh.cnt_old[k] - sh.removed[k];
+            for (uint32_t b = 0; b < ni; b += T) {
+                const uint32_t i = b + rank;
+                const uint32_t s = i < ni ? X.ins_final[i] : NONE32;
+                const bool pred = s != NONE32 && ((pairs[s].y >> k) & 1u);
+                uint32_t tot;
+                const uint32_t r = t.scan_pred(pred, tot);
+                if (pred) {
+                    const uint32_t sp = Sinv[s];
+                    L[gpos + r] = sp;
+                    inv[sp] = gpos + r;
+                }
+                gpos += tot;
+            }
+        }
+    }
+    t.sync();
+
+    // ---- S10: rebuild groups whose kind changed or whose capacity changed; free the rest
+    uint32_t rebuilt = 0;
+    // free blocks that are not kept
+    if (rank == 0) {
+        for (uint32_t m = REGo & ~REGk; m; m &= m - 1) pool_free(G.pool, sh.gref_old[__ffs(m) - 1] & GOFF_MASK, 2ull * capa0);
+        if (!keepS && h0.sref) {
+            pool_free(G.pool, h0.sref, 2ull * capa0);
+            for (uint32_t m = SPo; m; m &= m - 1) pool_free(G.pool, sh.gref_old[__ffs(m) - 1] & GOFF_MASK, 2ull * caps0);
+        }
+    }
+    for (int k = rank; k < 32; k += T) {
+        const uint32_t bit = 1u << k;
+        if (!(maskn & bit) || (!(REGn & bit) && !(SPn & bit) && !(ONEn & bit))) sh.gref_new[k] = 0;  // dense / empty
+    }
+    t.sync();
+    for (uint32_t m = REGn & ~REGk; m; m &= m - 1) {
+        const uint32_t k = __ffs(m) - 1;
+        if (rank == 0) sh.alloc_off = pool_alloc(G.pool, 2ull * capa1);
+        t.sync();
+        const uint64_t off = sh.alloc_off;
+        if (off) build_regular(t, G, adj, d1, k, off, capa1);
+        if (rank == 0) sh.gref_new[k] = off;
+        rebuilt++;
+        t.sync();
+    }
+    uint64_t sref1 = keepS ? h0.sref : 0;
+    uint32_t caps1 = keepS ? caps0 : 0;
+    if (!keepS && SPn) {
+        if (rank == 0) sh.alloc_off = pool_alloc(G.pool, 2ull * capa1);
+        t.sync();
+        sref1 = sh.alloc_off;
+        t.sync();
+        if (sref1) {
+            nsp1 = build_slist(t, G, adj, d1, SPn, sref1, capa1);
+            t.sync();
+            caps1 = caps_for(nsp1);
+            for (uint32_t m = SPn; m; m &= m - 1) {
+                const uint32_t k = __ffs(m) - 1;
+                if (rank == 0) sh.alloc_off = pool_alloc(G.pool, 2ull * caps1);
+                t.sync();
+                const uint64_t off = sh.alloc_off;
+                if (off) build_sparse(t, G, adj, sref1, nsp1, k, off, caps1);
+                if (rank == 0) sh.gref_new[k] = off;
+                rebuilt++;
+                t.sync();
+            }
+        }
+    }
+    for (uint32_t m = ONEn & ~ONEk; m; m &= m - 1) {
+        const uint32_t k = __ffs(m) - 1;
+        const uint32_t s = find_one(t, G, adj, d1, k);
+        if (rank == 0) sh.gref_new[k] = s;
+        rebuilt++;
+    }
+    t.sync();
+
+    // ---- S11: write back
+    for (uint32_t k = rank; k < 32; k += T) {
+        G.cnt[(uint64_t)v * 32 + k] = sh.cnt_new[k];
+        G.gref[(uint64_t)v * 32 + k] = sh.gref_new[k];
+    }
+    if (rank == 0) {
+        VHdr h;
+        h.adj = adj;
+        h.deg = d1;
+        h.mask = maskn;
+        h.sref = SPn ? sref1 : 0;
+        h.nsp = SPn ? nsp1 : 0;
+        h.lcapa = capa1 ? (uint8_t)(log2_u32(capa1) + 1) : 0;
+        h.lcaps = SPn ? (uint8_t)(log2_u32(caps1) + 1) : 0;
+        h.pad = 0;
+        G.hdr[v] = h;
+        // ---- S12: stats
+        atomicAdd(stats + S_INS, (unsigned long long)ni);
+        atomicAdd(stats + S_DEL, (unsigned long long)found);
+        atomicAdd(stats + S_NF, (unsigned long long)(nd - found));
+        atomicAdd(stats + S_TOUCH, 1ull);
+        if (rebuilt) atomicAdd(stats + S_REBUILT, (unsigned long long)rebuilt);
+        for (int k = 0; k < 32; k++) {
+            const uint32_t ko = kind_of(sh.cnt_old[k], d0, G.alpha, G.beta);
+            const uint32_t kn = kind_of(sh.cnt_new[k], d1, G.alpha, G.beta);
+            if (ko != kn) atomicAdd(stats + S_CONV + ko * 5 + kn, 1ull);
+        }
+    }
+    t.sync();
+}
+
+// ------------------------------------------------------------------------------------------- batch kernels
+
+struct BatchArgs {
+    const uint4* ups;
+    uint64_t count;
+    uint32_t n, max_bits, bn;
+    uint64_t* keys;
+    uint32_t* vals;
+    uint64_t* packed;     // per record: nkeys (low 32) | is_insert (high 32)
+    uint64_t* pscan;      // exclusive scan of packed
+    uint32_t* status;
+};
+
+__global__ void k_expand(BatchArgs A) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (uint64_t i = tid; i < A.count; i += nt) {
+        const uint4 u = A.ups[i];
+        const bool ins = u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS;
+        const bool del = u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS;
+        bad |= u.x >= A.n || u.y >= A.n || u.w > 2;
+        if (ins) bad |= u.z == 0 || (A.max_bits < 32 && (u.z >> A.max_bits) != 0);
+        A.packed[i] = (uint64_t)(ins ? 1 : 0) + (del ? 1 : 0) + ((uint64_t)(ins ? 1 : 0) << 32);
+    }
+    if (bad) atomicOr(A.status, ST_INVALID);
+}
+
+__global__ void k_make_keys(BatchArgs A) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = tid; i < A.count; i += nt) {
+        const uint4 u = A.ups[i];
+        if (u.x >= A.n || u.y >= A.n || u.w > 2) continue;
+        uint64_t pos = A.pscan[i] & 0xFFFFFFFFull;
+        const uint64_t sk = (uint64_t)u.x << (A.bn + 1);
+        if (u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS) {
+            A.keys[pos] = sk;
+            A.vals[pos] = (uint32_t)i;
+            pos++;
+        }
+        if (u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS) {
+            A.keys[pos] = sk | (1ull << A.bn) | u.y;
+            A.vals[pos] = (uint32_t)i;
+        }
+    }
+}
+
+__global__ void k_seg_flags(const uint64_t* __restrict__ keys, uint64_t nkeys, uint32_t bn, uint64_t* __restrict__ flag) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = tid; i < nkeys; i += nt)
+        flag[i] = (i == 0 || (keys[i] >> (bn + 1)) != (keys[i - 1] >> (bn + 1))) ? 1 : 0;
+}
+
+__global__ void k_seg_write(const uint64_t* __restrict__ flag, const uint64_t* __restrict__ segid, uint64_t nkeys,
+                            uint32_t* __restrict__ seg_start) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = tid; i < nkeys; i += nt) {
+        if (flag[i]) seg_start[segid[i]] = (uint32_t)i;
+        if (i == nkeys - 1) seg_start[segid[i] + flag[i]] = (uint32_t)nkeys;
+    }
+}
+
+struct SegArgs {
+    BatchArgs B;
+    const uint64_t* sorted_keys;
+    const uint32_t* sorted_vals;
+    const uint32_t* seg_start;
+    const uint64_t* nseg_dev;
+    uint32_t* small_list;
+    uint32_t* big_list;
+    unsigned long long* counts;   // [0] small, [1] big, [2] pool bound
+    uint32_t big_slots;
+    uint64_t eid_base;
+    uint32_t* holes;
+    uint32_t* surv;
+    uint32_t* slot_scratch;
+    unsigned long long* best;
+    unsigned long long* stats;
+};
+
+// Per segment: insertion count, and the worst-case pool words the segment may allocate.
+__global__ void k_seg_classify(DevGraph G, SegArgs S) {
+    const uint64_t nseg = *S.nseg_dev;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    unsigned long long bound = 0;
+    for (uint64_t sidx = tid; sidx < nseg; sidx += nt) {
+        const uint32_t a = S.seg_start[sidx], b = S.seg_start[sidx + 1];
+        const uint32_t v = (uint32_t)(S.sorted_keys[a] >> (S.B.bn + 1));
+        uint32_t lo = a, hi = b;  // first deletion key
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if ((S.sorted_keys[mid] >> S.B.bn) & 1ull) hi = mid; else lo = mid + 1;
+        }
+        const uint32_t ni = lo - a;
+        const VHdr h = G.hdr[v];
+        const uint32_t dtot = h.deg + ni;
+        const uint32_t capa1 = dtot > capa_of(h) ? capa_for(dtot) : capa_of(h);
+        uint32_t insbits = 0;
+        for (uint32_t i = a; i < lo; i++) insbits |= S.B.ups[S.sorted_vals[i]].z;
+        uint32_t ngroups = 0;
+        for (int k = 0; k < 32; k++) {
+            const uint32_t c = G.cnt[(uint64_t)v * 32 + k] + (((insbits >> k) & 1u) ? ni : 0u);
+            ngroups += c >= 2;
+        }
+        if (dtot > capa_of(h)) bound += 4ull * capa1;
+        if (ngroups) bound += 2ull * capa1 * (ngroups + 1) + 2ull * caps_for(dtot) * ngroups;
+        const bool big = dtot > 4096 || (b - a) > 256;
+        if (big) S.big_list[atomicAdd(&S.counts[1], 1ull)] = (uint32_t)sidx;
+        else S.small_list[atomicAdd(&S.counts[0], 1ull)] = (uint32_t)sidx;
+    }
+    if (bound) atomicAdd(&S.counts[2], bound);
+}
+
+__global__ void k_oom_check(DevGraph G, const unsigned long long* counts) {
+    const unsigned long long top = *G.pool.top;
+    if (top + counts[2] > G.pool.words) atomicOr(G.pool.status, ST_OOM);
+}
+
+template <class Team>
+__device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, const SegArgs& S, SegSh& sh, uint32_t sidx) {
+    const uint32_t a = S.seg_start[sidx], b = S.seg_start[sidx + 1];
+    const uint32_t v = (uint32_t)(S.sorted_keys[a] >> (S.B.bn + 1));
+    uint32_t lo = a, hi = b;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((S.sorted_keys[mid] >> S.B.bn) & 1ull) hi = mid; else lo = mid + 1;
+    }
+    const uint32_t ni = lo - a, nd = b - lo;
+    BatchSrc src;
+    src.ups = S.B.ups;
+    src.keys = S.sorted_keys;
+    src.vals = S.sorted_vals;
+    src.rank = S.B.pscan;
+    src.eid_base = S.eid_base;
+    src.dmask = (1ull << S.B.bn) - 1;
+    src.start = a;
+    src.ni = ni;
+    SegScratch X;
+    X.holes = S.holes + a;
+    X.surv = S.surv + a;
+    X.ins_final = S.slot_scratch + a;
+    X.del_slot = S.slot_scratch + a + ni;
+    X.best = S.best + a + ni;
+    apply_segment(t, G, sh, v, ni, nd, src, X, S.stats);
+}
+
+__global__ void __launch_bounds__(APPLY_WARPS * 32) k_apply_small(DevGraph G, SegArgs S) {
+    __shared__ SegSh sh[APPLY_WARPS];
+    if (*G.pool.status & ST_STOP) return;
+    const uint32_t w = threadIdx.x >> 5;
+    const unsigned long long nsmall = S.counts[0];
+    WarpTeam t;
+    for (uint64_t i = (uint64_t)blockIdx.x * APPLY_WARPS + w; i < nsmall; i += (uint64_t)gridDim.x * APPLY_WARPS)
+        run_segment(t, G, S, sh[w], S.small_list[i]);
+}
+
+__global__ void __launch_bounds__(BIG_THREADS) k_apply_big(DevGraph G, SegArgs S) {
+    __shared__ SegSh sh;
+    if (*G.pool.status & ST_STOP) return;
+    const unsigned long long nbig = S.counts[1];
+    BlockTeam t;
+    t.sm = sh.tscratch;
+    for (uint64_t i = blockIdx.x; i < nbig; i += gridDim.x) run_segment(t, G, S, sh, S.big_list[i]);
+}
+
+// edge-index maintenance: +1 for every insertion record, -1 for every deletion that found an edge
+__global__ void k_eh_apply(DevGraph G, SegArgs S, uint64_t nkeys) {
+    if (*G.pool.status & ST_STOP) return;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = tid; i < nkeys; i += nt) {
+        const uint64_t key = S.sorted_keys[i];
+        const bool del = (key >> S.B.bn) & 1ull;
+        const uint32_t src = (uint32_t)(key >> (S.B.bn + 1));
+        const uint4 u = S.B.ups[S.sorted_vals[i]];
+        if (del && S.slot_scratch[i] == NONE32) continue;
+        const unsigned long long k = ((unsigned long long)src << 32) | u.y;
+        uint64_t p = eh_hash(k) & G.eh_mask;
+        for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
+            if (!del) {
+                const unsigned long long old = atomicCAS(G.eh_key + p, EH_EMPTY, k);
+                if (old == EH_EMPTY || old == k) { atomicAdd(G.eh_cnt + p, 1u); break; }
+            } else {
+                const unsigned long long cur = G.eh_key[p];
+                if (cur == k) { atomicSub(G.eh_cnt + p, 1u); break; }
+                if (cur == EH_EMPTY) break;
+            }
+            p = (p + 1) & G.eh_mask;
+        }
+    }
+}
+
+// Make this batch's frees reusable (single block).
+__global__ void k_finalize_pool(DevGraph G) {
+    Pool P = G.pool;
+    for (int c = threadIdx.x; c < NCLASS; c += blockDim.x)
+        if (P.fcount[c] < 0) P.fcount[c] = 0;
+    __syncthreads();
+    const unsigned long long np = *P.npending;
+    const unsigned long long lim = np < P.pcap ? np : P.pcap;
+    for (unsigned long long i = threadIdx.x; i < lim; i += blockDim.x) {
+        const uint64_t x = P.pending[i];
+        const uint32_t c = (uint32_t)(x & 0xFF);
+        const uint64_t off = x >> 8;
+        const long long idx = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&P.fcount[c]), 1ull);
+        if ((uint64_t)idx < P.fcap) P.fstack[(uint64_t)c * P.fcap + (uint64_t)idx] = off;
+        else atomicAdd(P.leaked, (unsigned long long)(8ull << c));
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < NCLASS; c += blockDim.x)
+        if ((uint64_t)P.fcount[c] > P.fcap) P.fcount[c] = (long long)P.fcap;
+    if (threadIdx.x == 0) *P.npending = 0;
+}
+
+// Streaming: one warp applies the records in order, each as a batch of one.
+__global__ void k_stream(DevGraph G, const uint4* __restrict__ ups, uint64_t count, uint64_t eid_base,
+                         uint32_t* scratch, unsigned long long* best, unsigned long long* stats,
+                         unsigned long long* applied) {
+    __shared__ SegSh sh;
+    WarpTeam t;
+    if (threadIdx.x >= 32) return;
+    uint64_t eid = eid_base;
+    for (uint64_t i = 0; i < count; i++) {
+        if (*G.pool.status & ST_STOP) break;
+        const uint4 u = ups[i];
+        const uint32_t ni = (u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
+        const uint32_t nd = (u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
+        // pool headroom for this record before touching anything
+        const VHdr h = G.hdr[u.x];
+        const uint32_t capa1 = capa_for(h.deg + ni > capa_of(h) ? h.deg + ni : capa_of(h));
+        const unsigned long long need = 4ull * capa1 + 2ull * capa1 * 34 + 2ull * caps_for(h.deg + ni) * 32;
+        if (*G.pool.top + need > G.pool.words) {
+            if (t.rank() == 0) atomicOr(G.pool.status, ST_OOM);
+            break;
+        }
+        OneSrc src;
+        src.dst = u.y;
+        src.bias = u.z;
+        src.eid = eid;
+        SegScratch X;
+        X.holes = scratch;
+        X.surv = scratch + 2;
+        X.ins_final = scratch + 4;
+        X.del_slot = scratch + 5;
+        X.best = best;
+        apply_segment(t, G, sh, u.x, ni, nd, src, X, stats);
+        // edge index
+        if (G.eh_mask && t.rank() == 0) {
+            const unsigned long long k = ((unsigned long long)u.x << 32) | u.y;
+            if (ni) {
+                uint64_t p = eh_hash(k) & G.eh_mask;
+                for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
+                    const unsigned long long old = atomicCAS(G.eh_key + p, EH_EMPTY, k);
+                    if (old == EH_EMPTY || old == k) { atomicAdd(G.eh_cnt + p, 1u); break; }
+                    p = (p + 1) & G.eh_mask;
+                }
+            }
+            if (nd && X.del_slot[0] != NONE32) {
+                uint64_t p = eh_hash(k) & G.eh_mask;
+                for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
+                    const unsigned long long cur = G.eh_key[p];
+                    if (cur == k) { atomicSub(G.eh_cnt + p, 1u); break; }
+                    if (cur == EH_EMPTY) break;
+                    p = (p + 1) & G.eh_mask;
+                }
+            }
+        }
+        __syncwarp();
+        eid += ni;
+        if (t.rank() == 0) *applied = i + 1;
+    }
+}
+
+__global__ void k_validate_stream(const uint4* ups, uint64_t count, uint32_t n, uint32_t max_bits, uint32_t* status,
+                                  unsigned long long* ninserts) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    unsigned long long ins = 0;
+    for (uint64_t i = tid; i < count; i += nt) {
+        const uint4 u = ups[i];
+        const bool isins = u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS;
+        bad |= u.x >= n || u.y >= n || u.w > 2;
+        if (isins) bad |= u.z == 0 || (max_bits < 32 && (u.z >> max_bits) != 0);
+        ins += isins;
+    }
+    if (bad) atomicOr(status, ST_INVALID);
+    if (ins) atomicAdd(ninserts, ins);
+}
+
+uint32_t bits_for(uint32_t n) {
+    uint32_t b = 1;
+    while (b < 31 && (1u << b) < n) b++;
+    return b;
+}
+
+bingo_status read_stats(bingo_graph* g, cudaStream_t s, bingo_update_stats* stats, uint32_t* status_out) {
+    uint64_t* ctl = (uint64_t*)g->d_ctl;
+    uint64_t host[CTL_WORDS];
+    CK(cudaMemcpyAsync(host, ctl, sizeof(host), cudaMemcpyDeviceToHost, s), "stats read");
+    CK(cudaStreamSynchronize(s), "update");
+    *status_out = (uint32_t)host[CTL_STATUS];
+    const uint64_t* st = host + CTL_STATS;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->inserted = st[S_INS];
+        stats->deleted = st[S_DEL];
+        stats->not_found = st[S_NF];
+        stats->vertices_touched = st[S_TOUCH];
+        stats->groups_rebuilt = st[S_REBUILT];
+        for (int a = 0; a < 5; a++)
+            for (int b = 0; b < 5; b++) stats->conversions[a][b] = st[S_CONV + a * 5 + b];
+    }
+    return BINGO_OK;
+}
+
+}  // namespace
+
+namespace bingo {
+bingo_status edge_index_build(bingo_graph* g, cudaStream_t s);
+}
+
+static unsigned grid_cap(const bingo_graph* g, uint64_t items, unsigned block, unsigned per_sm = 16) {
+    uint64_t b = (items + block - 1) / block;
+    const uint64_t cap = (uint64_t)g->num_sms * per_sm;
+    if (b > cap) b = cap;
+    return b ? (unsigned)b : 1u;
+}
+
+static bingo_status finish_batch(bingo_graph* g, cudaStream_t s, bingo_update_stats* stats, uint64_t inserts_expected) {
+    k_finalize_pool<<<1, 1024, 0, s>>>(g->G);
+    g->launches++;
+    uint32_t status = 0;
+    bingo_update_stats tmp;
+    bingo_status st = read_stats(g, s, &tmp, &status);
+    if (st != BINGO_OK) return st;
+    if (stats) *stats = tmp;
+    if (status & ST_INVALID) {
+        set_error("invalid update record (id >= n, op > 2, or bias outside [1, 2^max_bits)); batch rejected");
+        return BINGO_E_INVALID;
+    }
+    g->next_eid += tmp.inserted;
+    g->m_live = g->m_live + tmp.inserted - tmp.deleted;
+    (void)inserts_expected;
+    if (status & ST_STATE) {
+        g->broken = true;
+        set_error("update found an inconsistent group structure; the graph is marked unusable");
+        return BINGO_E_STATE;
+    }
+    if (status & ST_OOM) {
+        set_error("device pool exhausted; batch rejected before any change");
+        return BINGO_E_OOM;
+    }
+    if (status & ST_TIMEOUT) {
+        set_error("a bounded device loop gave up");
+        return BINGO_E_TIMEOUT;
+    }
+    return BINGO_OK;
+}
+
+extern "C" {
+
+bingo_status bingo_apply_updates(bingo_graph* g, const bingo_update* ups, uint64_t count, void* stream,
+                                 bingo_update_stats* stats) {
+    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+    if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
+    if (count && !ups) { set_error("NULL update array"); return BINGO_E_INVALID; }
+    if (count >= 0x7FFFFFFFull) { set_error("batch too large"); return BINGO_E_INVALID; }
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t* ctl = (uint64_t*)g->d_ctl;
+    CK(cudaMemsetAsync(ctl + CTL_STATUS, 0, 8, s), "status reset");
+    CK(cudaMemsetAsync(ctl + CTL_STATS, 0, (CTL_WORDS - CTL_STATS) * 8, s), "stats reset");
+    if (count == 0) {
+        if (stats) memset(stats, 0, sizeof(*stats));
+        return BINGO_OK;
+    }
+    const uint4* dups = (const uint4*)ups;
+    if (!is_device_ptr(ups)) {
+        CK(ensure(g->s_in, count * 16), "update staging");
+        CK(cudaMemcpyAsync(g->s_in.p, ups, count * 16, cudaMemcpyHostToDevice, s), "update upload");
+        dups = (const uint4*)g->s_in.p;
+    }
+    const uint64_t maxkeys = 2 * count;
+    CK(ensure(g->s_rank, 16 * count + 64), "update scratch");
+    CK(ensure(g->s_keys, 8 * maxkeys), "update scratch");
+    CK(ensure(g->s_keys2, 8 * maxkeys), "update scratch");
+    CK(ensure(g->s_vals, 4 * maxkeys), "update scratch");
+    CK(ensure(g->s_vals2, 4 * maxkeys), "update scratch");
+    BatchArgs A;
+    A.ups = dups;
+    A.count = count;
+    A.n = g->n;
+    A.max_bits = g->cfg.max_bits;
+    A.bn = bits_for(g->n);
+    A.keys = (uint64_t*)g->s_keys.p;
+    A.vals = (uint32_t*)g->s_vals.p;
+    A.packed = (uint64_t*)g->s_rank.p;
+    A.pscan = A.packed + count;
+    A.status = (uint32_t*)(ctl + CTL_STATUS);
+    uint64_t* total = (uint64_t*)(ctl + CTL_SCR + 4);  // scan total
+    k_expand<<<grid_cap(g, count, 256), 256, 0, s>>>(A);
+    CK(scan_excl_u64(A.packed, A.pscan, count, total, g->s_tmp, s, &g->launches), "update scan");
+    k_make_keys<<<grid_cap(g, count, 256), 256, 0, s>>>(A);
+    g->launches += 2;
+    uint64_t tot_host = 0;
+    uint32_t status_host = 0;
+    CK(cudaMemcpyAsync(&tot_host, total, 8, cudaMemcpyDeviceToHost, s), "key count");
+    CK(cudaMemcpyAsync(&status_host, A.status, 4, cudaMemcpyDeviceToHost, s), "status");
+    CK(cudaStreamSynchronize(s), "update expand");
+    CK(cudaMemsetAsync(total, 0, 8, s), "scratch reset");
+    if (status_host & ST_INVALID) {
+        set_error("invalid update record (id >= n, op > 2, or bias outside [1, 2^max_bits)); batch rejected");
+        if (stats) memset(stats, 0, sizeof(*stats));
+        return BINGO_E_INVALID;
+    }
+    const uint64_t nkeys = tot_host & 0xFFFFFFFFull, ninserts = tot_host >> 32;
+    const uint32_t keybits = 2 * A.bn + 1;
+    bool alt = false;
+    CK(radix_sort_pairs(A.keys, A.vals, (uint64_t*)g->s_keys2.p, (uint32_t*)g->s_vals2.p, nkeys, keybits, g->s_tmp, s,
+                        &alt, &g->launches),
+       "update sort");
+    const uint64_t* skeys = alt ? (uint64_t*)g->s_keys2.p : A.keys;
+    const uint32_t* svals = alt ? (uint32_t*)g->s_vals2.p : A.vals;
+    // segments
+    CK(ensure(g->s_seg, 8 * nkeys * 2 + 4 * (nkeys + 2) * 3 + 64), "segment scratch");
+    uint64_t* flag = (uint64_t*)g->s_seg.p;
+    uint64_t* segid = flag + nkeys;
+    uint32_t* seg_start = (uint32_t*)(segid + nkeys);
+    uint32_t* small_list = seg_start + nkeys + 2;
+    uint32_t* big_list = small_list + nkeys + 2;
+    uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
+    k_seg_flags<<<grid_cap(g, nkeys, 256), 256, 0, s>>>(skeys, nkeys, A.bn, flag);
+    CK(scan_excl_u64(flag, segid, nkeys, nseg_dev, g->s_tmp, s, &g->launches), "segment scan");
+    k_seg_write<<<grid_cap(g, nkeys, 256), 256, 0, s>>>(flag, segid, nkeys, seg_start);
+    g->launches += 2;
+    // per-key scratch
+    CK(ensure(g->s_aux, 4 * nkeys * 3 + 64), "apply scratch");
+    CK(ensure(g->s_best, 8 * nkeys + 64), "apply scratch");
+    unsigned long long* counts = (unsigned long long*)(ctl + CTL_SCR);  // small, big, pool bound
+    CK(cudaMemsetAsync(counts, 0, 24, s), "counts reset");
+    SegArgs S;
+    S.B = A;
+    S.sorted_keys = skeys;
+    S.sorted_vals = svals;
+    S.seg_start = seg_start;
+    S.nseg_dev = nseg_dev;
+    S.small_list = small_list;
+    S.big_list = big_list;
+    S.counts = counts;
+    S.eid_base = g->next_eid;
+    S.holes = (uint32_t*)g->s_aux.p;
+    S.surv = S.holes + nkeys;
+    S.slot_scratch = S.surv + nkeys;
+    S.best = (unsigned long long*)g->s_best.p;
+    S.stats = (unsigned long long*)(ctl + CTL_STATS);
+    k_seg_classify<<<grid_cap(g, nkeys, 256), 256, 0, s>>>(g->G, S);
+    k_oom_check<<<1, 1, 0, s>>>(g->G, counts);
+    k_apply_small<<<grid_cap(g, nkeys, APPLY_WARPS, 32), APPLY_WARPS * 32, 0, s>>>(g->G, S);
+    k_apply_big<<<grid_cap(g, nkeys, 1, 4), BIG_THREADS, 0, s>>>(g->G, S);
+    g->launches += 4;
+    if (g->G.eh_mask) {
+        k_eh_apply<<<grid_cap(g, nkeys, 256), 256, 0, s>>>(g->G, S, nkeys);
+        g->launches++;
+    }
+    CK(cudaGetLastError(), "update launch");
+    // scratch words used above live in the stats area; clear them before reporting
+    bingo_status st = finish_batch(g, s, stats, ninserts);
+    if (st == BINGO_OK && g->G.eh_mask && g->eh_distinct + ninserts > (g->G.eh_mask + 1) * 7 / 10) {
+        g->eh_distinct += ninserts;
+        st = edge_index_build(g, s);
+        if (st == BINGO_OK) CK(cudaStreamSynchronize(s), "edge index rebuild");
+    } else if (st == BINGO_OK) {
+        g->eh_distinct += ninserts;
+    }
+    return st;
+}
+
+bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint64_t count, void* stream,
+                                  bingo_update_stats* stats) {
+    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+    if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
+    if (count && !ups) { set_error("NULL update array"); return BINGO_E_INVALID; }
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t* ctl = (uint64_t*)g->d_ctl;
+    CK(cudaMemsetAsync(ctl + CTL_STATUS, 0, 8, s), "status reset");
+    CK(cudaMemsetAsync(ctl + CTL_STATS, 0, (CTL_WORDS - CTL_STATS) * 8, s), "stats reset");
+    if (count == 0) {
+        if (stats) memset(stats, 0, sizeof(*stats));
+        return BINGO_OK;
+    }
+    const uint4* dups = (const uint4*)ups;
+    if (!is_device_ptr(ups)) {
+        CK(ensure(g->s_in, count * 16), "update staging");
+        CK(cudaMemcpyAsync(g->s_in.p, ups, count * 16, cudaMemcpyHostToDevice, s), "update upload");
+        dups = (const uint4*)g->s_in.p;
+    }
+    CK(ensure(g->s_aux, 256), "stream scratch");
+    CK(ensure(g->s_best, 256), "stream scratch");
+    unsigned long long* ninserts = (unsigned long long*)(ctl + CTL_SCR + 6);
+    unsigned long long* applied = (unsigned long long*)(ctl + CTL_SCR + 5);
+    k_validate_stream<<<grid_cap(g, count, 256), 256, 0, s>>>(dups, count, g->n, g->cfg.max_bits,
+                                                                (uint32_t*)(ctl + CTL_STATUS), ninserts);
+    k_stream<<<1, 32, 0, s>>>(g->G, dups, count, g->next_eid, (uint32_t*)g->s_aux.p,
+                              (unsigned long long*)g->s_best.p, (unsigned long long*)(ctl + CTL_STATS), applied);
+    g->launches += 2;
+    CK(cudaGetLastError(), "stream launch");
+    bingo_status st = finish_batch(g, s, stats, 0);
+    if (st == BINGO_OK && g->G.eh_mask && g->eh_distinct + (stats ? stats->inserted : count) > (g->G.eh_mask + 1) * 7 / 10) {
+        st = edge_index_build(g, s);
+        if (st == BINGO_OK) CK(cudaStreamSynchronize(s), "edge index rebuild");
+    } else if (st == BINGO_OK) {
+        g->eh_distinct += stats ? stats->inserted : count;
+    }
+    return st;
+}
+
+}  // extern "C"

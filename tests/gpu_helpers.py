@@ -1,0 +1,157 @@
+"""Comparison of the CUDA path's exported state with the oracle, and walk checks.
+
+The GPU export is brought to the oracle's canonical form (edges by vertex and
+edge id; every group (v, k) as an ascending set of edge ids) and compared
+element by element.  Layout (member positions, inverted indexes, sparse
+lists) has no oracle counterpart and is checked here by its invariants.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+
+KINDS = (O.EMPTY, O.DENSE, O.ONE, O.SPARSE, O.REGULAR)
+
+
+def _segments(lengths):
+    lengths = np.asarray(lengths, dtype=np.int64)
+    starts = np.zeros(len(lengths), dtype=np.int64)
+    if len(lengths) > 1:
+        starts[1:] = np.cumsum(lengths)[:-1]
+    return starts
+
+
+def gpu_canonical(ex):
+    """Edges sorted by (vertex, eid) and group memberships sorted by (vertex, k, eid)."""
+    deg = ex["deg"].astype(np.int64)
+    n = len(deg)
+    eoff = _segments(deg)
+    vslot = np.repeat(np.arange(n, dtype=np.int64), deg)
+    eid = ex["eid"].astype(np.uint64)
+    order = np.lexsort((eid, vslot))
+    edges = (vslot[order], ex["dst"][order], ex["bias"][order], eid[order])
+    # groups: (v, k, eid) for every membership
+    kind = ex["kind"]
+    w = ex["bias"].astype(np.uint64)
+    vs, ks, es = [], [], []
+    # dense groups: filter the adjacency by bit k
+    for k in range(32):
+        bit = ((w >> np.uint64(k)) & np.uint64(1)).astype(bool)
+        dense_v = kind[:, k] == O.DENSE
+        sel = bit & dense_v[vslot]
+        vs.append(vslot[sel]); ks.append(np.full(int(sel.sum()), k, np.int64)); es.append(eid[sel])
+    # one-element groups
+    ov, ok = np.nonzero(kind == O.ONE)
+    oslot = ex["one_slot"][ov, ok].astype(np.int64)
+    vs.append(ov.astype(np.int64)); ks.append(ok.astype(np.int64)); es.append(eid[eoff[ov] + oslot])
+    # list groups
+    glen = ex["glen"].reshape(-1).astype(np.int64)
+    gv = np.repeat(np.arange(n * 32, dtype=np.int64) // 32, glen)
+    gk = np.repeat(np.arange(n * 32, dtype=np.int64) % 32, glen)
+    mem = ex["members"].astype(np.int64)
+    gkind = kind[gv, gk]
+    sp_off = _segments(ex["sp_len"])
+    slot = mem.copy()
+    sp = gkind == O.SPARSE
+    slot[sp] = ex["sp_list"][sp_off[gv[sp]] + mem[sp]].astype(np.int64)
+    vs.append(gv); ks.append(gk); es.append(eid[eoff[gv] + slot])
+    V, K, E = np.concatenate(vs), np.concatenate(ks), np.concatenate(es)
+    o = np.lexsort((E, K, V))
+    return edges, (V[o], K[o], E[o])
+
+
+def oracle_canonical(og: O.Graph):
+    offs, dst, w, eid = og.edges()
+    deg = np.diff(offs.astype(np.int64))
+    v = np.repeat(np.arange(og.n, dtype=np.int64), deg)
+    moffs, meids = og.members_all()
+    glen = np.diff(moffs.astype(np.int64))
+    gv = np.repeat(np.arange(og.n * 32, dtype=np.int64) // 32, glen)
+    gk = np.repeat(np.arange(og.n * 32, dtype=np.int64) % 32, glen)
+    return (v, dst, w, eid), (gv, gk, meids.astype(np.uint64))
+
+
+def check_layout_invariants(ex):
+    """Member lists compact and consistent with their inverted indexes; sparse lists exact."""
+    deg = ex["deg"].astype(np.int64)
+    n = len(deg)
+    kind = ex["kind"]
+    cnt = ex["cnt"].astype(np.int64)
+    glen = ex["glen"].astype(np.int64)
+    listk = (kind == O.REGULAR) | (kind == O.SPARSE)
+    assert (glen[listk] == cnt[listk]).all(), "list length != |G_k|"
+    assert (glen[~listk] == 0).all()
+    gl = glen.reshape(-1)
+    pos = np.arange(gl.sum(), dtype=np.int64) - np.repeat(_segments(gl), gl)
+    assert (ex["member_inv"].astype(np.int64) == pos).all(), "inverted index does not point back at its member"
+    gv = np.repeat(np.arange(n * 32, dtype=np.int64) // 32, gl)
+    gk = np.repeat(np.arange(n * 32, dtype=np.int64) % 32, gl)
+    mem = ex["members"].astype(np.int64)
+    reg = kind[gv, gk] == O.REGULAR
+    assert (mem[reg] < deg[gv[reg]]).all(), "regular member outside the adjacency"
+    spl = ex["sp_len"].astype(np.int64)
+    sp = ~reg
+    assert (mem[sp] < spl[gv[sp]]).all(), "sparse member outside the sparse list"
+    # members distinct within each group
+    key = gv * 32 + gk
+    pairs = np.unique(np.stack([key, mem]), axis=1)
+    assert pairs.shape[1] == len(mem), "duplicate member in a group"
+    # sparse list: inverse consistent, entries = edges in any sparse group
+    spos = np.arange(spl.sum(), dtype=np.int64) - np.repeat(_segments(spl), spl)
+    assert (ex["sp_inv"].astype(np.int64) == spos).all(), "sparse-list inverted index inconsistent"
+    spmask = np.zeros(n, dtype=np.uint64)
+    sv, sk = np.nonzero(kind == O.SPARSE)
+    np.bitwise_or.at(spmask, sv, (np.uint64(1) << sk.astype(np.uint64)))
+    eoff = _segments(deg)
+    vslot = np.repeat(np.arange(n, dtype=np.int64), deg)
+    in_s = (ex["bias"].astype(np.uint64) & spmask[vslot]) != 0
+    exp_cnt = np.bincount(vslot[in_s], minlength=n)
+    assert (exp_cnt == spl).all(), "sparse list size != edges in sparse groups"
+    sv2 = np.repeat(np.arange(n, dtype=np.int64), spl)
+    slots = ex["sp_list"].astype(np.int64)
+    assert (slots < deg[sv2]).all()
+    assert in_s[eoff[sv2] + slots].all(), "sparse list holds an edge of no sparse group"
+    # one-element slots hold the bit
+    ov, ok = np.nonzero(kind == O.ONE)
+    os_ = ex["one_slot"][ov, ok].astype(np.int64)
+    assert (os_ < deg[ov]).all()
+    assert (((ex["bias"][eoff[ov] + os_].astype(np.uint64) >> ok.astype(np.uint64)) & np.uint64(1)) == 1).all()
+
+
+def assert_state_matches(ex, og: O.Graph, alpha=40, beta=10):
+    """Bit-exact factorisation state (edges, |G_k|, kinds, memberships) + layout invariants."""
+    (gv, gd, gw, ge), (Gv, Gk, Ge) = gpu_canonical(ex)
+    (ov, od, ow, oe), (Ov, Ok, Oe) = oracle_canonical(og)
+    assert len(ge) == len(oe), f"edge count {len(ge)} != oracle {len(oe)}"
+    assert (gv == ov).all() and (gd == od).all() and (gw == ow).all() and (ge == oe).all(), "adjacency differs"
+    cnt, kd, sw = og.factor_all(alpha, beta)
+    assert (ex["cnt"] == cnt).all(), "group counts differ"
+    assert (ex["kind"] == kd).all(), "group kinds differ"
+    assert len(Ge) == len(Oe), f"membership count {len(Ge)} != oracle {len(Oe)}"
+    assert (Gv == Ov).all() and (Gk == Ok).all() and (Ge == Oe).all(), "group memberships differ"
+    check_layout_invariants(ex)
+
+
+def edge_keys(og: O.Graph):
+    offs, dst, _, _ = og.edges()
+    deg = np.diff(offs.astype(np.int64))
+    src = np.repeat(np.arange(og.n, dtype=np.uint64), deg)
+    return np.unique((src << np.uint64(32)) | dst.astype(np.uint64))
+
+
+def assert_steps_live(og: O.Graph, paths: np.ndarray, plen: np.ndarray, keys=None):
+    """Every consecutive pair of every path is a live edge of the oracle graph; padding is 0xFFFFFFFF."""
+    keys = edge_keys(og) if keys is None else keys
+    L = paths.shape[1]
+    idx = np.arange(L - 1)[None, :]
+    valid = idx < (plen.astype(np.int64)[:, None] - 1)
+    u = paths[:, :-1][valid].astype(np.uint64)
+    x = paths[:, 1:][valid].astype(np.uint64)
+    q = (u << np.uint64(32)) | x
+    pos = np.searchsorted(keys, q)
+    pos = np.minimum(pos, len(keys) - 1)
+    ok = keys[pos] == q
+    assert ok.all(), f"{int((~ok).sum())} steps are not live edges"
+    pad = np.arange(L)[None, :] >= plen.astype(np.int64)[:, None]
+    assert (paths[pad] == 0xFFFFFFFF).all(), "padding is not 0xFFFFFFFF"

@@ -1,0 +1,345 @@
+"""Walks on the CUDA path, through the C ABI, against the oracle.
+
+Statistical parity: one-step transition frequencies at >= 10^6 samples must
+agree with the oracle's w / sum w (TV <= 0.01 and chi-square p > 1e-3; more
+than 1,000 neighbours are binned in edge-id order with exact bin masses).
+Every step of every walk must be a live edge of the oracle graph at that
+epoch.  Bit-exact GPU-vs-GPU: paths do not depend on the team width, the
+launch form (persistent / stepwise) or on other requests in a merged launch.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.conftest import golden
+from tests.gpu_helpers import assert_steps_live, edge_keys
+from tests.stats import binned, chisq_p, tv
+
+pytestmark = pytest.mark.gpu
+N_SAMPLES = 1_000_000
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2504_10233_gb300 import _build
+
+    _build.build()
+    import paper_2504_10233_gb300 as B
+
+    B.load()
+    return B
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_walk(B, g, starts, policies, seed, stride, lengths=None, pids=None, mode=0):
+    import torch
+
+    n = len(starts)
+    paths = torch.empty((n, stride), dtype=torch.int32, device="cuda")
+    plen = torch.empty(n, dtype=torch.int32, device="cuda")
+    g.walk(dev(starts), policies, seed, stride, paths, plen,
+           lengths=None if lengths is None else dev(lengths),
+           policy_ids=None if pids is None else dev(pids), mode=mode)
+    g.check()
+    return paths.cpu().numpy().view(np.uint32), plen.cpu().numpy().view(np.uint32)
+
+
+def graph_of(B, G, **cfg):
+    return B.Graph(G.n, dev(G.row_ptr), dev(G.col), dev(G.w), max_bits=G.max_bits, **cfg)
+
+
+def one_step_check(B, g, og, v, seed):
+    """10^6 one-step samples from v against the oracle's w / sum w (duplicates merged)."""
+    offs, dst, w, _ = og.edges()
+    a, c = int(offs[v]), int(offs[v + 1])
+    d = dst[a:c].astype(np.int64)
+    ww = w[a:c].astype(np.float64)
+    uniq, inv = np.unique(d, return_inverse=True)
+    probs = np.bincount(inv, weights=ww)
+    starts = np.full(N_SAMPLES, v, dtype=np.uint32)
+    paths, plen = run_walk(B, g, starts, [B.policy(B.DEEPWALK, 1)], seed, 2)
+    assert (plen == 2).all()
+    got = paths[:, 1].astype(np.int64)
+    pos = np.searchsorted(uniq, got)
+    assert (uniq[np.minimum(pos, len(uniq) - 1)] == got).all(), "sampled a non-neighbour"
+    counts = np.bincount(pos, minlength=len(uniq)).astype(np.float64)
+    cb, pb = binned(counts, probs, 1000)
+    t, p = tv(cb, pb), chisq_p(cb, pb)
+    assert t <= 0.01, (v, t)
+    assert p > 1e-3, (v, p)
+    return t, p
+
+
+def pick_vertices(og, ex_kind, want):
+    """One vertex for each requested kind present among its groups, preferring higher degree."""
+    offs, _, _, _ = og.edges()
+    deg = np.diff(offs.astype(np.int64))
+    out = []
+    for kd in want:
+        cand = np.nonzero((ex_kind == kd).any(axis=1) & (deg > 0))[0]
+        if len(cand):
+            out.append(int(cand[np.argmax(deg[cand])]))
+    return sorted(set(out))
+
+
+def test_one_step_distribution_c1(B):
+    wl = W.make_workload("c1")
+    G = wl.graph
+    g = graph_of(B, G)
+    og = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    for i, v in enumerate((0, 333, 1023)):
+        one_step_check(B, g, og, v, 10 + i)
+
+
+def test_one_step_distribution_every_kind_and_after_updates(B):
+    wl = W.make_workload("c2", scale=16, m=1 << 20, nbatch=2, batch=50000)
+    G = wl.graph
+    g = graph_of(B, G)
+    og = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    kinds = g.export_state()["kind"]
+    vs = pick_vertices(og, kinds, [O.DENSE, O.ONE, O.SPARSE, O.REGULAR])
+    assert len(vs) >= 3
+    for i, v in enumerate(vs):
+        one_step_check(B, g, og, v, 100 + i)
+    for b in wl.batches:
+        rec = b.records()
+        g.apply_updates(dev(rec))
+        og.apply(rec, G.max_bits)
+    touched = np.unique(wl.batches[-1].src)
+    offs, _, _, _ = og.edges()
+    deg = np.diff(offs.astype(np.int64))
+    t = touched[np.argsort(-deg[touched])][:3]
+    for i, v in enumerate(t):
+        one_step_check(B, g, og, int(v), 200 + i)
+
+
+def test_hub_one_step_binned(B):
+    n = 1 << 12
+    rng = np.random.default_rng(4)
+    d = 30000
+    edges = [(0, int(rng.integers(0, n)), int(rng.integers(1, 1 << 20))) for _ in range(d)]
+    edges += [(v, int(rng.integers(0, n)), 1) for v in range(1, n) for _ in range(2)]
+    og = O.Graph.from_edges(n, edges)
+    offs, dst, w, _ = og.edges()
+    g = B.Graph(n, dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=20)
+    one_step_check(B, g, og, 0, 77)
+
+
+@pytest.mark.parametrize("name", ["c1", "c2s"])
+def test_every_step_is_a_live_edge(B, name):
+    wl = W.make_workload("c1") if name == "c1" else W.make_workload("c2", scale=15, m=1 << 19, nbatch=2, batch=20000)
+    G = wl.graph
+    g = graph_of(B, G)
+    og = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    nw = min(G.n, 1 << 15)
+    starts = W.walk_starts(G.n, nw, 0)
+    pol = B.policy(B.DEEPWALK, wl.length)
+    paths, plen = run_walk(B, g, starts, [pol], 0, wl.length + 1)
+    assert (paths[:, 0] == starts).all()
+    assert_steps_live(og, paths, plen)
+    for ep, b in enumerate(wl.batches):
+        rec = b.records()
+        g.apply_updates(dev(rec))
+        og.apply(rec, G.max_bits)
+        paths, plen = run_walk(B, g, starts, [pol], ep + 1, wl.length + 1)
+        assert_steps_live(og, paths, plen)
+
+
+def _mixed_policies(B):
+    return [B.policy(B.DEEPWALK, 20), B.policy(B.PPR, 30, 0.15), B.policy(B.NODE2VEC, 25, n2v_pq=(2.0, 0.5))]
+
+
+def test_paths_independent_of_team_width_and_launch_form(B):
+    wl = W.make_workload("c2", scale=14, m=1 << 18, nbatch=1, batch=4000)
+    G = wl.graph
+    g = graph_of(B, G)
+    nw = 20000
+    starts = W.walk_starts(G.n, nw, 1)
+    pids = (np.arange(nw) % 3).astype(np.uint8)
+    pols = _mixed_policies(B)
+    ref = None
+    for lanes in (1, 4, 32):
+        for wpb in (4, 8):
+            g.set_walk_config(lanes, wpb)
+            res = run_walk(B, g, starts, pols, 42, 31, pids=pids)
+            if ref is None:
+                ref = res
+            assert (res[0] == ref[0]).all() and (res[1] == ref[1]).all(), (lanes, wpb)
+    step = run_walk(B, g, starts, pols, 42, 31, pids=pids, mode=B.WALK_STEPWISE)
+    assert (step[0] == ref[0]).all() and (step[1] == ref[1]).all()
+    other = run_walk(B, g, starts, pols, 43, 31, pids=pids)
+    assert (other[0] != ref[0]).any()
+    og = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    assert_steps_live(og, ref[0], ref[1])
+
+
+def test_ppr_length_distribution(B):
+    n = 64
+    edges = [(v, (v + 1) % n, 1 + v % 5) for v in range(n)] + [(v, (v * 7 + 3) % n, 2) for v in range(n)]
+    og = O.Graph.from_edges(n, edges)
+    offs, dst, w, _ = og.edges()
+    g = B.Graph(n, dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=8)
+    s_u32, cap = 644245094, 30
+    paths, plen = run_walk(B, g, W.walk_starts(n, N_SAMPLES, 3), [B.policy(B.PPR, cap, s_u32)], 5, cap + 1)
+    steps = plen.astype(np.int64) - 1
+    counts = np.bincount(steps, minlength=cap + 1)
+    s = s_u32 / 2 ** 32
+    probs = np.array([(1 - s) ** l * s for l in range(cap)] + [(1 - s) ** cap])
+    assert tv(counts, probs) < 0.01
+    assert chisq_p(counts, probs) > 1e-3
+
+
+def _n2v_two_step(B, g, accept, seed):
+    starts = np.zeros(N_SAMPLES, dtype=np.uint32)
+    pol = B.policy(B.NODE2VEC, 2)
+    for i in range(3):
+        pol.n2v_accept[i] = accept[i]
+    return run_walk(B, g, starts, [pol], seed, 3)
+
+
+def test_node2vec_tiny_closed_form(B):
+    gd = golden("node2vec_tiny.json")
+    og = O.Graph.from_edges(gd["n"], [tuple(e) for e in gd["edges"]])
+    offs, dst, w, _ = og.edges()
+    g = B.Graph(gd["n"], dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=8)
+    paths, plen = _n2v_two_step(B, g, gd["accept_u32"], 9)
+    assert (plen == 3).all()
+    tp = gd["two_step_paths_from_0"]
+    keys = {tuple(p): i for i, p in enumerate(tp["paths"])}
+    code = paths[:, 1].astype(np.int64) * 16 + paths[:, 2].astype(np.int64)
+    counts = np.zeros(len(keys))
+    for (a, b, c), i in keys.items():
+        counts[i] = (code == b * 16 + c).sum()
+    assert counts.sum() == N_SAMPLES
+    probs = np.array(tp["prob_num"], float) / tp["prob_den"]
+    assert tv(counts, probs) < 0.01 and chisq_p(counts, probs) > 1e-3
+
+
+def test_node2vec_edge_index_follows_updates(B):
+    gd = golden("node2vec_tiny.json")
+    og = O.Graph.from_edges(gd["n"], [tuple(e) for e in gd["edges"]])
+    offs, dst, w, _ = og.edges()
+    g = B.Graph(gd["n"], dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=8)
+    _n2v_two_step(B, g, gd["accept_u32"], 1)  # builds the edge index
+    # delete 0 -> 2 and add 0 -> 3: from 1 after 0, neighbour 2 becomes distance 2 and 3 distance 1
+    rec = np.array([[0, 2, 0, 1], [0, 3, 1, 0]], dtype=np.uint32)
+    g.apply_updates(dev(rec))
+    og.apply(rec, 8)
+    paths, plen = _n2v_two_step(B, g, gd["accept_u32"], 2)
+    assert (paths[:, 1] == 1).sum() + (paths[:, 1] == 3).sum() == N_SAMPLES
+    sel = paths[:, 1] == 1
+    wts = og.n2v_weights(0, 1, gd["accept_u32"]).astype(np.float64)
+    o2, d2, _, _ = og.edges()
+    nb = d2[o2[1]:o2[2]].astype(np.int64)
+    counts = np.array([(paths[sel, 2] == x).sum() for x in nb], dtype=np.float64)
+    assert tv(counts, wts) < 0.01 and chisq_p(counts, wts) > 1e-3
+
+
+def test_padding_flag_and_host_buffers(B):
+    wl = W.make_workload("c1")
+    G = wl.graph
+    g = graph_of(B, G)
+    starts = W.walk_starts(G.n, 4096, 0)
+    pol = [B.policy(B.PPR, 40, 0.2)]
+    p1, l1 = run_walk(B, g, starts, pol, 7, 41)
+    # host numpy buffers through the same entry point
+    p2 = np.zeros((4096, 41), dtype=np.uint32)
+    l2 = np.zeros(4096, dtype=np.uint32)
+    g.walk(starts, pol, 7, 41, p2, l2)
+    assert (p1 == p2).all() and (l1 == l2).all()
+    # no-pad: entries beyond path_len untouched
+    p3 = np.full((4096, 41), 0x12345678, dtype=np.uint32)
+    g.walk(starts, pol, 7, 41, p3, l2, mode=B.WALK_NO_PAD)
+    idx = np.arange(41)[None, :] >= l1[:, None].astype(np.int64)
+    assert (p3[idx] == 0x12345678).all() and (p3[~idx] == p1[~idx]).all()
+
+
+def test_invalid_walk_arguments(B):
+    wl = W.make_workload("c1")
+    G = wl.graph
+    g = graph_of(B, G)
+    with pytest.raises(B.BingoError):  # max_len does not fit the stride
+        run_walk(B, g, np.zeros(4, np.uint32), [B.policy(B.DEEPWALK, 80)], 0, 10)
+    with pytest.raises(B.BingoError) as ei:  # start vertex out of range (latched on the device)
+        run_walk(B, g, np.array([0, G.n + 5], np.uint32), [B.policy(B.DEEPWALK, 3)], 0, 4)
+    assert ei.value.status == B.E_INVALID
+    # zero-length walks and dead ends
+    paths, plen = run_walk(B, g, np.array([1, 2], np.uint32), [B.policy(B.DEEPWALK, 0)], 0, 1)
+    assert (plen == 1).all() and (paths[:, 0] == [1, 2]).all()
+
+
+def test_autotune_keeps_results(B):
+    wl = W.make_workload("c2", scale=14, m=1 << 18, nbatch=1, batch=1000)
+    G = wl.graph
+    g = graph_of(B, G)
+    starts = W.walk_starts(G.n, 50000, 0)
+    pol = [B.policy(B.DEEPWALK, 30)]
+    before = run_walk(B, g, starts, pol, 3, 31)
+    cfg = g.autotune(dev(starts), 30)
+    assert cfg.lanes_per_walker in (1, 4, 32)
+    after = run_walk(B, g, starts, pol, 3, 31)
+    assert (before[0] == after[0]).all()
+
+
+def test_server_results_same_alone_and_in_the_mix(B):
+    import ctypes
+
+    wl = W.make_workload("c2", scale=14, m=1 << 18, nbatch=1, batch=2000)
+    G = wl.graph
+    g = graph_of(B, G)
+    L = B.load()
+    pol = B.policy(B.PPR, 40, 0.15)
+    reqs = [(W.walk_starts(G.n, int(nw), 10 + i), 1000 + i) for i, nw in enumerate([1, 37, 500, 4096, 9])]
+
+    def serve(subset, updates=None):
+        h = ctypes.c_void_p()
+        cfg = B.bingo_server_config()
+        assert L.bingo_server_create(g.h, ctypes.byref(cfg), ctypes.byref(h)) == 0
+        if updates is not None:
+            ep = ctypes.c_uint64()
+            assert L.bingo_server_submit_updates(h, updates.ctypes.data, len(updates), ctypes.byref(ep)) == 0
+            assert L.bingo_server_drain(h, 60000) == 0
+        tickets = []
+        for i in subset:
+            st, seed = reqs[i]
+            t = ctypes.c_uint64()
+            assert L.bingo_server_submit_walk(h, st.ctypes.data, len(st), ctypes.byref(pol), seed, ctypes.byref(t)) == 0
+            tickets.append((i, t.value))
+        out = {}
+        for i, t in tickets:
+            n = len(reqs[i][0])
+            p = np.zeros((n, 41), np.uint32)
+            l = np.zeros(n, np.uint32)
+            ep = ctypes.c_uint64()
+            assert L.bingo_server_wait(h, t, 60000, p.ctypes.data, l.ctypes.data, ctypes.byref(ep)) == 0
+            out[i] = (p, l, ep.value)
+        stats = B.bingo_server_stats()
+        L.bingo_server_stats_get(h, ctypes.byref(stats))
+        L.bingo_server_destroy(h)
+        return out, stats
+
+    mix, stats = serve(range(len(reqs)))
+    assert stats.requests_done == len(reqs) and stats.p99_ms >= stats.p50_ms > 0
+    for i in range(len(reqs)):
+        alone, _ = serve([i])
+        assert (alone[i][0] == mix[i][0]).all() and (alone[i][1] == mix[i][1]).all(), i
+    # the same request equals a direct bingo_walk with its seed
+    st, seed = reqs[2]
+    p, l = run_walk(B, g, st, [pol], seed, 41)
+    assert (p == mix[2][0]).all() and (l == mix[2][1]).all()
+    # updates submitted to the server are applied at an epoch boundary before later requests
+    og = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    upd = wl.batches[0].records()
+    og.apply(upd, G.max_bits)
+    after, stats2 = serve([3], updates=upd)
+    assert after[3][2] >= 1 and stats2.updates_applied == len(upd)
+    assert_steps_live(og, after[3][0], after[3][1])
