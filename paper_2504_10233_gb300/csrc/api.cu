@@ -89,6 +89,9 @@ bingo_status bingo_walk(bingo_graph* g, uint64_t nwalkers, const uint32_t* start
     if (host_paths) {
         CK(ensure(g->w_paths, 4ull * nwalkers * stride), "walk output staging");
         dpaths = (uint32_t*)g->w_paths.p;
+        // without padding, entries past path_len must keep the caller's values through the round trip
+        if (!pad)
+            CK(cudaMemcpyAsync(dpaths, paths, 4ull * nwalkers * stride, cudaMemcpyHostToDevice, s), "paths upload");
     }
     if (host_plen) {
         CK(ensure(g->w_plen, 4ull * nwalkers), "walk output staging");

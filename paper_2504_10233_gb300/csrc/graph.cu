@@ -376,7 +376,7 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
     size_t fr = 0, tt = 0;
     cudaMemGetInfo(&fr, &tt);
     if (pool_words == 0) {
-        pool_words = need + need / 2 + (64ull << 20);
+        pool_words = 2 * need + (256ull << 20);  // room for growth and for the per-batch worst-case check
         const uint64_t avail = fr > (4ull << 30) ? (fr - (4ull << 30)) / 4 : 0;
         if (pool_words > avail) pool_words = std::max<uint64_t>(need + (need >> 4), avail);
     }

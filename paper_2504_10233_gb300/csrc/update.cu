@@ -700,8 +700,10 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
             const uint32_t c = G.cnt[(uint64_t)v * 32 + k] + (((insbits >> k) & 1u) ? ni : 0u);
             ngroups += c >= 2;
         }
+        // worst case: a grown adjacency, and every group that could hold >= 2 members gets a new
+        // block (regular: 2*capA words; sparse: 2*capS <= 2*capA) plus a new sparse list (2*capA)
         if (dtot > capa_of(h)) bound += 4ull * capa1;
-        if (ngroups) bound += 2ull * capa1 * (ngroups + 1) + 2ull * caps_for(dtot) * ngroups;
+        if (ngroups) bound += 2ull * capa1 * (ngroups + 1);
         const bool big = dtot > 4096 || (b - a) > 256;
         if (big) S.big_list[atomicAdd(&S.counts[1], 1ull)] = (uint32_t)sidx;
         else S.small_list[atomicAdd(&S.counts[0], 1ull)] = (uint32_t)sidx;
