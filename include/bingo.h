@@ -179,6 +179,36 @@ bingo_status bingo_walk(bingo_graph* g, uint64_t nwalkers, const uint32_t* start
                         uint32_t stride, uint32_t* paths, uint32_t* path_len, uint32_t mode, void* stream);
 
 /*
+ * Allocation-free variant of bingo_walk.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they
+ * walk (code inside an allocator or memory-pool callback, frameworks that
+ * reserve all device memory up front, real-time loops that forbid
+ * cudaMalloc/cudaFree because they can synchronise the device).  It runs the
+ * same persistent walker and gives bit-identical results to bingo_walk, and it
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ * Its scratch (work counter and policy table) is a fixed 1 KiB array that the
+ * library reserves on every device that loads it, held until process exit.
+ *  - Limits: npolicies 1..16 (the table's capacity); larger counts return
+ *    BINGO_E_INVALID.  Only BINGO_WALK_PERSISTENT (optionally with
+ *    BINGO_WALK_NO_PAD).  starts, lengths, policy_ids, paths and path_len must
+ *    be device pointers (host pointers would need staging: BINGO_E_INVALID).
+ *    node2vec needs the edge index that an earlier bingo_walk built
+ *    (BINGO_E_STATE otherwise).
+ *  - The first call on each device resolves the scratch array's address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array and the counter is reset at
+ *    the start of each call, so calls whose work overlaps on the GPU (different
+ *    streams, or host threads without ordering) race; serialise them on one
+ *    stream.  Asynchronous on `stream`; device-side errors are latched as for
+ *    bingo_walk and reported by bingo_check.
+ */
+bingo_status bingo_walk_noalloc(bingo_graph* g, uint64_t nwalkers, const uint32_t* starts, const uint32_t* lengths,
+                                const uint8_t* policy_ids, const bingo_policy* policies, uint32_t npolicies,
+                                uint64_t seed, uint32_t stride, uint32_t* paths, uint32_t* path_len, uint32_t mode,
+                                void* stream);
+
+/*
  * Synchronise `stream` and return the device status latched by earlier
  * asynchronous calls on this graph (BINGO_E_INVALID for a bad start vertex,
  * policy id or length; BINGO_E_TIMEOUT if a bounded rejection loop gave up),

@@ -87,6 +87,8 @@ SIGNATURES = {
     "bingo_stream_updates": (c.c_int, [VP, VP, c.c_uint64, VP, c.POINTER(bingo_update_stats)]),
     "bingo_walk": (c.c_int, [VP, c.c_uint64, VP, VP, VP, c.POINTER(bingo_policy), c.c_uint32, c.c_uint64,
                              c.c_uint32, VP, VP, c.c_uint32, VP]),
+    "bingo_walk_noalloc": (c.c_int, [VP, c.c_uint64, VP, VP, VP, c.POINTER(bingo_policy), c.c_uint32, c.c_uint64,
+                                     c.c_uint32, VP, VP, c.c_uint32, VP]),
     "bingo_check": (c.c_int, [VP, VP]),
     "bingo_state_sizes_get": (c.c_int, [VP, c.POINTER(bingo_state_sizes)]),
     "bingo_export_state": (c.c_int, [VP] + [VP] * 13),
@@ -217,6 +219,14 @@ def bingo_walk(h, nwalkers, starts, policies, seed, stride, paths, path_len, len
     arr = (bingo_policy * len(policies))(*policies)
     _err(load().bingo_walk(h, nwalkers, _ptr(starts), _ptr(lengths), _ptr(policy_ids), arr, len(policies), seed,
                            stride, _ptr(paths), _ptr(path_len), mode, _stream(stream)))
+
+
+def bingo_walk_noalloc(h, nwalkers, starts, policies, seed, stride, paths, path_len, lengths=None, policy_ids=None,
+                       mode=WALK_PERSISTENT, stream=None):
+    """bingo_walk without any device allocation (device buffers only; see include/bingo.h)."""
+    arr = (bingo_policy * len(policies))(*policies)
+    _err(load().bingo_walk_noalloc(h, nwalkers, _ptr(starts), _ptr(lengths), _ptr(policy_ids), arr, len(policies),
+                                   seed, stride, _ptr(paths), _ptr(path_len), mode, _stream(stream)))
 
 
 def bingo_check(h, stream=None):
