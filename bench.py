@@ -333,7 +333,7 @@ def run_ours(args):
     h_plen = torch.empty(nw, dtype=torch.int32).pin_memory()
     h_recs = [torch.from_numpy(np.ascontiguousarray(b.records())).pin_memory() for b in wl.batches]
     e2e_steps, e2e_t = 0, 0.0
-    for i in range(min(args.steps, 3)):
+    for i in range(0 if args.no_e2e else min(args.steps, 3)):
         flush.fill_(i)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -342,7 +342,7 @@ def run_ours(args):
         e2e_t += time.perf_counter() - t0
         e2e_steps += int((h_plen.numpy().astype(np.int64) - 1).sum())
     e2e_t = max_over_ranks(e2e_t, dev)
-    e2e = {"value": sum_over_ranks(float(e2e_steps), dev) / e2e_t, "unit": "steps/s",
+    e2e = {"value": sum_over_ranks(float(e2e_steps), dev) / e2e_t if e2e_t > 0 else None, "unit": "steps/s",
            "h2d_bytes_per_step": int(h_starts.numel() * 4 + h_recs[0].numel() * 4),
            "d2h_bytes_per_step": int(h_paths.numel() * 4 + h_plen.numel() * 4)}
 
@@ -379,6 +379,7 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-walkers", type=int, default=16384)
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per walk launch, if captured")
