@@ -359,7 +359,8 @@ def run_ours(args):
                            "length": wl.length, "updates_per_step": len(wl.batches[0]),
                            "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); state > L2",
                            "walk_config": {"lanes_per_walker": g.config().lanes_per_walker,
-                                           "warps_per_block": g.config().warps_per_block}},
+                                           "warps_per_block": g.config().warps_per_block,
+                                           "reg_variant": g.config().reg_variant}},
                 "updated_edges_per_s": upd_rate, "walk_steps_per_s": walk_rate,
                 "update_ms_per_step": float(np.mean(upd_ms)), "walk_ms_per_step": float(np.mean(walk_ms)),
                 "wall_s_timed": wall, "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),

@@ -73,7 +73,7 @@ typedef struct {
     uint32_t warps_per_block;  /* walker kernel block size in warps; 0 = tuned default */
     uint32_t blocks_per_sm;    /* walker kernel persistent blocks per SM; 0 = tuned default */
     uint32_t update_chunk;     /* segments above this many adjacency slots use a whole block; 0 = default */
-    uint32_t reserved;
+    uint32_t reg_variant;      /* walker register budget: 0 = 64 registers, 1 = 40 registers (more resident warps) */
     uint64_t pool_words;       /* device pool for adjacency and group blocks, in 4-byte words; 0 = auto */
 } bingo_config;
 
@@ -254,7 +254,7 @@ bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, ui
 bingo_status bingo_memory_report(bingo_graph* g, uint64_t out[6]);
 
 /*
- * Autotune the walker launch (lanes per walker, warps per block, blocks per SM)
+ * Autotune the walker launch (lanes per walker, warps per block, register variant)
  * on this graph with a trial walk of `nwalkers` DeepWalk walkers of `length`
  * steps from the given device/host starts; the best setting is stored in the
  * graph's config.  out_cfg (nullable) receives it.  Synchronises `stream`.
@@ -265,7 +265,7 @@ bingo_status bingo_autotune(bingo_graph* g, uint64_t nwalkers, const uint32_t* s
 /* Current configuration of the graph (host pointer). */
 bingo_status bingo_get_config(bingo_graph* g, bingo_config* out);
 bingo_status bingo_set_walk_config(bingo_graph* g, uint32_t lanes_per_walker, uint32_t warps_per_block,
-                                   uint32_t blocks_per_sm);
+                                   uint32_t blocks_per_sm, uint32_t reg_variant);
 
 /* Kernel launches issued by this graph so far (walk, update and build kernels). */
 uint64_t bingo_kernel_launches(bingo_graph* g);

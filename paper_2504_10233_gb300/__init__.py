@@ -40,7 +40,7 @@ class BingoError(RuntimeError):
 class bingo_config(c.Structure):
     _fields_ = [("alpha_pct", c.c_uint32), ("beta_pct", c.c_uint32), ("max_bits", c.c_uint32),
                 ("lanes_per_walker", c.c_uint32), ("warps_per_block", c.c_uint32), ("blocks_per_sm", c.c_uint32),
-                ("update_chunk", c.c_uint32), ("reserved", c.c_uint32), ("pool_words", c.c_uint64)]
+                ("update_chunk", c.c_uint32), ("reg_variant", c.c_uint32), ("pool_words", c.c_uint64)]
 
 
 class bingo_update_stats(c.Structure):
@@ -95,7 +95,7 @@ SIGNATURES = {
     "bingo_memory_report": (c.c_int, [VP, c.POINTER(c.c_uint64)]),
     "bingo_autotune": (c.c_int, [VP, c.c_uint64, VP, c.c_uint32, VP, c.POINTER(bingo_config)]),
     "bingo_get_config": (c.c_int, [VP, c.POINTER(bingo_config)]),
-    "bingo_set_walk_config": (c.c_int, [VP, c.c_uint32, c.c_uint32, c.c_uint32]),
+    "bingo_set_walk_config": (c.c_int, [VP, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32]),
     "bingo_kernel_launches": (c.c_uint64, [VP]),
     "bingo_server_create": (c.c_int, [VP, c.POINTER(bingo_server_config), c.POINTER(VP)]),
     "bingo_server_destroy": (c.c_int, [VP]),
@@ -252,8 +252,8 @@ def bingo_get_config(h):
     return cfg
 
 
-def bingo_set_walk_config(h, lanes, warps_per_block, blocks_per_sm=0):
-    _err(load().bingo_set_walk_config(h, lanes, warps_per_block, blocks_per_sm))
+def bingo_set_walk_config(h, lanes, warps_per_block, blocks_per_sm=0, reg_variant=0):
+    _err(load().bingo_set_walk_config(h, lanes, warps_per_block, blocks_per_sm, reg_variant))
 
 
 def bingo_kernel_launches(h) -> int:
@@ -334,8 +334,8 @@ class Graph:
     def autotune(self, starts, length, stream=None):
         return bingo_autotune(self.h, len(starts), starts, length, stream)
 
-    def set_walk_config(self, lanes, warps_per_block, blocks_per_sm=0):
-        bingo_set_walk_config(self.h, lanes, warps_per_block, blocks_per_sm)
+    def set_walk_config(self, lanes, warps_per_block, blocks_per_sm=0, reg_variant=0):
+        bingo_set_walk_config(self.h, lanes, warps_per_block, blocks_per_sm, reg_variant)
 
     def config(self):
         return bingo_get_config(self.h)

@@ -184,15 +184,18 @@ bingo_status bingo_autotune(bingo_graph* g, uint64_t nwalkers, const uint32_t* s
     const WalkTune saved = g->tune;
     const uint32_t lanes_c[3] = {1, 4, 32};
     const uint32_t wpb_c[3] = {4, 8, 16};
+    const uint32_t occ_c[2] = {0, 1};
     float best = 1e30f;
     WalkTune bestt = saved;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     for (uint32_t li = 0; li < 3; li++) {
-        for (uint32_t wi = 0; wi < 3; wi++) {
+        for (uint32_t wi = 0; wi < 6; wi++) {
+            if (occ_c[wi / 3] && wpb_c[wi % 3] > 8) continue;
             g->tune.lanes = lanes_c[li];
-            g->tune.warps_per_block = wpb_c[wi];
+            g->tune.warps_per_block = wpb_c[wi % 3];
+            g->tune.occ = occ_c[wi / 3];
             g->tune.blocks_per_sm = 0;
             float tsum = 0;
             bool ok = true;

@@ -58,6 +58,7 @@ struct WalkTune {
     uint32_t lanes = 1;         // lanes per walker: 1, 4, 32
     uint32_t warps_per_block = 8;
     uint32_t blocks_per_sm = 0; // 0 = occupancy maximum
+    uint32_t occ = 0;           // register budget variant: 0 = 64 registers, 1 = 40 registers
 };
 
 }  // namespace bingo
@@ -71,9 +72,7 @@ struct bingo_graph {
     uint64_t next_eid = 0;
     bingo::DevGraph G{};
     // owned device allocations
-    void* d_hdr = nullptr;
-    void* d_cnt = nullptr;
-    void* d_gref = nullptr;
+    void* d_hdr = nullptr;      // VRec[n]
     void* d_pool = nullptr;
     void* d_ctl = nullptr;      // control words: top, npending, leaked, status, queue, counters
     void* d_fcount = nullptr;

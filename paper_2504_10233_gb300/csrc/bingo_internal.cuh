@@ -1,17 +1,20 @@
 // Internal device structures and primitives of the radix-factorised sampler.
 //
-// Device state of a graph (all in HBM, indexed by vertex v):
-//   hdr[v]      VHdr, one 32-byte sector: adjacency block, degree d, nonempty-group mask,
-//               sparse-list block, |S|, log2 capacities.
-//   cnt[v][32]  |G_k| for k < 32, one 128-byte line per vertex (Eq. wpk: W(p_k) = 2^k |G_k|).
-//   gref[v][32] per-group reference: one-element -> slot of its member; regular/sparse ->
-//               word offset of the group block; dense/empty -> 0.
-//   pool        u32 words holding every variable-size block, in power-of-two sizes:
-//                 adjacency   4*capA words: capA x {dst, bias} (8 B, AoS) then capA x u64 edge id
-//                 regular k   2*capA words: member slots [capA] then inverted index [capA] (by slot)
-//                 sparse list 2*capA words: S = slots of edges in any sparse group [capA], then
-//                             S_inv [capA] (by slot)
-//                 sparse k    2*capS words: member positions in S [capS] then inverted index [capS]
+// Device state of a graph (all in HBM):
+//   vr[v]   VRec, 288 bytes (nine 32-byte sectors), one per vertex:
+//             bytes   0..15  header {adjacency block, degree d, nonempty-group mask, sparse-list block}
+//             bytes  16..271 32 x {|G_k|, ref} (Eq. wpk: W(p_k) = 2^k |G_k|); ref = slot of the member of a
+//                            one-element group, or the group block of a regular/sparse group, else 0
+//             bytes 272..287 update-only fields (|S|, log2 capacities)
+//           so the header, the mask and groups 0-1 share the first sector and a group's count and
+//           reference share a sector.
+//   pool    u32 words holding every variable-size block, in power-of-two sizes (offsets stored in
+//           32-byte units):
+//             adjacency   4*capA words: capA x {dst, bias} (8 B, AoS) then capA x u64 edge id
+//             regular k   2*capA words: member slots [capA] then inverted index [capA] (by slot)
+//             sparse list 2*capA words: S = slots of edges in any sparse group [capA], then
+//                         S_inv [capA] (by slot)
+//             sparse k    2*capS words: member positions in S [capS] then inverted index [capS]
 // A group's kind is never stored: it is the pure function of (|G_k|, d) given by Eq. group.
 #pragma once
 
@@ -25,7 +28,6 @@ namespace bingo {
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr uint32_t NONE32 = 0xFFFFFFFFu;
 constexpr uint64_t DEAD_BIT = 1ull << 63;      // set in an adjacency edge id while its slot is being deleted
-constexpr uint64_t GOFF_MASK = (1ull << 56) - 1;
 constexpr uint32_t MIN_CAPA = 4;               // smallest adjacency capacity of a vertex with edges
 constexpr uint32_t MIN_CAPS = 4;
 constexpr int NCLASS = 48;                     // pool size classes: block of 8 << c words
@@ -41,7 +43,8 @@ enum : uint32_t {
     ST_STATE = 8u,
 };
 
-struct __align__(32) VHdr {
+// Decoded vertex header (offsets in pool words); the stored form is VRec.
+struct VHdr {
     uint64_t adj;   // word offset of the adjacency block (0 = none)
     uint32_t deg;   // live edges d
     uint32_t mask;  // bit k set iff |G_k| > 0
@@ -51,7 +54,24 @@ struct __align__(32) VHdr {
     uint8_t lcaps;  // log2(capS) + 1, 0 = no sparse groups
     uint16_t pad;
 };
-static_assert(sizeof(VHdr) == 32, "VHdr must be one sector");
+
+struct __align__(32) VRec {
+    uint32_t adj;   // adjacency block, 32-byte units
+    uint32_t deg;
+    uint32_t mask;
+    uint32_t sref;  // sparse-list block, 32-byte units
+    uint2 g[32];    // {|G_k|, ref}
+    uint32_t nsp;
+    uint8_t lcapa, lcaps;
+    uint16_t pad;
+    uint32_t spare0, spare1;
+};
+static_assert(sizeof(VRec) == 288, "VRec must be nine sectors");
+
+constexpr uint64_t POOL_UNIT_WORDS = 8;  // offsets are stored in 32-byte units
+constexpr uint64_t MAX_POOL_WORDS = (1ull << 32) * POOL_UNIT_WORDS;
+__host__ __device__ __forceinline__ uint64_t words_of(uint64_t ref) { return ref * POOL_UNIT_WORDS; }
+__host__ __device__ __forceinline__ uint32_t ref_of(uint64_t words) { return (uint32_t)(words / POOL_UNIT_WORDS); }
 
 __host__ __device__ __forceinline__ uint32_t capa_of(const VHdr& h) { return h.lcapa ? (1u << (h.lcapa - 1)) : 0u; }
 __host__ __device__ __forceinline__ uint32_t caps_of(const VHdr& h) { return h.lcaps ? (1u << (h.lcaps - 1)) : 0u; }
@@ -145,9 +165,7 @@ struct DevGraph {
     uint32_t n;
     uint32_t max_bits;
     uint32_t alpha, beta;
-    VHdr* hdr;
-    uint32_t* cnt;
-    uint64_t* gref;
+    VRec* vr;
     Pool pool;
     // edge index (node2vec distance probe): open addressing over (src << 32 | dst) -> live copies
     unsigned long long* eh_key;  // EH_EMPTY = empty
@@ -157,6 +175,33 @@ struct DevGraph {
 constexpr unsigned long long EH_EMPTY = 0xFFFFFFFFFFFFFFFFull;
 
 #ifdef __CUDACC__
+__device__ __forceinline__ VHdr load_hdr(const DevGraph& G, uint64_t v) {
+    const VRec& r = G.vr[v];
+    VHdr h;
+    h.adj = words_of(r.adj);
+    h.deg = r.deg;
+    h.mask = r.mask;
+    h.sref = words_of(r.sref);
+    h.nsp = r.nsp;
+    h.lcapa = r.lcapa;
+    h.lcaps = r.lcaps;
+    h.pad = 0;
+    return h;
+}
+__device__ __forceinline__ void store_hdr(const DevGraph& G, uint64_t v, const VHdr& h) {
+    VRec& r = G.vr[v];
+    r.adj = ref_of(h.adj);
+    r.deg = h.deg;
+    r.mask = h.mask;
+    r.sref = ref_of(h.sref);
+    r.nsp = h.nsp;
+    r.lcapa = h.lcapa;
+    r.lcaps = h.lcaps;
+    r.pad = 0;
+}
+__device__ __forceinline__ uint32_t& cnt_ref(const DevGraph& G, uint64_t v, uint32_t k) { return G.vr[v].g[k].x; }
+__device__ __forceinline__ uint32_t& gref_ref(const DevGraph& G, uint64_t v, uint32_t k) { return G.vr[v].g[k].y; }
+
 __device__ __forceinline__ uint2* adj_pairs(const DevGraph& G, uint64_t adj) { return reinterpret_cast<uint2*>(G.pool.base + adj); }
 __device__ __forceinline__ uint64_t* adj_eids(const DevGraph& G, uint64_t adj, uint32_t capa) {
     return reinterpret_cast<uint64_t*>(G.pool.base + adj + 2ull * capa);
@@ -268,6 +313,8 @@ __device__ __forceinline__ uint64_t below64(StepRng& R, uint64_t range, uint32_t
 // A team is the set of threads that cooperates on one vertex: a warp or a block.
 // Every member must reach every team call (loops run a team-uniform trip count).
 
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -305,6 +352,11 @@ struct WarpTeam {
         return x;
     }
     __device__ __forceinline__ bool any(bool p) const { return __any_sync(FULL, p); }
+    __device__ __forceinline__ uint32_t or_all(uint32_t x) const {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) x |= __shfl_xor_sync(FULL, x, d);
+        return x;
+    }
 };
 
 // Block team; needs `sm` = shared scratch of at least 40 words, private to the team.
@@ -363,6 +415,17 @@ struct BlockTeam {
         return r;
     }
     __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
+    __device__ __forceinline__ uint32_t or_all(uint32_t x) const {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) x |= __shfl_xor_sync(FULL, x, d);
+        if (threadIdx.x == 0) sm[33] = 0;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) atomicOr(&sm[33], x);
+        __syncthreads();
+        const uint32_t r = sm[33];
+        __syncthreads();
+        return r;
+    }
 };
 #endif  // __CUDACC__
 

@@ -58,7 +58,8 @@ __global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const
                 if (lane == (uint32_t)k) c += __popc(bb);
             }
         }
-        G.cnt[v * 32 + lane] = c;
+        cnt_ref(G, v, lane) = c;
+        gref_ref(G, v, lane) = 0;
         const uint32_t kd = kind_of(c, d, G.alpha, G.beta);
         const uint32_t mask = __ballot_sync(FULL, c > 0);
         const uint32_t regm = __ballot_sync(FULL, kd == K_REGULAR);
@@ -73,8 +74,8 @@ __global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const
         if (lane == 0) {
             const uint32_t capa = capa_for(d);
             const uint32_t caps = spm ? caps_for(nsp) : 0;
-            uint64_t wd = (uint64_t)4 * capa + (uint64_t)__popc(regm) * 2 * capa;
-            if (spm) wd += 2ull * capa + (uint64_t)__popc(spm) * 2 * caps;
+            uint64_t wd = (uint64_t)4 * capa + (uint64_t)__popc(regm) * 4 * capa;
+            if (spm) wd += 2ull * capa + (uint64_t)__popc(spm) * 4 * caps;
             words[v] = wd;
             VHdr h;
             h.adj = 0;
@@ -85,7 +86,7 @@ __global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const
             h.lcapa = capa ? (uint8_t)(log2_u32(capa) + 1) : 0;
             h.lcaps = caps ? (uint8_t)(log2_u32(caps) + 1) : 0;
             h.pad = 0;
-            G.hdr[v] = h;
+            store_hdr(G, v, h);
         }
     }
 }
@@ -98,16 +99,16 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     WarpTeam t;
     for (uint64_t v = warp; v < G.n; v += nwarps) {
-        VHdr h = G.hdr[v];
+        VHdr h = load_hdr(G, v);
         const uint32_t d = h.deg, capa = capa_of(h), caps = caps_of(h);
         const uint64_t a = rp[v];
         uint64_t next = base + offs[v];
-        const uint32_t c = G.cnt[v * 32 + lane];
+        const uint32_t c = cnt_ref(G, v, lane);
         const uint32_t kd = kind_of(c, d, G.alpha, G.beta);
         const uint32_t regm = __ballot_sync(FULL, kd == K_REGULAR);
         const uint32_t spm = __ballot_sync(FULL, kd == K_SPARSE);
         const uint32_t onem = __ballot_sync(FULL, kd == K_ONE);
-        uint64_t gref = 0;
+        uint32_t gref = 0;
         if (d) {
             h.adj = next;
             uint2* pairs = adj_pairs(G, h.adj);
@@ -122,8 +123,8 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
         for (uint32_t m = regm; m; m &= m - 1) {
             const uint32_t k = __ffs(m) - 1;
             build_regular(t, G, h.adj, d, k, next, capa);
-            if (lane == k) gref = next;
-            next += 2ull * capa;
+            if (lane == k) gref = ref_of(next);
+            next += 4ull * capa;
         }
         if (spm) {
             h.sref = next;
@@ -133,17 +134,18 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
             for (uint32_t m = spm; m; m &= m - 1) {
                 const uint32_t k = __ffs(m) - 1;
                 build_sparse(t, G, h.adj, h.sref, ns, k, next, caps);
-                if (lane == k) gref = next;
-                next += 2ull * caps;
+                if (lane == k) gref = ref_of(next);
+                next += 4ull * caps;
             }
         }
         for (uint32_t m = onem; m; m &= m - 1) {
             const uint32_t k = __ffs(m) - 1;
             const uint32_t s = find_one(t, G, h.adj, d, k);
-            if (lane == k) gref = s;
+            if (lane == k) gref = s < d ? adj_pairs(G, h.adj)[s].x : NONE32;  // the member's destination
         }
-        G.gref[v * 32 + lane] = gref;
-        if (lane == 0) G.hdr[v] = h;
+        gref_ref(G, v, lane) = gref;
+        __syncwarp();
+        if (lane == 0) store_hdr(G, v, h);
     }
 }
 
@@ -155,8 +157,8 @@ __global__ void k_export_sizes(DevGraph G, uint64_t* __restrict__ deg64, uint64_
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t v = warp; v < G.n; v += nwarps) {
-        const VHdr h = G.hdr[v];
-        const uint32_t c = G.cnt[v * 32 + lane];
+        const VHdr h = load_hdr(G, v);
+        const uint32_t c = cnt_ref(G, v, lane);
         const uint32_t kd = kind_of(c, h.deg, G.alpha, G.beta);
         glen64[v * 32 + lane] = is_list(kd) ? c : 0;
         if (lane == 0) {
@@ -169,13 +171,15 @@ __global__ void k_export_sizes(DevGraph G, uint64_t* __restrict__ deg64, uint64_
 __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, const uint64_t* __restrict__ goff,
                               const uint64_t* __restrict__ soff, uint32_t* __restrict__ odst,
                               uint32_t* __restrict__ obias, uint64_t* __restrict__ oeid, uint8_t* __restrict__ okind,
-                              uint32_t* __restrict__ oone, uint32_t* __restrict__ omem, uint32_t* __restrict__ ominv,
-                              uint32_t* __restrict__ osp, uint32_t* __restrict__ ospinv) {
+                              uint32_t* __restrict__ oone, uint32_t* __restrict__ ocnt, uint32_t* __restrict__ omem,
+                              uint32_t* __restrict__ ominv,
+                              uint32_t* __restrict__ osp, uint32_t* __restrict__ ospinv,
+                              unsigned long long* __restrict__ bad) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t v = warp; v < G.n; v += nwarps) {
-        const VHdr h = G.hdr[v];
+        const VHdr h = load_hdr(G, v);
         const uint32_t d = h.deg, capa = capa_of(h), caps = caps_of(h);
         if (d) {
             const uint2* pairs = adj_pairs(G, h.adj);
@@ -187,25 +191,40 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
                 oeid[eoff[v] + j] = eids[j];
             }
         }
-        const uint32_t c = G.cnt[v * 32 + lane];
+        const uint32_t c = cnt_ref(G, v, lane);
         const uint32_t kd = kind_of(c, d, G.alpha, G.beta);
-        const uint64_t gr = G.gref[v * 32 + lane];
+        const uint32_t gr = gref_ref(G, v, lane);
         okind[v * 32 + lane] = (uint8_t)kd;
-        oone[v * 32 + lane] = kd == K_ONE ? (uint32_t)gr : NONE32;
+        ocnt[v * 32 + lane] = c;
+        uint32_t one_slot = NONE32;
+        if (kd == K_ONE) {  // the stored reference is the destination; locate the member's slot
+            const uint2* pairs = adj_pairs(G, h.adj);
+            for (uint32_t j = 0; j < d; j++)
+                if ((pairs[j].y >> lane) & 1u) { one_slot = j; break; }
+            if (one_slot == NONE32 || pairs[one_slot].x != gr) atomicAdd(bad, 1ull);
+        }
+        oone[v * 32 + lane] = one_slot;
         const uint32_t listm = __ballot_sync(FULL, is_list(kd));
         for (uint32_t m = listm; m; m &= m - 1) {
             const uint32_t k = __ffs(m) - 1;
-            const uint64_t g = __shfl_sync(FULL, gr, k) & GOFF_MASK;
+            const uint64_t g = words_of(__shfl_sync(FULL, gr, k));
             const uint32_t ck = __shfl_sync(FULL, c, k);
             const uint32_t kk = __shfl_sync(FULL, kd, k);
             const uint32_t icap = kk == K_REGULAR ? capa : caps;
-            const uint32_t* mem = G.pool.base + g;
+            const uint32_t* mdst = G.pool.base + g;
+            const uint32_t* mem = mdst + icap;
             const uint32_t* inv = mem + icap;
             const uint64_t o = goff[v * 32 + k];
+            const uint2* pairs = adj_pairs(G, h.adj);
+            const uint32_t* S = h.sref ? G.pool.base + h.sref : nullptr;
             for (uint32_t i = lane; i < ck; i += 32) {
                 const uint32_t x = mem[i];
                 omem[o + i] = x;
                 ominv[o + i] = x < icap ? inv[x] : NONE32;
+                // the stored destination must be the member's edge destination
+                uint32_t slot = x;
+                if (kk == K_SPARSE) slot = (S && x < h.nsp) ? S[x] : NONE32;
+                if (slot >= d || pairs[slot].x != mdst[i]) atomicAdd(bad, 1ull);
             }
         }
         if (h.sref) {
@@ -227,14 +246,14 @@ __global__ void k_memory(DevGraph G, unsigned long long* out) {
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long a = 0, r = 0, s = 0;
     for (uint64_t v = warp; v < G.n; v += nwarps) {
-        const VHdr h = G.hdr[v];
+        const VHdr h = load_hdr(G, v);
         const uint32_t capa = capa_of(h), caps = caps_of(h);
-        const uint32_t kd = kind_of(G.cnt[v * 32 + lane], h.deg, G.alpha, G.beta);
+        const uint32_t kd = kind_of(cnt_ref(G, v, lane), h.deg, G.alpha, G.beta);
         const uint32_t regm = __ballot_sync(FULL, kd == K_REGULAR), spm = __ballot_sync(FULL, kd == K_SPARSE);
         if (lane == 0) {
             a += 4ull * capa;
-            r += (unsigned long long)__popc(regm) * 2 * capa;
-            if (h.sref) s += 2ull * capa + (unsigned long long)__popc(spm) * 2 * caps;
+            r += (unsigned long long)__popc(regm) * 4 * capa;
+            if (h.sref) s += 2ull * capa + (unsigned long long)__popc(spm) * 4 * caps;
         }
     }
     if (lane == 0) {
@@ -256,7 +275,7 @@ static unsigned grid_for(const bingo_graph* g, uint64_t work_items, unsigned blo
 
 static void free_graph(bingo_graph* g) {
     if (!g) return;
-    void* ptrs[] = {g->d_hdr, g->d_cnt, g->d_gref, g->d_pool, g->d_ctl, g->d_fcount, g->d_fstack, g->d_pending, g->d_eh};
+    void* ptrs[] = {g->d_hdr, g->d_pool, g->d_ctl, g->d_fcount, g->d_fstack, g->d_pending, g->d_eh};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     Buf* bufs[] = {&g->s_in, &g->s_keys, &g->s_keys2, &g->s_vals, &g->s_vals2, &g->s_tmp, &g->s_seg,
@@ -341,17 +360,13 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
         release_stage();
         return fail(BINGO_E_INVALID);
     }
-    if (!cu(cudaMalloc(&g->d_hdr, sizeof(VHdr) * (size_t)n), "vertex headers") ||
-        !cu(cudaMalloc(&g->d_cnt, sizeof(uint32_t) * 32 * (size_t)n), "group counts") ||
-        !cu(cudaMalloc(&g->d_gref, sizeof(uint64_t) * 32 * (size_t)n), "group refs")) { release_stage(); return fail(st); }
+    if (!cu(cudaMalloc(&g->d_hdr, sizeof(VRec) * (size_t)n), "vertex records")) { release_stage(); return fail(st); }
     DevGraph& G = g->G;
     G.n = n;
     G.max_bits = c.max_bits;
     G.alpha = c.alpha_pct;
     G.beta = c.beta_pct;
-    G.hdr = (VHdr*)g->d_hdr;
-    G.cnt = (uint32_t*)g->d_cnt;
-    G.gref = (uint64_t*)g->d_gref;
+    G.vr = (VRec*)g->d_hdr;
     G.pool.status = status;
     G.pool.top = (unsigned long long*)(ctl + CTL_TOP);
     G.pool.npending = (unsigned long long*)(ctl + CTL_NPENDING);
@@ -381,6 +396,7 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
         if (pool_words > avail) pool_words = std::max<uint64_t>(need + (need >> 4), avail);
     }
     pool_words = (pool_words + 7) & ~7ull;
+    if (pool_words > MAX_POOL_WORDS) pool_words = MAX_POOL_WORDS;  // 32-bit offsets in 32-byte units
     if (pool_words < need) {
         set_error("pool too small: need %llu words, have %llu", (unsigned long long)need, (unsigned long long)pool_words);
         release_all();
@@ -415,6 +431,7 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
     g->tune.lanes = c.lanes_per_walker ? c.lanes_per_walker : 1;
     g->tune.warps_per_block = c.warps_per_block ? c.warps_per_block : 8;
     g->tune.blocks_per_sm = c.blocks_per_sm;
+    g->tune.occ = c.reg_variant ? 1 : 0;
     *out = g;
     return BINGO_OK;
 }
@@ -434,19 +451,21 @@ bingo_status bingo_get_config(bingo_graph* g, bingo_config* out) {
     out->lanes_per_walker = g->tune.lanes;
     out->warps_per_block = g->tune.warps_per_block;
     out->blocks_per_sm = g->tune.blocks_per_sm;
+    out->reg_variant = g->tune.occ;
     out->pool_words = g->G.pool.words;
     return BINGO_OK;
 }
 
-bingo_status bingo_set_walk_config(bingo_graph* g, uint32_t lanes, uint32_t wpb, uint32_t bps) {
+bingo_status bingo_set_walk_config(bingo_graph* g, uint32_t lanes, uint32_t wpb, uint32_t bps, uint32_t regv) {
     if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
-    if (!(lanes == 1 || lanes == 4 || lanes == 32) || wpb == 0 || wpb > 32) {
-        set_error("invalid walk config (lanes %u, warps/block %u)", lanes, wpb);
+    if (!(lanes == 1 || lanes == 4 || lanes == 32) || wpb == 0 || wpb > 32 || regv > 1 || (regv && wpb > 8)) {
+        set_error("invalid walk config (lanes %u, warps/block %u, register variant %u)", lanes, wpb, regv);
         return BINGO_E_INVALID;
     }
     g->tune.lanes = lanes;
     g->tune.warps_per_block = wpb;
     g->tune.blocks_per_sm = bps;
+    g->tune.occ = regv;
     return BINGO_OK;
 }
 
@@ -508,8 +527,9 @@ bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, ui
     if (st != BINGO_OK) { P.release_all(); return st; }
     const uint64_t n = g->n, m = t[0], L = t[1], S = t[2];
     Buf o;
-    // device staging: dst, bias (u32 m each), eid (u64 m), kind (u8 32n), one (u32 32n), mem/minv (L), sp/spinv (S)
-    const size_t bytes = 8 * m + 8 * m + 32 * n + 4 * 32 * n + 8 * L + 8 * S + 64;
+    // device staging: dst, bias (u32 m each), eid (u64 m), kind (u8 32n), one and cnt (u32 32n each), mem/minv (L),
+    // sp/spinv (S)
+    const size_t bytes = 8 * m + 8 * m + 32 * n + 8 * 32 * n + 8 * L + 8 * S + 128;
     cudaError_t e = ensure(o, bytes);
     if (e != cudaSuccess) { P.release_all(); return cuda_fail(e, "export staging"); }
     char* p = (char*)o.p;
@@ -517,15 +537,20 @@ bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, ui
     uint32_t* odst = (uint32_t*)p; p += 4 * m;
     uint32_t* obias = (uint32_t*)p; p += 4 * m;
     uint32_t* oone = (uint32_t*)p; p += 4 * 32 * n;
+    uint32_t* ocnt = (uint32_t*)p; p += 4 * 32 * n;
     uint32_t* omem = (uint32_t*)p; p += 4 * L;
     uint32_t* ominv = (uint32_t*)p; p += 4 * L;
     uint32_t* osp = (uint32_t*)p; p += 4 * S;
     uint32_t* ospinv = (uint32_t*)p; p += 4 * S;
-    uint8_t* okind = (uint8_t*)p;
+    uint8_t* okind = (uint8_t*)p; p += 32 * n;
+    unsigned long long* obad = (unsigned long long*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    cudaMemset(obad, 0, 8);
     k_export_fill<<<grid_for(g, n * 32, 256), 256>>>(g->G, (uint64_t*)P.eoff.p, (uint64_t*)P.goff.p,
-                                                     (uint64_t*)P.soff.p, odst, obias, oeid, okind, oone, omem, ominv,
-                                                     osp, ospinv);
+                                                     (uint64_t*)P.soff.p, odst, obias, oeid, okind, oone, ocnt, omem,
+                                                     ominv, osp, ospinv, obad);
     e = cudaDeviceSynchronize();
+    unsigned long long nbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&nbad, obad, 8, cudaMemcpyDeviceToHost);
     std::vector<uint64_t> tmp;
     auto d2h32 = [&](uint32_t* dsth, const void* src, uint64_t cnt64) -> cudaError_t {
         if (!dsth || cnt64 == 0) return cudaSuccess;
@@ -549,7 +574,7 @@ bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, ui
     if (e == cudaSuccess) e = d2h32(dst, odst, m);
     if (e == cudaSuccess) e = d2h32(bias, obias, m);
     if (e == cudaSuccess && eid && m) e = cudaMemcpy(eid, oeid, 8 * m, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = d2h32(cnt, g->G.cnt, 32 * n);
+    if (e == cudaSuccess) e = d2h32(cnt, ocnt, 32 * n);
     if (e == cudaSuccess && kind) e = cudaMemcpy(kind, okind, 32 * n, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = d2h32(one_slot, oone, 32 * n);
     if (e == cudaSuccess) e = d2h32(members, omem, L);
@@ -559,6 +584,10 @@ bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, ui
     release(o);
     P.release_all();
     if (e != cudaSuccess) return cuda_fail(e, "export copy");
+    if (nbad) {
+        set_error("export: %llu stored member destinations disagree with the adjacency", nbad);
+        return BINGO_E_STATE;
+    }
     return BINGO_OK;
 }
 
@@ -573,7 +602,7 @@ bingo_status bingo_memory_report(bingo_graph* g, uint64_t out[6]) {
     release(b);
     if (e != cudaSuccess) return cuda_fail(e, "memory report");
     out[0] = 4ull * w[0];
-    out[1] = (uint64_t)g->n * (sizeof(VHdr) + 128 + 256);
+    out[1] = (uint64_t)g->n * sizeof(VRec);
     out[2] = 4ull * w[1];
     out[3] = 4ull * w[2];
     out[4] = g->G.eh_mask ? (g->G.eh_mask + 1) * 12 : 0;

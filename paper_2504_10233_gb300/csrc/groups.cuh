@@ -8,12 +8,16 @@
 
 namespace bingo {
 
+// Group blocks hold [member destinations | member list | inverted index | spare], cap words each:
+// a walker reads a uniform member's destination with one access at the block's start.
+
 // Regular group k: member list of slots with bit k set, inverted index by slot.
 template <class Team>
 __device__ void build_regular(const Team& t, const DevGraph& G, uint64_t adj, uint32_t d, uint32_t k, uint64_t goff,
                               uint32_t capa) {
     const uint2* pairs = adj_pairs(G, adj);
-    uint32_t* mem = G.pool.base + goff;
+    uint32_t* mdst = G.pool.base + goff;
+    uint32_t* mem = mdst + capa;
     uint32_t* inv = mem + capa;
     uint32_t pos = 0;
     for (uint32_t b = 0; b < d; b += t.size()) {
@@ -24,6 +28,7 @@ __device__ void build_regular(const Team& t, const DevGraph& G, uint64_t adj, ui
         if (p) {
             mem[pos + r] = j;
             inv[j] = pos + r;
+            mdst[pos + r] = pairs[j].x;
         }
         pos += tot;
     }
@@ -57,17 +62,20 @@ __device__ void build_sparse(const Team& t, const DevGraph& G, uint64_t adj, uin
                              uint64_t goff, uint32_t caps) {
     const uint2* pairs = adj_pairs(G, adj);
     const uint32_t* S = G.pool.base + sref;
-    uint32_t* mem = G.pool.base + goff;
+    uint32_t* mdst = G.pool.base + goff;
+    uint32_t* mem = mdst + caps;
     uint32_t* inv = mem + caps;
     uint32_t pos = 0;
     for (uint32_t b = 0; b < nsp; b += t.size()) {
         const uint32_t i = b + t.rank();
-        const bool p = i < nsp && ((pairs[S[i]].y >> k) & 1u);
+        const uint2 e = i < nsp ? pairs[S[i]] : make_uint2(0, 0);
+        const bool p = i < nsp && ((e.y >> k) & 1u);
         uint32_t tot;
         const uint32_t r = t.scan_pred(p, tot);
         if (p) {
             mem[pos + r] = i;
             inv[i] = pos + r;
+            mdst[pos + r] = e.x;
         }
         pos += tot;
     }

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "bingo_host.h"
@@ -74,7 +75,43 @@ struct SegSh {
     uint32_t nsp_del, nsp_add;
     uint32_t rounds;
     uint32_t found;
+    uint32_t kmask[8];
 };
+
+// Kind masks of the 32 groups from (cnt[k], d): lane k of the first warp evaluates Eq. group for
+// group k and ballots form the masks (published through shared memory for block teams).
+struct KindMasks {
+    uint32_t sp, reg, one, nonempty;
+};
+template <class Team>
+__device__ __forceinline__ KindMasks kind_masks(const Team& t, SegSh& sh, const uint32_t* cnt, uint32_t d,
+                                                const DevGraph& G, int slot) {
+    KindMasks km;
+    constexpr bool warp_team = std::is_same<Team, WarpTeam>::value;
+    if (warp_team || threadIdx.x < 32) {
+        const uint32_t lane = threadIdx.x & 31;
+        const uint32_t c = cnt[lane];
+        const uint32_t kd = kind_of(c, d, G.alpha, G.beta);
+        km.sp = __ballot_sync(FULL, kd == K_SPARSE);
+        km.reg = __ballot_sync(FULL, kd == K_REGULAR);
+        km.one = __ballot_sync(FULL, kd == K_ONE);
+        km.nonempty = __ballot_sync(FULL, c > 0);
+    }
+    if constexpr (!warp_team) {
+        if (threadIdx.x == 0) {
+            sh.kmask[4 * slot + 0] = km.sp;
+            sh.kmask[4 * slot + 1] = km.reg;
+            sh.kmask[4 * slot + 2] = km.one;
+            sh.kmask[4 * slot + 3] = km.nonempty;
+        }
+        t.sync();
+        km.sp = sh.kmask[4 * slot + 0];
+        km.reg = sh.kmask[4 * slot + 1];
+        km.one = sh.kmask[4 * slot + 2];
+        km.nonempty = sh.kmask[4 * slot + 3];
+    }
+    return km;
+}
 
 // equal range of x among the segment's (sorted) deletion destinations
 template <class Src>
@@ -98,9 +135,10 @@ __device__ __forceinline__ void del_range(const Src& B, uint32_t nd, uint32_t x,
 // cand(i), i < ncand, yields a position to delete or NONE32.  Phase 1 marks the N deleted
 // positions; the N tail positions [c-N, c) then hold gamma deleted entries and N-gamma survivors,
 // and phase 2 moves the survivors (ascending) into the N-gamma holes below c-N (in candidate
-// order).  move(value, from, to) patches the inverted index of each moved entry.
+// order), with their entries of the parallel array M (nullable).  move(value, from, to) patches the
+// inverted index of each moved entry.
 template <class Team, class Cand, class Move>
-__device__ uint32_t dswap(const Team& t, uint32_t* L, uint32_t c, uint32_t ncand, Cand cand, Move move,
+__device__ uint32_t dswap(const Team& t, uint32_t* L, uint32_t* M, uint32_t c, uint32_t ncand, Cand cand, Move move,
                           uint32_t* holes, uint32_t* surv, uint32_t* status) {
     uint32_t nrem = 0;
     for (uint32_t b = 0; b < ncand; b += t.size()) {
@@ -146,6 +184,7 @@ __device__ uint32_t dswap(const Team& t, uint32_t* L, uint32_t c, uint32_t ncand
             } else {
                 const uint32_t val = L[s];
                 L[h] = val;
+                if (M) M[h] = M[s];  // the member's destination travels with it
                 move(val, s, h);
             }
         }
@@ -167,12 +206,13 @@ template <class Team, class Src>
 __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint32_t v, uint32_t ni, uint32_t nd,
                               const Src& B, const SegScratch& X, unsigned long long* stats) {
     const uint32_t rank = t.rank(), T = t.size();
-    const VHdr h0 = G.hdr[v];
+    const VHdr h0 = load_hdr(G, v);
     const uint32_t d0 = h0.deg, capa0 = capa_of(h0), caps0 = caps_of(h0);
     const uint32_t dtot = d0 + ni;
     for (uint32_t k = rank; k < 32; k += T) {
-        sh.cnt_old[k] = G.cnt[(uint64_t)v * 32 + k];
-        sh.gref_old[k] = G.gref[(uint64_t)v * 32 + k];
+        const uint2 gk = G.vr[v].g[k];
+        sh.cnt_old[k] = gk.x;
+        sh.gref_old[k] = gk.y;
         sh.gref_new[k] = sh.gref_old[k];
         sh.delta[k] = 0;
         sh.removed[k] = 0;
@@ -186,13 +226,8 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     }
     t.sync();
     // old kinds
-    uint32_t SPo = 0, REGo = 0, ONEo = 0;
-    for (int k = 0; k < 32; k++) {
-        const uint32_t kd = kind_of(sh.cnt_old[k], d0, G.alpha, G.beta);
-        SPo |= (kd == K_SPARSE) << k;
-        REGo |= (kd == K_REGULAR) << k;
-        ONEo |= (kd == K_ONE) << k;
-    }
+    const KindMasks kmo = kind_masks(t, sh, sh.cnt_old, d0, G, 0);
+    const uint32_t SPo = kmo.sp, REGo = kmo.reg, ONEo = kmo.one;
 
     // ---- S1: adjacency capacity for the insertions
     uint32_t capa1 = capa0;
@@ -299,16 +334,10 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     t.sync();
     for (uint32_t k = rank; k < 32; k += T) sh.cnt_new[k] = (uint32_t)((int32_t)sh.cnt_old[k] + sh.delta[k]);
     t.sync();
-    uint32_t SPn = 0, REGn = 0, ONEn = 0, maskn = 0, deadbits = 0;
-    for (int k = 0; k < 32; k++) {
-        const uint32_t kd = kind_of(sh.cnt_new[k], d1, G.alpha, G.beta);
-        SPn |= (kd == K_SPARSE) << k;
-        REGn |= (kd == K_REGULAR) << k;
-        ONEn |= (kd == K_ONE) << k;
-        maskn |= (sh.cnt_new[k] > 0) << k;
-        deadbits |= (sh.removed[k] > 0) << k;
-    }
-    (void)deadbits_local;
+    const KindMasks kmn = kind_masks(t, sh, sh.cnt_new, d1, G, 1);
+    const uint32_t SPn = kmn.sp, REGn = kmn.reg, ONEn = kmn.one, maskn = kmn.nonempty;
+    // bits of the deleted pre-existing edges (the groups that lose members)
+    const uint32_t deadbits = t.or_all(deadbits_local);
     const uint32_t REGk = full ? 0u : (REGo & REGn);              // regular groups updated in place
     const uint32_t ONEk = full ? 0u : (ONEo & ONEn & ~deadbits);   // one-element groups whose member survives
     bool keepS = !full && SPo == SPn && SPn != 0 && h0.sref != 0;
@@ -332,11 +361,12 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     // ---- S6: remove deleted members from regular groups kept in place
     for (uint32_t m = REGk & deadbits; m; m &= m - 1) {
         const uint32_t k = __ffs(m) - 1;
-        uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+        uint32_t* M = G.pool.base + words_of(sh.gref_old[k]);
+        uint32_t* L = M + capa0;
         uint32_t* inv = L + capa0;
         const uint32_t icap_guard = capa0;
         dswap(
-            t, L, sh.cnt_old[k], nd,
+            t, L, M, sh.cnt_old[k], nd,
             [&](uint32_t j) -> uint32_t {
                 const uint32_t s = X.del_slot[j];
                 return (s != NONE32 && s < d0 && ((pairs[s].y >> k) & 1u)) ? inv[s] : NONE32;
@@ -350,11 +380,12 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
         uint32_t* Sinv = S + capa0;
         for (uint32_t m = SPn & deadbits; m; m &= m - 1) {
             const uint32_t k = __ffs(m) - 1;
-            uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+            uint32_t* M = G.pool.base + words_of(sh.gref_old[k]);
+            uint32_t* L = M + caps0;
             uint32_t* inv = L + caps0;
             const uint32_t icap_guard = caps0;
             dswap(
-                t, L, sh.cnt_old[k], nd,
+                t, L, M, sh.cnt_old[k], nd,
                 [&](uint32_t j) -> uint32_t {
                     const uint32_t s = X.del_slot[j];
                     if (!(s != NONE32 && s < d0 && ((pairs[s].y >> k) & 1u))) return NONE32;
@@ -364,7 +395,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
                 [&](uint32_t val, uint32_t, uint32_t to) { if (val < icap_guard) inv[val] = to; }, X.holes, X.surv, G.pool.status);
         }
         nsp_after_del = dswap(
-            t, S, h0.nsp, nd,
+            t, S, nullptr, h0.nsp, nd,
             [&](uint32_t j) -> uint32_t {
                 const uint32_t s = X.del_slot[j];
                 return (s != NONE32 && s < d0 && (pairs[s].y & SPo)) ? Sinv[s] : NONE32;
@@ -375,7 +406,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
                 const uint32_t w = pairs[e].y & SPn;
                 for (uint32_t b = w; b; b &= b - 1) {
                     const uint32_t k = __ffs(b) - 1;
-                    uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+                    uint32_t* L = G.pool.base + words_of(sh.gref_old[k]) + caps0;
                     uint32_t* inv = L + caps0;
                     const uint32_t mpos = inv[from];
                     if (mpos < caps0) {
@@ -424,7 +455,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
                 if (p < d0) {
                     for (uint32_t bb = e.y & REGk; bb; bb &= bb - 1) {
                         const uint32_t k = __ffs(bb) - 1;
-                        uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+                        uint32_t* L = G.pool.base + words_of(sh.gref_old[k]) + capa0;
                         uint32_t* inv = L + capa0;
                         const uint32_t mpos = inv[p];
                         if (mpos < capa0) {
@@ -443,7 +474,6 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
                             atomicOr(G.pool.status, ST_STATE);
                         }
                     }
-                    for (uint32_t bb = e.y & ONEk; bb; bb &= bb - 1) sh.gref_new[__ffs(bb) - 1] = q;
                 } else {
                     X.ins_final[p - d0] = q;
                 }
@@ -455,7 +485,8 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     // ---- S9: append surviving new edges to the groups kept in place
     for (uint32_t m = REGk & REGn; m; m &= m - 1) {
         const uint32_t k = __ffs(m) - 1;
-        uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+        uint32_t* M = G.pool.base + words_of(sh.gref_old[k]);
+        uint32_t* L = M + capa0;
         uint32_t* inv = L + capa0;
         uint32_t pos = sh.cnt_old[k] - sh.removed[k];
         for (uint32_t b = 0; b < ni; b += T) {
@@ -467,6 +498,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
             if (pred) {
                 L[pos + r] = s;
                 inv[s] = pos + r;
+                M[pos + r] = pairs[s].x;
             }
             pos += tot;
         }
@@ -490,7 +522,8 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
         t.sync();
         for (uint32_t m = SPn; m; m &= m - 1) {
             const uint32_t k = __ffs(m) - 1;
-            uint32_t* L = G.pool.base + (sh.gref_old[k] & GOFF_MASK);
+            uint32_t* M = G.pool.base + words_of(sh.gref_old[k]);
+            uint32_t* L = M + caps0;
             uint32_t* inv = L + caps0;
             uint32_t gpos = sh.cnt_old[k] - sh.removed[k];
             for (uint32_t b = 0; b < ni; b += T) {
@@ -503,6 +536,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
                     const uint32_t sp = Sinv[s];
                     L[gpos + r] = sp;
                     inv[sp] = gpos + r;
+                    M[gpos + r] = pairs[s].x;
                 }
                 gpos += tot;
             }
@@ -514,10 +548,10 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     uint32_t rebuilt = 0;
     // free blocks that are not kept
     if (rank == 0) {
-        for (uint32_t m = REGo & ~REGk; m; m &= m - 1) pool_free(G.pool, sh.gref_old[__ffs(m) - 1] & GOFF_MASK, 2ull * capa0);
+        for (uint32_t m = REGo & ~REGk; m; m &= m - 1) pool_free(G.pool, words_of(sh.gref_old[__ffs(m) - 1]), 4ull * capa0);
         if (!keepS && h0.sref) {
             pool_free(G.pool, h0.sref, 2ull * capa0);
-            for (uint32_t m = SPo; m; m &= m - 1) pool_free(G.pool, sh.gref_old[__ffs(m) - 1] & GOFF_MASK, 2ull * caps0);
+            for (uint32_t m = SPo; m; m &= m - 1) pool_free(G.pool, words_of(sh.gref_old[__ffs(m) - 1]), 4ull * caps0);
         }
     }
     for (int k = rank; k < 32; k += T) {
@@ -527,11 +561,11 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     t.sync();
     for (uint32_t m = REGn & ~REGk; m; m &= m - 1) {
         const uint32_t k = __ffs(m) - 1;
-        if (rank == 0) sh.alloc_off = pool_alloc(G.pool, 2ull * capa1);
+        if (rank == 0) sh.alloc_off = pool_alloc(G.pool, 4ull * capa1);
         t.sync();
         const uint64_t off = sh.alloc_off;
         if (off) build_regular(t, G, adj, d1, k, off, capa1);
-        if (rank == 0) sh.gref_new[k] = off;
+        if (rank == 0) sh.gref_new[k] = ref_of(off);
         rebuilt++;
         t.sync();
     }
@@ -548,11 +582,11 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
             caps1 = caps_for(nsp1);
             for (uint32_t m = SPn; m; m &= m - 1) {
                 const uint32_t k = __ffs(m) - 1;
-                if (rank == 0) sh.alloc_off = pool_alloc(G.pool, 2ull * caps1);
+                if (rank == 0) sh.alloc_off = pool_alloc(G.pool, 4ull * caps1);
                 t.sync();
                 const uint64_t off = sh.alloc_off;
                 if (off) build_sparse(t, G, adj, sref1, nsp1, k, off, caps1);
-                if (rank == 0) sh.gref_new[k] = off;
+                if (rank == 0) sh.gref_new[k] = ref_of(off);
                 rebuilt++;
                 t.sync();
             }
@@ -561,15 +595,14 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     for (uint32_t m = ONEn & ~ONEk; m; m &= m - 1) {
         const uint32_t k = __ffs(m) - 1;
         const uint32_t s = find_one(t, G, adj, d1, k);
-        if (rank == 0) sh.gref_new[k] = s;
+        if (rank == 0) sh.gref_new[k] = s < d1 ? pairs[s].x : NONE32;  // one-element: the member's destination
         rebuilt++;
     }
     t.sync();
 
     // ---- S11: write back
     for (uint32_t k = rank; k < 32; k += T) {
-        G.cnt[(uint64_t)v * 32 + k] = sh.cnt_new[k];
-        G.gref[(uint64_t)v * 32 + k] = sh.gref_new[k];
+        G.vr[v].g[k] = make_uint2(sh.cnt_new[k], (uint32_t)sh.gref_new[k]);
     }
     if (rank == 0) {
         VHdr h;
@@ -581,18 +614,18 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
         h.lcapa = capa1 ? (uint8_t)(log2_u32(capa1) + 1) : 0;
         h.lcaps = SPn ? (uint8_t)(log2_u32(caps1) + 1) : 0;
         h.pad = 0;
-        G.hdr[v] = h;
+        store_hdr(G, v, h);
         // ---- S12: stats
         atomicAdd(stats + S_INS, (unsigned long long)ni);
         atomicAdd(stats + S_DEL, (unsigned long long)found);
         atomicAdd(stats + S_NF, (unsigned long long)(nd - found));
         atomicAdd(stats + S_TOUCH, 1ull);
         if (rebuilt) atomicAdd(stats + S_REBUILT, (unsigned long long)rebuilt);
-        for (int k = 0; k < 32; k++) {
-            const uint32_t ko = kind_of(sh.cnt_old[k], d0, G.alpha, G.beta);
-            const uint32_t kn = kind_of(sh.cnt_new[k], d1, G.alpha, G.beta);
-            if (ko != kn) atomicAdd(stats + S_CONV + ko * 5 + kn, 1ull);
-        }
+    }
+    for (uint32_t k = rank; k < 32; k += T) {
+        const uint32_t ko = kind_of(sh.cnt_old[k], d0, G.alpha, G.beta);
+        const uint32_t kn = kind_of(sh.cnt_new[k], d1, G.alpha, G.beta);
+        if (ko != kn) atomicAdd(stats + S_CONV + ko * 5 + kn, 1ull);
     }
     t.sync();
 }
@@ -690,20 +723,20 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
             if ((S.sorted_keys[mid] >> S.B.bn) & 1ull) hi = mid; else lo = mid + 1;
         }
         const uint32_t ni = lo - a;
-        const VHdr h = G.hdr[v];
+        const VHdr h = load_hdr(G, v);
         const uint32_t dtot = h.deg + ni;
         const uint32_t capa1 = dtot > capa_of(h) ? capa_for(dtot) : capa_of(h);
         uint32_t insbits = 0;
         for (uint32_t i = a; i < lo; i++) insbits |= S.B.ups[S.sorted_vals[i]].z;
         uint32_t ngroups = 0;
         for (int k = 0; k < 32; k++) {
-            const uint32_t c = G.cnt[(uint64_t)v * 32 + k] + (((insbits >> k) & 1u) ? ni : 0u);
+            const uint32_t c = cnt_ref(G, v, k) + (((insbits >> k) & 1u) ? ni : 0u);
             ngroups += c >= 2;
         }
         // worst case: a grown adjacency, and every group that could hold >= 2 members gets a new
-        // block (regular: 2*capA words; sparse: 2*capS <= 2*capA) plus a new sparse list (2*capA)
+        // block (regular: 4*capA words; sparse: 4*capS <= 4*capA) plus a new sparse list (2*capA)
         if (dtot > capa_of(h)) bound += 4ull * capa1;
-        if (ngroups) bound += 2ull * capa1 * (ngroups + 1);
+        if (ngroups) bound += 4ull * capa1 * ngroups + 2ull * capa1;
         const bool big = dtot > 4096 || (b - a) > 256;
         if (big) S.big_list[atomicAdd(&S.counts[1], 1ull)] = (uint32_t)sidx;
         else S.small_list[atomicAdd(&S.counts[0], 1ull)] = (uint32_t)sidx;
@@ -825,9 +858,9 @@ __global__ void k_stream(DevGraph G, const uint4* __restrict__ ups, uint64_t cou
         const uint32_t ni = (u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
         const uint32_t nd = (u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
         // pool headroom for this record before touching anything
-        const VHdr h = G.hdr[u.x];
+        const VHdr h = load_hdr(G, u.x);
         const uint32_t capa1 = capa_for(h.deg + ni > capa_of(h) ? h.deg + ni : capa_of(h));
-        const unsigned long long need = 4ull * capa1 + 2ull * capa1 * 34 + 2ull * caps_for(h.deg + ni) * 32;
+        const unsigned long long need = 4ull * capa1 * 34;
         if (*G.pool.top + need > G.pool.words) {
             if (t.rank() == 0) atomicOr(G.pool.status, ST_OOM);
             break;

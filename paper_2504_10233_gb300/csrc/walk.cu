@@ -52,129 +52,129 @@ struct WalkParams {
     uint32_t* s_prev;
 };
 
-// Identity of a walker: Philox key, local id (the counter's walker field) and policy.
-struct WalkerId {
-    uint2 key;
-    uint64_t lid;
-    uint32_t pid;
-};
-
-__device__ __forceinline__ WalkerId walker_id(const WalkParams& A, uint64_t wid) {
-    WalkerId w;
+// Policy index of walker `wid`: its request in request mode, else policy_ids[wid] (default 0).
+__device__ __forceinline__ uint32_t walker_pid(const WalkParams& A, uint64_t wid) {
     if (A.req_off) {
         uint32_t lo = 0, hi = A.nreq;  // last r with req_off[r] <= wid
         while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) >> 1;
             if (__ldg(A.req_off + mid) <= wid) lo = mid; else hi = mid;
         }
-        const uint64_t k = __ldg(A.req_key + lo);
-        w.key = make_uint2((uint32_t)k, (uint32_t)(k >> 32));
-        w.lid = wid - __ldg(A.req_off + lo);
-        w.pid = lo;
-    } else {
-        w.key = A.key;
-        w.lid = wid;
-        w.pid = A.pids ? __ldg(A.pids + wid) : 0u;
+        return lo;
     }
-    return w;
+    return A.pids ? __ldg(A.pids + wid) : 0u;
+}
+// Philox key and counter walker-id of walker `wid` (re-derived each step instead of kept live).
+__device__ __forceinline__ void walker_stream(const WalkParams& A, uint64_t wid, uint32_t pid, uint2& key,
+                                              uint64_t& lid) {
+    if (A.req_off) {
+        const uint64_t k = __ldg(A.req_key + pid);
+        key = make_uint2((uint32_t)k, (uint32_t)(k >> 32));
+        lid = wid - __ldg(A.req_off + pid);
+    } else {
+        key = A.key;
+        lid = wid;
+    }
 }
 
-struct PolicyRegs {
-    uint32_t kind, max_len, stop;
-    uint64_t a0, a1, a2;
+// First sector of a vertex record: the header and groups 0 and 1.
+struct Sec0 {
+    uint32_t adj, deg, mask, sref;
+    uint2 g0, g1;
 };
-__device__ __forceinline__ PolicyRegs load_policy(const bingo_policy* p) {
-    PolicyRegs r;
-    r.kind = __ldg(&p->kind);
-    r.max_len = __ldg(&p->max_len);
-    r.stop = __ldg(&p->ppr_stop_u32);
-    r.a0 = __ldg(reinterpret_cast<const unsigned long long*>(&p->n2v_accept[0]));
-    r.a1 = __ldg(reinterpret_cast<const unsigned long long*>(&p->n2v_accept[1]));
-    r.a2 = __ldg(reinterpret_cast<const unsigned long long*>(&p->n2v_accept[2]));
-    return r;
-}
-
-__device__ __forceinline__ VHdr ld_hdr(const VHdr* p) {
-    const uint4* q = reinterpret_cast<const uint4*>(p);
+__device__ __forceinline__ Sec0 ld_sec0(const DevGraph& G, uint32_t v) {
+    const uint4* q = reinterpret_cast<const uint4*>(G.vr + v);
     const uint4 a = __ldg(q), b = __ldg(q + 1);
-    VHdr h;
-    h.adj = ((uint64_t)a.y << 32) | a.x;
-    h.deg = a.z;
-    h.mask = a.w;
-    h.sref = ((uint64_t)b.y << 32) | b.x;
-    h.nsp = b.z;
-    h.lcapa = (uint8_t)(b.w & 0xFF);
-    h.lcaps = (uint8_t)((b.w >> 8) & 0xFF);
-    h.pad = 0;
-    return h;
+    Sec0 s;
+    s.adj = a.x;
+    s.deg = a.y;
+    s.mask = a.z;
+    s.sref = a.w;
+    s.g0 = make_uint2(b.x, b.y);
+    s.g1 = make_uint2(b.z, b.w);
+    return s;
 }
+// Groups 2i and 2i+1 of vertex v as {c_2i, ref_2i, c_2i+1, ref_2i+1} (16-byte aligned).
+__device__ __forceinline__ uint4 ld_pair(const DevGraph& G, uint32_t v, uint32_t i) {
+    return __ldg(reinterpret_cast<const uint4*>(G.vr + v) + 1 + i);
+}
+__device__ __forceinline__ uint64_t pair_w(uint4 x, uint32_t i) {
+    return ((uint64_t)x.x << (2 * i)) + ((uint64_t)x.z << (2 * i + 1));
+}
+// pairs with at least one nonempty group, as bits 2i of the result
+__device__ __forceinline__ uint32_t pair_bits(uint32_t mask) { return (mask | (mask >> 1)) & 0x55555555u; }
 
 // --------------------------------------------------------------------------------- group selection
 // All variants pick k* = min{k : sum_{j<=k} 2^j |G_j| > r} with r uniform in [0, sum_j 2^j |G_j|),
 // i.e. group k with probability W(p_k) / sum W (Eq. group_prob); they differ only in how a team
-// of T lanes shares the count line.
+// of T lanes shares the vertex record.  Outputs k*, |G_k*| and the group's ref.
 
-// T = 1: one lane per walker; the count line is read as 16-byte vectors, only where the mask has bits.
-__device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, uint32_t mask, StepRng& R,
-                                               uint32_t& ks, uint32_t& cs, uint32_t* status) {
-    const uint4* line = reinterpret_cast<const uint4*>(G.cnt + (uint64_t)v * 32);
-    uint64_t part[8];
-    uint64_t tot = 0;
+// T = 1: one lane per walker.  Pair 0 came with the header; pairs 1..15 are read in four batches of
+// four, each batch's loads issued together (predicated on the mask), keeping per-batch sums; the
+// batch holding k* is re-read (L1 hits) to find the group.
+__device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
+                                               uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status) {
+    const uint32_t pb = pair_bits(h.mask);
+    const uint64_t w0 = (uint64_t)h.g0.x + ((uint64_t)h.g1.x << 1);
+    uint64_t part[4];
+    uint64_t tot = w0;
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-        part[q] = 0;
-        if ((mask >> (4 * q)) & 0xFu) {
-            const uint4 x = __ldg(line + q);
-            part[q] = ((uint64_t)x.x << (4 * q)) + ((uint64_t)x.y << (4 * q + 1)) + ((uint64_t)x.z << (4 * q + 2)) +
-                      ((uint64_t)x.w << (4 * q + 3));
+    for (int b = 0; b < 4; b++) {
+        part[b] = 0;
+        if ((pb >> (8 * b + 2)) & 0x55u) {
+            uint4 x[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t i = 4 * b + 1 + j;
+                x[j] = (i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair(G, v, i) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) part[b] += pair_w(x[j], 4 * b + 1 + j);
         }
-        tot += part[q];
+        tot += part[b];
     }
     const uint64_t r = below64(R, tot, status);
-    uint64_t acc = 0;
-    int qs = 7;
-    uint64_t base = 0;
+    if (r < (uint64_t)h.g0.x) { ks = 0; cs = h.g0.x; ref = h.g0.y; return; }
+    if (r < w0) { ks = 1; cs = h.g1.x; ref = h.g1.y; return; }
+    uint64_t acc = w0;
+    int bs = 3;
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        if (bs == 3 && b < 3 && r < acc + part[b]) bs = b;
+        else if (bs == 3 && b < 3) acc += part[b];
+    }
+    // re-read batch bs and scan its groups in order
+    ks = 31;
+    cs = 0;
+    ref = 0;
     bool found = false;
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-        const uint64_t nacc = acc + part[q];
-        const bool hit = !found && r < nacc;
-        qs = hit ? q : qs;
-        base = hit ? acc : base;
-        found |= hit;
-        acc = nacc;
-    }
-    const uint4 x = __ldg(line + qs);
-    const uint32_t c4[4] = {x.x, x.y, x.z, x.w};
-    ks = 4 * qs + 3;
-    cs = x.w;
-    found = false;
-#pragma unroll
     for (int j = 0; j < 4; j++) {
-        base += (uint64_t)c4[j] << (4 * qs + j);
-        const bool hit = !found && r < base;
-        ks = hit ? (uint32_t)(4 * qs + j) : ks;
-        cs = hit ? c4[j] : cs;
-        found |= hit;
+        const uint32_t i = 4 * bs + 1 + j;
+        if (!found && i < 16 && ((pb >> (2 * i)) & 1u)) {
+            const uint4 x = ld_pair(G, v, i);
+            const uint64_t lo = acc + ((uint64_t)x.x << (2 * i));
+            if (r < lo) { ks = 2 * i; cs = x.x; ref = x.y; found = true; }
+            else {
+                acc = lo + ((uint64_t)x.z << (2 * i + 1));
+                if (r < acc) { ks = 2 * i + 1; cs = x.z; ref = x.w; found = true; }
+            }
+        }
     }
+    if (!found) atomicOr(status, ST_STATE);
 }
 
-// T = 4: lane t of the team owns groups [8t, 8t+8) (one 32-byte sector of the line); a
-// two-level shuffle prefix over the team, a ballot finds the lane holding k*.
-__device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, uint32_t mask, StepRng& R,
-                                               uint32_t& ks, uint32_t& cs, uint32_t* status, uint32_t tl,
-                                               uint32_t team_mask, uint32_t team_base) {
-    const uint4* line = reinterpret_cast<const uint4*>(G.cnt + (uint64_t)v * 32);
-    uint32_t c[8];
+// T = 4: lane t of the team owns pairs [4t, 4t+4) (groups 8t..8t+7); a two-level shuffle prefix
+// over the team and a ballot find the lane holding k*, which searches its pairs again.
+__device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
+                                               uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status,
+                                               uint32_t tl, uint32_t team_mask, uint32_t team_base) {
+    const uint32_t mine = (pair_bits(h.mask) >> (8 * tl)) & 0x55u;
     uint64_t s = 0;
-    const uint32_t byte = (mask >> (8 * tl)) & 0xFFu;
-    uint4 x0 = make_uint4(0, 0, 0, 0), x1 = make_uint4(0, 0, 0, 0);
-    if (byte & 0x0Fu) x0 = __ldg(line + 2 * tl);
-    if (byte & 0xF0u) x1 = __ldg(line + 2 * tl + 1);
-    c[0] = x0.x; c[1] = x0.y; c[2] = x0.z; c[3] = x0.w;
-    c[4] = x1.x; c[5] = x1.y; c[6] = x1.z; c[7] = x1.w;
-#pragma unroll
-    for (int j = 0; j < 8; j++) s += (uint64_t)c[j] << (8 * tl + j);
+    for (uint32_t m = mine; m; m &= m - 1) {
+        const uint32_t i = 4 * tl + ((__ffs(m) - 1) >> 1);
+        s += pair_w(ld_pair(G, v, i), i);
+    }
     uint64_t incl = s;
 #pragma unroll
     for (int d = 1; d < 4; d <<= 1) {
@@ -184,30 +184,34 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, ui
     const uint64_t tot = __shfl_sync(team_mask, incl, team_base + 3);
     const uint64_t r = below64(R, tot, status);
     const uint64_t excl = incl - s;
-    const bool mine = r < incl && r >= excl;
-    const uint32_t b = __ballot_sync(team_mask, mine) & team_mask;
+    const uint32_t b = __ballot_sync(team_mask, r < incl && r >= excl) & team_mask;
     const uint32_t owner = __ffs(b) - 1;
-    uint32_t k_l = 8 * tl + 7, c_l = c[7];
-    uint64_t acc = excl;
-    bool found = false;
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-        acc += (uint64_t)c[j] << (8 * tl + j);
-        const bool hit = !found && r < acc;
-        k_l = hit ? 8 * tl + j : k_l;
-        c_l = hit ? c[j] : c_l;
-        found |= hit;
+    uint32_t k_l = 0, c_l = 0, r_l = 0;
+    if (lane_id() == owner) {
+        uint64_t acc = excl;
+        bool found = false;
+        for (uint32_t m = mine; m && !found; m &= m - 1) {
+            const uint32_t i = 4 * tl + ((__ffs(m) - 1) >> 1);
+            const uint4 x = ld_pair(G, v, i);
+            acc += (uint64_t)x.x << (2 * i);
+            if (r < acc) { k_l = 2 * i; c_l = x.x; r_l = x.y; found = true; break; }
+            acc += (uint64_t)x.z << (2 * i + 1);
+            if (r < acc) { k_l = 2 * i + 1; c_l = x.z; r_l = x.w; found = true; }
+        }
     }
     ks = __shfl_sync(team_mask, k_l, owner);
     cs = __shfl_sync(team_mask, c_l, owner);
+    ref = __shfl_sync(team_mask, r_l, owner);
 }
 
 // T = 32: lane k owns group k; a warp-wide shuffle prefix of W_k = 2^k |G_k| and a ballot of
 // (prefix > r) give k* as the first set bit.
-__device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, uint32_t mask, StepRng& R,
-                                                uint32_t& ks, uint32_t& cs, uint32_t* status, uint32_t lane) {
-    const uint32_t c = ((mask >> lane) & 1u) ? __ldg(G.cnt + (uint64_t)v * 32 + lane) : 0u;
-    uint64_t incl = (uint64_t)c << lane;
+__device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
+                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status,
+                                                uint32_t lane) {
+    uint2 gk = make_uint2(0, 0);
+    if ((h.mask >> lane) & 1u) gk = __ldg(&G.vr[v].g[lane]);
+    uint64_t incl = (uint64_t)gk.x << lane;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const uint64_t y = __shfl_up_sync(FULL, incl, d);
@@ -217,69 +221,79 @@ __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, u
     const uint64_t r = below64(R, tot, status);
     const uint32_t b = __ballot_sync(FULL, r < incl);
     ks = __ffs(b) - 1;
-    cs = __shfl_sync(FULL, c, ks);
+    cs = __shfl_sync(FULL, gk.x, ks);
+    ref = __shfl_sync(FULL, gk.y, ks);
 }
 
 // --------------------------------------------------------------------------------- intra-group pick
-// Uniform member of G_k* (Eq. pvp): stored index (one-element), uniform position of the member list
-// (regular), of the sparse group's list of sparse-list positions (sparse), or rejection over the whole
-// neighbour list accepting a slot whose bias has bit k* (dense).  Returns the destination vertex.
-__device__ __forceinline__ uint32_t pick_member(const DevGraph& G, const VHdr& h, uint32_t v, uint32_t ks,
-                                                uint32_t cs, StepRng& R, uint32_t* status) {
+// Uniform member of G_k* (Eq. pvp).  One-element groups store their member's destination; regular
+// and sparse groups keep their members' destinations at the head of the group block, so a uniform
+// position costs one access.  Dense groups use rejection over the whole neighbour list, accepting a
+// slot whose bias has bit k* (Section 5.1).  Returns the destination vertex.
+__device__ __forceinline__ uint32_t pick_member(const DevGraph& G, const Sec0& h, uint32_t ks, uint32_t cs,
+                                                uint32_t ref, StepRng& R, uint32_t* status) {
     const uint32_t kd = kind_of(cs, h.deg, G.alpha, G.beta);
-    const uint2* pairs = adj_pairs(G, h.adj);
     if (kd == K_DENSE) {
-        for (int t = 0; t < MAX_DENSE_TRIES; t++) {
-            const uint32_t j = below32(R, h.deg, status);
-            const uint2 e = __ldg(pairs + j);
-            if ((e.y >> ks) & 1u) return e.x;
+        const uint2* pairs = adj_pairs(G, words_of(h.adj));
+        // Rejection in rounds of B candidates drawn in order, whose loads are in flight together; the
+        // first accepted candidate in draw order is the one sequential rejection would return.
+        // B grows as the acceptance rate |G_k|/d falls (it is > 0.4 for a dense group).
+        const uint32_t B = (4ull * cs >= 3ull * h.deg) ? 1u : (2ull * cs >= h.deg) ? 2u : 3u;
+        for (int t = 0; t < MAX_DENSE_TRIES; t += 3) {
+            const uint32_t j0 = below32(R, h.deg, status);
+            const uint32_t j1 = B > 1 ? below32(R, h.deg, status) : 0u;
+            const uint32_t j2 = B > 2 ? below32(R, h.deg, status) : 0u;
+            const uint2 e0 = __ldg(pairs + j0);
+            const uint2 e1 = B > 1 ? __ldg(pairs + j1) : make_uint2(0, 0);
+            const uint2 e2 = B > 2 ? __ldg(pairs + j2) : make_uint2(0, 0);
+            if ((e0.y >> ks) & 1u) return e0.x;
+            if ((e1.y >> ks) & 1u) return e1.x;
+            if ((e2.y >> ks) & 1u) return e2.x;
         }
         atomicOr(status, ST_TIMEOUT);
         return NONE32;
     }
-    const uint64_t gr = __ldg(G.gref + (uint64_t)v * 32 + ks);
-    uint32_t slot;
-    if (kd == K_ONE) {
-        slot = (uint32_t)gr;
-    } else {
-        const uint32_t pos = below32(R, cs, status);
-        slot = __ldg(G.pool.base + (gr & GOFF_MASK) + pos);
-        if (kd == K_SPARSE) {
-            if (slot >= h.nsp) { atomicOr(status, ST_STATE); return NONE32; }
-            slot = __ldg(G.pool.base + h.sref + slot);
-        }
-    }
-    if (slot >= h.deg) { atomicOr(status, ST_STATE); return NONE32; }  // state inconsistent: never index past d
-    return __ldg(reinterpret_cast<const uint32_t*>(pairs + slot));
+    if (kd == K_ONE) return ref;
+    if (words_of(ref) >= G.pool.words) { atomicOr(status, ST_STATE); return NONE32; }  // never read past the pool
+    const uint32_t pos = below32(R, cs, status);
+    return __ldg(G.pool.base + words_of(ref) + pos);
 }
 
 // One step of a walker at `cur`.  Returns false if the walk ends here (PPR stop, no out-edge, error).
 template <int T>
-__device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A, const PolicyRegs& P, uint2 key,
-                                          uint64_t lid, uint32_t step, uint32_t& cur, uint32_t& prev, uint32_t tl,
+__device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A, uint64_t wid, uint32_t pid,
+                                          uint32_t step, uint32_t& cur, uint32_t& prev, uint32_t tl,
                                           uint32_t team_mask, uint32_t team_base, uint32_t lane) {
+    const bingo_policy* P = A.pols + pid;
+    const uint32_t kind = __ldg(&P->kind);
     StepRng R;
-    R.init(key, lid, step);
-    if (P.kind == BINGO_PPR && R.next() < P.stop) return false;
-    const VHdr h = ld_hdr(G.hdr + cur);
+    {
+        uint2 key;
+        uint64_t lid;
+        walker_stream(A, wid, pid, key, lid);
+        R.init(key, lid, step);
+    }
+    if (kind == BINGO_PPR && R.next() < __ldg(&P->ppr_stop_u32)) return false;
+    const Sec0 h = ld_sec0(G, cur);
     if (h.deg == 0) return false;
     for (int attempt = 0; attempt < MAX_N2V_TRIES; attempt++) {
-        uint32_t ks, cs;
-        if constexpr (T == 1) select_group_1(G, cur, h.mask, R, ks, cs, A.status);
-        else if constexpr (T == 4) select_group_4(G, cur, h.mask, R, ks, cs, A.status, tl, team_mask, team_base);
-        else select_group_32(G, cur, h.mask, R, ks, cs, A.status, lane);
-        const uint32_t x = pick_member(G, h, cur, ks, cs, R, A.status);
+        uint32_t ks, cs, ref;
+        if constexpr (T == 1) select_group_1(G, cur, h, R, ks, cs, ref, A.status);
+        else if constexpr (T == 4) select_group_4(G, cur, h, R, ks, cs, ref, A.status, tl, team_mask, team_base);
+        else select_group_32(G, cur, h, R, ks, cs, ref, A.status, lane);
+        const uint32_t x = pick_member(G, h, ks, cs, ref, R, A.status);
         if (x >= G.n) {
             if (x != NONE32) atomicOr(A.status, ST_STATE);
             return false;
         }
-        if (P.kind == BINGO_NODE2VEC && prev != NONE32) {
+        if (kind == BINGO_NODE2VEC && prev != NONE32) {
             const uint64_t u = R.next();
+            const unsigned long long* acc_t = reinterpret_cast<const unsigned long long*>(P->n2v_accept);
             bool acc;
             if (x == prev) {
-                acc = u < P.a0;
+                acc = u < __ldg(acc_t + 0);
             } else {
-                const uint64_t a1 = P.a1, a2 = P.a2;
+                const uint64_t a1 = __ldg(acc_t + 1), a2 = __ldg(acc_t + 2);
                 const uint64_t lo = a1 < a2 ? a1 : a2, hi = a1 < a2 ? a2 : a1;
                 if (u < lo) acc = true;        // accepted at either distance: no probe needed
                 else if (u >= hi) acc = false; // rejected at either distance
@@ -303,18 +317,15 @@ __device__ __forceinline__ void finish_walker(const WalkParams& A, uint64_t wid,
         for (uint32_t t = steps + 1 + tl; t < A.stride; t += T) row[t] = NONE32;
 }
 
-template <int T>
-__global__ void __launch_bounds__(1024) k_walk_persistent(DevGraph G, WalkParams A) {
+// OCC selects the register budget: 0 = up to 64 registers (1,024-thread bound), 1 = 40 registers
+// (256-thread blocks, six per SM), trading spills to L1 for 50% more resident warps.
+template <int T, int OCC>
+__global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persistent(DevGraph G, WalkParams A) {
     const uint32_t lane = threadIdx.x & 31, tl = lane % T, team = lane / T;
     const uint32_t team_base = team * T;
     const uint32_t team_mask = (T == 32) ? FULL : (((1u << T) - 1u) << team_base);
     uint64_t wid = 0;
-    WalkerId W;
-    W.key = make_uint2(0, 0);
-    W.lid = 0;
-    W.pid = 0;
-    PolicyRegs P;
-    uint32_t cur = 0, prev = NONE32, step = 0, L = 0;
+    uint32_t pid = 0, cur = 0, prev = NONE32, step = 0, L = 0;
     bool have = false, drained = false;
     for (;;) {
         if (!drained) {
@@ -330,11 +341,10 @@ __global__ void __launch_bounds__(1024) k_walk_persistent(DevGraph G, WalkParams
                 if (base + __popc(nm) >= A.nwalkers) drained = true;
                 if (!have && mine < A.nwalkers) {
                     wid = mine;
-                    W = walker_id(A, wid);
-                    if (W.pid >= A.npol) { W.pid = 0; atomicOr(A.status, ST_INVALID); }
-                    P = load_policy(A.pols + W.pid);
+                    pid = walker_pid(A, wid);
+                    if (pid >= A.npol) { pid = 0; atomicOr(A.status, ST_INVALID); }
                     cur = __ldg(A.starts + wid);
-                    L = A.lengths ? __ldg(A.lengths + wid) : P.max_len;
+                    L = A.lengths ? __ldg(A.lengths + wid) : __ldg(&A.pols[pid].max_len);
                     if (L + 1 > A.stride) { L = A.stride - 1; atomicOr(A.status, ST_INVALID); }
                     if (cur >= G.n) { L = 0; atomicOr(A.status, ST_INVALID); }
                     prev = NONE32;
@@ -353,7 +363,7 @@ __global__ void __launch_bounds__(1024) k_walk_persistent(DevGraph G, WalkParams
             continue;
         }
         if (have) {
-            const bool took = walk_step<T>(G, A, P, W.key, W.lid, step, cur, prev, tl, team_mask, team_base, lane);
+            const bool took = walk_step<T>(G, A, wid, pid, step, cur, prev, tl, team_mask, team_base, lane);
             if (took) {
                 step++;
                 if (tl == 0) A.paths[wid * (uint64_t)A.stride + step] = cur;
@@ -370,10 +380,9 @@ __global__ void __launch_bounds__(1024) k_walk_persistent(DevGraph G, WalkParams
 __global__ void k_walk_step(DevGraph G, WalkParams A, uint32_t s) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t wid = tid; wid < A.nwalkers; wid += nt) {
-        WalkerId W = walker_id(A, wid);
-        if (W.pid >= A.npol) W.pid = 0;
-        const PolicyRegs P = load_policy(A.pols + W.pid);
-        uint32_t L = A.lengths ? __ldg(A.lengths + wid) : P.max_len;
+        uint32_t pid = walker_pid(A, wid);
+        if (pid >= A.npol) pid = 0;
+        uint32_t L = A.lengths ? __ldg(A.lengths + wid) : __ldg(&A.pols[pid].max_len);
         if (L + 1 > A.stride) L = A.stride - 1;
         uint32_t cur, prev;
         if (s == 0) {
@@ -391,7 +400,7 @@ __global__ void k_walk_step(DevGraph G, WalkParams A, uint32_t s) {
             if (cur == NONE32) continue;
             prev = A.s_prev[wid];
         }
-        const bool took = walk_step<1>(G, A, P, W.key, W.lid, s, cur, prev, 0, 0, 0, 0);
+        const bool took = walk_step<1>(G, A, wid, pid, s, cur, prev, 0, 0, 0, 0);
         if (took) A.paths[wid * (uint64_t)A.stride + s + 1] = cur;
         if (!took || s + 1 == L) {
             finish_walker(A, wid, took ? s + 1 : s, 0, 1);
@@ -410,7 +419,7 @@ __global__ void k_eh_build(DevGraph G) {
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t v = warp; v < G.n; v += nwarps) {
-        const VHdr h = G.hdr[v];
+        const VHdr h = load_hdr(G, v);
         const uint2* pairs = adj_pairs(G, h.adj);
         for (uint32_t j = lane; j < h.deg; j += 32) {
             const unsigned long long key = (v << 32) | pairs[j].x;
@@ -452,20 +461,25 @@ bingo_status edge_index_build(bingo_graph* g, cudaStream_t s) {
     return BINGO_OK;
 }
 
-static int g_occ_cache[3][33];
+static int g_occ_cache[2][3][33];
 
-static int walk_blocks_per_sm(int lanes, int wpb) {
-    int li = lanes == 1 ? 0 : lanes == 4 ? 1 : 2;
+template <int T, int OCC>
+static void* walk_kernel_ptr() { return (void*)k_walk_persistent<T, OCC>; }
+
+static void* walk_kernel(int lanes, int occ) {
+    if (occ) return lanes == 1 ? walk_kernel_ptr<1, 1>() : lanes == 4 ? walk_kernel_ptr<4, 1>() : walk_kernel_ptr<32, 1>();
+    return lanes == 1 ? walk_kernel_ptr<1, 0>() : lanes == 4 ? walk_kernel_ptr<4, 0>() : walk_kernel_ptr<32, 0>();
+}
+
+static int walk_blocks_per_sm(int lanes, int wpb, int occ) {
+    const int li = lanes == 1 ? 0 : lanes == 4 ? 1 : 2;
     if (wpb < 1 || wpb > 32) return 1;
-    if (g_occ_cache[li][wpb]) return g_occ_cache[li][wpb];
+    int& c = g_occ_cache[occ ? 1 : 0][li][wpb];
+    if (c) return c;
     int nb = 0;
-    const int threads = wpb * 32;
-    if (lanes == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk_persistent<1>, threads, 0);
-    else if (lanes == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk_persistent<4>, threads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk_persistent<32>, threads, 0);
-    if (nb < 1) nb = 1;
-    g_occ_cache[li][wpb] = nb;
-    return nb;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel(lanes, occ), wpb * 32, 0);
+    c = nb < 1 ? 1 : nb;
+    return c;
 }
 
 // Launch the walk on device buffers (all pointers device).  Pre: policies validated.
@@ -505,18 +519,20 @@ bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
     }
     CK(cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), s), "walk queue reset");
     g->launches++;
-    const int lanes = (int)g->tune.lanes, wpb = (int)g->tune.warps_per_block;
+    const int lanes = (int)g->tune.lanes, occ_mode = (int)g->tune.occ;
+    int wpb = (int)g->tune.warps_per_block;
+    if (occ_mode && wpb > 8) wpb = 8;  // the 40-register variant is bounded to 256-thread blocks
     int bps = (int)g->tune.blocks_per_sm;
-    const int occ = walk_blocks_per_sm(lanes, wpb);
+    const int occ = walk_blocks_per_sm(lanes, wpb, occ_mode);
     if (bps <= 0 || bps > occ) bps = occ;
     uint64_t blocks = (uint64_t)g->num_sms * bps;
     const uint64_t walkers_per_block = (uint64_t)wpb * (32 / lanes);
     const uint64_t useful = (nwalkers + walkers_per_block - 1) / walkers_per_block;
     if (blocks > useful) blocks = useful;
     if (blocks == 0) blocks = 1;
-    if (lanes == 1) k_walk_persistent<1><<<(unsigned)blocks, wpb * 32, 0, s>>>(g->G, A);
-    else if (lanes == 4) k_walk_persistent<4><<<(unsigned)blocks, wpb * 32, 0, s>>>(g->G, A);
-    else k_walk_persistent<32><<<(unsigned)blocks, wpb * 32, 0, s>>>(g->G, A);
+    void* args[] = {(void*)&g->G, (void*)&A};
+    CK(cudaLaunchKernel(walk_kernel(lanes, occ_mode), dim3((unsigned)blocks), dim3(wpb * 32), args, 0, s),
+       "walk launch");
     g->launches++;
     CK(cudaGetLastError(), "walk launch");
     return BINGO_OK;

@@ -179,12 +179,12 @@ def test_paths_independent_of_team_width_and_launch_form(B):
     pols = _mixed_policies(B)
     ref = None
     for lanes in (1, 4, 32):
-        for wpb in (4, 8):
-            g.set_walk_config(lanes, wpb)
+        for wpb, regv in ((4, 0), (8, 0), (16, 0), (4, 1), (8, 1)):
+            g.set_walk_config(lanes, wpb, 0, regv)
             res = run_walk(B, g, starts, pols, 42, 31, pids=pids)
             if ref is None:
                 ref = res
-            assert (res[0] == ref[0]).all() and (res[1] == ref[1]).all(), (lanes, wpb)
+            assert (res[0] == ref[0]).all() and (res[1] == ref[1]).all(), (lanes, wpb, regv)
     step = run_walk(B, g, starts, pols, 42, 31, pids=pids, mode=B.WALK_STEPWISE)
     assert (step[0] == ref[0]).all() and (step[1] == ref[1]).all()
     other = run_walk(B, g, starts, pols, 43, 31, pids=pids)
