@@ -72,7 +72,8 @@ struct bingo_graph {
     uint64_t next_eid = 0;
     bingo::DevGraph G{};
     // owned device allocations
-    void* d_hdr = nullptr;      // VRec[n]
+    void* d_hdr = nullptr;      // VHot[n]
+    void* d_cold = nullptr;     // VCold[n]
     void* d_pool = nullptr;
     void* d_ctl = nullptr;      // control words: top, npending, leaked, status, queue, counters
     void* d_fcount = nullptr;

@@ -1,20 +1,19 @@
 // Internal device structures and primitives of the radix-factorised sampler.
 //
 // Device state of a graph (all in HBM):
-//   vr[v]   VRec, 288 bytes (nine 32-byte sectors), one per vertex:
-//             bytes   0..15  header {adjacency block, degree d, nonempty-group mask, sparse-list block}
-//             bytes  16..271 32 x {|G_k|, ref} (Eq. wpk: W(p_k) = 2^k |G_k|); ref = slot of the member of a
-//                            one-element group, or the group block of a regular/sparse group, else 0
-//             bytes 272..287 update-only fields (|S|, log2 capacities)
-//           so the header, the mask and groups 0-1 share the first sector and a group's count and
-//           reference share a sector.
+//   vh[v]   VHot, 64 bytes: header {adjacency block, degree d, nonempty-group mask, sparse-list
+//           block} and groups 0-5 as {|G_k|, ref} (Eq. wpk: W(p_k) = 2^k |G_k|); ref = destination of
+//           the member of a one-element group, or the group block of a regular/sparse group, else 0.
+//           The hot array is n x 64 B, small enough to stay largely in L2.
+//   vc[v]   VCold, 224 bytes: groups 6-31 and the update-only fields (|S|, log2 capacities).
 //   pool    u32 words holding every variable-size block, in power-of-two sizes (offsets stored in
 //           32-byte units):
 //             adjacency   4*capA words: capA x {dst, bias} (8 B, AoS) then capA x u64 edge id
-//             regular k   2*capA words: member slots [capA] then inverted index [capA] (by slot)
+//             regular k   4*capA words: member destinations, member slots, inverted index (by slot), spare
 //             sparse list 2*capA words: S = slots of edges in any sparse group [capA], then
 //                         S_inv [capA] (by slot)
-//             sparse k    2*capS words: member positions in S [capS] then inverted index [capS]
+//             sparse k    4*capS words: member destinations, member positions in S, inverted index
+//                         (by S position), spare
 // A group's kind is never stored: it is the pure function of (|G_k|, d) given by Eq. group.
 #pragma once
 
@@ -55,18 +54,23 @@ struct VHdr {
     uint16_t pad;
 };
 
-struct __align__(32) VRec {
+constexpr uint32_t HOT_GROUPS = 6;
+struct __align__(64) VHot {
     uint32_t adj;   // adjacency block, 32-byte units
     uint32_t deg;
     uint32_t mask;
     uint32_t sref;  // sparse-list block, 32-byte units
-    uint2 g[32];    // {|G_k|, ref}
+    uint2 g[HOT_GROUPS];
+};
+struct __align__(32) VCold {
+    uint2 g[32 - HOT_GROUPS];
     uint32_t nsp;
     uint8_t lcapa, lcaps;
     uint16_t pad;
     uint32_t spare0, spare1;
 };
-static_assert(sizeof(VRec) == 288, "VRec must be nine sectors");
+static_assert(sizeof(VHot) == 64, "VHot must be two sectors");
+static_assert(sizeof(VCold) == 224, "VCold must be seven sectors");
 
 constexpr uint64_t POOL_UNIT_WORDS = 8;  // offsets are stored in 32-byte units
 constexpr uint64_t MAX_POOL_WORDS = (1ull << 32) * POOL_UNIT_WORDS;
@@ -165,7 +169,8 @@ struct DevGraph {
     uint32_t n;
     uint32_t max_bits;
     uint32_t alpha, beta;
-    VRec* vr;
+    VHot* vh;
+    VCold* vc;
     Pool pool;
     // edge index (node2vec distance probe): open addressing over (src << 32 | dst) -> live copies
     unsigned long long* eh_key;  // EH_EMPTY = empty
@@ -176,31 +181,37 @@ constexpr unsigned long long EH_EMPTY = 0xFFFFFFFFFFFFFFFFull;
 
 #ifdef __CUDACC__
 __device__ __forceinline__ VHdr load_hdr(const DevGraph& G, uint64_t v) {
-    const VRec& r = G.vr[v];
+    const VHot& a = G.vh[v];
+    const VCold& b = G.vc[v];
     VHdr h;
-    h.adj = words_of(r.adj);
-    h.deg = r.deg;
-    h.mask = r.mask;
-    h.sref = words_of(r.sref);
-    h.nsp = r.nsp;
-    h.lcapa = r.lcapa;
-    h.lcaps = r.lcaps;
+    h.adj = words_of(a.adj);
+    h.deg = a.deg;
+    h.mask = a.mask;
+    h.sref = words_of(a.sref);
+    h.nsp = b.nsp;
+    h.lcapa = b.lcapa;
+    h.lcaps = b.lcaps;
     h.pad = 0;
     return h;
 }
 __device__ __forceinline__ void store_hdr(const DevGraph& G, uint64_t v, const VHdr& h) {
-    VRec& r = G.vr[v];
-    r.adj = ref_of(h.adj);
-    r.deg = h.deg;
-    r.mask = h.mask;
-    r.sref = ref_of(h.sref);
-    r.nsp = h.nsp;
-    r.lcapa = h.lcapa;
-    r.lcaps = h.lcaps;
-    r.pad = 0;
+    VHot& a = G.vh[v];
+    VCold& b = G.vc[v];
+    a.adj = ref_of(h.adj);
+    a.deg = h.deg;
+    a.mask = h.mask;
+    a.sref = ref_of(h.sref);
+    b.nsp = h.nsp;
+    b.lcapa = h.lcapa;
+    b.lcaps = h.lcaps;
+    b.pad = 0;
 }
-__device__ __forceinline__ uint32_t& cnt_ref(const DevGraph& G, uint64_t v, uint32_t k) { return G.vr[v].g[k].x; }
-__device__ __forceinline__ uint32_t& gref_ref(const DevGraph& G, uint64_t v, uint32_t k) { return G.vr[v].g[k].y; }
+// {|G_k|, ref} of group k of vertex v
+__device__ __forceinline__ uint2& grp(const DevGraph& G, uint64_t v, uint32_t k) {
+    return k < HOT_GROUPS ? G.vh[v].g[k] : G.vc[v].g[k - HOT_GROUPS];
+}
+__device__ __forceinline__ uint32_t& cnt_ref(const DevGraph& G, uint64_t v, uint32_t k) { return grp(G, v, k).x; }
+__device__ __forceinline__ uint32_t& gref_ref(const DevGraph& G, uint64_t v, uint32_t k) { return grp(G, v, k).y; }
 
 __device__ __forceinline__ uint2* adj_pairs(const DevGraph& G, uint64_t adj) { return reinterpret_cast<uint2*>(G.pool.base + adj); }
 __device__ __forceinline__ uint64_t* adj_eids(const DevGraph& G, uint64_t adj, uint32_t capa) {

@@ -275,7 +275,7 @@ static unsigned grid_for(const bingo_graph* g, uint64_t work_items, unsigned blo
 
 static void free_graph(bingo_graph* g) {
     if (!g) return;
-    void* ptrs[] = {g->d_hdr, g->d_pool, g->d_ctl, g->d_fcount, g->d_fstack, g->d_pending, g->d_eh};
+    void* ptrs[] = {g->d_hdr, g->d_cold, g->d_pool, g->d_ctl, g->d_fcount, g->d_fstack, g->d_pending, g->d_eh};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     Buf* bufs[] = {&g->s_in, &g->s_keys, &g->s_keys2, &g->s_vals, &g->s_vals2, &g->s_tmp, &g->s_seg,
@@ -360,13 +360,15 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
         release_stage();
         return fail(BINGO_E_INVALID);
     }
-    if (!cu(cudaMalloc(&g->d_hdr, sizeof(VRec) * (size_t)n), "vertex records")) { release_stage(); return fail(st); }
+    if (!cu(cudaMalloc(&g->d_hdr, sizeof(VHot) * (size_t)n), "vertex records (hot)") ||
+        !cu(cudaMalloc(&g->d_cold, sizeof(VCold) * (size_t)n), "vertex records (cold)")) { release_stage(); return fail(st); }
     DevGraph& G = g->G;
     G.n = n;
     G.max_bits = c.max_bits;
     G.alpha = c.alpha_pct;
     G.beta = c.beta_pct;
-    G.vr = (VRec*)g->d_hdr;
+    G.vh = (VHot*)g->d_hdr;
+    G.vc = (VCold*)g->d_cold;
     G.pool.status = status;
     G.pool.top = (unsigned long long*)(ctl + CTL_TOP);
     G.pool.npending = (unsigned long long*)(ctl + CTL_NPENDING);
@@ -602,7 +604,7 @@ bingo_status bingo_memory_report(bingo_graph* g, uint64_t out[6]) {
     release(b);
     if (e != cudaSuccess) return cuda_fail(e, "memory report");
     out[0] = 4ull * w[0];
-    out[1] = (uint64_t)g->n * sizeof(VRec);
+    out[1] = (uint64_t)g->n * (sizeof(VHot) + sizeof(VCold));
     out[2] = 4ull * w[1];
     out[3] = 4ull * w[2];
     out[4] = g->G.eh_mask ? (g->G.eh_mask + 1) * 12 : 0;

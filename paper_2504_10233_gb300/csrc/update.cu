@@ -210,7 +210,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     const uint32_t d0 = h0.deg, capa0 = capa_of(h0), caps0 = caps_of(h0);
     const uint32_t dtot = d0 + ni;
     for (uint32_t k = rank; k < 32; k += T) {
-        const uint2 gk = G.vr[v].g[k];
+        const uint2 gk = grp(G, v, k);
         sh.cnt_old[k] = gk.x;
         sh.gref_old[k] = gk.y;
         sh.gref_new[k] = sh.gref_old[k];
@@ -602,7 +602,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
 
     // ---- S11: write back
     for (uint32_t k = rank; k < 32; k += T) {
-        G.vr[v].g[k] = make_uint2(sh.cnt_new[k], (uint32_t)sh.gref_new[k]);
+        grp(G, v, k) = make_uint2(sh.cnt_new[k], (uint32_t)sh.gref_new[k]);
     }
     if (rank == 0) {
         VHdr h;

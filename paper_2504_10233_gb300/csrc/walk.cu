@@ -77,26 +77,28 @@ __device__ __forceinline__ void walker_stream(const WalkParams& A, uint64_t wid,
     }
 }
 
-// First sector of a vertex record: the header and groups 0 and 1.
+// Hot part of a vertex record: the header and groups 0-5 (pairs 0-2), one 64-byte line.
 struct Sec0 {
     uint32_t adj, deg, mask, sref;
-    uint2 g0, g1;
+    uint4 p0, p1, p2;
 };
 __device__ __forceinline__ Sec0 ld_sec0(const DevGraph& G, uint32_t v) {
-    const uint4* q = reinterpret_cast<const uint4*>(G.vr + v);
-    const uint4 a = __ldg(q), b = __ldg(q + 1);
+    const uint4* q = reinterpret_cast<const uint4*>(G.vh + v);
+    const uint4 a = __ldg(q);
     Sec0 s;
     s.adj = a.x;
     s.deg = a.y;
     s.mask = a.z;
     s.sref = a.w;
-    s.g0 = make_uint2(b.x, b.y);
-    s.g1 = make_uint2(b.z, b.w);
+    s.p0 = __ldg(q + 1);
+    s.p1 = __ldg(q + 2);
+    s.p2 = __ldg(q + 3);
     return s;
 }
 // Groups 2i and 2i+1 of vertex v as {c_2i, ref_2i, c_2i+1, ref_2i+1} (16-byte aligned).
 __device__ __forceinline__ uint4 ld_pair(const DevGraph& G, uint32_t v, uint32_t i) {
-    return __ldg(reinterpret_cast<const uint4*>(G.vr + v) + 1 + i);
+    if (i < HOT_GROUPS / 2) return __ldg(reinterpret_cast<const uint4*>(G.vh + v) + 1 + i);
+    return __ldg(reinterpret_cast<const uint4*>(G.vc + v) + (i - HOT_GROUPS / 2));
 }
 __device__ __forceinline__ uint64_t pair_w(uint4 x, uint32_t i) {
     return ((uint64_t)x.x << (2 * i)) + ((uint64_t)x.z << (2 * i + 1));
@@ -109,57 +111,58 @@ __device__ __forceinline__ uint32_t pair_bits(uint32_t mask) { return (mask | (m
 // i.e. group k with probability W(p_k) / sum W (Eq. group_prob); they differ only in how a team
 // of T lanes shares the vertex record.  Outputs k*, |G_k*| and the group's ref.
 
-// T = 1: one lane per walker.  Pair 0 came with the header; pairs 1..15 are read in four batches of
-// four, each batch's loads issued together (predicated on the mask), keeping per-batch sums; the
-// batch holding k* is re-read (L1 hits) to find the group.
+__device__ __forceinline__ bool scan_pair(uint4 x, uint32_t i, uint64_t r, uint64_t& acc, uint32_t& ks, uint32_t& cs,
+                                          uint32_t& ref) {
+    const uint64_t lo = acc + ((uint64_t)x.x << (2 * i));
+    if (r < lo) { ks = 2 * i; cs = x.x; ref = x.y; return true; }
+    acc = lo + ((uint64_t)x.z << (2 * i + 1));
+    if (r < acc) { ks = 2 * i + 1; cs = x.z; ref = x.w; return true; }
+    return false;
+}
+
+// T = 1: one lane per walker.  Pairs 0-2 came with the header; the cold pairs 3..15 are read in
+// batches of four whose loads are issued together (predicated on the mask), keeping per-batch
+// sums; the batch holding k* is re-read (L1 hits) to find the group.
 __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status) {
     const uint32_t pb = pair_bits(h.mask);
-    const uint64_t w0 = (uint64_t)h.g0.x + ((uint64_t)h.g1.x << 1);
+    const uint64_t whot = pair_w(h.p0, 0) + pair_w(h.p1, 1) + pair_w(h.p2, 2);
     uint64_t part[4];
-    uint64_t tot = w0;
+    uint64_t tot = whot;
 #pragma unroll
     for (int b = 0; b < 4; b++) {
         part[b] = 0;
-        if ((pb >> (8 * b + 2)) & 0x55u) {
+        if ((pb >> (8 * b + 6)) & 0x55u) {
             uint4 x[4];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const uint32_t i = 4 * b + 1 + j;
+                const uint32_t i = 3 + 4 * b + j;
                 x[j] = (i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair(G, v, i) : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
-            for (int j = 0; j < 4; j++) part[b] += pair_w(x[j], 4 * b + 1 + j);
+            for (int j = 0; j < 4; j++) part[b] += pair_w(x[j], 3 + 4 * b + j);
         }
         tot += part[b];
     }
     const uint64_t r = below64(R, tot, status);
-    if (r < (uint64_t)h.g0.x) { ks = 0; cs = h.g0.x; ref = h.g0.y; return; }
-    if (r < w0) { ks = 1; cs = h.g1.x; ref = h.g1.y; return; }
-    uint64_t acc = w0;
+    uint64_t acc = 0;
+    if (scan_pair(h.p0, 0, r, acc, ks, cs, ref)) return;
+    if (scan_pair(h.p1, 1, r, acc, ks, cs, ref)) return;
+    if (scan_pair(h.p2, 2, r, acc, ks, cs, ref)) return;
     int bs = 3;
 #pragma unroll
-    for (int b = 0; b < 4; b++) {
-        if (bs == 3 && b < 3 && r < acc + part[b]) bs = b;
-        else if (bs == 3 && b < 3) acc += part[b];
+    for (int b = 0; b < 3; b++) {
+        if (bs == 3 && r < acc + part[b]) bs = b;
+        else if (bs == 3) acc += part[b];
     }
-    // re-read batch bs and scan its groups in order
     ks = 31;
     cs = 0;
     ref = 0;
     bool found = false;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-        const uint32_t i = 4 * bs + 1 + j;
-        if (!found && i < 16 && ((pb >> (2 * i)) & 1u)) {
-            const uint4 x = ld_pair(G, v, i);
-            const uint64_t lo = acc + ((uint64_t)x.x << (2 * i));
-            if (r < lo) { ks = 2 * i; cs = x.x; ref = x.y; found = true; }
-            else {
-                acc = lo + ((uint64_t)x.z << (2 * i + 1));
-                if (r < acc) { ks = 2 * i + 1; cs = x.z; ref = x.w; found = true; }
-            }
-        }
+        const uint32_t i = 3 + 4 * bs + j;
+        if (!found && i < 16 && ((pb >> (2 * i)) & 1u)) found = scan_pair(ld_pair(G, v, i), i, r, acc, ks, cs, ref);
     }
     if (!found) atomicOr(status, ST_STATE);
 }
@@ -210,7 +213,8 @@ __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, c
                                                 uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status,
                                                 uint32_t lane) {
     uint2 gk = make_uint2(0, 0);
-    if ((h.mask >> lane) & 1u) gk = __ldg(&G.vr[v].g[lane]);
+    if ((h.mask >> lane) & 1u)
+        gk = __ldg(lane < HOT_GROUPS ? &G.vh[v].g[lane] : &G.vc[v].g[lane - HOT_GROUPS]);
     uint64_t incl = (uint64_t)gk.x << lane;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
