@@ -8,6 +8,33 @@
 
 namespace bingo {
 
+// Order-preserving team compaction over [0, n): each thread tests IT consecutive elements per
+// chunk (their loads in flight together), one team scan per chunk of IT * team size, and
+// emit(j, position) for every j with pred(j) true, positions ascending with j.  Returns the count.
+constexpr int COMPACT_IT = 8;
+template <class Team, class Pred, class Emit>
+__device__ __forceinline__ uint32_t team_compact(const Team& t, uint32_t n, Pred pred, Emit emit) {
+    uint32_t pos = 0;
+    const uint32_t chunk = COMPACT_IT * t.size();
+    for (uint32_t base = 0; base < n; base += chunk) {
+        const uint32_t j0 = base + t.rank() * COMPACT_IT;
+        bool p[COMPACT_IT];
+        uint32_t c = 0;
+#pragma unroll
+        for (int q = 0; q < COMPACT_IT; q++) {
+            p[q] = (j0 + q < n) && pred(j0 + q);
+            c += p[q] ? 1u : 0u;
+        }
+        uint32_t tot;
+        uint32_t off = t.scan_excl(c, tot);
+#pragma unroll
+        for (int q = 0; q < COMPACT_IT; q++)
+            if (p[q]) emit(j0 + q, pos + off++);
+        pos += tot;
+    }
+    return pos;
+}
+
 // Group blocks hold [member destinations | member list | inverted index | spare], cap words each:
 // a walker reads a uniform member's destination with one access at the block's start.
 
@@ -19,19 +46,13 @@ __device__ void build_regular(const Team& t, const DevGraph& G, uint64_t adj, ui
     uint32_t* mdst = G.pool.base + goff;
     uint32_t* mem = mdst + capa;
     uint32_t* inv = mem + capa;
-    uint32_t pos = 0;
-    for (uint32_t b = 0; b < d; b += t.size()) {
-        const uint32_t j = b + t.rank();
-        const bool p = j < d && ((pairs[j].y >> k) & 1u);
-        uint32_t tot;
-        const uint32_t r = t.scan_pred(p, tot);
-        if (p) {
-            mem[pos + r] = j;
-            inv[j] = pos + r;
-            mdst[pos + r] = pairs[j].x;
-        }
-        pos += tot;
-    }
+    team_compact(
+        t, d, [&](uint32_t j) { return ((pairs[j].y >> k) & 1u) != 0; },
+        [&](uint32_t j, uint32_t pos) {
+            mem[pos] = j;
+            inv[j] = pos;
+            mdst[pos] = pairs[j].x;
+        });
 }
 
 // Sparse neighbour list S: slots of edges with any bit of spmask set, S_inv by slot.
@@ -41,19 +62,12 @@ __device__ uint32_t build_slist(const Team& t, const DevGraph& G, uint64_t adj, 
     const uint2* pairs = adj_pairs(G, adj);
     uint32_t* S = G.pool.base + sref;
     uint32_t* Sinv = S + capa;
-    uint32_t pos = 0;
-    for (uint32_t b = 0; b < d; b += t.size()) {
-        const uint32_t j = b + t.rank();
-        const bool p = j < d && (pairs[j].y & spmask) != 0u;
-        uint32_t tot;
-        const uint32_t r = t.scan_pred(p, tot);
-        if (p) {
-            S[pos + r] = j;
-            Sinv[j] = pos + r;
-        }
-        pos += tot;
-    }
-    return pos;
+    return team_compact(
+        t, d, [&](uint32_t j) { return (pairs[j].y & spmask) != 0u; },
+        [&](uint32_t j, uint32_t pos) {
+            S[pos] = j;
+            Sinv[j] = pos;
+        });
 }
 
 // Sparse group k: member list of positions in S, inverted index by S position.
@@ -65,37 +79,30 @@ __device__ void build_sparse(const Team& t, const DevGraph& G, uint64_t adj, uin
     uint32_t* mdst = G.pool.base + goff;
     uint32_t* mem = mdst + caps;
     uint32_t* inv = mem + caps;
-    uint32_t pos = 0;
-    for (uint32_t b = 0; b < nsp; b += t.size()) {
-        const uint32_t i = b + t.rank();
-        const uint2 e = i < nsp ? pairs[S[i]] : make_uint2(0, 0);
-        const bool p = i < nsp && ((e.y >> k) & 1u);
-        uint32_t tot;
-        const uint32_t r = t.scan_pred(p, tot);
-        if (p) {
-            mem[pos + r] = i;
-            inv[i] = pos + r;
-            mdst[pos + r] = e.x;
-        }
-        pos += tot;
-    }
+    team_compact(
+        t, nsp, [&](uint32_t i) { return ((pairs[S[i]].y >> k) & 1u) != 0; },
+        [&](uint32_t i, uint32_t pos) {
+            mem[pos] = i;
+            inv[i] = pos;
+            mdst[pos] = pairs[S[i]].x;
+        });
 }
 
 // Slot of the (unique) edge with bit k set; NONE32 if there is none.
 template <class Team>
 __device__ uint32_t find_one(const Team& t, const DevGraph& G, uint64_t adj, uint32_t d, uint32_t k) {
     const uint2* pairs = adj_pairs(G, adj);
-    uint32_t best = NONE32;
-    for (uint32_t b = 0; b < d; b += t.size()) {
-        const uint32_t j = b + t.rank();
-        const bool p = j < d && ((pairs[j].y >> k) & 1u);
-        const uint32_t cand = p ? j : NONE32;
-        // team minimum via max of complements
-        const uint32_t m = ~t.max(~cand);
-        best = best < m ? best : m;
-        if (best != NONE32) break;  // team-uniform
+    const uint32_t chunk = COMPACT_IT * t.size();
+    for (uint32_t base = 0; base < d; base += chunk) {
+        const uint32_t j0 = base + t.rank() * COMPACT_IT;
+        uint32_t cand = NONE32;
+#pragma unroll
+        for (int q = COMPACT_IT - 1; q >= 0; q--)
+            if (j0 + q < d && ((pairs[j0 + q].y >> k) & 1u)) cand = j0 + q;
+        const uint32_t m = ~t.max(~cand);  // team minimum
+        if (m != NONE32) return m;         // team-uniform
     }
-    return best;
+    return NONE32;
 }
 
 }  // namespace bingo

@@ -31,8 +31,6 @@ using namespace bingo;
 namespace {
 
 constexpr unsigned long long INF64 = 0xFFFFFFFFFFFFFFFFull;
-constexpr uint32_t APPLY_WARPS = 8;      // warp teams per block
-constexpr uint32_t BIG_THREADS = 512;    // block team size
 constexpr uint32_t ST_STOP = ST_INVALID | ST_OOM | ST_STATE;
 
 // stats layout inside CTL_STATS: 0 inserted, 1 deleted, 2 not_found, 3 touched, 4 rebuilt, 5.. conv[5][5]
@@ -48,14 +46,20 @@ struct BatchSrc {
     uint64_t dmask;
     uint64_t start;  // first key of the segment
     uint32_t ni;
+    const uint32_t* sdel;  // deletion destinations staged in shared memory (nullable)
     __device__ __forceinline__ uint4 ins(uint32_t i) const { return ups[vals[start + i]]; }
     __device__ __forceinline__ uint64_t ins_eid(uint32_t i) const { return eid_base + (rank[vals[start + i]] >> 32); }
-    __device__ __forceinline__ uint32_t del_dst(uint32_t j) const { return (uint32_t)(keys[start + ni + j] & dmask); }
+    __device__ __forceinline__ uint32_t del_dst_global(uint32_t j) const {
+        return (uint32_t)(keys[start + ni + j] & dmask);
+    }
+    __device__ __forceinline__ uint32_t del_dst(uint32_t j) const { return sdel ? sdel[j] : del_dst_global(j); }
 };
 
 struct OneSrc {
     uint32_t dst, bias;
     uint64_t eid;
+    const uint32_t* sdel = nullptr;
+    __device__ __forceinline__ uint32_t del_dst_global(uint32_t) const { return dst; }
     __device__ __forceinline__ uint4 ins(uint32_t) const { return make_uint4(0, dst, bias, 0); }
     __device__ __forceinline__ uint64_t ins_eid(uint32_t) const { return eid; }
     __device__ __forceinline__ uint32_t del_dst(uint32_t) const { return dst; }
@@ -204,7 +208,8 @@ struct SegScratch {
 // Apply one vertex's segment (ni insertions then nd deletions).  Returns false if the graph ran out of pool.
 template <class Team, class Src>
 __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint32_t v, uint32_t ni, uint32_t nd,
-                              const Src& B, const SegScratch& X, unsigned long long* stats) {
+                              Src B, const SegScratch& X, unsigned long long* stats, uint32_t* sdel_buf,
+                              uint32_t sdel_cap, uint32_t* cand_buf = nullptr, uint32_t cand_cap = 0) {
     const uint32_t rank = t.rank(), T = t.size();
     const VHdr h0 = load_hdr(G, v);
     const uint32_t d0 = h0.deg, capa0 = capa_of(h0), caps0 = caps_of(h0);
@@ -273,7 +278,13 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     t.sync();
 
     // ---- S3: resolve each deletion to the earliest live copy (smallest edge id) of (v, dst);
-    // the r-th deletion of the same dst takes the r-th earliest copy (round r).
+    // the r-th deletion of the same dst takes the r-th earliest copy (round r).  The sorted
+    // deletion destinations are staged in shared memory when they fit, for the per-slot searches.
+    if (nd && sdel_buf && nd <= sdel_cap) {
+        for (uint32_t j = rank; j < nd; j += T) sdel_buf[j] = B.del_dst_global(j);
+        t.sync();
+        B.sdel = sdel_buf;
+    }
     if (nd) {
         uint32_t mr = 0;
         for (uint32_t j = rank; j < nd; j += T) {
@@ -282,23 +293,94 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
             mr = max(mr, j - lo + 1);
         }
         const uint32_t rounds = t.max(mr);
-        for (uint32_t r = 0; r < rounds; r++) {
-            for (uint32_t j = rank; j < dtot; j += T) {
-                const uint64_t e = eids[j];
-                if (e & DEAD_BIT) continue;
-                uint32_t lo, hi;
-                del_range(B, nd, pairs[j].x, lo, hi);
-                if (hi - lo > r) atomicMin(&X.best[lo + r], (unsigned long long)e);
+        // Candidates: live slots whose destination is deleted in this segment, collected once (a
+        // duplicated edge repeated in the batch needs one round per repetition, and RMAT hubs carry
+        // many duplicates); the rounds then scan only the candidates.
+        uint32_t ncand = 0;
+        bool use_cand = cand_buf != nullptr;
+        if (use_cand) {
+            ncand = team_compact(
+                t, dtot,
+                [&](uint32_t j) {
+                    if (eids[j] & DEAD_BIT) return false;
+                    const uint32_t x = pairs[j].x;
+                    uint32_t lo = 0, hi = nd;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (B.del_dst(mid) < x) lo = mid + 1; else hi = mid;
+                    }
+                    return lo < nd && B.del_dst(lo) == x;
+                },
+                [&](uint32_t j, uint32_t pos) {
+                    if (pos < cand_cap) cand_buf[pos] = j;
+                });
+            use_cand = ncand <= cand_cap;
+            t.sync();
+        }
+        if (use_cand) {
+            for (uint32_t r = 0; r < rounds; r++) {
+                for (uint32_t i = rank; i < ncand; i += T) {
+                    const uint32_t j = cand_buf[i];
+                    const uint64_t e = eids[j];
+                    if (e & DEAD_BIT) continue;
+                    uint32_t lo, hi;
+                    del_range(B, nd, pairs[j].x, lo, hi);
+                    if (hi - lo > r) atomicMin(&X.best[lo + r], (unsigned long long)e);
+                }
+                t.sync();
+                for (uint32_t i = rank; i < ncand; i += T) {
+                    const uint32_t j = cand_buf[i];
+                    const uint64_t e = eids[j];
+                    if (e & DEAD_BIT) continue;
+                    uint32_t lo, hi;
+                    del_range(B, nd, pairs[j].x, lo, hi);
+                    if (hi - lo > r && X.best[lo + r] == e) {
+                        eids[j] = e | DEAD_BIT;
+                        X.del_slot[lo + r] = j;
+                    }
+                }
+                t.sync();
+            }
+        }
+        // Each thread takes RES_IT consecutive slots per iteration with their loads in flight together.
+        constexpr int RES_IT = 8;
+        for (uint32_t r = 0; r < (use_cand ? 0u : rounds); r++) {
+            for (uint32_t j0 = rank * RES_IT; j0 < dtot; j0 += T * RES_IT) {
+                uint32_t x[RES_IT];
+                uint64_t e[RES_IT];
+#pragma unroll
+                for (int q = 0; q < RES_IT; q++) {
+                    const bool in = j0 + q < dtot;
+                    x[q] = in ? pairs[j0 + q].x : 0u;
+                    e[q] = in ? eids[j0 + q] : DEAD_BIT;
+                }
+#pragma unroll
+                for (int q = 0; q < RES_IT; q++) {
+                    if (e[q] & DEAD_BIT) continue;
+                    uint32_t lo, hi;
+                    del_range(B, nd, x[q], lo, hi);
+                    if (hi - lo > r) atomicMin(&X.best[lo + r], (unsigned long long)e[q]);
+                }
             }
             t.sync();
-            for (uint32_t j = rank; j < dtot; j += T) {
-                const uint64_t e = eids[j];
-                if (e & DEAD_BIT) continue;
-                uint32_t lo, hi;
-                del_range(B, nd, pairs[j].x, lo, hi);
-                if (hi - lo > r && X.best[lo + r] == e) {
-                    eids[j] = e | DEAD_BIT;
-                    X.del_slot[lo + r] = j;
+            for (uint32_t j0 = rank * RES_IT; j0 < dtot; j0 += T * RES_IT) {
+                uint32_t x[RES_IT];
+                uint64_t e[RES_IT];
+#pragma unroll
+                for (int q = 0; q < RES_IT; q++) {
+                    const bool in = j0 + q < dtot;
+                    x[q] = in ? pairs[j0 + q].x : 0u;
+                    e[q] = in ? eids[j0 + q] : DEAD_BIT;
+                }
+#pragma unroll
+                for (int q = 0; q < RES_IT; q++) {
+                    if (e[q] & DEAD_BIT) continue;
+                    uint32_t lo, hi;
+                    del_range(B, nd, x[q], lo, hi);
+                    if (hi - lo > r && X.best[lo + r] == e[q]) {
+                        eids[j0 + q] = e[q] | DEAD_BIT;
+                        X.del_slot[lo + r] = j0 + q;
+                    }
                 }
             }
             t.sync();
@@ -750,7 +832,9 @@ __global__ void k_oom_check(DevGraph G, const unsigned long long* counts) {
 }
 
 template <class Team>
-__device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, const SegArgs& S, SegSh& sh, uint32_t sidx) {
+__device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, const SegArgs& S, SegSh& sh, uint32_t sidx,
+                                            uint32_t* sdel_buf, uint32_t sdel_cap, uint32_t* cand_buf,
+                                            uint32_t cand_cap) {
     const uint32_t a = S.seg_start[sidx], b = S.seg_start[sidx + 1];
     const uint32_t v = (uint32_t)(S.sorted_keys[a] >> (S.B.bn + 1));
     uint32_t lo = a, hi = b;
@@ -774,26 +858,52 @@ __device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, co
     X.ins_final = S.slot_scratch + a;
     X.del_slot = S.slot_scratch + a + ni;
     X.best = S.best + a + ni;
-    apply_segment(t, G, sh, v, ni, nd, src, X, S.stats);
+    src.sdel = nullptr;
+    apply_segment(t, G, sh, v, ni, nd, src, X, S.stats, sdel_buf, sdel_cap, cand_buf, cand_cap);
 }
 
-__global__ void __launch_bounds__(APPLY_WARPS * 32) k_apply_small(DevGraph G, SegArgs S) {
-    __shared__ SegSh sh[APPLY_WARPS];
+constexpr uint32_t SMALL_SDEL = 64;    // staged deletion destinations per warp team
+constexpr uint32_t SMALL_CAND = 64;    // resolution candidates per warp team
+constexpr uint32_t BIG_SDEL = 4096;    // per block team
+constexpr uint32_t BIG_CAND = 4096;
+constexpr uint32_t APPLY_THREADS = 512;
+constexpr uint32_t APPLY_TEAMS = APPLY_THREADS / 32;
+
+// One launch for every segment: the first `nbig` blocks each take a big segment as one 512-thread
+// team (dispatched first, they are the long poles); the remaining blocks run 16 warp teams each
+// over the small segments.
+struct BigShared {
+    SegSh sh;
+    uint32_t sdel[BIG_SDEL];
+    uint32_t cand[BIG_CAND];
+};
+struct SmallShared {
+    SegSh sh[APPLY_TEAMS];
+    uint32_t sdel[APPLY_TEAMS][SMALL_SDEL];
+    uint32_t cand[APPLY_TEAMS][SMALL_CAND];
+};
+union ApplyShared {
+    BigShared big;
+    SmallShared small;
+};
+
+__global__ void __launch_bounds__(APPLY_THREADS) k_apply(DevGraph G, SegArgs S, uint32_t big_blocks) {
+    __shared__ ApplyShared smem;
     if (*G.pool.status & ST_STOP) return;
+    const unsigned long long nbig = S.counts[1], nsmall = S.counts[0];
+    if (blockIdx.x < big_blocks) {
+        BlockTeam t;
+        t.sm = smem.big.sh.tscratch;
+        for (uint64_t i = blockIdx.x; i < nbig; i += big_blocks)
+            run_segment(t, G, S, smem.big.sh, S.big_list[i], smem.big.sdel, BIG_SDEL, smem.big.cand, BIG_CAND);
+        return;
+    }
     const uint32_t w = threadIdx.x >> 5;
-    const unsigned long long nsmall = S.counts[0];
+    const uint64_t nblk = gridDim.x - big_blocks;
     WarpTeam t;
-    for (uint64_t i = (uint64_t)blockIdx.x * APPLY_WARPS + w; i < nsmall; i += (uint64_t)gridDim.x * APPLY_WARPS)
-        run_segment(t, G, S, sh[w], S.small_list[i]);
-}
-
-__global__ void __launch_bounds__(BIG_THREADS) k_apply_big(DevGraph G, SegArgs S) {
-    __shared__ SegSh sh;
-    if (*G.pool.status & ST_STOP) return;
-    const unsigned long long nbig = S.counts[1];
-    BlockTeam t;
-    t.sm = sh.tscratch;
-    for (uint64_t i = blockIdx.x; i < nbig; i += gridDim.x) run_segment(t, G, S, sh, S.big_list[i]);
+    for (uint64_t i = (uint64_t)(blockIdx.x - big_blocks) * APPLY_TEAMS + w; i < nsmall; i += nblk * APPLY_TEAMS)
+        run_segment(t, G, S, smem.small.sh[w], S.small_list[i], smem.small.sdel[w], SMALL_SDEL, smem.small.cand[w],
+                    SMALL_CAND);
 }
 
 // edge-index maintenance: +1 for every insertion record, -1 for every deletion that found an edge
@@ -875,7 +985,7 @@ __global__ void k_stream(DevGraph G, const uint4* __restrict__ ups, uint64_t cou
         X.ins_final = scratch + 4;
         X.del_slot = scratch + 5;
         X.best = best;
-        apply_segment(t, G, sh, u.x, ni, nd, src, X, stats);
+        apply_segment(t, G, sh, u.x, ni, nd, src, X, stats, nullptr, 0u);
         // edge index
         if (G.eh_mask && t.rank() == 0) {
             const unsigned long long k = ((unsigned long long)u.x << 32) | u.y;
@@ -1086,9 +1196,14 @@ bingo_status bingo_apply_updates(bingo_graph* g, const bingo_update* ups, uint64
     S.stats = (unsigned long long*)(ctl + CTL_STATS);
     k_seg_classify<<<grid_cap(g, nkeys, 256), 256, 0, s>>>(g->G, S);
     k_oom_check<<<1, 1, 0, s>>>(g->G, counts);
-    k_apply_small<<<grid_cap(g, nkeys, APPLY_WARPS, 32), APPLY_WARPS * 32, 0, s>>>(g->G, S);
-    k_apply_big<<<grid_cap(g, nkeys, 1, 4), BIG_THREADS, 0, s>>>(g->G, S);
-    g->launches += 4;
+    {
+        // big-segment blocks first (at most one per SM), then warp-team blocks for the small segments
+        const uint32_t big_blocks = (uint32_t)std::min<uint64_t>(nkeys, (uint64_t)g->num_sms);
+        const uint64_t small_blocks = std::max<uint64_t>(1, std::min<uint64_t>((nkeys + APPLY_TEAMS - 1) / APPLY_TEAMS,
+                                                                                 (uint64_t)g->num_sms * 8));
+        k_apply<<<(unsigned)(big_blocks + small_blocks), APPLY_THREADS, 0, s>>>(g->G, S, big_blocks);
+    }
+    g->launches += 3;
     if (g->G.eh_mask) {
         k_eh_apply<<<grid_cap(g, nkeys, 256), 256, 0, s>>>(g->G, S, nkeys);
         g->launches++;
