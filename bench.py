@@ -254,7 +254,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     B.load()
     nsteps = args.warmup + args.steps
-    wl = W.make_workload(args.workload, nbatch=nsteps)
+    wl = W.make_workload(args.workload, nbatch=nsteps + 1)  # the last batch feeds the streaming measurement
     G = wl.graph
     stream = torch.cuda.Stream(device=dev)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -346,6 +346,26 @@ def run_ours(args):
            "h2d_bytes_per_step": int(h_starts.numel() * 4 + h_recs[0].numel() * 4),
            "d2h_bytes_per_step": int(h_paths.numel() * 4 + h_plen.numel() * 4)}
 
+    # streaming: the same kind of records applied as batches of one (Section 4.2), device buffers
+    streaming = None
+    if not args.no_e2e:
+        srec = t(wl.batches[-1].records()[: args.stream_records])
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        g.stream_updates(srec, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        one_ms = []
+        for j in range(30):  # single-record calls: the latency of one streamed update through the API
+            r1 = srec[j: j + 1]
+            t0 = time.perf_counter()
+            g.stream_updates(r1, stream=stream)
+            one_ms.append(1e3 * (time.perf_counter() - t0))
+        streaming = {"records": int(srec.shape[0]), "updates_per_s": int(srec.shape[0]) / (e0.elapsed_time(e1) / 1e3),
+                     "single_record_call_ms_median": float(np.median(one_ms)),
+                     "batched_over_streaming": upd_rate / (int(srec.shape[0]) / (e0.elapsed_time(e1) / 1e3))}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(G, wl.batches[0], wl.length, 77, args.cpu_seconds)
@@ -364,11 +384,285 @@ def run_ours(args):
                 "updated_edges_per_s": upd_rate, "walk_steps_per_s": walk_rate,
                 "update_ms_per_step": float(np.mean(upd_ms)), "walk_ms_per_step": float(np.mean(walk_ms)),
                 "wall_s_timed": wall, "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
-                "roofline": roof, "cpu_baseline": cpu}
+                "roofline": roof, "cpu_baseline": cpu, "streaming": streaming}
         print(json.dumps(line), flush=True)
     g.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _clocks_and_graph(args, name, **mk):
+    import torch
+
+    import paper_2504_10233_gb300 as B
+
+    B.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    wl = W.make_workload(name, **mk)
+    t_gen = time.perf_counter() - t0
+    G = wl.graph
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    t0 = time.perf_counter()
+    g = B.Graph(G.n, t(G.row_ptr), t(G.col), t(G.w), max_bits=G.max_bits)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    return B, torch, dev, wl, G, g, t, {"generate_s": t_gen, "create_s": t_create}
+
+
+def run_mixed(args):
+    """RMAT-24, 4M walkers in one persistent launch: node2vec (p=2, q=0.5, L=80) and PPR (stop 0.15,
+    cap 100) interleaved by walker id, against the same walkers run stepwise (one launch per step) and
+    as one launch per policy."""
+    B, torch, dev, wl, G, g, t, setup = _clocks_and_graph(args, "c3")
+    nw = wl.nwalkers
+    stride = 101
+    starts = t(W.walk_starts(G.n, nw, wl.walk_seed))
+    pids_np = (np.arange(nw) % 2).astype(np.uint8)
+    pids = t(pids_np)
+    pols = [B.policy(B.NODE2VEC, 80, n2v_pq=(2.0, 0.5)), B.policy(B.PPR, 100, 0.15)]
+    paths = torch.empty((nw, stride), dtype=torch.int32, device=dev)
+    plen = torch.empty(nw, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    if args.autotune:
+        g.autotune(starts[: 1 << 18], 80, stream=stream)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    mode = B.WALK_PERSISTENT | B.WALK_NO_PAD
+
+    def timed_walk(seed, st_, pid_, m_, n_):
+        flush.fill_(seed & 0xFF)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        g.walk(st_, pols, seed, stride, paths[:n_], plen[:n_], policy_ids=pid_, mode=m_, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), int((plen[:n_].to(torch.int64) - 1).sum().item())
+
+    for i in range(args.warmup):
+        timed_walk(100 + i, starts, pids, mode, nw)
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = g.kernel_launches()
+    ms, steps = [], 0
+    for i in range(args.steps):
+        a, b = timed_walk(200 + i, starts, pids, mode, nw)
+        ms.append(a)
+        steps += b
+    launches = g.kernel_launches() - launches0
+    clocks = sampler.stop()
+    g.check(stream)
+    value = steps / (sum(ms) / 1e3)
+    # plain forms on the same walkers
+    sw_ms, sw_steps = timed_walk(200, starts, pids, B.WALK_STEPWISE | B.WALK_NO_PAD, nw)
+    per_ms, per_steps = 0.0, 0
+    for p in (0, 1):
+        sel = np.nonzero(pids_np == p)[0]
+        a, b = timed_walk(200, t(W.walk_starts(G.n, nw, wl.walk_seed)[sel]), t(pids_np[sel]), mode, len(sel))
+        per_ms += a
+        per_steps += b
+    # first-order roofline model over the last launch (node2vec retries and probes not counted)
+    ex = g.export_state()
+    per_v = expected_bytes_per_vertex(ex)
+    a, b = timed_walk(300, starts, pids, mode, nw)
+    abytes = walk_bytes(per_v, paths.cpu().numpy().view(np.uint32), plen.cpu().numpy().view(np.uint32))
+    pk, pk_src = peaks()
+    achieved = abytes / (a / 1e3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        og = O.Graph(G.n, G.row_ptr, G.col, G.w)
+        on = 1 << 13
+        opol = [O.policy(O.NODE2VEC, 80, 0, [p for p in pols[0].n2v_accept]), O.policy(O.PPR, 100, pols[1].ppr_stop_u32)]
+        t0 = time.perf_counter()
+        _, ol = og.walk(W.walk_starts(G.n, on, 9), opol, 9, policy_ids=(np.arange(on) % 2).astype(np.uint8))
+        dt = time.perf_counter() - t0
+        osteps = float((ol.astype(np.int64) - 1).sum())
+        cpu = {"value": osteps / dt, "unit": "steps/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"{on} walkers (half node2vec, half PPR) on the same graph; {osteps:.0f} steps in {dt:.1f} s"}
+    line = {"metric": "sampled walk steps/s, mixed node2vec + PPR in one persistent launch", "value": value,
+            "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32/u64", "data": "synthetic",
+            "config": {"workload": "RMAT-24 (2^24 vertices, 2^28 edges), fixed-point biases w_fx in [128, 25600); "
+                                   "4M walkers: node2vec p=2 q=0.5 L=80 and PPR stop 0.15 cap 100, interleaved",
+                       "l2": "flushed between steps; state > L2", "setup": setup,
+                       "walk_config": {"lanes_per_walker": g.config().lanes_per_walker,
+                                       "warps_per_block": g.config().warps_per_block,
+                                       "reg_variant": g.config().reg_variant}},
+            "plain_forms": {"stepwise_steps_per_s": sw_steps / (sw_ms / 1e3),
+                            "one_launch_per_policy_steps_per_s": per_steps / (per_ms / 1e3),
+                            "persistent_over_stepwise": value / (sw_steps / (sw_ms / 1e3))},
+            "clocks": clocks, "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": "k_walk_persistent",
+                         "peak_source": f"{pk_src} hbm_gbs", "model": "first-order bytes per accepted step"},
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
+def run_sweep(args):
+    """RMAT-26 + 64 hubs of 10^6 extra out-edges, uniform 31-bit biases: update batches of
+    10^3 .. 10^7 (50/50) applied in place, then rounds of 16M PPR walkers (stop 0.15, cap 100)."""
+    sizes = [10 ** e for e in range(3, 8)]
+    B, torch, dev, wl, G, g, t, setup = _clocks_and_graph(args, "c5", nbatch=1, batch=sum(sizes) + 10 ** 6 * (args.steps + args.warmup))
+    stream = torch.cuda.Stream(device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    allrec = wl.batches[0].records()
+    off = 0
+    sweep = []
+    for sz in sizes:
+        rec = t(allrec[off: off + sz])
+        off += sz
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        st = g.apply_updates(rec, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sweep.append({"batch": sz, "ms": ms, "updated_edges_per_s": sz / (ms / 1e3), "not_found": st["not_found"]})
+    nw = wl.nwalkers
+    stride = 101
+    starts = t(W.walk_starts(G.n, nw, wl.walk_seed))
+    paths = torch.empty((nw, stride), dtype=torch.int32, device=dev)
+    plen = torch.empty(nw, dtype=torch.int32, device=dev)
+    pols = [B.policy(B.PPR, 100, 0.15)]
+    mode = B.WALK_PERSISTENT | B.WALK_NO_PAD
+    sampler = None
+    ms_u, ms_w, steps, nupd = [], [], 0, 0
+    for i in range(args.warmup + args.steps):
+        rec = t(allrec[off: off + 10 ** 6])
+        off += 10 ** 6
+        if i == args.warmup:
+            sampler = ClockSampler(0)
+            sampler.start()
+            launches0 = g.kernel_launches()
+        torch.cuda.synchronize()
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record(stream)
+        g.apply_updates(rec, stream=stream)
+        e1.record(stream)
+        g.walk(starts, pols, 500 + i, stride, paths, plen, mode=mode, stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ms_u.append(e0.elapsed_time(e1))
+            ms_w.append(e1.elapsed_time(e2))
+            steps += int((plen.to(torch.int64) - 1).sum().item())
+            nupd += 10 ** 6
+    launches = g.kernel_launches() - launches0
+    clocks = sampler.stop()
+    g.check(stream)
+    mem = g.memory_report()
+    line = {"metric": "sampled walk steps/s (10^6-update batch + 16M PPR walkers per step); updated edges/s sweep",
+            "value": steps / ((sum(ms_u) + sum(ms_w)) / 1e3), "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(np.array(ms_u) + np.array(ms_w))),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
+            "config": {"workload": "RMAT-26 (2^26 vertices, 2^30 edges) + 64 hubs x 10^6 extra out-edges, uniform "
+                                   "biases in [1, 2^31); batches 50/50 from the hold-out protocol; 16M PPR walkers",
+                       "setup": setup, "memory_bytes": mem},
+            "walk_steps_per_s": steps / (sum(ms_w) / 1e3), "updated_edges_per_s": nupd / (sum(ms_u) / 1e3),
+            "batch_sweep": sweep, "clocks": clocks, "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
+def run_serving(args):
+    """RMAT-22, uniform 16-bit biases: a Poisson stream of single-edge updates (10^5/s, 70% insert)
+    interleaved with Poisson walk requests of 1..10^4 walkers (log-uniform), DeepWalk length 40,
+    served by the continuous-batching server; p50/p99 latency per offered request rate, merged
+    launches against one launch per request."""
+    import ctypes
+
+    B, torch, dev, wl, G, g, t, setup = _clocks_and_graph(args, "c4", nbatch=1, batch=int(1e5 * args.serve_seconds * 8))
+    L = B.load()
+    ups = np.ascontiguousarray(wl.batches[0].records())
+    pol = B.policy(B.DEEPWALK, 40)
+    results = []
+    uoff = 0
+    for merge in (True, False):
+        for rate in args.serve_rates:
+            rng_u = W.uniform01(200000, 12345 + int(rate), 0)
+            gaps = -np.log(1.0 - rng_u) / rate
+            arrivals = np.cumsum(gaps)
+            arrivals = arrivals[arrivals < args.serve_seconds]
+            sizes = np.floor(10 ** (4 * W.uniform01(len(arrivals), 777 + int(rate), 1))).astype(np.int64)
+            sizes = np.maximum(sizes, 1)
+            nup = int(1e5 * args.serve_seconds)
+            up_times = np.arange(nup) / 1e5
+            cfg = B.bingo_server_config()
+            cfg.flags = 0 if merge else B.SERVER_NO_MERGE
+            h = ctypes.c_void_p()
+            assert L.bingo_server_create(g.h, ctypes.byref(cfg), ctypes.byref(h)) == 0
+            starts_all = W.walk_starts(G.n, int(sizes.sum()) + 1, 4242 + int(rate))
+            soff = np.concatenate([[0], np.cumsum(sizes)])
+            tickets = []
+            done = []
+
+            def collector():
+                p = np.zeros((10 ** 4, 41), np.uint32)
+                l = np.zeros(10 ** 4, np.uint32)
+                ep = ctypes.c_uint64()
+                k = 0
+                while True:
+                    while k >= len(tickets):
+                        if done:
+                            return
+                        time.sleep(0.0002)
+                    L.bingo_server_wait(h, tickets[k], 120000, p.ctypes.data, l.ctypes.data, ctypes.byref(ep))
+                    k += 1
+
+            th = threading.Thread(target=collector, daemon=True)
+            th.start()
+            ui = 0
+            ri = 0
+            t0 = time.perf_counter()
+            while ri < len(arrivals) or ui < nup:
+                now = time.perf_counter() - t0
+                uj = ui
+                while uj < nup and up_times[uj] <= now:
+                    uj += 1
+                if uj > ui:
+                    chunk = ups[uoff + ui: uoff + uj]
+                    L.bingo_server_submit_updates(h, chunk.ctypes.data, len(chunk), None)
+                    ui = uj
+                while ri < len(arrivals) and arrivals[ri] <= now:
+                    st = starts_all[soff[ri]: soff[ri + 1]]
+                    tk = ctypes.c_uint64()
+                    L.bingo_server_submit_walk(h, st.ctypes.data, len(st), ctypes.byref(pol), 1000 + ri, ctypes.byref(tk))
+                    tickets.append(tk.value)
+                    ri += 1
+                time.sleep(0.00005)
+            L.bingo_server_drain(h, 600000)
+            elapsed = time.perf_counter() - t0
+            done.append(1)
+            th.join(timeout=600)
+            stt = B.bingo_server_stats()
+            L.bingo_server_stats_get(h, ctypes.byref(stt))
+            L.bingo_server_destroy(h)
+            uoff += nup
+            results.append({"merged": merge, "offered_req_per_s": rate, "requests": int(stt.requests_done),
+                            "p50_ms": stt.p50_ms, "p99_ms": stt.p99_ms, "mean_ms": stt.mean_ms,
+                            "walk_steps_per_s": stt.steps_done / elapsed, "updates_applied": int(stt.updates_applied),
+                            "epochs": int(stt.epochs), "elapsed_s": elapsed})
+    g.check()
+    mid = [r for r in results if r["merged"] and r["offered_req_per_s"] == args.serve_rates[len(args.serve_rates) // 2]][0]
+    line = {"metric": "p99 request latency (ms) under a Poisson request and update stream; walk steps/s served",
+            "value": mid["p99_ms"], "unit": "ms", "n_gpus": 1, "steps": len(results), "warmup": 0,
+            "ms_per_step": None, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
+            "data": "synthetic",
+            "config": {"workload": "RMAT-22 (2^22 vertices, 2^26 edges), biases U[1, 2^16); updates 10^5/s (70% "
+                                   "insert); requests of floor(10^U[0,4]) DeepWalk walkers, L = 40",
+                       "offered_req_per_s_for_value": mid["offered_req_per_s"], "setup": setup,
+                       "seconds_per_rate": args.serve_seconds},
+            "sweep": results}
+    print(json.dumps(line), flush=True)
+    g.close()
 
 
 def main():
@@ -384,11 +678,20 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-walkers", type=int, default=16384)
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per walk launch, if captured")
+    ap.add_argument("--stream-records", type=int, default=20000)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[100.0, 1000.0, 10000.0])
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c3":
+        run_mixed(args)
+    elif args.workload == "c4":
+        run_serving(args)
+    elif args.workload == "c5":
+        run_sweep(args)
     else:
         run_ours(args)
 

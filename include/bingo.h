@@ -148,10 +148,16 @@ bingo_status bingo_apply_updates(bingo_graph* g, const bingo_update* ups, uint64
                                  bingo_update_stats* stats);
 
 /*
- * Streaming updates (Section 4.2): apply the records one at a time, in order,
- * each as a batch of size one (so kinds are re-evaluated after every record),
- * inside a single launch.  Same validation, errors and stats as
- * bingo_apply_updates.  Synchronises `stream` before returning.
+ * Streaming updates (Section 4.2): the result is that of applying the records
+ * one at a time, in order, each as a batch of size one (so kinds are
+ * re-evaluated after every record and a deletion sees every earlier
+ * insertion).  Records of one source vertex are applied in record order by one
+ * warp; records of different source vertices touch disjoint state and run
+ * concurrently; edge ids follow record order.  Same validation and stats as
+ * bingo_apply_updates (an invalid record rejects the whole call before any
+ * change).  BINGO_E_OOM: a record whose worst-case growth no longer fits the
+ * pool is not applied and processing stops; records already applied (of any
+ * vertex) stay applied, each one complete.  Synchronises `stream`.
  */
 bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint64_t count, void* stream,
                                   bingo_update_stats* stats);
@@ -273,9 +279,11 @@ uint64_t bingo_kernel_launches(bingo_graph* g);
 /* ---------------------------------------------------------------------------------------------- serving
  * Continuous-batching request loop (the paper's "integrate all updates before
  * each walk", Section 6 (ii)): a host thread owns the graph; streaming updates
- * are queued and applied at epoch boundaries; walk requests are admitted while
- * device memory and walker slots allow, merged into shared launches, and
- * complete independently.  A request binds to the epoch current at admission,
+ * are queued and applied at epoch boundaries (immediately when no walk launch
+ * is in flight; otherwise new admissions pause once the oldest queued update
+ * has waited update_delay_us, the in-flight launches drain, and the epoch
+ * advances); walk requests are admitted while device memory and walker slots
+ * allow, merged into shared launches, and complete independently.  A request binds to the epoch current at admission,
  * and its paths depend only on (that epoch's state, its seed, walker index).
  */
 typedef struct {
@@ -285,6 +293,8 @@ typedef struct {
     uint32_t concurrent_launches;  /* walk launches in flight at once; 0 = 4 */
     uint32_t max_len_cap;          /* longest step limit a request may ask for; 0 = 128 */
     uint32_t flags;                /* BINGO_SERVER_NO_MERGE: one request per launch (the plain form) */
+    uint32_t update_delay_us;      /* longest time a queued update waits while walks keep being admitted; 0 = 1000 */
+    uint32_t reserved;
 } bingo_server_config;
 
 enum { BINGO_SERVER_NO_MERGE = 1 };

@@ -67,7 +67,7 @@ class bingo_state_sizes(c.Structure):
 class bingo_server_config(c.Structure):
     _fields_ = [("max_inflight_walkers", c.c_uint64), ("hbm_reserve_bytes", c.c_uint64),
                 ("max_update_batch", c.c_uint32), ("concurrent_launches", c.c_uint32), ("max_len_cap", c.c_uint32),
-                ("flags", c.c_uint32)]
+                ("flags", c.c_uint32), ("update_delay_us", c.c_uint32), ("reserved", c.c_uint32)]
 
 
 class bingo_server_stats(c.Structure):

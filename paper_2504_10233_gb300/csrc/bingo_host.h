@@ -28,8 +28,10 @@ cudaError_t scan_excl_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint64_
                           cudaStream_t s, uint64_t* launches);
 
 // stable LSD radix sort of (key u64, value u32) pairs on the low `bits` key bits
+// (sorts the key bits [lo_bit, lo_bit + bits))
 cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, uint64_t n,
-                             uint32_t bits, Buf& tmp, cudaStream_t s, bool* result_in_alt, uint64_t* launches);
+                             uint32_t bits, Buf& tmp, cudaStream_t s, bool* result_in_alt, uint64_t* launches,
+                             uint32_t lo_bit = 0);
 
 // One walk launch, all pointers on the device.
 struct WalkReq {

@@ -70,6 +70,7 @@ struct bingo_server {
     std::deque<Request*> queue;
     std::map<uint64_t, Request*> reqs;
     uint64_t next_ticket = 1, epoch = 0, update_seq = 0;
+    double updates_since = 0;  // arrival of the oldest queued update
     std::vector<Slot> slots;
     uint64_t inflight = 0;
     cudaStream_t ustream = nullptr;
@@ -179,8 +180,11 @@ void worker_main(bingo_server* S) {
         bool any_busy = false;
         for (Slot& sl : S->slots) any_busy |= sl.busy;
         if (S->stop && S->queue.empty() && S->updates.empty() && !any_busy) break;
-        // 2. epoch boundary: apply queued updates once no launch reads the graph
-        if (!S->updates.empty()) {
+        // 2. epoch boundary: apply queued updates once no launch reads the graph.  While launches are
+        // in flight, admission continues until the oldest queued update has waited update_delay_us.
+        const bool updates_due =
+            !S->updates.empty() && (now_s() - S->updates_since) * 1e6 >= (double)S->cfg.update_delay_us;
+        if (!S->updates.empty() && (updates_due || S->queue.empty())) {
             if (!any_busy) {
                 const size_t nb = std::min<size_t>(S->updates.size(), S->cfg.max_update_batch);
                 std::vector<bingo_update> batch(S->updates.begin(), S->updates.begin() + nb);
@@ -193,10 +197,12 @@ void worker_main(bingo_server* S) {
                 S->updates_applied += nb;
                 S->epoch++;
                 S->epochs++;
+                S->updates_since = now_s();  // what remains queued now waits from this epoch on
                 S->cv_done.notify_all();
                 continue;
             }
-        } else if (!S->queue.empty()) {
+        }
+        if (!S->queue.empty() && !updates_due) {
             // 3. admission into a free slot
             Slot* free_slot = nullptr;
             for (Slot& sl : S->slots)
@@ -255,6 +261,7 @@ bingo_status bingo_server_create(bingo_graph* g, const bingo_server_config* cfg,
     if (!S->cfg.max_update_batch) S->cfg.max_update_batch = 65536;
     if (!S->cfg.concurrent_launches) S->cfg.concurrent_launches = 4;
     if (!S->cfg.max_len_cap) S->cfg.max_len_cap = 128;
+    if (!S->cfg.update_delay_us) S->cfg.update_delay_us = 1000;
     S->slots.resize(S->cfg.concurrent_launches);
     for (Slot& sl : S->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -294,6 +301,7 @@ bingo_status bingo_server_submit_updates(bingo_server* S, const bingo_update* up
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->stop) { set_error("server stopping"); return BINGO_E_STATE; }
+        if (S->updates.empty() && n) S->updates_since = now_s();
         for (uint64_t i = 0; i < n; i++) S->updates.push_back(ups[i]);
         if (epoch) *epoch = S->epoch + 1;
     }

@@ -773,6 +773,48 @@ __global__ void k_seg_write(const uint64_t* __restrict__ flag, const uint64_t* _
     }
 }
 
+// Worst-case pool words a vertex can allocate when its counts move within [c - nd, c + ni_k] and its
+// degree within [d + ni - nd, d + ni]: a new adjacency block if it grows, one group block (4 * capA
+// words) for every group that can reach a list kind (Eq. group) other than its current kind, the
+// blocks of every group that can be sparse when the set of sparse groups can change (they are
+// rebuilt together), and a sparse list.
+__device__ __forceinline__ unsigned long long pool_bound(const DevGraph& G, uint32_t v, const VHdr& h, uint32_t ni,
+                                                         uint32_t nd, uint32_t insbits) {
+    const uint32_t d0 = h.deg, dmin = d0 + ni >= nd ? d0 + ni - nd : 0, dmax = d0 + ni;
+    const bool grows = dmax > capa_of(h);
+    const uint32_t capa1 = grows ? capa_for(dmax) : capa_of(h);
+    uint32_t nblocks = 0, sp_possible = 0;
+    bool sp_set_may_change = false, any_old_sp = false;
+    for (uint32_t k = 0; k < 32; k++) {
+        const uint32_t c = cnt_ref(G, v, k);
+        const uint32_t cmax = c + (((insbits >> k) & 1u) ? ni : 0u), cmin = c > nd ? c - nd : 0u;
+        const uint32_t old = kind_of(c, d0, G.alpha, G.beta);
+        if (cmax < 2) continue;  // can never be a list kind (and is not one now)
+        const uint32_t lo2 = cmin > 2 ? cmin : 2;
+        // sparse reachable: the smallest count >= 2 stays below beta% of the largest degree
+        const bool can_sp = 100ull * lo2 < (uint64_t)G.beta * dmax;
+        // regular reachable: [lo2, cmax] meets [ceil(beta dmin / 100), floor(alpha dmax / 100)]
+        const uint64_t rlo = ((uint64_t)G.beta * dmin + 99) / 100, rhi = ((uint64_t)G.alpha * dmax) / 100;
+        const bool can_reg = lo2 <= rhi && cmax >= rlo && rlo <= rhi;
+        const bool can_dense = 100ull * cmax > (uint64_t)G.alpha * dmin;
+        if ((can_reg && (old != K_REGULAR || grows)) || (can_sp && (old != K_SPARSE || grows))) nblocks++;
+        if (can_sp) sp_possible++;
+        if (old == K_SPARSE) {
+            any_old_sp = true;
+            if (cmin <= 1 || can_reg || can_dense) sp_set_may_change = true;  // may leave the sparse set
+        } else if (can_sp) {
+            sp_set_may_change = true;  // may join it
+        }
+    }
+    // the sparse list and all sparse groups are rebuilt together when the set changes, the adjacency
+    // grows, or insertions may outgrow the sparse capacity
+    const bool sp_rebuild = sp_set_may_change || grows || (ni > 0 && any_old_sp);
+    unsigned long long words = grows ? 4ull * capa1 : 0ull;
+    words += 4ull * capa1 * nblocks;
+    if (sp_possible && sp_rebuild) words += 2ull * capa1 + 4ull * capa1 * sp_possible;
+    return words;
+}
+
 struct SegArgs {
     BatchArgs B;
     const uint64_t* sorted_keys;
@@ -807,18 +849,9 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
         const uint32_t ni = lo - a;
         const VHdr h = load_hdr(G, v);
         const uint32_t dtot = h.deg + ni;
-        const uint32_t capa1 = dtot > capa_of(h) ? capa_for(dtot) : capa_of(h);
         uint32_t insbits = 0;
         for (uint32_t i = a; i < lo; i++) insbits |= S.B.ups[S.sorted_vals[i]].z;
-        uint32_t ngroups = 0;
-        for (int k = 0; k < 32; k++) {
-            const uint32_t c = cnt_ref(G, v, k) + (((insbits >> k) & 1u) ? ni : 0u);
-            ngroups += c >= 2;
-        }
-        // worst case: a grown adjacency, and every group that could hold >= 2 members gets a new
-        // block (regular: 4*capA words; sparse: 4*capS <= 4*capA) plus a new sparse list (2*capA)
-        if (dtot > capa_of(h)) bound += 4ull * capa1;
-        if (ngroups) bound += 4ull * capa1 * ngroups + 2ull * capa1;
+        bound += pool_bound(G, v, h, ni, b - lo, insbits);
         const bool big = dtot > 4096 || (b - a) > 256;
         if (big) S.big_list[atomicAdd(&S.counts[1], 1ull)] = (uint32_t)sidx;
         else S.small_list[atomicAdd(&S.counts[0], 1ull)] = (uint32_t)sidx;
@@ -954,79 +987,88 @@ __global__ void k_finalize_pool(DevGraph G) {
     if (threadIdx.x == 0) *P.npending = 0;
 }
 
-// Streaming: one warp applies the records in order, each as a batch of one.
-__global__ void k_stream(DevGraph G, const uint4* __restrict__ ups, uint64_t count, uint64_t eid_base,
-                         uint32_t* scratch, unsigned long long* best, unsigned long long* stats,
-                         unsigned long long* applied) {
-    __shared__ SegSh sh;
+// Streaming (Section 4.2): every record is applied as a batch of one, in record order.  Records of
+// different source vertices touch disjoint state and edge ids are fixed by record position, so the
+// records are grouped by source (stable sort) and one warp applies each vertex's records in order
+// while vertices proceed in parallel: the result equals strict one-at-a-time application.
+constexpr uint32_t STREAM_TEAMS = 16;
+struct StreamScratch {
+    uint32_t holes[2], surv[2], ins_final[2], del_slot[2];
+    unsigned long long best[2];
+};
+
+__global__ void __launch_bounds__(STREAM_TEAMS * 32) k_stream_apply(DevGraph G, SegArgs S,
+                                                                    unsigned long long* reserved) {
+    __shared__ SegSh sh[STREAM_TEAMS];
+    __shared__ StreamScratch xs[STREAM_TEAMS];
+    const uint32_t w = threadIdx.x >> 5;
     WarpTeam t;
-    if (threadIdx.x >= 32) return;
-    uint64_t eid = eid_base;
-    for (uint64_t i = 0; i < count; i++) {
-        if (*G.pool.status & ST_STOP) break;
-        const uint4 u = ups[i];
-        const uint32_t ni = (u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
-        const uint32_t nd = (u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
-        // pool headroom for this record before touching anything
-        const VHdr h = load_hdr(G, u.x);
-        const uint32_t capa1 = capa_for(h.deg + ni > capa_of(h) ? h.deg + ni : capa_of(h));
-        const unsigned long long need = 4ull * capa1 * 34;
-        if (*G.pool.top + need > G.pool.words) {
-            if (t.rank() == 0) atomicOr(G.pool.status, ST_OOM);
-            break;
-        }
-        OneSrc src;
-        src.dst = u.y;
-        src.bias = u.z;
-        src.eid = eid;
-        SegScratch X;
-        X.holes = scratch;
-        X.surv = scratch + 2;
-        X.ins_final = scratch + 4;
-        X.del_slot = scratch + 5;
-        X.best = best;
-        apply_segment(t, G, sh, u.x, ni, nd, src, X, stats, nullptr, 0u);
-        // edge index
-        if (G.eh_mask && t.rank() == 0) {
-            const unsigned long long k = ((unsigned long long)u.x << 32) | u.y;
-            if (ni) {
-                uint64_t p = eh_hash(k) & G.eh_mask;
-                for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
-                    const unsigned long long old = atomicCAS(G.eh_key + p, EH_EMPTY, k);
-                    if (old == EH_EMPTY || old == k) { atomicAdd(G.eh_cnt + p, 1u); break; }
-                    p = (p + 1) & G.eh_mask;
+    const uint64_t nseg = *S.nseg_dev;
+    for (uint64_t sidx = (uint64_t)blockIdx.x * STREAM_TEAMS + w; sidx < nseg; sidx += (uint64_t)gridDim.x * STREAM_TEAMS) {
+        const uint32_t a = S.seg_start[sidx], b = S.seg_start[sidx + 1];
+        for (uint32_t r = a; r < b; r++) {
+            if (*G.pool.status & ST_STOP) return;
+            const uint32_t rec = S.sorted_vals[r];
+            const uint4 u = S.B.ups[rec];
+            const uint32_t ni = (u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
+            const uint32_t nd = (u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
+            // reserve this record's worst-case pool growth so no allocation inside it can fail
+            const VHdr h = load_hdr(G, u.x);
+            const unsigned long long need = pool_bound(G, u.x, h, ni, nd, ni ? u.z : 0u);
+            int ok = 1;
+            if (t.rank() == 0) {
+                const unsigned long long prev = atomicAdd(reserved, need);
+                if (*G.pool.top + prev + need > G.pool.words) {
+                    atomicAdd(reserved, 0ull - need);
+                    atomicOr(G.pool.status, ST_OOM);
+                    ok = 0;
                 }
             }
-            if (nd && X.del_slot[0] != NONE32) {
-                uint64_t p = eh_hash(k) & G.eh_mask;
-                for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
-                    const unsigned long long cur = G.eh_key[p];
-                    if (cur == k) { atomicSub(G.eh_cnt + p, 1u); break; }
-                    if (cur == EH_EMPTY) break;
-                    p = (p + 1) & G.eh_mask;
+            ok = __shfl_sync(FULL, ok, 0);
+            if (!ok) return;
+            OneSrc src;
+            src.dst = u.y;
+            src.bias = u.z;
+            src.eid = S.eid_base + (S.B.pscan[rec] >> 32);
+            SegScratch X;
+            X.holes = xs[w].holes;
+            X.surv = xs[w].surv;
+            X.ins_final = xs[w].ins_final;
+            X.del_slot = xs[w].del_slot;
+            X.best = xs[w].best;
+            apply_segment(t, G, sh[w], u.x, ni, nd, src, X, S.stats, nullptr, 0u);
+            if (G.eh_mask && t.rank() == 0) {  // edge index: +1 per insertion, -1 per deletion that found an edge
+                const unsigned long long k = ((unsigned long long)u.x << 32) | u.y;
+                if (ni) {
+                    uint64_t p = eh_hash(k) & G.eh_mask;
+                    for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
+                        const unsigned long long old = atomicCAS(G.eh_key + p, EH_EMPTY, k);
+                        if (old == EH_EMPTY || old == k) { atomicAdd(G.eh_cnt + p, 1u); break; }
+                        p = (p + 1) & G.eh_mask;
+                    }
+                }
+                if (nd && X.del_slot[0] != NONE32) {
+                    uint64_t p = eh_hash(k) & G.eh_mask;
+                    for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
+                        const unsigned long long cur = G.eh_key[p];
+                        if (cur == k) { atomicSub(G.eh_cnt + p, 1u); break; }
+                        if (cur == EH_EMPTY) break;
+                        p = (p + 1) & G.eh_mask;
+                    }
                 }
             }
+            if (t.rank() == 0) atomicAdd(reserved, 0ull - need);
+            __syncwarp();
         }
-        __syncwarp();
-        eid += ni;
-        if (t.rank() == 0) *applied = i + 1;
     }
 }
 
-__global__ void k_validate_stream(const uint4* ups, uint64_t count, uint32_t n, uint32_t max_bits, uint32_t* status,
-                                  unsigned long long* ninserts) {
+__global__ void k_stream_keys(BatchArgs A) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
-    bool bad = false;
-    unsigned long long ins = 0;
-    for (uint64_t i = tid; i < count; i += nt) {
-        const uint4 u = ups[i];
-        const bool isins = u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS;
-        bad |= u.x >= n || u.y >= n || u.w > 2;
-        if (isins) bad |= u.z == 0 || (max_bits < 32 && (u.z >> max_bits) != 0);
-        ins += isins;
+    for (uint64_t i = tid; i < A.count; i += nt) {
+        A.keys[i] = (uint64_t)A.ups[i].x << (A.bn + 1);
+        A.vals[i] = (uint32_t)i;
     }
-    if (bad) atomicOr(status, ST_INVALID);
-    if (ins) atomicAdd(ninserts, ins);
 }
 
 uint32_t bits_for(uint32_t n) {
@@ -1075,6 +1117,9 @@ static bingo_status finish_batch(bingo_graph* g, cudaStream_t s, bingo_update_st
     bingo_update_stats tmp;
     bingo_status st = read_stats(g, s, &tmp, &status);
     if (st != BINGO_OK) return st;
+    // this call reports its device status through its return value; clear it so that it does not
+    // surface again in a later bingo_check
+    CK(cudaMemsetAsync((uint64_t*)g->d_ctl + CTL_STATUS, 0, 8, s), "status clear");
     if (stats) *stats = tmp;
     if (status & ST_INVALID) {
         set_error("invalid update record (id >= n, op > 2, or bias outside [1, 2^max_bits)); batch rejected");
@@ -1226,6 +1271,7 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
     if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
     if (count && !ups) { set_error("NULL update array"); return BINGO_E_INVALID; }
+    if (count >= 0x7FFFFFFFull) { set_error("too many records"); return BINGO_E_INVALID; }
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t* ctl = (uint64_t*)g->d_ctl;
     CK(cudaMemsetAsync(ctl + CTL_STATUS, 0, 8, s), "status reset");
@@ -1240,15 +1286,54 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
         CK(cudaMemcpyAsync(g->s_in.p, ups, count * 16, cudaMemcpyHostToDevice, s), "update upload");
         dups = (const uint4*)g->s_in.p;
     }
-    CK(ensure(g->s_aux, 256), "stream scratch");
-    CK(ensure(g->s_best, 256), "stream scratch");
-    unsigned long long* ninserts = (unsigned long long*)(ctl + CTL_SCR + 6);
-    unsigned long long* applied = (unsigned long long*)(ctl + CTL_SCR + 5);
-    k_validate_stream<<<grid_cap(g, count, 256), 256, 0, s>>>(dups, count, g->n, g->cfg.max_bits,
-                                                                (uint32_t*)(ctl + CTL_STATUS), ninserts);
-    k_stream<<<1, 32, 0, s>>>(g->G, dups, count, g->next_eid, (uint32_t*)g->s_aux.p,
-                              (unsigned long long*)g->s_best.p, (unsigned long long*)(ctl + CTL_STATS), applied);
+    CK(ensure(g->s_rank, 16 * count + 64), "stream scratch");
+    CK(ensure(g->s_keys, 8 * count), "stream scratch");
+    CK(ensure(g->s_keys2, 8 * count), "stream scratch");
+    CK(ensure(g->s_vals, 4 * count), "stream scratch");
+    CK(ensure(g->s_vals2, 4 * count), "stream scratch");
+    CK(ensure(g->s_seg, 8 * count * 2 + 4 * (count + 2) * 3 + 64), "segment scratch");
+    BatchArgs A;
+    A.ups = dups;
+    A.count = count;
+    A.n = g->n;
+    A.max_bits = g->cfg.max_bits;
+    A.bn = bits_for(g->n);
+    A.keys = (uint64_t*)g->s_keys.p;
+    A.vals = (uint32_t*)g->s_vals.p;
+    A.packed = (uint64_t*)g->s_rank.p;
+    A.pscan = A.packed + count;
+    A.status = (uint32_t*)(ctl + CTL_STATUS);
+    uint64_t* total = (uint64_t*)(ctl + CTL_SCR + 4);
+    k_expand<<<grid_cap(g, count, 256), 256, 0, s>>>(A);  // validation + insertion flags
+    CK(scan_excl_u64(A.packed, A.pscan, count, total, g->s_tmp, s, &g->launches), "stream scan");
+    k_stream_keys<<<grid_cap(g, count, 256), 256, 0, s>>>(A);
     g->launches += 2;
+    bool alt = false;
+    CK(radix_sort_pairs(A.keys, A.vals, (uint64_t*)g->s_keys2.p, (uint32_t*)g->s_vals2.p, count, A.bn, g->s_tmp, s,
+                        &alt, &g->launches, A.bn + 1),
+       "stream sort");
+    const uint64_t* skeys = alt ? (uint64_t*)g->s_keys2.p : A.keys;
+    const uint32_t* svals = alt ? (uint32_t*)g->s_vals2.p : A.vals;
+    uint64_t* flag = (uint64_t*)g->s_seg.p;
+    uint64_t* segid = flag + count;
+    uint32_t* seg_start = (uint32_t*)(segid + count);
+    uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
+    k_seg_flags<<<grid_cap(g, count, 256), 256, 0, s>>>(skeys, count, A.bn, flag);
+    CK(scan_excl_u64(flag, segid, count, nseg_dev, g->s_tmp, s, &g->launches), "stream segments");
+    k_seg_write<<<grid_cap(g, count, 256), 256, 0, s>>>(flag, segid, count, seg_start);
+    SegArgs S;
+    memset(&S, 0, sizeof(S));
+    S.B = A;
+    S.sorted_keys = skeys;
+    S.sorted_vals = svals;
+    S.seg_start = seg_start;
+    S.nseg_dev = nseg_dev;
+    S.eid_base = g->next_eid;
+    S.stats = (unsigned long long*)(ctl + CTL_STATS);
+    unsigned long long* reserved = (unsigned long long*)(ctl + CTL_SCR + 7);
+    const unsigned blocks = grid_cap(g, count, STREAM_TEAMS, 8);
+    k_stream_apply<<<blocks, STREAM_TEAMS * 32, 0, s>>>(g->G, S, reserved);
+    g->launches += 3;
     CK(cudaGetLastError(), "stream launch");
     bingo_status st = finish_batch(g, s, stats, 0);
     if (st == BINGO_OK && g->G.eh_mask && g->eh_distinct + (stats ? stats->inserted : count) > (g->G.eh_mask + 1) * 7 / 10) {

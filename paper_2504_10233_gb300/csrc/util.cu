@@ -227,7 +227,8 @@ __global__ void k_rs_scatter(const uint64_t* __restrict__ keys, const uint32_t* 
 }
 
 cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, uint64_t n,
-                             uint32_t bits, Buf& tmp, cudaStream_t s, bool* result_in_alt, uint64_t* launches) {
+                             uint32_t bits, Buf& tmp, cudaStream_t s, bool* result_in_alt, uint64_t* launches,
+                             uint32_t lo_bit) {
     *result_in_alt = false;
     if (n <= 1 || bits == 0) return cudaSuccess;
     const uint64_t nb = (n + RS_TILE - 1) / RS_TILE;
@@ -244,7 +245,7 @@ cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
     uint64_t *ik = keys, *ok = keys_alt;
     uint32_t *iv = vals, *ov = vals_alt;
     bool alt = false;
-    for (uint32_t shift = 0; shift < bits; shift += 8) {
+    for (uint32_t shift = lo_bit; shift < lo_bit + bits; shift += 8) {
         k_rs_hist<<<(unsigned)nb, RS_T, 0, s>>>(ik, n, shift, nb, hist);
         e = scan_excl_u64(hist, offs, nh, nullptr, part, s, launches);
         if (e != cudaSuccess) return e;

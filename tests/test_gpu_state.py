@@ -290,3 +290,38 @@ def test_c2_full_size_first_batches(B):
     for b in wl.batches:
         apply_both(g, og, b.records(), G.max_bits)
     assert_state_matches(g.export_state(), og)
+
+
+def test_pool_exhaustion_rejects_batch_unchanged(B):
+    """A pool sized to the created state leaves no room for growth: a batch that grows vertices must be
+    rejected with BINGO_E_OOM before any change, and the streaming path must stop cleanly."""
+    wl = W.make_workload("c1")
+    G = wl.graph
+    probe = make(B, G)
+    used = probe.export_state()["sizes"]["pool_words_used"]
+    probe.close()
+    g = make(B, G, pool_words=int(used) + 64)
+    before = g.export_state()
+    rng = np.random.default_rng(1)
+    grow = np.array([[v, int(rng.integers(0, G.n)), 1 + int(rng.integers(0, 200)), 0]
+                     for v in range(0, 64) for _ in range(40)], dtype=np.uint32)
+    with pytest.raises(B.BingoError) as ei:
+        g.apply_updates(dev(grow))
+    assert ei.value.status == B.E_OOM
+    after = g.export_state()
+    for k in ("deg", "dst", "bias", "eid", "cnt", "kind", "members", "sp_list"):
+        assert (before[k] == after[k]).all(), k
+    og = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    assert_state_matches(after, og)  # still the created state, exactly
+    import torch
+
+    paths = torch.empty((64, 11), dtype=torch.int32, device="cuda")
+    plen = torch.empty(64, dtype=torch.int32, device="cuda")
+    g.walk(dev(np.arange(64, dtype=np.uint32)), [B.policy(B.DEEPWALK, 10)], 3, 11, paths, plen)
+    g.check()
+    with pytest.raises(B.BingoError) as ei:
+        g.stream_updates(dev(grow))
+    assert ei.value.status == B.E_OOM
+    ex = g.export_state()  # whatever streamed before the stop is complete and consistent
+    from tests.gpu_helpers import check_layout_invariants
+    check_layout_invariants(ex)
