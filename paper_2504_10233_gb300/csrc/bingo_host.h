@@ -28,10 +28,13 @@ cudaError_t scan_excl_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint64_
                           cudaStream_t s, uint64_t* launches);
 
 // stable LSD radix sort of (key u64, value u32) pairs on the low `bits` key bits
-// (sorts the key bits [lo_bit, lo_bit + bits))
+// (sorts the key bits [lo_bit, lo_bit + bits)).  With n_dev, n is a capacity: grids are sized for n
+// and the live length is read from *n_dev on the device (for graph capture).
 cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, uint64_t n,
                              uint32_t bits, Buf& tmp, cudaStream_t s, bool* result_in_alt, uint64_t* launches,
-                             uint32_t lo_bit = 0);
+                             uint32_t lo_bit = 0, const uint64_t* n_dev = nullptr);
+size_t radix_sort_tmp_bytes(uint64_t n);
+size_t scan_tmp_bytes(uint64_t n);
 
 // One walk launch, all pointers on the device.
 struct WalkReq {
@@ -88,6 +91,12 @@ struct bingo_graph {
     bingo::Buf w_starts, w_len, w_pid, w_paths, w_plen, w_pols;
     // walk tuning
     bingo::WalkTune tune;
+    // captured update pipelines: one graph per record capacity (power of two)
+    uint64_t upd_cap = 0;
+    bool upd_graph_eh = false;
+    cudaGraphExec_t upd_graph = nullptr;
+    uint64_t upd_graph_launches = 0;   // kernels per replay
+    cudaStream_t cap_stream = nullptr; // capture stream (the caller's may be the legacy stream)
     uint64_t launches = 0;
     bool broken = false;        // a device-side failure left the state unusable
 };

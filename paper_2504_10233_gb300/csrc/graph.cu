@@ -275,6 +275,8 @@ static unsigned grid_for(const bingo_graph* g, uint64_t work_items, unsigned blo
 
 static void free_graph(bingo_graph* g) {
     if (!g) return;
+    if (g->upd_graph) cudaGraphExecDestroy(g->upd_graph);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     void* ptrs[] = {g->d_hdr, g->d_cold, g->d_pool, g->d_ctl, g->d_fcount, g->d_fstack, g->d_pending, g->d_eh};
     for (void* p : ptrs)
         if (p) cudaFree(p);

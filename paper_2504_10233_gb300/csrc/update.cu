@@ -716,7 +716,8 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
 
 struct BatchArgs {
     const uint4* ups;
-    uint64_t count;
+    uint64_t count;                // record capacity (grid size); the live count is *count_dev when set
+    const uint64_t* count_dev;
     uint32_t n, max_bits, bn;
     uint64_t* keys;
     uint32_t* vals;
@@ -725,10 +726,17 @@ struct BatchArgs {
     uint32_t* status;
 };
 
+__device__ __forceinline__ uint64_t live_count(const BatchArgs& A) { return A.count_dev ? *A.count_dev : A.count; }
+
 __global__ void k_expand(BatchArgs A) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t cnt = live_count(A);
     bool bad = false;
     for (uint64_t i = tid; i < A.count; i += nt) {
+        if (i >= cnt) {  // capacity tail: contributes nothing to the scans
+            A.packed[i] = 0;
+            continue;
+        }
         const uint4 u = A.ups[i];
         const bool ins = u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS;
         const bool del = u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS;
@@ -741,7 +749,8 @@ __global__ void k_expand(BatchArgs A) {
 
 __global__ void k_make_keys(BatchArgs A) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = tid; i < A.count; i += nt) {
+    const uint64_t cnt = live_count(A);
+    for (uint64_t i = tid; i < cnt; i += nt) {
         const uint4 u = A.ups[i];
         if (u.x >= A.n || u.y >= A.n || u.w > 2) continue;
         uint64_t pos = A.pscan[i] & 0xFFFFFFFFull;
@@ -758,15 +767,20 @@ __global__ void k_make_keys(BatchArgs A) {
     }
 }
 
-__global__ void k_seg_flags(const uint64_t* __restrict__ keys, uint64_t nkeys, uint32_t bn, uint64_t* __restrict__ flag) {
+__global__ void k_key_count(const uint64_t* total, uint64_t* nkeys) { *nkeys = *total & 0xFFFFFFFFull; }
+
+__global__ void k_seg_flags(const uint64_t* __restrict__ keys, uint64_t cap, const uint64_t* __restrict__ nkeys_dev,
+                            uint32_t bn, uint64_t* __restrict__ flag) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = tid; i < nkeys; i += nt)
-        flag[i] = (i == 0 || (keys[i] >> (bn + 1)) != (keys[i - 1] >> (bn + 1))) ? 1 : 0;
+    const uint64_t nkeys = nkeys_dev ? *nkeys_dev : cap;
+    for (uint64_t i = tid; i < cap; i += nt)
+        flag[i] = i < nkeys && (i == 0 || (keys[i] >> (bn + 1)) != (keys[i - 1] >> (bn + 1))) ? 1 : 0;
 }
 
-__global__ void k_seg_write(const uint64_t* __restrict__ flag, const uint64_t* __restrict__ segid, uint64_t nkeys,
-                            uint32_t* __restrict__ seg_start) {
+__global__ void k_seg_write(const uint64_t* __restrict__ flag, const uint64_t* __restrict__ segid, uint64_t cap,
+                            const uint64_t* __restrict__ nkeys_dev, uint32_t* __restrict__ seg_start) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t nkeys = nkeys_dev ? *nkeys_dev : cap;
     for (uint64_t i = tid; i < nkeys; i += nt) {
         if (flag[i]) seg_start[segid[i]] = (uint32_t)i;
         if (i == nkeys - 1) seg_start[segid[i] + flag[i]] = (uint32_t)nkeys;
@@ -826,6 +840,7 @@ struct SegArgs {
     unsigned long long* counts;   // [0] small, [1] big, [2] pool bound
     uint32_t big_slots;
     uint64_t eid_base;
+    const unsigned long long* eid_base_dev;  // when set, the edge-id base is read on the device
     uint32_t* holes;
     uint32_t* surv;
     uint32_t* slot_scratch;
@@ -835,12 +850,14 @@ struct SegArgs {
 
 // Per segment: insertion count, and the worst-case pool words the segment may allocate.
 __global__ void k_seg_classify(DevGraph G, SegArgs S) {
+    if (*G.pool.status & ST_STOP) return;  // an invalid batch may carry ids >= n
     const uint64_t nseg = *S.nseg_dev;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     unsigned long long bound = 0;
     for (uint64_t sidx = tid; sidx < nseg; sidx += nt) {
         const uint32_t a = S.seg_start[sidx], b = S.seg_start[sidx + 1];
         const uint32_t v = (uint32_t)(S.sorted_keys[a] >> (S.B.bn + 1));
+        if (v >= G.n) { atomicOr(G.pool.status, ST_INVALID); continue; }
         uint32_t lo = a, hi = b;  // first deletion key
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
@@ -881,7 +898,7 @@ __device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, co
     src.keys = S.sorted_keys;
     src.vals = S.sorted_vals;
     src.rank = S.B.pscan;
-    src.eid_base = S.eid_base;
+    src.eid_base = S.eid_base_dev ? *S.eid_base_dev : S.eid_base;
     src.dmask = (1ull << S.B.bn) - 1;
     src.start = a;
     src.ni = ni;
@@ -940,8 +957,9 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_apply(DevGraph G, SegArgs S, 
 }
 
 // edge-index maintenance: +1 for every insertion record, -1 for every deletion that found an edge
-__global__ void k_eh_apply(DevGraph G, SegArgs S, uint64_t nkeys) {
+__global__ void k_eh_apply(DevGraph G, SegArgs S, uint64_t cap, const uint64_t* nkeys_dev) {
     if (*G.pool.status & ST_STOP) return;
+    const uint64_t nkeys = nkeys_dev ? *nkeys_dev : cap;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = tid; i < nkeys; i += nt) {
         const uint64_t key = S.sorted_keys[i];
@@ -1110,9 +1128,12 @@ static unsigned grid_cap(const bingo_graph* g, uint64_t items, unsigned block, u
     return b ? (unsigned)b : 1u;
 }
 
-static bingo_status finish_batch(bingo_graph* g, cudaStream_t s, bingo_update_stats* stats, uint64_t inserts_expected) {
-    k_finalize_pool<<<1, 1024, 0, s>>>(g->G);
-    g->launches++;
+static bingo_status finish_batch(bingo_graph* g, cudaStream_t s, bingo_update_stats* stats, uint64_t inserts_expected,
+                                 bool finalize = true) {
+    if (finalize) {
+        k_finalize_pool<<<1, 1024, 0, s>>>(g->G);
+        g->launches++;
+    }
     uint32_t status = 0;
     bingo_update_stats tmp;
     bingo_status st = read_stats(g, s, &tmp, &status);
@@ -1144,87 +1165,82 @@ static bingo_status finish_batch(bingo_graph* g, cudaStream_t s, bingo_update_st
     return BINGO_OK;
 }
 
-extern "C" {
+__global__ void k_set_words(uint64_t* w, uint64_t count, uint64_t eid_base) {
+    w[0] = count;
+    w[1] = eid_base;
+}
 
-bingo_status bingo_apply_updates(bingo_graph* g, const bingo_update* ups, uint64_t count, void* stream,
-                                 bingo_update_stats* stats) {
-    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
-    if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
-    if (count && !ups) { set_error("NULL update array"); return BINGO_E_INVALID; }
-    if (count >= 0x7FFFFFFFull) { set_error("batch too large"); return BINGO_E_INVALID; }
-    cudaStream_t s = (cudaStream_t)stream;
+// Scratch sized for `count` records rounded up to a power of two (at least 1,024); reallocation
+// invalidates the captured pipeline.
+static bingo_status update_capacity(bingo_graph* g, uint64_t count) {
+    uint64_t cap = 1024;
+    while (cap < count) cap <<= 1;
+    if (cap <= g->upd_cap) return BINGO_OK;
+    if (g->upd_graph) cudaGraphExecDestroy(g->upd_graph);
+    g->upd_graph = nullptr;
+    cudaDeviceSynchronize();  // buffers may still be read by earlier work
+    const uint64_t kc = 2 * cap;
+    CK(ensure(g->s_in, 16 * cap), "update scratch");
+    CK(ensure(g->s_rank, 16 * cap + 64), "update scratch");
+    CK(ensure(g->s_keys, 8 * kc), "update scratch");
+    CK(ensure(g->s_keys2, 8 * kc), "update scratch");
+    CK(ensure(g->s_vals, 4 * kc), "update scratch");
+    CK(ensure(g->s_vals2, 4 * kc), "update scratch");
+    CK(ensure(g->s_seg, 8 * kc * 2 + 4 * (kc + 2) * 3 + 64), "update scratch");
+    CK(ensure(g->s_aux, 4 * kc * 3 + 64), "update scratch");
+    CK(ensure(g->s_best, 8 * kc + 64), "update scratch");
+    CK(ensure(g->s_tmp, std::max(radix_sort_tmp_bytes(kc), scan_tmp_bytes(kc))), "update scratch");
+    g->upd_cap = cap;
+    return BINGO_OK;
+}
+
+// The whole batch pipeline for a record capacity `cap`, with every size read on the device
+// (record count, key count, segment count, edge-id base), so it can be captured once and replayed.
+static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s) {
     uint64_t* ctl = (uint64_t*)g->d_ctl;
+    const uint64_t kc = 2 * cap;
     CK(cudaMemsetAsync(ctl + CTL_STATUS, 0, 8, s), "status reset");
-    CK(cudaMemsetAsync(ctl + CTL_STATS, 0, (CTL_WORDS - CTL_STATS) * 8, s), "stats reset");
-    if (count == 0) {
-        if (stats) memset(stats, 0, sizeof(*stats));
-        return BINGO_OK;
-    }
-    const uint4* dups = (const uint4*)ups;
-    if (!is_device_ptr(ups)) {
-        CK(ensure(g->s_in, count * 16), "update staging");
-        CK(cudaMemcpyAsync(g->s_in.p, ups, count * 16, cudaMemcpyHostToDevice, s), "update upload");
-        dups = (const uint4*)g->s_in.p;
-    }
-    const uint64_t maxkeys = 2 * count;
-    CK(ensure(g->s_rank, 16 * count + 64), "update scratch");
-    CK(ensure(g->s_keys, 8 * maxkeys), "update scratch");
-    CK(ensure(g->s_keys2, 8 * maxkeys), "update scratch");
-    CK(ensure(g->s_vals, 4 * maxkeys), "update scratch");
-    CK(ensure(g->s_vals2, 4 * maxkeys), "update scratch");
+    CK(cudaMemsetAsync(ctl + CTL_STATS, 0, (CTL_SCR + 8 - CTL_STATS) * 8, s), "stats reset");
     BatchArgs A;
-    A.ups = dups;
-    A.count = count;
+    A.ups = (const uint4*)g->s_in.p;
+    A.count = cap;
+    A.count_dev = ctl + CTL_SCR + 8;
     A.n = g->n;
     A.max_bits = g->cfg.max_bits;
     A.bn = bits_for(g->n);
     A.keys = (uint64_t*)g->s_keys.p;
     A.vals = (uint32_t*)g->s_vals.p;
     A.packed = (uint64_t*)g->s_rank.p;
-    A.pscan = A.packed + count;
+    A.pscan = A.packed + cap;
     A.status = (uint32_t*)(ctl + CTL_STATUS);
-    uint64_t* total = (uint64_t*)(ctl + CTL_SCR + 4);  // scan total
-    k_expand<<<grid_cap(g, count, 256), 256, 0, s>>>(A);
-    CK(scan_excl_u64(A.packed, A.pscan, count, total, g->s_tmp, s, &g->launches), "update scan");
-    k_make_keys<<<grid_cap(g, count, 256), 256, 0, s>>>(A);
-    g->launches += 2;
-    uint64_t tot_host = 0;
-    uint32_t status_host = 0;
-    CK(cudaMemcpyAsync(&tot_host, total, 8, cudaMemcpyDeviceToHost, s), "key count");
-    CK(cudaMemcpyAsync(&status_host, A.status, 4, cudaMemcpyDeviceToHost, s), "status");
-    CK(cudaStreamSynchronize(s), "update expand");
-    CK(cudaMemsetAsync(total, 0, 8, s), "scratch reset");
-    if (status_host & ST_INVALID) {
-        set_error("invalid update record (id >= n, op > 2, or bias outside [1, 2^max_bits)); batch rejected");
-        if (stats) memset(stats, 0, sizeof(*stats));
-        return BINGO_E_INVALID;
-    }
-    const uint64_t nkeys = tot_host & 0xFFFFFFFFull, ninserts = tot_host >> 32;
+    uint64_t* total = (uint64_t*)(ctl + CTL_SCR + 4);  // low 32 bits: key count; high: insertions
+    uint64_t* nkeys_dev = (uint64_t*)(ctl + CTL_SCR + 10);
+    k_expand<<<grid_cap(g, cap, 256), 256, 0, s>>>(A);
+    CK(scan_excl_u64(A.packed, A.pscan, cap, total, g->s_tmp, s, &g->launches), "update scan");
+    k_make_keys<<<grid_cap(g, cap, 256), 256, 0, s>>>(A);
+    k_key_count<<<1, 1, 0, s>>>(total, nkeys_dev);
+    g->launches += 3;
     const uint32_t keybits = 2 * A.bn + 1;
     bool alt = false;
-    CK(radix_sort_pairs(A.keys, A.vals, (uint64_t*)g->s_keys2.p, (uint32_t*)g->s_vals2.p, nkeys, keybits, g->s_tmp, s,
-                        &alt, &g->launches),
+    CK(radix_sort_pairs(A.keys, A.vals, (uint64_t*)g->s_keys2.p, (uint32_t*)g->s_vals2.p, kc, keybits, g->s_tmp, s,
+                        &alt, &g->launches, 0, nkeys_dev),
        "update sort");
     const uint64_t* skeys = alt ? (uint64_t*)g->s_keys2.p : A.keys;
     const uint32_t* svals = alt ? (uint32_t*)g->s_vals2.p : A.vals;
-    // segments
-    CK(ensure(g->s_seg, 8 * nkeys * 2 + 4 * (nkeys + 2) * 3 + 64), "segment scratch");
     uint64_t* flag = (uint64_t*)g->s_seg.p;
-    uint64_t* segid = flag + nkeys;
-    uint32_t* seg_start = (uint32_t*)(segid + nkeys);
-    uint32_t* small_list = seg_start + nkeys + 2;
-    uint32_t* big_list = small_list + nkeys + 2;
+    uint64_t* segid = flag + kc;
+    uint32_t* seg_start = (uint32_t*)(segid + kc);
+    uint32_t* small_list = seg_start + kc + 2;
+    uint32_t* big_list = small_list + kc + 2;
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
-    k_seg_flags<<<grid_cap(g, nkeys, 256), 256, 0, s>>>(skeys, nkeys, A.bn, flag);
-    CK(scan_excl_u64(flag, segid, nkeys, nseg_dev, g->s_tmp, s, &g->launches), "segment scan");
-    k_seg_write<<<grid_cap(g, nkeys, 256), 256, 0, s>>>(flag, segid, nkeys, seg_start);
+    k_seg_flags<<<grid_cap(g, kc, 256), 256, 0, s>>>(skeys, kc, nkeys_dev, A.bn, flag);
+    CK(scan_excl_u64(flag, segid, kc, nseg_dev, g->s_tmp, s, &g->launches), "segment scan");
+    k_seg_write<<<grid_cap(g, kc, 256), 256, 0, s>>>(flag, segid, kc, nkeys_dev, seg_start);
     g->launches += 2;
-    // per-key scratch
-    CK(ensure(g->s_aux, 4 * nkeys * 3 + 64), "apply scratch");
-    CK(ensure(g->s_best, 8 * nkeys + 64), "apply scratch");
     unsigned long long* counts = (unsigned long long*)(ctl + CTL_SCR);  // small, big, pool bound
     CK(cudaMemsetAsync(counts, 0, 24, s), "counts reset");
     SegArgs S;
+    memset(&S, 0, sizeof(S));
     S.B = A;
     S.sorted_keys = skeys;
     S.sorted_vals = svals;
@@ -1233,35 +1249,90 @@ bingo_status bingo_apply_updates(bingo_graph* g, const bingo_update* ups, uint64
     S.small_list = small_list;
     S.big_list = big_list;
     S.counts = counts;
-    S.eid_base = g->next_eid;
+    S.eid_base = 0;
+    S.eid_base_dev = (const unsigned long long*)(ctl + CTL_SCR + 9);
     S.holes = (uint32_t*)g->s_aux.p;
-    S.surv = S.holes + nkeys;
-    S.slot_scratch = S.surv + nkeys;
+    S.surv = S.holes + kc;
+    S.slot_scratch = S.surv + kc;
     S.best = (unsigned long long*)g->s_best.p;
     S.stats = (unsigned long long*)(ctl + CTL_STATS);
-    k_seg_classify<<<grid_cap(g, nkeys, 256), 256, 0, s>>>(g->G, S);
+    k_seg_classify<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S);
     k_oom_check<<<1, 1, 0, s>>>(g->G, counts);
     {
         // big-segment blocks first (at most one per SM), then warp-team blocks for the small segments
-        const uint32_t big_blocks = (uint32_t)std::min<uint64_t>(nkeys, (uint64_t)g->num_sms);
-        const uint64_t small_blocks = std::max<uint64_t>(1, std::min<uint64_t>((nkeys + APPLY_TEAMS - 1) / APPLY_TEAMS,
-                                                                                 (uint64_t)g->num_sms * 8));
+        const uint32_t big_blocks = (uint32_t)std::min<uint64_t>(kc, (uint64_t)g->num_sms);
+        const uint64_t small_blocks =
+            std::max<uint64_t>(1, std::min<uint64_t>((kc + APPLY_TEAMS - 1) / APPLY_TEAMS, (uint64_t)g->num_sms * 8));
         k_apply<<<(unsigned)(big_blocks + small_blocks), APPLY_THREADS, 0, s>>>(g->G, S, big_blocks);
     }
     g->launches += 3;
     if (g->G.eh_mask) {
-        k_eh_apply<<<grid_cap(g, nkeys, 256), 256, 0, s>>>(g->G, S, nkeys);
+        k_eh_apply<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S, kc, nkeys_dev);
         g->launches++;
     }
+    k_finalize_pool<<<1, 1024, 0, s>>>(g->G);
+    g->launches++;
     CK(cudaGetLastError(), "update launch");
-    // scratch words used above live in the stats area; clear them before reporting
-    bingo_status st = finish_batch(g, s, stats, ninserts);
-    if (st == BINGO_OK && g->G.eh_mask && g->eh_distinct + ninserts > (g->G.eh_mask + 1) * 7 / 10) {
-        g->eh_distinct += ninserts;
-        st = edge_index_build(g, s);
+    return BINGO_OK;
+}
+
+extern "C" {
+
+bingo_status bingo_apply_updates(bingo_graph* g, const bingo_update* ups, uint64_t count, void* stream,
+                                 bingo_update_stats* stats) {
+    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+    if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
+    if (count && !ups) { set_error("NULL update array"); return BINGO_E_INVALID; }
+    if (count >= 0x3FFFFFFFull) { set_error("batch too large"); return BINGO_E_INVALID; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (count == 0) {
+        if (stats) memset(stats, 0, sizeof(*stats));
+        return BINGO_OK;
+    }
+    bingo_status st = update_capacity(g, count);
+    if (st != BINGO_OK) return st;
+    // the batch goes into the pipeline's fixed input buffer; count and edge-id base into device words
+    CK(cudaMemcpyAsync(g->s_in.p, ups, count * 16, is_device_ptr(ups) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       s),
+       "update upload");
+    uint64_t* ctl = (uint64_t*)g->d_ctl;
+    k_set_words<<<1, 1, 0, s>>>(ctl + CTL_SCR + 8, count, g->next_eid);
+    g->launches++;
+    const bool has_eh = g->G.eh_mask != 0;
+    if (!g->upd_graph || g->upd_graph_eh != has_eh) {
+        if (g->upd_graph) cudaGraphExecDestroy(g->upd_graph);
+        g->upd_graph = nullptr;
+        if (!g->cap_stream) CK(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking), "capture stream");
+        const uint64_t l0 = g->launches;
+        CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal), "update capture");
+        const bingo_status est = enqueue_updates(g, g->upd_cap, g->cap_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(g->cap_stream, &graph);
+        if (est != BINGO_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return est;
+        }
+        CK(ce, "update capture");
+        cudaError_t ie = cudaGraphInstantiate(&g->upd_graph, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie, "update graph instantiate");
+        g->upd_graph_eh = has_eh;
+        g->upd_graph_launches = g->launches - l0;
+        g->launches = l0;
+    }
+    CK(cudaGraphLaunch(g->upd_graph, s), "update graph launch");
+    g->launches += g->upd_graph_launches;
+    bingo_update_stats local;
+    if (!stats) stats = &local;
+    st = finish_batch(g, s, stats, 0, false);
+    if (st == BINGO_OK && g->G.eh_mask && stats && g->eh_distinct + stats->inserted > (g->G.eh_mask + 1) * 7 / 10) {
+        g->eh_distinct += stats->inserted;
+        st = edge_index_build(g, s);  // new edge-index pointers: the captured pipeline is re-captured
+        if (g->upd_graph) cudaGraphExecDestroy(g->upd_graph);
+        g->upd_graph = nullptr;
         if (st == BINGO_OK) CK(cudaStreamSynchronize(s), "edge index rebuild");
-    } else if (st == BINGO_OK) {
-        g->eh_distinct += ninserts;
+    } else if (st == BINGO_OK && stats) {
+        g->eh_distinct += stats->inserted;
     }
     return st;
 }
@@ -1295,6 +1366,7 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     BatchArgs A;
     A.ups = dups;
     A.count = count;
+    A.count_dev = nullptr;
     A.n = g->n;
     A.max_bits = g->cfg.max_bits;
     A.bn = bits_for(g->n);
@@ -1318,9 +1390,9 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     uint64_t* segid = flag + count;
     uint32_t* seg_start = (uint32_t*)(segid + count);
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
-    k_seg_flags<<<grid_cap(g, count, 256), 256, 0, s>>>(skeys, count, A.bn, flag);
+    k_seg_flags<<<grid_cap(g, count, 256), 256, 0, s>>>(skeys, count, nullptr, A.bn, flag);
     CK(scan_excl_u64(flag, segid, count, nseg_dev, g->s_tmp, s, &g->launches), "stream segments");
-    k_seg_write<<<grid_cap(g, count, 256), 256, 0, s>>>(flag, segid, count, seg_start);
+    k_seg_write<<<grid_cap(g, count, 256), 256, 0, s>>>(flag, segid, count, nullptr, seg_start);
     SegArgs S;
     memset(&S, 0, sizeof(S));
     S.B = A;
@@ -1329,6 +1401,7 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     S.seg_start = seg_start;
     S.nseg_dev = nseg_dev;
     S.eid_base = g->next_eid;
+    S.eid_base_dev = nullptr;
     S.stats = (unsigned long long*)(ctl + CTL_STATS);
     unsigned long long* reserved = (unsigned long long*)(ctl + CTL_SCR + 7);
     const unsigned blocks = grid_cap(g, count, STREAM_TEAMS, 8);

@@ -166,9 +166,10 @@ constexpr int RS_I = 8;
 constexpr uint32_t RS_TILE = RS_T * RS_I;
 constexpr int RS_BINS = 256;
 
-__global__ void k_rs_hist(const uint64_t* __restrict__ keys, uint64_t n, uint32_t shift, uint64_t nblocks,
-                          uint64_t* __restrict__ hist) {
+__global__ void k_rs_hist(const uint64_t* __restrict__ keys, uint64_t n_host, const uint64_t* __restrict__ n_dev,
+                          uint32_t shift, uint64_t nblocks, uint64_t* __restrict__ hist) {
     __shared__ uint32_t h[RS_BINS];
+    const uint64_t n = n_dev ? *n_dev : n_host;
     h[threadIdx.x] = 0;
     __syncthreads();
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
@@ -182,9 +183,11 @@ __global__ void k_rs_hist(const uint64_t* __restrict__ keys, uint64_t n, uint32_
 }
 
 // Stable scatter: keys of the tile are ranked in index order, round by round.
-__global__ void k_rs_scatter(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t n,
-                             uint32_t shift, uint64_t nblocks, const uint64_t* __restrict__ offs,
-                             uint64_t* __restrict__ okeys, uint32_t* __restrict__ ovals) {
+__global__ void k_rs_scatter(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t n_host,
+                             const uint64_t* __restrict__ n_dev, uint32_t shift, uint64_t nblocks,
+                             const uint64_t* __restrict__ offs, uint64_t* __restrict__ okeys,
+                             uint32_t* __restrict__ ovals) {
+    const uint64_t n = n_dev ? *n_dev : n_host;
     __shared__ uint64_t base[RS_BINS];
     __shared__ uint32_t wc[RS_T / 32][RS_BINS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -226,16 +229,25 @@ __global__ void k_rs_scatter(const uint64_t* __restrict__ keys, const uint32_t* 
     (void)lane;
 }
 
+size_t radix_sort_tmp_bytes(uint64_t n) {
+    const uint64_t nb = (n + RS_TILE - 1) / RS_TILE;
+    const uint64_t nh = nb * RS_BINS;
+    const uint64_t nscan_parts = (nh + SCAN_TILE - 1) / SCAN_TILE;
+    return (2 * nh + nscan_parts + 8) * sizeof(uint64_t);
+}
+
+size_t scan_tmp_bytes(uint64_t n) { return ((n + SCAN_TILE - 1) / SCAN_TILE + 8) * sizeof(uint64_t); }
+
 cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, uint64_t n,
                              uint32_t bits, Buf& tmp, cudaStream_t s, bool* result_in_alt, uint64_t* launches,
-                             uint32_t lo_bit) {
+                             uint32_t lo_bit, const uint64_t* n_dev) {
     *result_in_alt = false;
-    if (n <= 1 || bits == 0) return cudaSuccess;
+    if ((n <= 1 && !n_dev) || bits == 0) return cudaSuccess;
     const uint64_t nb = (n + RS_TILE - 1) / RS_TILE;
     const uint64_t nh = nb * RS_BINS;
     const uint64_t nscan_parts = (nh + SCAN_TILE - 1) / SCAN_TILE;
     // tmp layout: hist [nh] | offs [nh] | scan parts
-    cudaError_t e = ensure(tmp, (2 * nh + nscan_parts + 8) * sizeof(uint64_t));
+    cudaError_t e = ensure(tmp, radix_sort_tmp_bytes(n));
     if (e != cudaSuccess) return e;
     uint64_t* hist = (uint64_t*)tmp.p;
     uint64_t* offs = hist + nh;
@@ -246,10 +258,10 @@ cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
     uint32_t *iv = vals, *ov = vals_alt;
     bool alt = false;
     for (uint32_t shift = lo_bit; shift < lo_bit + bits; shift += 8) {
-        k_rs_hist<<<(unsigned)nb, RS_T, 0, s>>>(ik, n, shift, nb, hist);
+        k_rs_hist<<<(unsigned)nb, RS_T, 0, s>>>(ik, n, n_dev, shift, nb, hist);
         e = scan_excl_u64(hist, offs, nh, nullptr, part, s, launches);
         if (e != cudaSuccess) return e;
-        k_rs_scatter<<<(unsigned)nb, RS_T, 0, s>>>(ik, iv, n, shift, nb, offs, ok, ov);
+        k_rs_scatter<<<(unsigned)nb, RS_T, 0, s>>>(ik, iv, n, n_dev, shift, nb, offs, ok, ov);
         if (launches) *launches += 2;
         uint64_t* tk = ik; ik = ok; ok = tk;
         uint32_t* tv = iv; iv = ov; ov = tv;
