@@ -72,6 +72,7 @@ struct bingo_graph {
     bingo_config cfg;
     int device = 0;
     int num_sms = 0;
+    unsigned apply_blocks = 0;  // resident k_apply blocks (persistent grid)
     uint32_t n = 0;
     uint64_t m_live = 0;
     uint64_t next_eid = 0;
@@ -88,6 +89,7 @@ struct bingo_graph {
     uint64_t eh_distinct = 0;   // keys ever placed in the edge index (tombstones included)
     // scratch
     bingo::Buf s_in, s_keys, s_keys2, s_vals, s_vals2, s_tmp, s_seg, s_rank, s_best, s_aux, s_walk, s_stage;
+    bingo::Buf s_rec, s_seginfo;  // sorted insertion records, per-segment {v, first key, ni, nd}
     bingo::Buf w_starts, w_len, w_pid, w_paths, w_plen, w_pols;
     // walk tuning
     bingo::WalkTune tune;

@@ -8,21 +8,26 @@
 
 namespace bingo {
 
-// Order-preserving team compaction over [0, n): each thread tests IT consecutive elements per
-// chunk (their loads in flight together), one team scan per chunk of IT * team size, and
-// emit(j, position) for every j with pred(j) true, positions ascending with j.  Returns the count.
+// Order-preserving team compaction over [0, n): each thread takes IT consecutive elements per chunk,
+// one team scan per chunk of IT * team size, and emit(j, position) for every j whose test passes,
+// positions ascending with j.  Returns the count.  load(j) reads what the test of element j needs;
+// the IT loads of a thread are issued before any test (indexes clamped into [0, n), the tail masked
+// afterwards), so they are in flight together instead of one dependent round trip per element.
 constexpr int COMPACT_IT = 8;
-template <class Team, class Pred, class Emit>
-__device__ __forceinline__ uint32_t team_compact(const Team& t, uint32_t n, Pred pred, Emit emit) {
+template <class Team, class Load, class Test, class Emit>
+__device__ __forceinline__ uint32_t team_compact_lt(const Team& t, uint32_t n, Load load, Test test, Emit emit) {
     uint32_t pos = 0;
     const uint32_t chunk = COMPACT_IT * t.size();
     for (uint32_t base = 0; base < n; base += chunk) {
         const uint32_t j0 = base + t.rank() * COMPACT_IT;
+        decltype(load(0u)) x[COMPACT_IT];
+#pragma unroll
+        for (int q = 0; q < COMPACT_IT; q++) x[q] = load(min(j0 + q, n - 1));
         bool p[COMPACT_IT];
         uint32_t c = 0;
 #pragma unroll
         for (int q = 0; q < COMPACT_IT; q++) {
-            p[q] = (j0 + q < n) && pred(j0 + q);
+            p[q] = (j0 + q < n) && test(x[q], j0 + q);
             c += p[q] ? 1u : 0u;
         }
         uint32_t tot;
@@ -33,6 +38,12 @@ __device__ __forceinline__ uint32_t team_compact(const Team& t, uint32_t n, Pred
         pos += tot;
     }
     return pos;
+}
+// The same with a predicate that is cheap to evaluate once its operand is loaded.
+template <class Team, class Pred, class Emit>
+__device__ __forceinline__ uint32_t team_compact(const Team& t, uint32_t n, Pred pred, Emit emit) {
+    return team_compact_lt(
+        t, n, [&](uint32_t j) { return pred(j); }, [](bool v, uint32_t) { return v; }, emit);
 }
 
 // Group blocks hold [member destinations | member list | inverted index | spare], cap words each:
@@ -95,10 +106,13 @@ __device__ uint32_t find_one(const Team& t, const DevGraph& G, uint64_t adj, uin
     const uint32_t chunk = COMPACT_IT * t.size();
     for (uint32_t base = 0; base < d; base += chunk) {
         const uint32_t j0 = base + t.rank() * COMPACT_IT;
+        uint32_t w[COMPACT_IT];
+#pragma unroll
+        for (int q = 0; q < COMPACT_IT; q++) w[q] = pairs[min(j0 + q, d - 1)].y;
         uint32_t cand = NONE32;
 #pragma unroll
         for (int q = COMPACT_IT - 1; q >= 0; q--)
-            if (j0 + q < d && ((pairs[j0 + q].y >> k) & 1u)) cand = j0 + q;
+            if (j0 + q < d && ((w[q] >> k) & 1u)) cand = j0 + q;
         const uint32_t m = ~t.max(~cand);  // team minimum
         if (m != NONE32) return m;         // team-uniform
     }

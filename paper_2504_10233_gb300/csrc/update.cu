@@ -38,17 +38,17 @@ enum { S_INS = 0, S_DEL = 1, S_NF = 2, S_TOUCH = 3, S_REBUILT = 4, S_CONV = 5 };
 
 // Source of a segment's records: insertions (dst, bias, edge id) and deletions (dst, sorted ascending).
 struct BatchSrc {
-    const uint4* ups;
+    const uint4* rec;      // per insertion key: {edge id low, dst, bias, edge id high}
     const uint64_t* keys;
-    const uint32_t* vals;
-    const uint64_t* rank;  // packed scan: high 32 bits = insert rank
-    uint64_t eid_base;
     uint64_t dmask;
     uint64_t start;  // first key of the segment
     uint32_t ni;
     const uint32_t* sdel;  // deletion destinations staged in shared memory (nullable)
-    __device__ __forceinline__ uint4 ins(uint32_t i) const { return ups[vals[start + i]]; }
-    __device__ __forceinline__ uint64_t ins_eid(uint32_t i) const { return eid_base + (rank[vals[start + i]] >> 32); }
+    __device__ __forceinline__ uint4 ins(uint32_t i) const { return rec[start + i]; }
+    __device__ __forceinline__ uint64_t ins_eid(uint32_t i) const {
+        const uint4 r = rec[start + i];
+        return (uint64_t)r.x | ((uint64_t)r.w << 32);
+    }
     __device__ __forceinline__ uint32_t del_dst_global(uint32_t j) const {
         return (uint32_t)(keys[start + ni + j] & dmask);
     }
@@ -299,11 +299,11 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
         uint32_t ncand = 0;
         bool use_cand = cand_buf != nullptr;
         if (use_cand) {
-            ncand = team_compact(
-                t, dtot,
-                [&](uint32_t j) {
-                    if (eids[j] & DEAD_BIT) return false;
-                    const uint32_t x = pairs[j].x;
+            ncand = team_compact_lt(
+                t, dtot, [&](uint32_t j) { return make_uint2(pairs[j].x, (uint32_t)(eids[j] >> 32)); },
+                [&](uint2 xe, uint32_t) {
+                    if (xe.y & (uint32_t)(DEAD_BIT >> 32)) return false;
+                    const uint32_t x = xe.x;
                     uint32_t lo = 0, hi = nd;
                     while (lo < hi) {
                         const uint32_t mid = (lo + hi) >> 1;
@@ -769,12 +769,26 @@ __global__ void k_make_keys(BatchArgs A) {
 
 __global__ void k_key_count(const uint64_t* total, uint64_t* nkeys) { *nkeys = *total & 0xFFFFFFFFull; }
 
-__global__ void k_seg_flags(const uint64_t* __restrict__ keys, uint64_t cap, const uint64_t* __restrict__ nkeys_dev,
-                            uint32_t bn, uint64_t* __restrict__ flag) {
+// Segment heads of the sorted keys; for each insertion key, the record it applies in key order
+// ({edge id low, dst, bias, edge id high}, the edge id from the insertion's batch rank), so the
+// per-vertex pass reads its insertions contiguously.
+__global__ void k_seg_flags(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t cap,
+                            const uint64_t* __restrict__ nkeys_dev, uint32_t bn, const uint4* __restrict__ ups,
+                            const uint64_t* __restrict__ pscan, const unsigned long long* __restrict__ eid_base,
+                            uint64_t* __restrict__ flag, uint4* __restrict__ rec) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t nkeys = nkeys_dev ? *nkeys_dev : cap;
-    for (uint64_t i = tid; i < cap; i += nt)
-        flag[i] = i < nkeys && (i == 0 || (keys[i] >> (bn + 1)) != (keys[i - 1] >> (bn + 1))) ? 1 : 0;
+    for (uint64_t i = tid; i < cap; i += nt) {
+        const bool live = i < nkeys;
+        const uint64_t k = live ? keys[i] : 0;
+        flag[i] = live && (i == 0 || (k >> (bn + 1)) != (keys[i - 1] >> (bn + 1))) ? 1 : 0;
+        if (rec && live && !((k >> bn) & 1ull)) {
+            const uint32_t r = vals[i];
+            const uint4 u = ups[r];
+            const uint64_t eid = *eid_base + (pscan[r] >> 32);
+            rec[i] = make_uint4((uint32_t)eid, u.y, u.z, (uint32_t)(eid >> 32));
+        }
+    }
 }
 
 __global__ void k_seg_write(const uint64_t* __restrict__ flag, const uint64_t* __restrict__ segid, uint64_t cap,
@@ -838,7 +852,9 @@ struct SegArgs {
     uint32_t* small_list;
     uint32_t* big_list;
     unsigned long long* counts;   // [0] small, [1] big, [2] pool bound
-    uint32_t big_slots;
+    unsigned long long* queue;    // [0] next small segment, [1] next big segment (k_apply work queues)
+    uint4* rec;                   // per key: the insertion record {edge id low, dst, bias, edge id high}
+    uint4* seginfo;               // per segment: {v, first key, ni, nd}
     uint64_t eid_base;
     const unsigned long long* eid_base_dev;  // when set, the edge-id base is read on the device
     uint32_t* holes;
@@ -864,10 +880,11 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
             if ((S.sorted_keys[mid] >> S.B.bn) & 1ull) hi = mid; else lo = mid + 1;
         }
         const uint32_t ni = lo - a;
+        S.seginfo[sidx] = make_uint4(v, a, ni, b - lo);
         const VHdr h = load_hdr(G, v);
         const uint32_t dtot = h.deg + ni;
         uint32_t insbits = 0;
-        for (uint32_t i = a; i < lo; i++) insbits |= S.B.ups[S.sorted_vals[i]].z;
+        for (uint32_t i = a; i < lo; i++) insbits |= S.rec[i].z;
         bound += pool_bound(G, v, h, ni, b - lo, insbits);
         const bool big = dtot > 4096 || (b - a) > 256;
         if (big) S.big_list[atomicAdd(&S.counts[1], 1ull)] = (uint32_t)sidx;
@@ -876,40 +893,50 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
     if (bound) atomicAdd(&S.counts[2], bound);
 }
 
-__global__ void k_oom_check(DevGraph G, const unsigned long long* counts) {
+__global__ void k_oom_check(DevGraph G, const unsigned long long* counts, unsigned long long* queue) {
     const unsigned long long top = *G.pool.top;
     if (top + counts[2] > G.pool.words) atomicOr(G.pool.status, ST_OOM);
+    queue[0] = 0;
+    queue[1] = 0;
 }
+
+// Per-team scratch in shared memory for segments of at most SMALL_X insertions and deletions, so the
+// per-deletion and per-slot lists between phases stay on the SM instead of round-tripping to L2.
+constexpr uint32_t SMALL_X = 32;
+struct SmallScratch {
+    uint32_t holes[SMALL_X], surv[SMALL_X], ins_final[SMALL_X], del_slot[SMALL_X];
+    unsigned long long best[SMALL_X];
+};
 
 template <class Team>
 __device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, const SegArgs& S, SegSh& sh, uint32_t sidx,
                                             uint32_t* sdel_buf, uint32_t sdel_cap, uint32_t* cand_buf,
-                                            uint32_t cand_cap) {
-    const uint32_t a = S.seg_start[sidx], b = S.seg_start[sidx + 1];
-    const uint32_t v = (uint32_t)(S.sorted_keys[a] >> (S.B.bn + 1));
-    uint32_t lo = a, hi = b;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if ((S.sorted_keys[mid] >> S.B.bn) & 1ull) hi = mid; else lo = mid + 1;
-    }
-    const uint32_t ni = lo - a, nd = b - lo;
+                                            uint32_t cand_cap, SmallScratch* sx = nullptr,
+                                            unsigned long long* stats = nullptr) {
+    const uint4 info = S.seginfo[sidx];
+    const uint32_t v = info.x, a = info.y, ni = info.z, nd = info.w;
     BatchSrc src;
-    src.ups = S.B.ups;
+    src.rec = S.rec;
     src.keys = S.sorted_keys;
-    src.vals = S.sorted_vals;
-    src.rank = S.B.pscan;
-    src.eid_base = S.eid_base_dev ? *S.eid_base_dev : S.eid_base;
     src.dmask = (1ull << S.B.bn) - 1;
     src.start = a;
     src.ni = ni;
     SegScratch X;
-    X.holes = S.holes + a;
-    X.surv = S.surv + a;
-    X.ins_final = S.slot_scratch + a;
-    X.del_slot = S.slot_scratch + a + ni;
-    X.best = S.best + a + ni;
+    if (sx && ni <= SMALL_X && nd <= SMALL_X) {
+        X.holes = sx->holes;
+        X.surv = sx->surv;
+        X.ins_final = sx->ins_final;
+        X.del_slot = sx->del_slot;
+        X.best = sx->best;
+    } else {
+        X.holes = S.holes + a;
+        X.surv = S.surv + a;
+        X.ins_final = S.slot_scratch + a;
+        X.del_slot = S.slot_scratch + a + ni;
+        X.best = S.best + a + ni;
+    }
     src.sdel = nullptr;
-    apply_segment(t, G, sh, v, ni, nd, src, X, S.stats, sdel_buf, sdel_cap, cand_buf, cand_cap);
+    apply_segment(t, G, sh, v, ni, nd, src, X, stats ? stats : S.stats, sdel_buf, sdel_cap, cand_buf, cand_cap);
 }
 
 constexpr uint32_t SMALL_SDEL = 64;    // staged deletion destinations per warp team
@@ -919,9 +946,10 @@ constexpr uint32_t BIG_CAND = 4096;
 constexpr uint32_t APPLY_THREADS = 512;
 constexpr uint32_t APPLY_TEAMS = APPLY_THREADS / 32;
 
-// One launch for every segment: the first `nbig` blocks each take a big segment as one 512-thread
-// team (dispatched first, they are the long poles); the remaining blocks run 16 warp teams each
-// over the small segments.
+// One persistent launch for every segment (grid = resident blocks).  Each block first takes big
+// segments, one at a time as a 512-thread team, from a shared queue (they are the long poles, so
+// they start first); when that queue is empty its 16 warps become warp teams that pull small
+// segments one by one, so no warp idles while work is left.
 struct BigShared {
     SegSh sh;
     uint32_t sdel[BIG_SDEL];
@@ -931,29 +959,48 @@ struct SmallShared {
     SegSh sh[APPLY_TEAMS];
     uint32_t sdel[APPLY_TEAMS][SMALL_SDEL];
     uint32_t cand[APPLY_TEAMS][SMALL_CAND];
+    SmallScratch x[APPLY_TEAMS];
 };
 union ApplyShared {
     BigShared big;
     SmallShared small;
 };
 
-__global__ void __launch_bounds__(APPLY_THREADS) k_apply(DevGraph G, SegArgs S, uint32_t big_blocks) {
+__global__ void __launch_bounds__(APPLY_THREADS, 2) k_apply(DevGraph G, SegArgs S) {
     __shared__ ApplyShared smem;
-    if (*G.pool.status & ST_STOP) return;
+    __shared__ unsigned long long next;
+    __shared__ unsigned long long bstats[S_CONV + 25];  // block totals, added to the batch's once at the end
+    for (uint32_t i = threadIdx.x; i < S_CONV + 25; i += blockDim.x) bstats[i] = 0;
     const unsigned long long nbig = S.counts[1], nsmall = S.counts[0];
-    if (blockIdx.x < big_blocks) {
+    {
         BlockTeam t;
         t.sm = smem.big.sh.tscratch;
-        for (uint64_t i = blockIdx.x; i < nbig; i += big_blocks)
-            run_segment(t, G, S, smem.big.sh, S.big_list[i], smem.big.sdel, BIG_SDEL, smem.big.cand, BIG_CAND);
-        return;
+        for (;;) {
+            if (threadIdx.x == 0)
+                next = (*(volatile uint32_t*)G.pool.status & ST_STOP) ? nbig : atomicAdd(S.queue + 1, 1ull);
+            __syncthreads();
+            const unsigned long long i = next;
+            __syncthreads();
+            if (i >= nbig) break;
+            run_segment(t, G, S, smem.big.sh, S.big_list[i], smem.big.sdel, BIG_SDEL, smem.big.cand, BIG_CAND, nullptr,
+                        bstats);
+        }
     }
-    const uint32_t w = threadIdx.x >> 5;
-    const uint64_t nblk = gridDim.x - big_blocks;
+    __syncthreads();  // shared memory changes from the big-segment to the warp-team layout
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpTeam t;
-    for (uint64_t i = (uint64_t)(blockIdx.x - big_blocks) * APPLY_TEAMS + w; i < nsmall; i += nblk * APPLY_TEAMS)
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0)
+            i = (*(volatile uint32_t*)G.pool.status & ST_STOP) ? nsmall : atomicAdd(S.queue, 1ull);
+        i = __shfl_sync(FULL, i, 0);
+        if (i >= nsmall) break;
         run_segment(t, G, S, smem.small.sh[w], S.small_list[i], smem.small.sdel[w], SMALL_SDEL, smem.small.cand[w],
-                    SMALL_CAND);
+                    SMALL_CAND, &smem.small.x[w], bstats);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < S_CONV + 25; i += blockDim.x)
+        if (bstats[i]) atomicAdd(S.stats + i, bstats[i]);
 }
 
 // edge-index maintenance: +1 for every insertion record, -1 for every deletion that found an edge
@@ -1189,7 +1236,14 @@ static bingo_status update_capacity(bingo_graph* g, uint64_t count) {
     CK(ensure(g->s_seg, 8 * kc * 2 + 4 * (kc + 2) * 3 + 64), "update scratch");
     CK(ensure(g->s_aux, 4 * kc * 3 + 64), "update scratch");
     CK(ensure(g->s_best, 8 * kc + 64), "update scratch");
+    CK(ensure(g->s_rec, 16 * kc), "update scratch");
+    CK(ensure(g->s_seginfo, 16 * kc + 16), "update scratch");
     CK(ensure(g->s_tmp, std::max(radix_sort_tmp_bytes(kc), scan_tmp_bytes(kc))), "update scratch");
+    if (!g->apply_blocks) {
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply, APPLY_THREADS, 0), "apply occupancy");
+        g->apply_blocks = (unsigned)std::max(1, per_sm) * (unsigned)g->num_sms;
+    }
     g->upd_cap = cap;
     return BINGO_OK;
 }
@@ -1233,7 +1287,9 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     uint32_t* small_list = seg_start + kc + 2;
     uint32_t* big_list = small_list + kc + 2;
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
-    k_seg_flags<<<grid_cap(g, kc, 256), 256, 0, s>>>(skeys, kc, nkeys_dev, A.bn, flag);
+    k_seg_flags<<<grid_cap(g, kc, 256), 256, 0, s>>>(skeys, svals, kc, nkeys_dev, A.bn, A.ups, A.pscan,
+                                                     (const unsigned long long*)(ctl + CTL_SCR + 9), flag,
+                                                     (uint4*)g->s_rec.p);
     CK(scan_excl_u64(flag, segid, kc, nseg_dev, g->s_tmp, s, &g->launches), "segment scan");
     k_seg_write<<<grid_cap(g, kc, 256), 256, 0, s>>>(flag, segid, kc, nkeys_dev, seg_start);
     g->launches += 2;
@@ -1251,20 +1307,17 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     S.counts = counts;
     S.eid_base = 0;
     S.eid_base_dev = (const unsigned long long*)(ctl + CTL_SCR + 9);
+    S.rec = (uint4*)g->s_rec.p;
+    S.seginfo = (uint4*)g->s_seginfo.p;
     S.holes = (uint32_t*)g->s_aux.p;
     S.surv = S.holes + kc;
     S.slot_scratch = S.surv + kc;
     S.best = (unsigned long long*)g->s_best.p;
     S.stats = (unsigned long long*)(ctl + CTL_STATS);
     k_seg_classify<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S);
-    k_oom_check<<<1, 1, 0, s>>>(g->G, counts);
-    {
-        // big-segment blocks first (at most one per SM), then warp-team blocks for the small segments
-        const uint32_t big_blocks = (uint32_t)std::min<uint64_t>(kc, (uint64_t)g->num_sms);
-        const uint64_t small_blocks =
-            std::max<uint64_t>(1, std::min<uint64_t>((kc + APPLY_TEAMS - 1) / APPLY_TEAMS, (uint64_t)g->num_sms * 8));
-        k_apply<<<(unsigned)(big_blocks + small_blocks), APPLY_THREADS, 0, s>>>(g->G, S, big_blocks);
-    }
+    S.queue = (unsigned long long*)(ctl + CTL_SCR + 11);
+    k_oom_check<<<1, 1, 0, s>>>(g->G, counts, S.queue);
+    k_apply<<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
     g->launches += 3;
     if (g->G.eh_mask) {
         k_eh_apply<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S, kc, nkeys_dev);
@@ -1390,7 +1443,8 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     uint64_t* segid = flag + count;
     uint32_t* seg_start = (uint32_t*)(segid + count);
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
-    k_seg_flags<<<grid_cap(g, count, 256), 256, 0, s>>>(skeys, count, nullptr, A.bn, flag);
+    k_seg_flags<<<grid_cap(g, count, 256), 256, 0, s>>>(skeys, svals, count, nullptr, A.bn, A.ups, A.pscan, nullptr,
+                                                        flag, nullptr);
     CK(scan_excl_u64(flag, segid, count, nseg_dev, g->s_tmp, s, &g->launches), "stream segments");
     k_seg_write<<<grid_cap(g, count, 256), 256, 0, s>>>(flag, segid, count, nullptr, seg_start);
     SegArgs S;

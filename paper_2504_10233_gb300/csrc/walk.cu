@@ -77,6 +77,18 @@ __device__ __forceinline__ void walker_stream(const WalkParams& A, uint64_t wid,
     }
 }
 
+// Hot lines are re-read at every visit of their vertex, while member reads and path stores mostly
+// touch a line once: hot-line loads carry an L2 evict-last policy.
+__device__ __forceinline__ uint4 ld_hot(const uint4* q) {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    uint4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(q), "l"(pol));
+    return r;
+}
+
 // Hot part of a vertex record: the header and groups 0-5 (pairs 0-2), one 64-byte line.
 struct Sec0 {
     uint32_t adj, deg, mask, sref;
@@ -84,20 +96,20 @@ struct Sec0 {
 };
 __device__ __forceinline__ Sec0 ld_sec0(const DevGraph& G, uint32_t v) {
     const uint4* q = reinterpret_cast<const uint4*>(G.vh + v);
-    const uint4 a = __ldg(q);
+    const uint4 a = ld_hot(q);
     Sec0 s;
     s.adj = a.x;
     s.deg = a.y;
     s.mask = a.z;
     s.sref = a.w;
-    s.p0 = __ldg(q + 1);
-    s.p1 = __ldg(q + 2);
-    s.p2 = __ldg(q + 3);
+    s.p0 = ld_hot(q + 1);
+    s.p1 = ld_hot(q + 2);
+    s.p2 = ld_hot(q + 3);
     return s;
 }
 // Groups 2i and 2i+1 of vertex v as {c_2i, ref_2i, c_2i+1, ref_2i+1} (16-byte aligned).
 __device__ __forceinline__ uint4 ld_pair(const DevGraph& G, uint32_t v, uint32_t i) {
-    if (i < HOT_GROUPS / 2) return __ldg(reinterpret_cast<const uint4*>(G.vh + v) + 1 + i);
+    if (i < HOT_GROUPS / 2) return ld_hot(reinterpret_cast<const uint4*>(G.vh + v) + 1 + i);
     return __ldg(reinterpret_cast<const uint4*>(G.vc + v) + (i - HOT_GROUPS / 2));
 }
 __device__ __forceinline__ uint64_t pair_w(uint4 x, uint32_t i) {
