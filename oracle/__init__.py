@@ -72,6 +72,8 @@ def _L():
                 "o_sample_many": (None, [c.c_void_p, c.c_uint32, c.c_uint64, c.c_uint64, U64P]),
                 "o_num_threads": (c.c_int, []),
                 "o_float_factor": (None, [c.c_uint64, DP, c.c_double, U32P, U64P, DP, DP]),
+                "o_set_lambda": (c.c_int, [c.c_void_p, c.c_double]),
+                "o_export_real": (None, [c.c_void_p, U32P, U32P, U64P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -149,6 +151,21 @@ class Graph:
         st = np.zeros(3, dtype=np.uint64)
         rc = _L().o_apply(self._h, _p(r), r.shape[0], max_bits, _p(st))
         return rc, tuple(int(x) for x in st)
+
+    def set_lambda(self, lam: float) -> int:
+        """Real-valued biases (Section 4.3): stored words are binary32 encodings, weights
+        2^8 floor(lam b) + floor(frac(lam b) 2^8).  Returns the status (0 = ok)."""
+        return int(_L().o_set_lambda(self._h, float(lam)))
+
+    def real_parts(self):
+        """(I u32[m], q u32[m], qsum u64[n]): integer and decimal parts per edge in the order of
+        edges(), and the decimal total per vertex."""
+        m = self.m
+        I = np.empty(m, dtype=np.uint32)
+        q = np.empty(m, dtype=np.uint32)
+        qs = np.empty(self.n, dtype=np.uint64)
+        _L().o_export_real(self._h, _p(I), _p(q), _p(qs))
+        return I, q, qs
 
     def edges(self):
         """(offs u64[n+1], dst u32[m], w u32[m], eid u64[m]) per vertex in ascending eid order."""

@@ -23,7 +23,10 @@
  *     sum_k P(p_k) P(v_i | p_k) (Eqs. group_prob and pvp, Theorem 1), as a
  *     reduced fraction, for pinning Theorem 1 on small inputs;
  *   - floating-point biases with an amortisation factor lambda: integer part
- *     radix-decomposed, decimal parts in one extra group (Section 4.3).
+ *     radix-decomposed, decimal parts in one extra group (Section 4.3), both
+ *     for a single vertex (o_float_factor, real arithmetic) and as a graph
+ *     mode (o_set_lambda) whose edge weight is lambda*b kept to 2^-8:
+ *     256*floor(lambda b) + floor(frac(lambda b) * 256), in integers.
  *
  * Randomness: the oracle's own counter hash; its stream is unrelated to the
  * GPU path's, so walks are compared statistically, never path by path.
@@ -44,7 +47,54 @@ enum { O_DEEPWALK = 0, O_PPR = 1, O_NODE2VEC = 2 };
 
 typedef struct { uint32_t dst, w; uint64_t eid; } o_edge;
 typedef struct { o_edge* e; uint64_t len, cap; } o_adj;
-typedef struct { uint32_t n; o_adj* a; uint64_t next_eid; } o_graph;
+typedef struct { uint32_t n; o_adj* a; uint64_t next_eid; double lam; } o_graph;
+
+/* ------------------------------------------------------------------------------ real biases */
+
+/*
+ * Real-valued bias of an edge (Section 4.3, steps (i)-(ii)): the stored 32-bit
+ * word is the IEEE-754 binary32 encoding of b.  x = lam * b is rounded once to
+ * binary64; its integer part I = floor(x) is radix-decomposed like an integer
+ * bias and its decimal part x - I is kept to 8 fractional bits,
+ * q = floor((x - I) * 256).  Invalid: b not finite or b < 0, x >= 2^31, or a
+ * zero weight (I = q = 0).  Returns 0 when valid.
+ */
+#define O_FRAC_BITS 8
+static int o_real_parts(uint32_t bits, double lam, uint32_t* I, uint32_t* q) {
+    float b;
+    memcpy(&b, &bits, sizeof b);
+    if (!isfinite(b) || b < 0.0f) return 1;
+    const double x = lam * (double)b;
+    if (!(x < 2147483648.0)) return 1;
+    const double ip = floor(x);
+    const double fr = x - ip;
+    *I = (uint32_t)ip;
+    *q = (uint32_t)floor(fr * (double)(1u << O_FRAC_BITS));
+    return (*I == 0 && *q == 0) ? 1 : 0;
+}
+
+/* Integer part, the part of an edge that is radix-decomposed. */
+static inline uint32_t o_int_part(const o_graph* g, uint32_t w) {
+    if (g->lam == 0.0) return w;
+    uint32_t I, q;
+    o_real_parts(w, g->lam, &I, &q);
+    return I;
+}
+
+/* Sampling weight of an edge: the integer bias, or 2^8 * I + q for real biases. */
+static inline uint64_t o_weight(const o_graph* g, uint32_t w) {
+    if (g->lam == 0.0) return w;
+    uint32_t I, q;
+    o_real_parts(w, g->lam, &I, &q);
+    return ((uint64_t)I << O_FRAC_BITS) + q;
+}
+
+static inline uint32_t o_dec_part(const o_graph* g, uint32_t w) {
+    if (g->lam == 0.0) return 0;
+    uint32_t I, q;
+    o_real_parts(w, g->lam, &I, &q);
+    return q;
+}
 
 /* ------------------------------------------------------------------------------ graph */
 
@@ -111,6 +161,37 @@ void o_export_edges(const o_graph* g, uint64_t* offs, uint32_t* dst, uint32_t* w
     offs[g->n] = p;
 }
 
+/* Switch the graph to real-valued biases with amortisation factor lam > 0
+ * (stored words are binary32 encodings).  O_INVALID if any edge is invalid. */
+int o_set_lambda(o_graph* g, double lam) {
+    if (!(lam > 0.0)) return O_INVALID;
+    for (uint32_t v = 0; v < g->n; v++)
+        for (uint64_t j = 0; j < g->a[v].len; j++) {
+            uint32_t I, q;
+            if (o_real_parts(g->a[v].e[j].w, lam, &I, &q)) return O_INVALID;
+        }
+    g->lam = lam;
+    return O_OK;
+}
+
+/* Integer and decimal parts of every live edge, in the order of o_export_edges,
+ * and the decimal total Q_D = sum of q per vertex. */
+void o_export_real(const o_graph* g, uint32_t* I, uint32_t* q, uint64_t* qsum) {
+    uint64_t p = 0;
+    for (uint32_t v = 0; v < g->n; v++) {
+        uint64_t s = 0;
+        for (uint64_t j = 0; j < g->a[v].len; j++, p++) {
+            uint32_t ii = 0, qq = 0;
+            if (g->lam != 0.0) o_real_parts(g->a[v].e[j].w, g->lam, &ii, &qq);
+            else ii = g->a[v].e[j].w;
+            I[p] = ii;
+            q[p] = qq;
+            s += qq;
+        }
+        qsum[v] = s;
+    }
+}
+
 /* 1 iff a live edge u -> x exists (linear scan). */
 int o_has_edge(const o_graph* g, uint32_t u, uint32_t x) {
     const o_adj* a = &g->a[u];
@@ -140,6 +221,11 @@ int o_apply(o_graph* g, const uint32_t* rec, uint64_t count, uint32_t max_bits, 
         const uint32_t* r = rec + 4 * i;
         if (r[0] >= g->n || r[1] >= g->n || r[3] > 2) return O_INVALID;
         if (r[3] != 1) {
+            if (g->lam != 0.0) {
+                uint32_t I, q;
+                if (o_real_parts(r[2], g->lam, &I, &q)) return O_INVALID;
+                continue;
+            }
             if (r[2] == 0) return O_INVALID;
             if (max_bits < 32 && (r[2] >> max_bits) != 0) return O_INVALID;
         }
@@ -182,16 +268,17 @@ int o_kind(uint64_t cnt, uint64_t d, uint32_t alpha, uint32_t beta) {
     return O_REGULAR;
 }
 
-/* For vertex v: |G_k| for k < 32 (Eq. dwi: edge i is in group k iff w_i AND 2^k != 0),
- * the kinds of Eq. group, and sum of biases. */
+/* For vertex v: |G_k| for k < 32 (Eq. dwi: edge i is in group k iff w_i AND 2^k != 0,
+ * w_i the integer part for real biases), the kinds of Eq. group, and the sum of the
+ * sampling weights. */
 void o_factor(const o_graph* g, uint32_t v, uint32_t alpha, uint32_t beta, uint32_t* cnt, uint8_t* kind,
               uint64_t* sumw) {
     const o_adj* a = &g->a[v];
     uint64_t s = 0;
     for (int k = 0; k < 32; k++) cnt[k] = 0;
     for (uint64_t j = 0; j < a->len; j++) {
-        uint32_t w = a->e[j].w;
-        s += w;
+        uint32_t w = o_int_part(g, a->e[j].w);
+        s += o_weight(g, a->e[j].w);
         for (int k = 0; k < 32; k++)
             if (w & (1u << k)) cnt[k]++;
     }
@@ -205,13 +292,21 @@ void o_factor_all(const o_graph* g, uint32_t alpha, uint32_t beta, uint32_t* cnt
         o_factor(g, (uint32_t)v, alpha, beta, cnt + 32 * v, kind + 32 * v, sumw + v);
 }
 
-/* Group totals W(p_k) = sum_i (w_i AND 2^k) (Eq. wpk), summed directly. */
+/* Group totals W(p_k) = sum_i (w_i AND 2^k) (Eq. wpk), summed directly.  For real
+ * biases, in units of 2^-8 (each integer part counts 2^8 times) and W[31] is the
+ * decimal group's total Q_D. */
 void o_group_totals(const o_graph* g, uint32_t v, uint64_t* W) {
     const o_adj* a = &g->a[v];
+    const int sh = g->lam != 0.0 ? O_FRAC_BITS : 0;
     for (int k = 0; k < 32; k++) {
         uint64_t s = 0;
-        for (uint64_t j = 0; j < a->len; j++) s += (uint64_t)(a->e[j].w & (1u << k));
+        for (uint64_t j = 0; j < a->len; j++) s += (uint64_t)(o_int_part(g, a->e[j].w) & (1u << k)) << sh;
         W[k] = s;
+    }
+    if (sh) {
+        uint64_t s = 0;
+        for (uint64_t j = 0; j < a->len; j++) s += o_dec_part(g, a->e[j].w);
+        W[31] = s;
     }
 }
 
@@ -220,7 +315,7 @@ void o_group_totals(const o_graph* g, uint32_t v, uint64_t* W) {
 uint64_t o_members_count(const o_graph* g) {
     uint64_t t = 0;
     for (uint32_t v = 0; v < g->n; v++)
-        for (uint64_t j = 0; j < g->a[v].len; j++) t += (uint64_t)__builtin_popcount(g->a[v].e[j].w);
+        for (uint64_t j = 0; j < g->a[v].len; j++) t += (uint64_t)__builtin_popcount(o_int_part(g, g->a[v].e[j].w));
     return t;
 }
 
@@ -231,7 +326,7 @@ void o_members_all(const o_graph* g, uint64_t* offs, uint64_t* eids) {
         for (int k = 0; k < 32; k++) {
             offs[32 * (uint64_t)v + k] = p;
             for (uint64_t j = 0; j < a->len; j++)
-                if (a->e[j].w & (1u << k)) eids[p++] = a->e[j].eid;
+                if (o_int_part(g, a->e[j].w) & (1u << k)) eids[p++] = a->e[j].eid;
         }
     }
     offs[32 * (uint64_t)g->n] = p;
@@ -252,6 +347,10 @@ static unsigned __int128 gcd128(unsigned __int128 a, unsigned __int128 b) {
  * members by rejection on the whole neighbour list (Section 5.1): one trial
  * picks i with probability 1/d and succeeds with probability |G_k|/d, so the
  * conditional probability is (1/d) / (|G_k|/d), summed here as that ratio.
+ * Real biases (Section 4.3): the integer groups carry W(p_k) = 2^8 * 2^k |G_k|
+ * (units of 2^-8) and the decimal group D carries Q_D = sum of the decimal parts
+ * q_j; within D, neighbour i is drawn with probability q_i / Q_D (step (iii):
+ * ITS or rejection over the decimal parts), so its term is Q_D/tot * q_i/Q_D.
  * Returns 0 on success, 1 if the vertex has no edges.
  */
 int o_factored_prob(const o_graph* g, uint32_t v, uint64_t i, uint32_t alpha, uint32_t beta, uint64_t* num,
@@ -262,10 +361,15 @@ int o_factored_prob(const o_graph* g, uint32_t v, uint64_t i, uint32_t alpha, ui
     o_factor(g, v, alpha, beta, cnt, kind, &sw);
     const o_adj* a = &g->a[v];
     if (a->len == 0) return 1;
-    uint64_t W[32], tot = 0;
-    for (int k = 0; k < 32; k++) { W[k] = (uint64_t)cnt[k] << k; tot += W[k]; }
+    const int sh = g->lam != 0.0 ? O_FRAC_BITS : 0;
+    uint64_t W[32], tot = 0, QD = 0;
+    for (int k = 0; k < 32; k++) { W[k] = (uint64_t)cnt[k] << (k + sh); tot += W[k]; }
+    if (sh) {
+        for (uint64_t j = 0; j < a->len; j++) QD += o_dec_part(g, a->e[j].w);
+        tot += QD;
+    }
     unsigned __int128 pn = 0, pd = 1;
-    uint32_t wi = a->e[i].w;
+    uint32_t wi = o_int_part(g, a->e[i].w);
     for (int k = 0; k < 32; k++) {
         if (!(wi & (1u << k))) continue;
         /* term = (W_k / tot) * q_k where q_k is the within-group probability */
@@ -278,6 +382,16 @@ int o_factored_prob(const o_graph* g, uint32_t v, uint64_t i, uint32_t alpha, ui
             qd = cnt[k];
         }
         unsigned __int128 tn = (unsigned __int128)W[k] * qn, td = (unsigned __int128)tot * qd;
+        unsigned __int128 t = gcd128(tn, td);
+        tn /= t; td /= t;
+        pn = pn * td + tn * pd;
+        pd = pd * td;
+        t = gcd128(pn, pd);
+        pn /= t; pd /= t;
+    }
+    const uint32_t qi = o_dec_part(g, a->e[i].w);
+    if (qi) { /* decimal group: (Q_D / tot) * (q_i / Q_D) */
+        unsigned __int128 tn = (unsigned __int128)QD * qi, td = (unsigned __int128)tot * QD;
         unsigned __int128 t = gcd128(tn, td);
         tn /= t; td /= t;
         pn = pn * td + tn * pd;
@@ -327,7 +441,7 @@ uint64_t o_its_pick(const o_graph* g, uint32_t v, uint64_t r) {
     const o_adj* a = &g->a[v];
     uint64_t* c = (uint64_t*)malloc(sizeof(uint64_t) * (a->len ? a->len : 1));
     uint64_t s = 0;
-    for (uint64_t j = 0; j < a->len; j++) { s += a->e[j].w; c[j] = s; }
+    for (uint64_t j = 0; j < a->len; j++) { s += o_weight(g, a->e[j].w); c[j] = s; }
     uint64_t j = its_search(c, a->len, r);
     free(c);
     return j;
@@ -343,7 +457,7 @@ static int n2v_dist(const o_graph* g, uint32_t prev, uint32_t x) {
  * where a[] are the acceptance thresholds f/max f scaled by 2^32. */
 void o_n2v_weights(const o_graph* g, uint32_t prev, uint32_t u, const uint64_t* a, uint64_t* out) {
     const o_adj* A = &g->a[u];
-    for (uint64_t j = 0; j < A->len; j++) out[j] = (uint64_t)A->e[j].w * a[n2v_dist(g, prev, A->e[j].dst)];
+    for (uint64_t j = 0; j < A->len; j++) out[j] = o_weight(g, A->e[j].w) * a[n2v_dist(g, prev, A->e[j].dst)];
 }
 
 typedef struct {
@@ -373,7 +487,7 @@ void o_walk(const o_graph* g, uint64_t nwalkers, const uint32_t* starts, const u
 #pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t v = 0; v < (int64_t)g->n; v++) {
         uint64_t s = 0;
-        for (uint64_t j = 0; j < g->a[v].len; j++) { s += g->a[v].e[j].w; c[off[v] + j] = s; }
+        for (uint64_t j = 0; j < g->a[v].len; j++) { s += o_weight(g, g->a[v].e[j].w); c[off[v] + j] = s; }
     }
 #pragma omp parallel
     {
@@ -425,7 +539,7 @@ void o_sample_many(const o_graph* g, uint32_t v, uint64_t count, uint64_t seed, 
     const o_adj* a = &g->a[v];
     uint64_t* c = (uint64_t*)malloc(sizeof(uint64_t) * (a->len ? a->len : 1));
     uint64_t s = 0;
-    for (uint64_t j = 0; j < a->len; j++) { s += a->e[j].w; c[j] = s; }
+    for (uint64_t j = 0; j < a->len; j++) { s += o_weight(g, a->e[j].w); c[j] = s; }
 #pragma omp parallel for schedule(static)
     for (int64_t t = 0; t < (int64_t)count; t++) {
         o_rng r = {seed, (uint64_t)t, 0};

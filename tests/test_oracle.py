@@ -269,3 +269,113 @@ def test_oracle_walk_steps_are_live_edges_and_padding():
         for t in range(L - 1):
             assert g.has_edge(int(paths[i, t]), int(paths[i, t + 1]))
         assert (paths[i, L:] == O.PAD).all()
+
+
+# ----------------------------------------------------------------------------- real-valued biases
+
+
+def _f32_bits(xs):
+    return [int(b) for b in np.asarray(xs, dtype=np.float32).view(np.uint32)]
+
+
+def _real_vertex_graph(configs, lam):
+    """One source vertex per config (a tuple of binary32 biases), neighbours 0.. in order."""
+    n = len(configs) + max(len(c) for c in configs)
+    edges = [(v, len(configs) + j, b) for v, ws in enumerate(configs) for j, b in enumerate(_f32_bits(ws))]
+    g = O.Graph.from_edges(n, edges)
+    assert g.set_lambda(lam) == 0
+    return g
+
+
+def test_real_bias_worked_example():
+    """Section 4.3 / Fig. SAMPLING2: lambda = 10 scales 0.554, 0.726, 0.320 to 5.54, 7.26, 3.20;
+    integer parts 5, 7, 3 give groups 2^0 = {1,4,5}, 2^1 = {4,5}, 2^2 = {1,4}; every decimal part
+    is nonzero, so the decimal group is {1,4,5}; W_D / (W_I + W_D) = 1/16."""
+    gd = golden("float_example.json")
+    g = O.Graph.from_edges(6, [(2, d, b) for d, b in zip(gd["neighbors"], _f32_bits(gd["biases"]))])
+    assert g.set_lambda(gd["lambda"]) == 0
+    I, q, qsum = g.real_parts()
+    assert [int(x) for x in I] == gd["integer_parts"]
+    assert _groups_by_dst(g, 2) == {int(k): sorted(x) for k, x in gd["groups"].items()}
+    offs, dst, _, _ = g.edges()
+    assert sorted(int(d) for d, qq in zip(dst, q) if qq > 0) == gd["decimal_group"]
+    # decimal parts kept to 2^-8: within one unit of the printed scaled values' fractions
+    for qq, x in zip(q, gd["scaled"]):
+        assert abs(int(qq) / 256 - (x - int(x))) < 1 / 256
+    WI, WD = sum(int(x) for x in I), int(qsum[2]) / 256
+    assert abs(WD / (WI + WD) - gd["decimal_share"]) < 1e-3
+    # group totals in units of 2^-8, decimal total in slot 31
+    Wk = g.group_totals(2)
+    assert [int(Wk[k]) for k in range(3)] == [256 * 3 * 1, 256 * 2 * 2, 256 * 2 * 4]
+    assert int(Wk[31]) == int(qsum[2])
+
+
+def test_real_bias_weight_is_floor_of_scaled_value():
+    """When lambda * b is exact in binary64 (short mantissas, small integer lambda) the two parts
+    recombine to floor(2^8 lambda b), computed here in exact rationals."""
+    rng = np.random.default_rng(11)
+    mant = rng.integers(1, 1 << 12, size=400)
+    expo = rng.integers(-14, 10, size=400)
+    bs = np.ldexp(mant.astype(np.float64), expo).astype(np.float32)
+    bs = bs[(bs > 0) & (bs < 1e5)]
+    for lam in (1.0, 3.0, 10.0, 1000.0):
+        keep = [float(b) for b in bs if 256 * lam * float(b) >= 1 and lam * float(b) < 2**31]
+        g = _real_vertex_graph([tuple(keep)], lam)
+        I, q, _ = g.real_parts()
+        for b, ii, qq in zip(keep, I, q):
+            exact = Fraction(b) * Fraction(lam) * 256
+            assert (int(ii) << 8) + int(qq) == exact.numerator // exact.denominator
+
+
+def test_real_bias_theorem1_exact():
+    """Integer groups weighted 2^8 2^k |G_k| plus the decimal group weighted Q_D with members drawn
+    by q_i / Q_D give every neighbour probability (2^8 I_i + q_i) / sum (the decomposition loses
+    nothing): exact rationals, including vertices whose biases are all below 1/lambda."""
+    rng = np.random.default_rng(12)
+    for lam in (1.0, 10.0, 37.5):
+        configs = [tuple(rng.uniform(0.5, 100.0, size=int(rng.integers(1, 7))).astype(np.float32)) for _ in range(300)]
+        configs += [tuple(rng.uniform(0.01, 0.99, size=int(rng.integers(1, 7))).astype(np.float32) / lam)
+                    for _ in range(100)]
+        configs = [c for c in configs if all(256 * lam * float(b) >= 1 for b in c)]
+        g = _real_vertex_graph(configs, lam)
+        I, q, _ = g.real_parts()
+        offs, _, _, _ = g.edges()
+        decimal_only = 0
+        for v, ws in enumerate(configs):
+            a, b = int(offs[v]), int(offs[v + 1])
+            wts = [(int(I[j]) << 8) + int(q[j]) for j in range(a, b)]
+            decimal_only += all(int(I[j]) == 0 for j in range(a, b))
+            for i in range(b - a):
+                assert Fraction(*g.factored_prob(v, i)) == Fraction(wts[i], sum(wts)), (lam, ws, i)
+        assert decimal_only > 50
+
+
+def test_real_bias_its_enumeration():
+    rng = np.random.default_rng(13)
+    configs = [tuple(rng.uniform(0.05, 3.0, size=int(rng.integers(1, 5))).astype(np.float32)) for _ in range(60)]
+    g = _real_vertex_graph(configs, 2.0)
+    I, q, _ = g.real_parts()
+    offs, _, _, _ = g.edges()
+    for v in range(len(configs)):
+        a, b = int(offs[v]), int(offs[v + 1])
+        wts = [(int(I[j]) << 8) + int(q[j]) for j in range(a, b)]
+        hits = [0] * len(wts)
+        for r in range(sum(wts)):
+            hits[g.its_pick(v, r)] += 1
+        assert hits == wts
+
+
+def test_real_bias_validation():
+    bad = [float("nan"), float("inf"), -1.0, 0.0, 1e-9, 3e9]
+    for b in bad:
+        g = O.Graph.from_edges(3, [(0, 1, _f32_bits([b])[0])])
+        assert g.set_lambda(1.0) != 0, b
+    g = O.Graph.from_edges(3, [(0, 1, _f32_bits([1.5])[0])])
+    assert g.set_lambda(1.0) == 0
+    for b in bad:
+        rc, _ = g.apply(np.array([[0, 2, _f32_bits([b])[0], 0]], dtype=np.uint32))
+        assert rc != 0, b
+    rc, st = g.apply(np.array([[0, 2, _f32_bits([0.25])[0], 0]], dtype=np.uint32))
+    assert rc == 0 and st == (1, 0, 0)
+    I, q, qsum = g.real_parts()
+    assert [int(x) for x in I] == [1, 0] and [int(x) for x in q] == [128, 64] and int(qsum[0]) == 192
