@@ -23,7 +23,9 @@
  *    returns a thread-local message for the last failure on this thread.
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *    stream.
- *  - Vertex ids are < n < 2^31.  Biases are 1 <= w < 2^max_bits (max_bits <= 32).
+ *  - Vertex ids are < n < 2^31.  Integer biases are 1 <= w < 2^max_bits
+ *    (max_bits <= 32).  Graphs created with bias_format BINGO_BIAS_F32 take
+ *    real biases instead (see bingo_config and bingo_create).
  *  - Calls on one graph must not run concurrently from several host threads.
  */
 #ifndef BINGO_H
@@ -65,6 +67,12 @@ enum {
     BINGO_WALK_NO_PAD = 0x100  /* flag: leave path entries beyond path_len untouched instead of writing 0xFFFFFFFF */
 };
 
+/* Bias formats (bingo_config.bias_format). */
+enum {
+    BINGO_BIAS_U32 = 0, /* integer biases, radix-factorised directly (Section 4.1) */
+    BINGO_BIAS_F32 = 1  /* real biases with amortisation factor lambda (Section 4.3), see bingo_create */
+};
+
 typedef struct {
     uint32_t alpha_pct;        /* Eq. group alpha, percent (paper: 40) */
     uint32_t beta_pct;         /* Eq. group beta, percent (paper: 10) */
@@ -75,11 +83,14 @@ typedef struct {
     uint32_t update_chunk;     /* segments above this many adjacency slots use a whole block; 0 = default */
     uint32_t reg_variant;      /* walker register budget: 0 = 64 registers, 1 = 40 registers (more resident warps) */
     uint64_t pool_words;       /* device pool for adjacency and group blocks, in 4-byte words; 0 = auto */
+    uint32_t bias_format;      /* BINGO_BIAS_U32 (default) or BINGO_BIAS_F32 */
+    uint32_t reserved0;
+    double lambda;             /* BINGO_BIAS_F32: amortisation factor lambda > 0 (Section 4.3) */
 } bingo_config;
 
 /* One update record, 16 bytes. */
 typedef struct {
-    uint32_t src, dst, bias; /* bias ignored for BINGO_OP_DELETE */
+    uint32_t src, dst, bias; /* bias ignored for BINGO_OP_DELETE; binary32 encoding in BINGO_BIAS_F32 graphs */
     uint32_t op;             /* BINGO_OP_* */
 } bingo_update;
 
@@ -115,9 +126,20 @@ void bingo_default_config(bingo_config* cfg);
  *   m        number of edges
  *   row_ptr  uint64[n+1], row_ptr[0] = 0, row_ptr[n] = m
  *   col      uint32[m]  destination of each edge
- *   bias     uint32[m]  1 <= bias < 2^cfg->max_bits
+ *   bias     uint32[m]  1 <= bias < 2^cfg->max_bits; or, with cfg->bias_format =
+ *            BINGO_BIAS_F32, the IEEE-754 binary32 encoding of a real bias b
  *   cfg      nullable: defaults of bingo_default_config
  * Edge ids are assigned 0..m-1 in CSR order; later insertions continue the count.
+ * Real biases (Section 4.3, steps (i)-(iv)): x = lambda * b is rounded once to
+ * binary64 and split into its integer part I = floor(x), radix-factorised into
+ * groups 0..30 exactly like an integer bias, and its decimal part, kept to 8
+ * fractional bits as q = floor((x - I) * 256).  The decimal parts of a vertex
+ * form one extra group whose total Q_D = sum q occupies group slot 31; the
+ * sampler draws neighbour i with probability (256 I_i + q_i) / sum_j (256 I_j +
+ * q_j), the decimal group's member by rejection on q / 256 over the neighbour
+ * list (with an exact inverse-transform fallback).  Requirements: b finite and
+ * >= 0, lambda b < 2^31, 256 I + q >= 1 (no zero weights), degree < 2^24.
+ * max_bits is ignored for real biases.
  * Errors: BINGO_E_INVALID (bad ids or biases; nothing allocated), BINGO_E_OOM, BINGO_E_CUDA.
  * Synchronises `stream` before returning.  *out receives the new graph.
  */
@@ -255,7 +277,17 @@ bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, ui
                                 uint32_t* cnt, uint8_t* kind, uint32_t* one_slot, uint32_t* glen, uint32_t* members,
                                 uint32_t* member_inv, uint32_t* sp_len, uint32_t* sp_list, uint32_t* sp_inv);
 
-/* Bytes of device state by structure: [0] adjacency, [1] counts+headers+group refs,
+/*
+ * Real-bias graphs (BINGO_BIAS_F32, Section 4.3): the decimal part q of every live
+ * edge, in units of 2^-8, in the edge order of bingo_export_state (host pointer,
+ * m bytes).  The integer parts are that call's bias[] and the decimal totals
+ * Q_D its cnt[32 v + 31] (kind[32 v + 31] is BINGO_KIND_EMPTY: the decimal group
+ * is not a radix group).  BINGO_E_STATE on an integer-bias graph.  Synchronises
+ * the graph's internal stream.
+ */
+bingo_status bingo_export_decimal(bingo_graph* g, uint8_t* q);
+
+/* Bytes of device state by structure: [0] adjacency (with decimal parts), [1] counts+headers+group refs,
  * [2] regular groups, [3] sparse groups + sparse lists, [4] edge index, [5] pool capacity. */
 bingo_status bingo_memory_report(bingo_graph* g, uint64_t out[6]);
 

@@ -25,6 +25,7 @@ DEEPWALK, PPR, NODE2VEC = 0, 1, 2
 OP_INSERT, OP_DELETE, OP_SET_BIAS = 0, 1, 2
 WALK_PERSISTENT, WALK_STEPWISE, WALK_NO_PAD = 0, 1, 0x100
 SERVER_NO_MERGE = 1
+BIAS_U32, BIAS_F32 = 0, 1
 PAD = 0xFFFFFFFF
 
 c = ctypes
@@ -40,7 +41,8 @@ class BingoError(RuntimeError):
 class bingo_config(c.Structure):
     _fields_ = [("alpha_pct", c.c_uint32), ("beta_pct", c.c_uint32), ("max_bits", c.c_uint32),
                 ("lanes_per_walker", c.c_uint32), ("warps_per_block", c.c_uint32), ("blocks_per_sm", c.c_uint32),
-                ("update_chunk", c.c_uint32), ("reg_variant", c.c_uint32), ("pool_words", c.c_uint64)]
+                ("update_chunk", c.c_uint32), ("reg_variant", c.c_uint32), ("pool_words", c.c_uint64),
+                ("bias_format", c.c_uint32), ("reserved0", c.c_uint32), ("lambda_", c.c_double)]
 
 
 class bingo_update_stats(c.Structure):
@@ -92,6 +94,7 @@ SIGNATURES = {
     "bingo_check": (c.c_int, [VP, VP]),
     "bingo_state_sizes_get": (c.c_int, [VP, c.POINTER(bingo_state_sizes)]),
     "bingo_export_state": (c.c_int, [VP] + [VP] * 13),
+    "bingo_export_decimal": (c.c_int, [VP, VP]),
     "bingo_memory_report": (c.c_int, [VP, c.POINTER(c.c_uint64)]),
     "bingo_autotune": (c.c_int, [VP, c.c_uint64, VP, c.c_uint32, VP, c.POINTER(bingo_config)]),
     "bingo_get_config": (c.c_int, [VP, c.POINTER(bingo_config)]),
@@ -289,6 +292,21 @@ def bingo_export_state(h):
     return out
 
 
+def bingo_export_decimal(h):
+    """Decimal parts (units of 2^-8) of every live edge of a real-bias graph, in export order."""
+    L = load()
+    sz = bingo_state_sizes()
+    _err(L.bingo_state_sizes_get(h, c.byref(sz)))
+    q = np.zeros(max(sz.m, 1), np.uint8)
+    _err(L.bingo_export_decimal(h, _ptr(q)))
+    return q[: sz.m]
+
+
+def real_bias_bits(b) -> np.ndarray:
+    """binary32 encodings of real biases, the bias words of a BIAS_F32 graph or update."""
+    return np.ascontiguousarray(np.asarray(b, dtype=np.float32)).view(np.uint32)
+
+
 # ------------------------------------------------------------------------------------- object wrapper
 
 
@@ -327,6 +345,9 @@ class Graph:
 
     def export_state(self):
         return bingo_export_state(self.h)
+
+    def export_decimal(self):
+        return bingo_export_decimal(self.h)
 
     def memory_report(self):
         return bingo_memory_report(self.h)

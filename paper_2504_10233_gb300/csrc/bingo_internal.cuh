@@ -14,7 +14,12 @@
 //                         S_inv [capA] (by slot)
 //             sparse k    4*capS words: member destinations, member positions in S, inverted index
 //                         (by S position), spare
+//             decimal     max(8, capA/4) words: capA bytes, the decimal part q of each adjacency
+//                         slot (real-bias graphs only; referenced by group slot 31)
 // A group's kind is never stored: it is the pure function of (|G_k|, d) given by Eq. group.
+// Real-bias graphs (Section 4.3): slot k < 31 is the radix group of bit k of the integer parts,
+// weighted 2^8 2^k |G_k| (units of 2^-8); slot 31 is the decimal group {Q_D = sum q, decimal
+// block}, weighted Q_D, and is never given a kind.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -169,6 +174,8 @@ struct DevGraph {
     uint32_t n;
     uint32_t max_bits;
     uint32_t alpha, beta;
+    uint32_t fbits;   // 0: integer biases; FRAC_BITS: real biases (slot 31 = decimal group)
+    double lambda;    // real biases: amortisation factor
     VHot* vh;
     VCold* vc;
     Pool pool;
@@ -212,6 +219,46 @@ __device__ __forceinline__ uint2& grp(const DevGraph& G, uint64_t v, uint32_t k)
 }
 __device__ __forceinline__ uint32_t& cnt_ref(const DevGraph& G, uint64_t v, uint32_t k) { return grp(G, v, k).x; }
 __device__ __forceinline__ uint32_t& gref_ref(const DevGraph& G, uint64_t v, uint32_t k) { return grp(G, v, k).y; }
+
+// ---- real biases (Section 4.3)
+constexpr uint32_t FRAC_BITS = 8;
+constexpr uint32_t DEC_SLOT = 31;
+constexpr uint32_t REAL_MAX_DEG = 1u << 24;  // keeps Q_D < 2^32 and the vertex total < 2^64
+// Words of the decimal block of an adjacency of capacity capa (one byte per slot).
+__host__ __device__ __forceinline__ uint64_t dec_words(uint32_t capa) { return capa / 4 < 8 ? 8 : capa / 4; }
+// Split a real bias (binary32 encoding) into the integer part I = floor(lambda b) and the decimal
+// part q = floor((lambda b - I) 2^FRAC_BITS), with lambda b rounded once to binary64.  False if b is
+// not finite or negative, lambda b >= 2^31, or the weight 2^FRAC_BITS I + q is zero.
+__device__ __forceinline__ bool split_real_bias(uint32_t bits, double lambda, uint32_t& I, uint32_t& q) {
+    const float b = __uint_as_float(bits);
+    I = 0;
+    q = 0;
+    if (!isfinite(b) || b < 0.0f) return false;
+    const double x = __dmul_rn(lambda, (double)b);
+    if (!(x < 2147483648.0)) return false;
+    const double ip = floor(x);
+    I = (uint32_t)ip;
+    q = (uint32_t)floor(__dmul_rn(__dsub_rn(x, ip), (double)(1u << FRAC_BITS)));
+    return I != 0 || q != 0;
+}
+// The factorised part of an insertion's bias word: the integer bias, or the integer part of a real one.
+__device__ __forceinline__ uint32_t int_part(const DevGraph& G, uint32_t bits) {
+    if (!G.fbits) return bits;
+    uint32_t I, q;
+    split_real_bias(bits, G.lambda, I, q);
+    return I;
+}
+// Sampling weight of group slot k with count c (Eq. wpk), in units of 2^-fbits.
+__device__ __forceinline__ uint64_t slot_w(uint32_t c, uint32_t k, uint32_t fbits) {
+    return (fbits && k == DEC_SLOT) ? (uint64_t)c : ((uint64_t)c << (k + fbits));
+}
+// Kind of group slot k (Eq. group); the decimal slot of a real-bias graph has none.
+__device__ __forceinline__ uint32_t slot_kind(const DevGraph& G, uint32_t c, uint32_t d, uint32_t k) {
+    return (G.fbits && k == DEC_SLOT) ? (uint32_t)K_EMPTY : kind_of(c, d, G.alpha, G.beta);
+}
+__device__ __forceinline__ uint8_t* dec_bytes(const DevGraph& G, uint32_t ref) {
+    return reinterpret_cast<uint8_t*>(G.pool.base + words_of(ref));
+}
 
 __device__ __forceinline__ uint2* adj_pairs(const DevGraph& G, uint64_t adj) { return reinterpret_cast<uint2*>(G.pool.base + adj); }
 __device__ __forceinline__ uint64_t* adj_eids(const DevGraph& G, uint64_t adj, uint32_t capa) {

@@ -23,19 +23,36 @@ const char* last_error_cstr();
 
 // ------------------------------------------------------------------------------------------- kernels
 
+// Integer biases: 1 <= w < 2^max_bits.  Real biases (real = true) were checked by k_split_biases;
+// their degree must stay below REAL_MAX_DEG.
 __global__ void k_validate_csr(uint32_t n, uint64_t m, const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
-                               const uint32_t* __restrict__ bias, uint32_t max_bits, uint32_t* status) {
+                               const uint32_t* __restrict__ bias, uint32_t max_bits, bool real, uint32_t* status) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     bool bad = false;
     for (uint64_t j = tid; j < m; j += nt) {
         const uint32_t w = bias[j];
-        bad |= col[j] >= n || w == 0 || (max_bits < 32 && (w >> max_bits) != 0);
+        bad |= col[j] >= n || (!real && (w == 0 || (max_bits < 32 && (w >> max_bits) != 0)));
     }
+    const uint64_t dlim = real ? REAL_MAX_DEG : 0xFFFFFFFFull;
     for (uint64_t v = tid; v < n; v += nt) {
         const uint64_t a = rp[v], b = rp[v + 1];
-        bad |= b < a || b - a >= 0xFFFFFFFFull;
+        bad |= b < a || b - a >= dlim;
     }
     if (tid == 0) bad |= rp[0] != 0 || rp[n] != m;
+    if (bad) atomicOr(status, ST_INVALID);
+}
+
+// Real biases (Section 4.3): integer parts I[j] (factorised like integer biases) and decimal parts q[j].
+__global__ void k_split_biases(const uint32_t* __restrict__ bits, uint64_t m, double lambda, uint32_t* __restrict__ I,
+                               uint8_t* __restrict__ q, uint32_t* status) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (uint64_t j = tid; j < m; j += nt) {
+        uint32_t ii, qq;
+        bad |= !split_real_bias(bits[j], lambda, ii, qq);
+        I[j] = ii;
+        q[j] = (uint8_t)qq;
+    }
     if (bad) atomicOr(status, ST_INVALID);
 }
 
@@ -75,6 +92,7 @@ __global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const
             const uint32_t capa = capa_for(d);
             const uint32_t caps = spm ? caps_for(nsp) : 0;
             uint64_t wd = (uint64_t)4 * capa + (uint64_t)__popc(regm) * 4 * capa;
+            if (G.fbits && capa) wd += dec_words(capa);
             if (spm) wd += 2ull * capa + (uint64_t)__popc(spm) * 4 * caps;
             words[v] = wd;
             VHdr h;
@@ -93,7 +111,8 @@ __global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const
 
 // Copy edges into the vertex's adjacency block and build its group structures.
 __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
-                             const uint32_t* __restrict__ bias, const uint64_t* __restrict__ offs, uint64_t base) {
+                             const uint32_t* __restrict__ bias, const uint8_t* __restrict__ dec,
+                             const uint64_t* __restrict__ offs, uint64_t base) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -118,6 +137,19 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
                 eids[j] = a + j;
             }
             next += 4ull * capa;
+            if (G.fbits) {  // decimal block: q per slot; slot 31 = {Q_D, block}
+                uint8_t* qb = reinterpret_cast<uint8_t*>(G.pool.base + next);
+                uint32_t qs = 0;
+                for (uint32_t j = lane; j < d; j += 32) {
+                    qb[j] = dec[a + j];
+                    qs += dec[a + j];
+                }
+                qs = __reduce_add_sync(FULL, qs);
+                if (lane == DEC_SLOT) gref = ref_of(next);
+                if (qs) h.mask |= 1u << DEC_SLOT;
+                if (lane == 0) cnt_ref(G, v, DEC_SLOT) = qs;
+                next += dec_words(capa);
+            }
         }
         __syncwarp();
         for (uint32_t m = regm; m; m &= m - 1) {
@@ -159,7 +191,7 @@ __global__ void k_export_sizes(DevGraph G, uint64_t* __restrict__ deg64, uint64_
     for (uint64_t v = warp; v < G.n; v += nwarps) {
         const VHdr h = load_hdr(G, v);
         const uint32_t c = cnt_ref(G, v, lane);
-        const uint32_t kd = kind_of(c, h.deg, G.alpha, G.beta);
+        const uint32_t kd = slot_kind(G, c, h.deg, lane);
         glen64[v * 32 + lane] = is_list(kd) ? c : 0;
         if (lane == 0) {
             deg64[v] = h.deg;
@@ -192,7 +224,7 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
             }
         }
         const uint32_t c = cnt_ref(G, v, lane);
-        const uint32_t kd = kind_of(c, d, G.alpha, G.beta);
+        const uint32_t kd = slot_kind(G, c, d, lane);
         const uint32_t gr = gref_ref(G, v, lane);
         okind[v * 32 + lane] = (uint8_t)kd;
         ocnt[v * 32 + lane] = c;
@@ -239,6 +271,29 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
     }
 }
 
+// Decimal parts per edge in export order (real-bias graphs); counts slots whose Q_D disagrees.
+__global__ void k_export_dec(DevGraph G, const uint64_t* __restrict__ eoff, uint8_t* __restrict__ oq,
+                             unsigned long long* __restrict__ bad) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = warp; v < G.n; v += nwarps) {
+        const VHdr h = load_hdr(G, v);
+        const uint32_t ref = gref_ref(G, v, DEC_SLOT);
+        uint32_t qs = 0;
+        if (h.deg && ref) {
+            const uint8_t* qb = dec_bytes(G, ref);
+            for (uint32_t j = lane; j < h.deg; j += 32) {
+                oq[eoff[v] + j] = qb[j];
+                qs += qb[j];
+            }
+        }
+        qs = __reduce_add_sync(FULL, qs);
+        const bool flag = ((h.mask >> DEC_SLOT) & 1u) != (qs != 0);
+        if (lane == 0 && (qs != cnt_ref(G, v, DEC_SLOT) || flag || (h.deg && !ref))) atomicAdd(bad, 1ull);
+    }
+}
+
 // memory by structure: [0] adjacency words, [1] regular group words, [2] sparse words
 __global__ void k_memory(DevGraph G, unsigned long long* out) {
     const uint32_t lane = threadIdx.x & 31;
@@ -248,10 +303,10 @@ __global__ void k_memory(DevGraph G, unsigned long long* out) {
     for (uint64_t v = warp; v < G.n; v += nwarps) {
         const VHdr h = load_hdr(G, v);
         const uint32_t capa = capa_of(h), caps = caps_of(h);
-        const uint32_t kd = kind_of(cnt_ref(G, v, lane), h.deg, G.alpha, G.beta);
+        const uint32_t kd = slot_kind(G, cnt_ref(G, v, lane), h.deg, lane);
         const uint32_t regm = __ballot_sync(FULL, kd == K_REGULAR), spm = __ballot_sync(FULL, kd == K_SPARSE);
         if (lane == 0) {
-            a += 4ull * capa;
+            a += 4ull * capa + (G.fbits && capa ? dec_words(capa) : 0ull);
             r += (unsigned long long)__popc(regm) * 4 * capa;
             if (h.sref) s += 2ull * capa + (unsigned long long)__popc(spm) * 4 * caps;
         }
@@ -328,6 +383,11 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
         set_error("invalid config (max_bits=%u alpha=%u beta=%u)", c.max_bits, c.alpha_pct, c.beta_pct);
         return BINGO_E_INVALID;
     }
+    const bool real = c.bias_format == BINGO_BIAS_F32;
+    if (c.bias_format > BINGO_BIAS_F32 || (real && !(c.lambda > 0.0 && c.lambda < 1e300))) {
+        set_error("invalid bias format %u / lambda %g", c.bias_format, c.lambda);
+        return BINGO_E_INVALID;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     bingo_graph* g = new bingo_graph();
     g->cfg = c;
@@ -338,8 +398,8 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
     auto fail = [&](bingo_status x) { free_graph(g); return x; };
     const uint64_t* rp = nullptr;
     const uint32_t *cl = nullptr, *bs = nullptr;
-    Buf brp, bcl, bbs;
-    auto release_stage = [&]() { release(brp); release(bcl); release(bbs); };
+    Buf brp, bcl, bbs, bint, bdec;
+    auto release_stage = [&]() { release(brp); release(bcl); release(bbs); release(bint); release(bdec); };
     if ((st = stage_in(row_ptr, sizeof(uint64_t) * ((size_t)n + 1), brp, s, (const void**)&rp)) != BINGO_OK) { release_stage(); return fail(st); }
     if ((st = stage_in(col, sizeof(uint32_t) * m, bcl, s, (const void**)&cl)) != BINGO_OK) { release_stage(); return fail(st); }
     if ((st = stage_in(bias, sizeof(uint32_t) * m, bbs, s, (const void**)&bs)) != BINGO_OK) { release_stage(); return fail(st); }
@@ -352,13 +412,25 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
         !cu(cudaMemsetAsync(g->d_ctl, 0, CTL_WORDS * sizeof(uint64_t), s), "control init")) { release_stage(); return fail(st); }
     uint64_t* ctl = (uint64_t*)g->d_ctl;
     uint32_t* status = (uint32_t*)(ctl + CTL_STATUS);
-    k_validate_csr<<<grid_for(g, (m > n ? m : n), 256), 256, 0, s>>>(n, m, rp, cl, bs, c.max_bits, status);
+    const uint8_t* dq = nullptr;
+    if (real && m) {  // split every real bias; the integer parts are factorised from here on
+        if (!cu(ensure(bint, sizeof(uint32_t) * m), "integer parts") || !cu(ensure(bdec, m), "decimal parts")) {
+            release_stage(); return fail(st);
+        }
+        k_split_biases<<<grid_for(g, m, 256), 256, 0, s>>>(bs, m, c.lambda, (uint32_t*)bint.p, (uint8_t*)bdec.p, status);
+        g->launches++;
+        bs = (const uint32_t*)bint.p;
+        dq = (const uint8_t*)bdec.p;
+    }
+    k_validate_csr<<<grid_for(g, (m > n ? m : n), 256), 256, 0, s>>>(n, m, rp, cl, bs, c.max_bits, real, status);
     g->launches++;
     uint32_t hst = 0;
     if (!cu(cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, s), "status read") ||
         !cu(cudaStreamSynchronize(s), "validate")) { release_stage(); return fail(st); }
     if (hst & ST_INVALID) {
-        set_error("invalid CSR: ids >= n, zero or too-wide biases, or malformed row_ptr");
+        set_error(real ? "invalid CSR: ids >= n, real biases not finite / negative / zero-weight / lambda*b >= 2^31, "
+                         "degree >= 2^24, or malformed row_ptr"
+                       : "invalid CSR: ids >= n, zero or too-wide biases, or malformed row_ptr");
         release_stage();
         return fail(BINGO_E_INVALID);
     }
@@ -369,6 +441,8 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
     G.max_bits = c.max_bits;
     G.alpha = c.alpha_pct;
     G.beta = c.beta_pct;
+    G.fbits = real ? FRAC_BITS : 0;
+    G.lambda = real ? c.lambda : 0.0;
     G.vh = (VHot*)g->d_hdr;
     G.vc = (VCold*)g->d_cold;
     G.pool.status = status;
@@ -426,7 +500,7 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
     G.eh_cnt = nullptr;
     G.eh_mask = 0;
     if (!cu(cudaMemcpyAsync(G.pool.top, &need, 8, cudaMemcpyHostToDevice, s), "pool top")) { release_all(); return fail(st); }
-    k_build_fill<<<wblocks, 256, 0, s>>>(G, rp, cl, bs, (uint64_t*)offs.p, base);
+    k_build_fill<<<wblocks, 256, 0, s>>>(G, rp, cl, bs, dq, (uint64_t*)offs.p, base);
     g->launches++;
     if (!cu(cudaGetLastError(), "build fill") || !cu(cudaStreamSynchronize(s), "build fill")) { release_all(); return fail(st); }
     release_all();
@@ -517,6 +591,38 @@ bingo_status bingo_state_sizes_get(bingo_graph* g, bingo_state_sizes* out) {
     out->pool_words_used = top;
     out->pool_words_total = g->G.pool.words;
     out->next_edge_id = g->next_eid;
+    return BINGO_OK;
+}
+
+bingo_status bingo_export_decimal(bingo_graph* g, uint8_t* q) {
+    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+    if (!g->G.fbits) { set_error("not a real-bias graph"); return BINGO_E_STATE; }
+    CK(cudaDeviceSynchronize(), "sync");
+    ExportPlan P;
+    uint64_t t[3];
+    bingo_status st = export_plan(g, P, t);
+    if (st != BINGO_OK) { P.release_all(); return st; }
+    const uint64_t m = t[0];
+    Buf o;
+    cudaError_t e = ensure(o, m + 64);
+    if (e != cudaSuccess) { P.release_all(); return cuda_fail(e, "export staging"); }
+    unsigned long long* obad = (unsigned long long*)o.p;
+    uint8_t* oq = (uint8_t*)o.p + 16;
+    e = cudaMemset(obad, 0, 8);
+    if (e == cudaSuccess) {
+        k_export_dec<<<grid_for(g, (uint64_t)g->n * 32, 256), 256>>>(g->G, (uint64_t*)P.eoff.p, oq, obad);
+        e = cudaDeviceSynchronize();
+    }
+    unsigned long long nbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&nbad, obad, 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && q && m) e = cudaMemcpy(q, oq, m, cudaMemcpyDeviceToHost);
+    release(o);
+    P.release_all();
+    if (e != cudaSuccess) return cuda_fail(e, "export copy");
+    if (nbad) {
+        set_error("export: %llu vertices whose decimal total or flag disagrees with their decimal parts", nbad);
+        return BINGO_E_STATE;
+    }
     return BINGO_OK;
 }
 

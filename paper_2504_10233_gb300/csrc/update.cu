@@ -47,8 +47,9 @@ struct BatchSrc {
     __device__ __forceinline__ uint4 ins(uint32_t i) const { return rec[start + i]; }
     __device__ __forceinline__ uint64_t ins_eid(uint32_t i) const {
         const uint4 r = rec[start + i];
-        return (uint64_t)r.x | ((uint64_t)r.w << 32);
+        return (uint64_t)r.x | ((uint64_t)(r.w & 0xFFFFFFu) << 32);
     }
+    __device__ __forceinline__ uint32_t ins_q(uint32_t i) const { return rec[start + i].w >> 24; }
     __device__ __forceinline__ uint32_t del_dst_global(uint32_t j) const {
         return (uint32_t)(keys[start + ni + j] & dmask);
     }
@@ -56,12 +57,13 @@ struct BatchSrc {
 };
 
 struct OneSrc {
-    uint32_t dst, bias;
+    uint32_t dst, bias, q;  // bias: the factorised (integer) part; q: decimal part of a real bias
     uint64_t eid;
     const uint32_t* sdel = nullptr;
     __device__ __forceinline__ uint32_t del_dst_global(uint32_t) const { return dst; }
     __device__ __forceinline__ uint4 ins(uint32_t) const { return make_uint4(0, dst, bias, 0); }
     __device__ __forceinline__ uint64_t ins_eid(uint32_t) const { return eid; }
+    __device__ __forceinline__ uint32_t ins_q(uint32_t) const { return q; }
     __device__ __forceinline__ uint32_t del_dst(uint32_t) const { return dst; }
 };
 
@@ -95,7 +97,7 @@ __device__ __forceinline__ KindMasks kind_masks(const Team& t, SegSh& sh, const 
     if (warp_team || threadIdx.x < 32) {
         const uint32_t lane = threadIdx.x & 31;
         const uint32_t c = cnt[lane];
-        const uint32_t kd = kind_of(c, d, G.alpha, G.beta);
+        const uint32_t kd = slot_kind(G, c, d, lane);
         km.sp = __ballot_sync(FULL, kd == K_SPARSE);
         km.reg = __ballot_sync(FULL, kd == K_REGULAR);
         km.one = __ballot_sync(FULL, kd == K_ONE);
@@ -254,6 +256,22 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
                 ne[j] = oe[j];
             }
         }
+        if (G.fbits) {  // the decimal block follows the adjacency's capacity
+            if (rank == 0) sh.alloc_off = pool_alloc(G.pool, dec_words(capa1));
+            t.sync();
+            const uint64_t qoff = sh.alloc_off;
+            if (qoff == 0) return;
+            uint8_t* nq = reinterpret_cast<uint8_t*>(G.pool.base + qoff);
+            if (d0) {
+                const uint8_t* oq = dec_bytes(G, (uint32_t)sh.gref_old[DEC_SLOT]);
+                for (uint32_t j = rank; j < d0; j += T) nq[j] = oq[j];
+            }
+            t.sync();
+            if (rank == 0) {
+                if (capa0) pool_free(G.pool, words_of(sh.gref_old[DEC_SLOT]), dec_words(capa0));
+                sh.gref_new[DEC_SLOT] = ref_of(qoff);
+            }
+        }
         t.sync();
         if (rank == 0) {
             if (capa0) pool_free(G.pool, h0.adj, 4ull * capa0);
@@ -264,12 +282,15 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     const uint64_t adj = sh.adj;
     uint2* pairs = adj_pairs(G, adj);
     uint64_t* eids = adj_eids(G, adj, capa1);
+    // real biases: decimal part of each slot (moves with its edge)
+    uint8_t* qbytes = (G.fbits && sh.gref_new[DEC_SLOT]) ? dec_bytes(G, (uint32_t)sh.gref_new[DEC_SLOT]) : nullptr;
 
     // ---- S2: append insertions at slots d0 .. d0+ni-1
     for (uint32_t i = rank; i < ni; i += T) {
         const uint4 u = B.ins(i);
         pairs[d0 + i] = make_uint2(u.y, u.z);
         eids[d0 + i] = B.ins_eid(i);
+        if (qbytes) qbytes[d0 + i] = (uint8_t)B.ins_q(i);
     }
     for (uint32_t j = rank; j < nd; j += T) {
         X.del_slot[j] = NONE32;
@@ -413,8 +434,22 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
             for (uint32_t b = w; b; b &= b - 1) atomicAdd(&sh.delta[__ffs(b) - 1], 1);
         }
     }
+    uint32_t q_add = 0, q_sub = 0;  // decimal total: parts of surviving insertions minus deleted edges
+    if (qbytes) {
+        for (uint32_t b = 0; b < nd; b += T) {
+            const uint32_t j = b + rank;
+            const uint32_t s = j < nd ? X.del_slot[j] : NONE32;
+            q_sub += t.sum(s != NONE32 && s < d0 ? (uint32_t)qbytes[s] : 0u);
+        }
+        for (uint32_t b = 0; b < ni; b += T) {
+            const uint32_t i = b + rank;
+            q_add += t.sum(i < ni && !(eids[d0 + i] & DEAD_BIT) ? (uint32_t)qbytes[d0 + i] : 0u);
+        }
+    }
     t.sync();
-    for (uint32_t k = rank; k < 32; k += T) sh.cnt_new[k] = (uint32_t)((int32_t)sh.cnt_old[k] + sh.delta[k]);
+    for (uint32_t k = rank; k < 32; k += T)
+        sh.cnt_new[k] = (qbytes && k == DEC_SLOT) ? sh.cnt_old[k] + q_add - q_sub
+                                                  : (uint32_t)((int32_t)sh.cnt_old[k] + sh.delta[k]);
     t.sync();
     const KindMasks kmn = kind_masks(t, sh, sh.cnt_new, d1, G, 1);
     const uint32_t SPn = kmn.sp, REGn = kmn.reg, ONEn = kmn.one, maskn = kmn.nonempty;
@@ -534,6 +569,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
                 const uint2 e = pairs[p];
                 pairs[q] = e;
                 eids[q] = eids[p];
+                if (qbytes) qbytes[q] = qbytes[p];
                 if (p < d0) {
                     for (uint32_t bb = e.y & REGk; bb; bb &= bb - 1) {
                         const uint32_t k = __ffs(bb) - 1;
@@ -638,6 +674,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     }
     for (int k = rank; k < 32; k += T) {
         const uint32_t bit = 1u << k;
+        if (G.fbits && k == (int)DEC_SLOT) continue;  // the decimal block stays with the adjacency
         if (!(maskn & bit) || (!(REGn & bit) && !(SPn & bit) && !(ONEn & bit))) sh.gref_new[k] = 0;  // dense / empty
     }
     t.sync();
@@ -705,8 +742,8 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
         if (rebuilt) atomicAdd(stats + S_REBUILT, (unsigned long long)rebuilt);
     }
     for (uint32_t k = rank; k < 32; k += T) {
-        const uint32_t ko = kind_of(sh.cnt_old[k], d0, G.alpha, G.beta);
-        const uint32_t kn = kind_of(sh.cnt_new[k], d1, G.alpha, G.beta);
+        const uint32_t ko = slot_kind(G, sh.cnt_old[k], d0, k);
+        const uint32_t kn = slot_kind(G, sh.cnt_new[k], d1, k);
         if (ko != kn) atomicAdd(stats + S_CONV + ko * 5 + kn, 1ull);
     }
     t.sync();
@@ -719,6 +756,8 @@ struct BatchArgs {
     uint64_t count;                // record capacity (grid size); the live count is *count_dev when set
     const uint64_t* count_dev;
     uint32_t n, max_bits, bn;
+    uint32_t fbits;       // real biases (Section 4.3) when nonzero
+    double lambda;
     uint64_t* keys;
     uint32_t* vals;
     uint64_t* packed;     // per record: nkeys (low 32) | is_insert (high 32)
@@ -741,7 +780,12 @@ __global__ void k_expand(BatchArgs A) {
         const bool ins = u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS;
         const bool del = u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS;
         bad |= u.x >= A.n || u.y >= A.n || u.w > 2;
-        if (ins) bad |= u.z == 0 || (A.max_bits < 32 && (u.z >> A.max_bits) != 0);
+        if (ins && A.fbits) {
+            uint32_t I, q;
+            bad |= !split_real_bias(u.z, A.lambda, I, q);
+        } else if (ins) {
+            bad |= u.z == 0 || (A.max_bits < 32 && (u.z >> A.max_bits) != 0);
+        }
         A.packed[i] = (uint64_t)(ins ? 1 : 0) + (del ? 1 : 0) + ((uint64_t)(ins ? 1 : 0) << 32);
     }
     if (bad) atomicOr(A.status, ST_INVALID);
@@ -770,12 +814,12 @@ __global__ void k_make_keys(BatchArgs A) {
 __global__ void k_key_count(const uint64_t* total, uint64_t* nkeys) { *nkeys = *total & 0xFFFFFFFFull; }
 
 // Segment heads of the sorted keys; for each insertion key, the record it applies in key order
-// ({edge id low, dst, bias, edge id high}, the edge id from the insertion's batch rank), so the
-// per-vertex pass reads its insertions contiguously.
+// ({edge id low, dst, factorised bias, edge id bits 32-55 | decimal part << 24}, the edge id from
+// the insertion's batch rank), so the per-vertex pass reads its insertions contiguously.
 __global__ void k_seg_flags(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t cap,
                             const uint64_t* __restrict__ nkeys_dev, uint32_t bn, const uint4* __restrict__ ups,
                             const uint64_t* __restrict__ pscan, const unsigned long long* __restrict__ eid_base,
-                            uint64_t* __restrict__ flag, uint4* __restrict__ rec) {
+                            uint32_t fbits, double lambda, uint64_t* __restrict__ flag, uint4* __restrict__ rec) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t nkeys = nkeys_dev ? *nkeys_dev : cap;
     for (uint64_t i = tid; i < cap; i += nt) {
@@ -786,7 +830,9 @@ __global__ void k_seg_flags(const uint64_t* __restrict__ keys, const uint32_t* _
             const uint32_t r = vals[i];
             const uint4 u = ups[r];
             const uint64_t eid = *eid_base + (pscan[r] >> 32);
-            rec[i] = make_uint4((uint32_t)eid, u.y, u.z, (uint32_t)(eid >> 32));
+            uint32_t I = u.z, q = 0;
+            if (fbits) split_real_bias(u.z, lambda, I, q);
+            rec[i] = make_uint4((uint32_t)eid, u.y, I, ((uint32_t)(eid >> 32) & 0xFFFFFFu) | (q << 24));
         }
     }
 }
@@ -813,7 +859,8 @@ __device__ __forceinline__ unsigned long long pool_bound(const DevGraph& G, uint
     const uint32_t capa1 = grows ? capa_for(dmax) : capa_of(h);
     uint32_t nblocks = 0, sp_possible = 0;
     bool sp_set_may_change = false, any_old_sp = false;
-    for (uint32_t k = 0; k < 32; k++) {
+    const uint32_t nslots = G.fbits ? DEC_SLOT : 32u;  // the decimal slot is never a list
+    for (uint32_t k = 0; k < nslots; k++) {
         const uint32_t c = cnt_ref(G, v, k);
         const uint32_t cmax = c + (((insbits >> k) & 1u) ? ni : 0u), cmin = c > nd ? c - nd : 0u;
         const uint32_t old = kind_of(c, d0, G.alpha, G.beta);
@@ -837,7 +884,7 @@ __device__ __forceinline__ unsigned long long pool_bound(const DevGraph& G, uint
     // the sparse list and all sparse groups are rebuilt together when the set changes, the adjacency
     // grows, or insertions may outgrow the sparse capacity
     const bool sp_rebuild = sp_set_may_change || grows || (ni > 0 && any_old_sp);
-    unsigned long long words = grows ? 4ull * capa1 : 0ull;
+    unsigned long long words = grows ? 4ull * capa1 + (G.fbits ? dec_words(capa1) : 0ull) : 0ull;
     words += 4ull * capa1 * nblocks;
     if (sp_possible && sp_rebuild) words += 2ull * capa1 + 4ull * capa1 * sp_possible;
     return words;
@@ -883,6 +930,7 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
         S.seginfo[sidx] = make_uint4(v, a, ni, b - lo);
         const VHdr h = load_hdr(G, v);
         const uint32_t dtot = h.deg + ni;
+        if (G.fbits && dtot >= REAL_MAX_DEG) { atomicOr(G.pool.status, ST_INVALID); continue; }
         uint32_t insbits = 0;
         for (uint32_t i = a; i < lo; i++) insbits |= S.rec[i].z;
         bound += pool_bound(G, v, h, ni, b - lo, insbits);
@@ -1078,8 +1126,14 @@ __global__ void __launch_bounds__(STREAM_TEAMS * 32) k_stream_apply(DevGraph G, 
             const uint32_t ni = (u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
             const uint32_t nd = (u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
             // reserve this record's worst-case pool growth so no allocation inside it can fail
+            uint32_t I = u.z, qd = 0;
+            if (G.fbits && ni) split_real_bias(u.z, G.lambda, I, qd);
             const VHdr h = load_hdr(G, u.x);
-            const unsigned long long need = pool_bound(G, u.x, h, ni, nd, ni ? u.z : 0u);
+            if (G.fbits && h.deg + ni >= REAL_MAX_DEG) {
+                if (t.rank() == 0) atomicOr(G.pool.status, ST_INVALID);
+                return;
+            }
+            const unsigned long long need = pool_bound(G, u.x, h, ni, nd, ni ? I : 0u);
             int ok = 1;
             if (t.rank() == 0) {
                 const unsigned long long prev = atomicAdd(reserved, need);
@@ -1093,7 +1147,8 @@ __global__ void __launch_bounds__(STREAM_TEAMS * 32) k_stream_apply(DevGraph G, 
             if (!ok) return;
             OneSrc src;
             src.dst = u.y;
-            src.bias = u.z;
+            src.bias = I;
+            src.q = qd;
             src.eid = S.eid_base + (S.B.pscan[rec] >> 32);
             SegScratch X;
             X.holes = xs[w].holes;
@@ -1261,6 +1316,8 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     A.count_dev = ctl + CTL_SCR + 8;
     A.n = g->n;
     A.max_bits = g->cfg.max_bits;
+    A.fbits = g->G.fbits;
+    A.lambda = g->G.lambda;
     A.bn = bits_for(g->n);
     A.keys = (uint64_t*)g->s_keys.p;
     A.vals = (uint32_t*)g->s_vals.p;
@@ -1288,8 +1345,8 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     uint32_t* big_list = small_list + kc + 2;
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
     k_seg_flags<<<grid_cap(g, kc, 256), 256, 0, s>>>(skeys, svals, kc, nkeys_dev, A.bn, A.ups, A.pscan,
-                                                     (const unsigned long long*)(ctl + CTL_SCR + 9), flag,
-                                                     (uint4*)g->s_rec.p);
+                                                     (const unsigned long long*)(ctl + CTL_SCR + 9), A.fbits,
+                                                     A.lambda, flag, (uint4*)g->s_rec.p);
     CK(scan_excl_u64(flag, segid, kc, nseg_dev, g->s_tmp, s, &g->launches), "segment scan");
     k_seg_write<<<grid_cap(g, kc, 256), 256, 0, s>>>(flag, segid, kc, nkeys_dev, seg_start);
     g->launches += 2;
@@ -1337,6 +1394,7 @@ bingo_status bingo_apply_updates(bingo_graph* g, const bingo_update* ups, uint64
     if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
     if (count && !ups) { set_error("NULL update array"); return BINGO_E_INVALID; }
     if (count >= 0x3FFFFFFFull) { set_error("batch too large"); return BINGO_E_INVALID; }
+    if (g->next_eid + count >= (1ull << 56)) { set_error("edge id space exhausted"); return BINGO_E_INVALID; }
     cudaStream_t s = (cudaStream_t)stream;
     if (count == 0) {
         if (stats) memset(stats, 0, sizeof(*stats));
@@ -1396,6 +1454,7 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
     if (count && !ups) { set_error("NULL update array"); return BINGO_E_INVALID; }
     if (count >= 0x7FFFFFFFull) { set_error("too many records"); return BINGO_E_INVALID; }
+    if (g->next_eid + count >= (1ull << 56)) { set_error("edge id space exhausted"); return BINGO_E_INVALID; }
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t* ctl = (uint64_t*)g->d_ctl;
     CK(cudaMemsetAsync(ctl + CTL_STATUS, 0, 8, s), "status reset");
@@ -1422,6 +1481,8 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     A.count_dev = nullptr;
     A.n = g->n;
     A.max_bits = g->cfg.max_bits;
+    A.fbits = g->G.fbits;
+    A.lambda = g->G.lambda;
     A.bn = bits_for(g->n);
     A.keys = (uint64_t*)g->s_keys.p;
     A.vals = (uint32_t*)g->s_vals.p;
@@ -1444,7 +1505,7 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     uint32_t* seg_start = (uint32_t*)(segid + count);
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
     k_seg_flags<<<grid_cap(g, count, 256), 256, 0, s>>>(skeys, svals, count, nullptr, A.bn, A.ups, A.pscan, nullptr,
-                                                        flag, nullptr);
+                                                        0u, 0.0, flag, nullptr);
     CK(scan_excl_u64(flag, segid, count, nseg_dev, g->s_tmp, s, &g->launches), "stream segments");
     k_seg_write<<<grid_cap(g, count, 256), 256, 0, s>>>(flag, segid, count, nullptr, seg_start);
     SegArgs S;

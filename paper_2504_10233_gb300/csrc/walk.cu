@@ -112,8 +112,10 @@ __device__ __forceinline__ uint4 ld_pair(const DevGraph& G, uint32_t v, uint32_t
     if (i < HOT_GROUPS / 2) return ld_hot(reinterpret_cast<const uint4*>(G.vh + v) + 1 + i);
     return __ldg(reinterpret_cast<const uint4*>(G.vc + v) + (i - HOT_GROUPS / 2));
 }
-__device__ __forceinline__ uint64_t pair_w(uint4 x, uint32_t i) {
-    return ((uint64_t)x.x << (2 * i)) + ((uint64_t)x.z << (2 * i + 1));
+// fb = 0 for integer biases; for real biases every integer group counts 2^fb times and slot 31 (the
+// second half of pair 15) carries the decimal total itself.
+__device__ __forceinline__ uint64_t pair_w(uint4 x, uint32_t i, uint32_t fb) {
+    return slot_w(x.x, 2 * i, fb) + slot_w(x.z, 2 * i + 1, fb);
 }
 // pairs with at least one nonempty group, as bits 2i of the result
 __device__ __forceinline__ uint32_t pair_bits(uint32_t mask) { return (mask | (mask >> 1)) & 0x55555555u; }
@@ -124,10 +126,10 @@ __device__ __forceinline__ uint32_t pair_bits(uint32_t mask) { return (mask | (m
 // of T lanes shares the vertex record.  Outputs k*, |G_k*| and the group's ref.
 
 __device__ __forceinline__ bool scan_pair(uint4 x, uint32_t i, uint64_t r, uint64_t& acc, uint32_t& ks, uint32_t& cs,
-                                          uint32_t& ref) {
-    const uint64_t lo = acc + ((uint64_t)x.x << (2 * i));
+                                          uint32_t& ref, uint32_t fb) {
+    const uint64_t lo = acc + slot_w(x.x, 2 * i, fb);
     if (r < lo) { ks = 2 * i; cs = x.x; ref = x.y; return true; }
-    acc = lo + ((uint64_t)x.z << (2 * i + 1));
+    acc = lo + slot_w(x.z, 2 * i + 1, fb);
     if (r < acc) { ks = 2 * i + 1; cs = x.z; ref = x.w; return true; }
     return false;
 }
@@ -138,7 +140,8 @@ __device__ __forceinline__ bool scan_pair(uint4 x, uint32_t i, uint64_t r, uint6
 __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status) {
     const uint32_t pb = pair_bits(h.mask);
-    const uint64_t whot = pair_w(h.p0, 0) + pair_w(h.p1, 1) + pair_w(h.p2, 2);
+    const uint32_t fb = G.fbits;
+    const uint64_t whot = pair_w(h.p0, 0, fb) + pair_w(h.p1, 1, fb) + pair_w(h.p2, 2, fb);
     uint64_t part[4];
     uint64_t tot = whot;
 #pragma unroll
@@ -152,15 +155,15 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
                 x[j] = (i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair(G, v, i) : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
-            for (int j = 0; j < 4; j++) part[b] += pair_w(x[j], 3 + 4 * b + j);
+            for (int j = 0; j < 4; j++) part[b] += pair_w(x[j], 3 + 4 * b + j, fb);
         }
         tot += part[b];
     }
     const uint64_t r = below64(R, tot, status);
     uint64_t acc = 0;
-    if (scan_pair(h.p0, 0, r, acc, ks, cs, ref)) return;
-    if (scan_pair(h.p1, 1, r, acc, ks, cs, ref)) return;
-    if (scan_pair(h.p2, 2, r, acc, ks, cs, ref)) return;
+    if (scan_pair(h.p0, 0, r, acc, ks, cs, ref, fb)) return;
+    if (scan_pair(h.p1, 1, r, acc, ks, cs, ref, fb)) return;
+    if (scan_pair(h.p2, 2, r, acc, ks, cs, ref, fb)) return;
     int bs = 3;
 #pragma unroll
     for (int b = 0; b < 3; b++) {
@@ -174,7 +177,7 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
 #pragma unroll
     for (int j = 0; j < 4; j++) {
         const uint32_t i = 3 + 4 * bs + j;
-        if (!found && i < 16 && ((pb >> (2 * i)) & 1u)) found = scan_pair(ld_pair(G, v, i), i, r, acc, ks, cs, ref);
+        if (!found && i < 16 && ((pb >> (2 * i)) & 1u)) found = scan_pair(ld_pair(G, v, i), i, r, acc, ks, cs, ref, fb);
     }
     if (!found) atomicOr(status, ST_STATE);
 }
@@ -188,7 +191,7 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
     uint64_t s = 0;
     for (uint32_t m = mine; m; m &= m - 1) {
         const uint32_t i = 4 * tl + ((__ffs(m) - 1) >> 1);
-        s += pair_w(ld_pair(G, v, i), i);
+        s += pair_w(ld_pair(G, v, i), i, G.fbits);
     }
     uint64_t incl = s;
 #pragma unroll
@@ -208,9 +211,9 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
         for (uint32_t m = mine; m && !found; m &= m - 1) {
             const uint32_t i = 4 * tl + ((__ffs(m) - 1) >> 1);
             const uint4 x = ld_pair(G, v, i);
-            acc += (uint64_t)x.x << (2 * i);
+            acc += slot_w(x.x, 2 * i, G.fbits);
             if (r < acc) { k_l = 2 * i; c_l = x.x; r_l = x.y; found = true; break; }
-            acc += (uint64_t)x.z << (2 * i + 1);
+            acc += slot_w(x.z, 2 * i + 1, G.fbits);
             if (r < acc) { k_l = 2 * i + 1; c_l = x.z; r_l = x.w; found = true; }
         }
     }
@@ -227,7 +230,7 @@ __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, c
     uint2 gk = make_uint2(0, 0);
     if ((h.mask >> lane) & 1u)
         gk = __ldg(lane < HOT_GROUPS ? &G.vh[v].g[lane] : &G.vc[v].g[lane - HOT_GROUPS]);
-    uint64_t incl = (uint64_t)gk.x << lane;
+    uint64_t incl = slot_w(gk.x, lane, G.fbits);
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const uint64_t y = __shfl_up_sync(FULL, incl, d);
@@ -246,8 +249,44 @@ __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, c
 // and sparse groups keep their members' destinations at the head of the group block, so a uniform
 // position costs one access.  Dense groups use rejection over the whole neighbour list, accepting a
 // slot whose bias has bit k* (Section 5.1).  Returns the destination vertex.
+// Decimal group of a real-bias vertex (Section 4.3, step (iii)): neighbour j with probability
+// q_j / Q_D.  Rejection over the d slots, a uniform slot accepted iff a uniform byte < q_j, four
+// candidates per round with their loads in flight; after DEC_ROUNDS rounds, inverse transform over
+// the decimal parts.  Either way the output law is q_j / Q_D, so the fallback keeps it exact.
+constexpr int DEC_ROUNDS = 4;
+// Inverse transform over the decimal parts: the first slot whose running sum of q exceeds r < Q_D.
+__device__ __noinline__ uint32_t decimal_its(const uint8_t* qb, const uint2* pairs, uint32_t d, uint32_t r) {
+    uint32_t acc = 0;
+    for (uint32_t j = 0; j < d; j++) {
+        acc += __ldg(qb + j);
+        if (r < acc) return __ldg(&pairs[j].x);
+    }
+    return NONE32;
+}
+__device__ __forceinline__ uint32_t pick_decimal(const DevGraph& G, const Sec0& h, uint32_t qd, uint32_t ref,
+                                                 StepRng& R, uint32_t* status) {
+    if (words_of(ref) >= G.pool.words || qd == 0) { atomicOr(status, ST_STATE); return NONE32; }
+    const uint8_t* qb = dec_bytes(G, ref);
+    const uint2* pairs = adj_pairs(G, words_of(h.adj));
+    for (int t = 0; t < DEC_ROUNDS; t++) {
+        uint32_t j[4], q[4];
+        const uint32_t u = R.next();
+#pragma unroll
+        for (int c = 0; c < 4; c++) j[c] = below32(R, h.deg, status);
+#pragma unroll
+        for (int c = 0; c < 4; c++) q[c] = __ldg(qb + j[c]);
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+            if (((u >> (8 * c)) & 255u) < q[c]) return __ldg(&pairs[j[c]].x);
+    }
+    const uint32_t x = decimal_its(qb, pairs, h.deg, below32(R, qd, status));
+    if (x == NONE32) atomicOr(status, ST_STATE);
+    return x;
+}
+
 __device__ __forceinline__ uint32_t pick_member(const DevGraph& G, const Sec0& h, uint32_t ks, uint32_t cs,
                                                 uint32_t ref, StepRng& R, uint32_t* status) {
+    if (G.fbits && ks == DEC_SLOT) return pick_decimal(G, h, cs, ref, R, status);
     const uint32_t kd = kind_of(cs, h.deg, G.alpha, G.beta);
     if (kd == K_DENSE) {
         const uint2* pairs = adj_pairs(G, words_of(h.adj));
