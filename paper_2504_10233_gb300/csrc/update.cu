@@ -89,7 +89,7 @@ struct SegSh {
 struct KindMasks {
     uint32_t sp, reg, one, nonempty;
 };
-template <class Team>
+template <bool REAL, class Team>
 __device__ __forceinline__ KindMasks kind_masks(const Team& t, SegSh& sh, const uint32_t* cnt, uint32_t d,
                                                 const DevGraph& G, int slot) {
     KindMasks km;
@@ -97,7 +97,7 @@ __device__ __forceinline__ KindMasks kind_masks(const Team& t, SegSh& sh, const 
     if (warp_team || threadIdx.x < 32) {
         const uint32_t lane = threadIdx.x & 31;
         const uint32_t c = cnt[lane];
-        const uint32_t kd = slot_kind(G, c, d, lane);
+        const uint32_t kd = (REAL && lane == DEC_SLOT) ? (uint32_t)K_EMPTY : kind_of(c, d, G.alpha, G.beta);
         km.sp = __ballot_sync(FULL, kd == K_SPARSE);
         km.reg = __ballot_sync(FULL, kd == K_REGULAR);
         km.one = __ballot_sync(FULL, kd == K_ONE);
@@ -208,7 +208,8 @@ struct SegScratch {
 };
 
 // Apply one vertex's segment (ni insertions then nd deletions).  Returns false if the graph ran out of pool.
-template <class Team, class Src>
+// REAL: real-bias graphs (decimal parts follow their edges, slot 31 holds the decimal total).
+template <bool REAL, class Team, class Src>
 __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint32_t v, uint32_t ni, uint32_t nd,
                               Src B, const SegScratch& X, unsigned long long* stats, uint32_t* sdel_buf,
                               uint32_t sdel_cap, uint32_t* cand_buf = nullptr, uint32_t cand_cap = 0) {
@@ -233,7 +234,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     }
     t.sync();
     // old kinds
-    const KindMasks kmo = kind_masks(t, sh, sh.cnt_old, d0, G, 0);
+    const KindMasks kmo = kind_masks<REAL>(t, sh, sh.cnt_old, d0, G, 0);
     const uint32_t SPo = kmo.sp, REGo = kmo.reg, ONEo = kmo.one;
 
     // ---- S1: adjacency capacity for the insertions
@@ -256,7 +257,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
                 ne[j] = oe[j];
             }
         }
-        if (G.fbits) {  // the decimal block follows the adjacency's capacity
+        if constexpr (REAL) {  // the decimal block follows the adjacency's capacity
             if (rank == 0) sh.alloc_off = pool_alloc(G.pool, dec_words(capa1));
             t.sync();
             const uint64_t qoff = sh.alloc_off;
@@ -283,7 +284,9 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     uint2* pairs = adj_pairs(G, adj);
     uint64_t* eids = adj_eids(G, adj, capa1);
     // real biases: decimal part of each slot (moves with its edge)
-    uint8_t* qbytes = (G.fbits && sh.gref_new[DEC_SLOT]) ? dec_bytes(G, (uint32_t)sh.gref_new[DEC_SLOT]) : nullptr;
+    uint8_t* qbytes = nullptr;
+    if constexpr (REAL)
+        if (sh.gref_new[DEC_SLOT]) qbytes = dec_bytes(G, (uint32_t)sh.gref_new[DEC_SLOT]);
 
     // ---- S2: append insertions at slots d0 .. d0+ni-1
     for (uint32_t i = rank; i < ni; i += T) {
@@ -451,7 +454,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
         sh.cnt_new[k] = (qbytes && k == DEC_SLOT) ? sh.cnt_old[k] + q_add - q_sub
                                                   : (uint32_t)((int32_t)sh.cnt_old[k] + sh.delta[k]);
     t.sync();
-    const KindMasks kmn = kind_masks(t, sh, sh.cnt_new, d1, G, 1);
+    const KindMasks kmn = kind_masks<REAL>(t, sh, sh.cnt_new, d1, G, 1);
     const uint32_t SPn = kmn.sp, REGn = kmn.reg, ONEn = kmn.one, maskn = kmn.nonempty;
     // bits of the deleted pre-existing edges (the groups that lose members)
     const uint32_t deadbits = t.or_all(deadbits_local);
@@ -674,7 +677,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     }
     for (int k = rank; k < 32; k += T) {
         const uint32_t bit = 1u << k;
-        if (G.fbits && k == (int)DEC_SLOT) continue;  // the decimal block stays with the adjacency
+        if (REAL && k == (int)DEC_SLOT) continue;  // the decimal block stays with the adjacency
         if (!(maskn & bit) || (!(REGn & bit) && !(SPn & bit) && !(ONEn & bit))) sh.gref_new[k] = 0;  // dense / empty
     }
     t.sync();
@@ -742,8 +745,9 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
         if (rebuilt) atomicAdd(stats + S_REBUILT, (unsigned long long)rebuilt);
     }
     for (uint32_t k = rank; k < 32; k += T) {
-        const uint32_t ko = slot_kind(G, sh.cnt_old[k], d0, k);
-        const uint32_t kn = slot_kind(G, sh.cnt_new[k], d1, k);
+        const bool dec = REAL && k == DEC_SLOT;
+        const uint32_t ko = dec ? (uint32_t)K_EMPTY : kind_of(sh.cnt_old[k], d0, G.alpha, G.beta);
+        const uint32_t kn = dec ? (uint32_t)K_EMPTY : kind_of(sh.cnt_new[k], d1, G.alpha, G.beta);
         if (ko != kn) atomicAdd(stats + S_CONV + ko * 5 + kn, 1ull);
     }
     t.sync();
@@ -956,7 +960,7 @@ struct SmallScratch {
     unsigned long long best[SMALL_X];
 };
 
-template <class Team>
+template <bool REAL, class Team>
 __device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, const SegArgs& S, SegSh& sh, uint32_t sidx,
                                             uint32_t* sdel_buf, uint32_t sdel_cap, uint32_t* cand_buf,
                                             uint32_t cand_cap, SmallScratch* sx = nullptr,
@@ -984,7 +988,7 @@ __device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, co
         X.best = S.best + a + ni;
     }
     src.sdel = nullptr;
-    apply_segment(t, G, sh, v, ni, nd, src, X, stats ? stats : S.stats, sdel_buf, sdel_cap, cand_buf, cand_cap);
+    apply_segment<REAL>(t, G, sh, v, ni, nd, src, X, stats ? stats : S.stats, sdel_buf, sdel_cap, cand_buf, cand_cap);
 }
 
 constexpr uint32_t SMALL_SDEL = 64;    // staged deletion destinations per warp team
@@ -1014,6 +1018,7 @@ union ApplyShared {
     SmallShared small;
 };
 
+template <bool REAL>
 __global__ void __launch_bounds__(APPLY_THREADS, 2) k_apply(DevGraph G, SegArgs S) {
     __shared__ ApplyShared smem;
     __shared__ unsigned long long next;
@@ -1030,7 +1035,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) k_apply(DevGraph G, SegArgs 
             const unsigned long long i = next;
             __syncthreads();
             if (i >= nbig) break;
-            run_segment(t, G, S, smem.big.sh, S.big_list[i], smem.big.sdel, BIG_SDEL, smem.big.cand, BIG_CAND, nullptr,
+            run_segment<REAL>(t, G, S, smem.big.sh, S.big_list[i], smem.big.sdel, BIG_SDEL, smem.big.cand, BIG_CAND, nullptr,
                         bstats);
         }
     }
@@ -1043,7 +1048,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) k_apply(DevGraph G, SegArgs 
             i = (*(volatile uint32_t*)G.pool.status & ST_STOP) ? nsmall : atomicAdd(S.queue, 1ull);
         i = __shfl_sync(FULL, i, 0);
         if (i >= nsmall) break;
-        run_segment(t, G, S, smem.small.sh[w], S.small_list[i], smem.small.sdel[w], SMALL_SDEL, smem.small.cand[w],
+        run_segment<REAL>(t, G, S, smem.small.sh[w], S.small_list[i], smem.small.sdel[w], SMALL_SDEL, smem.small.cand[w],
                     SMALL_CAND, &smem.small.x[w], bstats);
     }
     __syncthreads();
@@ -1110,6 +1115,7 @@ struct StreamScratch {
     unsigned long long best[2];
 };
 
+template <bool REAL>
 __global__ void __launch_bounds__(STREAM_TEAMS * 32) k_stream_apply(DevGraph G, SegArgs S,
                                                                     unsigned long long* reserved) {
     __shared__ SegSh sh[STREAM_TEAMS];
@@ -1127,9 +1133,9 @@ __global__ void __launch_bounds__(STREAM_TEAMS * 32) k_stream_apply(DevGraph G, 
             const uint32_t nd = (u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
             // reserve this record's worst-case pool growth so no allocation inside it can fail
             uint32_t I = u.z, qd = 0;
-            if (G.fbits && ni) split_real_bias(u.z, G.lambda, I, qd);
+            if (REAL && ni) split_real_bias(u.z, G.lambda, I, qd);
             const VHdr h = load_hdr(G, u.x);
-            if (G.fbits && h.deg + ni >= REAL_MAX_DEG) {
+            if (REAL && h.deg + ni >= REAL_MAX_DEG) {
                 if (t.rank() == 0) atomicOr(G.pool.status, ST_INVALID);
                 return;
             }
@@ -1156,7 +1162,7 @@ __global__ void __launch_bounds__(STREAM_TEAMS * 32) k_stream_apply(DevGraph G, 
             X.ins_final = xs[w].ins_final;
             X.del_slot = xs[w].del_slot;
             X.best = xs[w].best;
-            apply_segment(t, G, sh[w], u.x, ni, nd, src, X, S.stats, nullptr, 0u);
+            apply_segment<REAL>(t, G, sh[w], u.x, ni, nd, src, X, S.stats, nullptr, 0u);
             if (G.eh_mask && t.rank() == 0) {  // edge index: +1 per insertion, -1 per deletion that found an edge
                 const unsigned long long k = ((unsigned long long)u.x << 32) | u.y;
                 if (ni) {
@@ -1296,7 +1302,9 @@ static bingo_status update_capacity(bingo_graph* g, uint64_t count) {
     CK(ensure(g->s_tmp, std::max(radix_sort_tmp_bytes(kc), scan_tmp_bytes(kc))), "update scratch");
     if (!g->apply_blocks) {
         int per_sm = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply, APPLY_THREADS, 0), "apply occupancy");
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, g->G.fbits ? k_apply<true> : k_apply<false>,
+                                                         APPLY_THREADS, 0),
+           "apply occupancy");
         g->apply_blocks = (unsigned)std::max(1, per_sm) * (unsigned)g->num_sms;
     }
     g->upd_cap = cap;
@@ -1374,7 +1382,8 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     k_seg_classify<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S);
     S.queue = (unsigned long long*)(ctl + CTL_SCR + 11);
     k_oom_check<<<1, 1, 0, s>>>(g->G, counts, S.queue);
-    k_apply<<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
+    if (g->G.fbits) k_apply<true><<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
+    else k_apply<false><<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
     g->launches += 3;
     if (g->G.eh_mask) {
         k_eh_apply<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S, kc, nkeys_dev);
@@ -1520,7 +1529,8 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     S.stats = (unsigned long long*)(ctl + CTL_STATS);
     unsigned long long* reserved = (unsigned long long*)(ctl + CTL_SCR + 7);
     const unsigned blocks = grid_cap(g, count, STREAM_TEAMS, 8);
-    k_stream_apply<<<blocks, STREAM_TEAMS * 32, 0, s>>>(g->G, S, reserved);
+    if (g->G.fbits) k_stream_apply<true><<<blocks, STREAM_TEAMS * 32, 0, s>>>(g->G, S, reserved);
+    else k_stream_apply<false><<<blocks, STREAM_TEAMS * 32, 0, s>>>(g->G, S, reserved);
     g->launches += 3;
     CK(cudaGetLastError(), "stream launch");
     bingo_status st = finish_batch(g, s, stats, 0);

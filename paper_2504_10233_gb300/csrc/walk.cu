@@ -137,10 +137,11 @@ __device__ __forceinline__ bool scan_pair(uint4 x, uint32_t i, uint64_t r, uint6
 // T = 1: one lane per walker.  Pairs 0-2 came with the header; the cold pairs 3..15 are read in
 // batches of four whose loads are issued together (predicated on the mask), keeping per-batch
 // sums; the batch holding k* is re-read (L1 hits) to find the group.
+template <bool REAL>
 __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status) {
     const uint32_t pb = pair_bits(h.mask);
-    const uint32_t fb = G.fbits;
+    constexpr uint32_t fb = REAL ? FRAC_BITS : 0u;
     const uint64_t whot = pair_w(h.p0, 0, fb) + pair_w(h.p1, 1, fb) + pair_w(h.p2, 2, fb);
     uint64_t part[4];
     uint64_t tot = whot;
@@ -184,6 +185,7 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
 
 // T = 4: lane t of the team owns pairs [4t, 4t+4) (groups 8t..8t+7); a two-level shuffle prefix
 // over the team and a ballot find the lane holding k*, which searches its pairs again.
+template <bool REAL>
 __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status,
                                                uint32_t tl, uint32_t team_mask, uint32_t team_base) {
@@ -191,7 +193,7 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
     uint64_t s = 0;
     for (uint32_t m = mine; m; m &= m - 1) {
         const uint32_t i = 4 * tl + ((__ffs(m) - 1) >> 1);
-        s += pair_w(ld_pair(G, v, i), i, G.fbits);
+        s += pair_w(ld_pair(G, v, i), i, REAL ? FRAC_BITS : 0u);
     }
     uint64_t incl = s;
 #pragma unroll
@@ -211,9 +213,9 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
         for (uint32_t m = mine; m && !found; m &= m - 1) {
             const uint32_t i = 4 * tl + ((__ffs(m) - 1) >> 1);
             const uint4 x = ld_pair(G, v, i);
-            acc += slot_w(x.x, 2 * i, G.fbits);
+            acc += slot_w(x.x, 2 * i, REAL ? FRAC_BITS : 0u);
             if (r < acc) { k_l = 2 * i; c_l = x.x; r_l = x.y; found = true; break; }
-            acc += slot_w(x.z, 2 * i + 1, G.fbits);
+            acc += slot_w(x.z, 2 * i + 1, REAL ? FRAC_BITS : 0u);
             if (r < acc) { k_l = 2 * i + 1; c_l = x.z; r_l = x.w; found = true; }
         }
     }
@@ -224,13 +226,14 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
 
 // T = 32: lane k owns group k; a warp-wide shuffle prefix of W_k = 2^k |G_k| and a ballot of
 // (prefix > r) give k* as the first set bit.
+template <bool REAL>
 __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                 uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status,
                                                 uint32_t lane) {
     uint2 gk = make_uint2(0, 0);
     if ((h.mask >> lane) & 1u)
         gk = __ldg(lane < HOT_GROUPS ? &G.vh[v].g[lane] : &G.vc[v].g[lane - HOT_GROUPS]);
-    uint64_t incl = slot_w(gk.x, lane, G.fbits);
+    uint64_t incl = slot_w(gk.x, lane, REAL ? FRAC_BITS : 0u);
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const uint64_t y = __shfl_up_sync(FULL, incl, d);
@@ -284,9 +287,11 @@ __device__ __forceinline__ uint32_t pick_decimal(const DevGraph& G, const Sec0& 
     return x;
 }
 
+template <bool REAL>
 __device__ __forceinline__ uint32_t pick_member(const DevGraph& G, const Sec0& h, uint32_t ks, uint32_t cs,
                                                 uint32_t ref, StepRng& R, uint32_t* status) {
-    if (G.fbits && ks == DEC_SLOT) return pick_decimal(G, h, cs, ref, R, status);
+    if constexpr (REAL)
+        if (ks == DEC_SLOT) return pick_decimal(G, h, cs, ref, R, status);
     const uint32_t kd = kind_of(cs, h.deg, G.alpha, G.beta);
     if (kd == K_DENSE) {
         const uint2* pairs = adj_pairs(G, words_of(h.adj));
@@ -315,7 +320,7 @@ __device__ __forceinline__ uint32_t pick_member(const DevGraph& G, const Sec0& h
 }
 
 // One step of a walker at `cur`.  Returns false if the walk ends here (PPR stop, no out-edge, error).
-template <int T>
+template <int T, bool REAL>
 __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A, uint64_t wid, uint32_t pid,
                                           uint32_t step, uint32_t& cur, uint32_t& prev, uint32_t tl,
                                           uint32_t team_mask, uint32_t team_base, uint32_t lane) {
@@ -333,10 +338,10 @@ __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A
     if (h.deg == 0) return false;
     for (int attempt = 0; attempt < MAX_N2V_TRIES; attempt++) {
         uint32_t ks, cs, ref;
-        if constexpr (T == 1) select_group_1(G, cur, h, R, ks, cs, ref, A.status);
-        else if constexpr (T == 4) select_group_4(G, cur, h, R, ks, cs, ref, A.status, tl, team_mask, team_base);
-        else select_group_32(G, cur, h, R, ks, cs, ref, A.status, lane);
-        const uint32_t x = pick_member(G, h, ks, cs, ref, R, A.status);
+        if constexpr (T == 1) select_group_1<REAL>(G, cur, h, R, ks, cs, ref, A.status);
+        else if constexpr (T == 4) select_group_4<REAL>(G, cur, h, R, ks, cs, ref, A.status, tl, team_mask, team_base);
+        else select_group_32<REAL>(G, cur, h, R, ks, cs, ref, A.status, lane);
+        const uint32_t x = pick_member<REAL>(G, h, ks, cs, ref, R, A.status);
         if (x >= G.n) {
             if (x != NONE32) atomicOr(A.status, ST_STATE);
             return false;
@@ -374,7 +379,8 @@ __device__ __forceinline__ void finish_walker(const WalkParams& A, uint64_t wid,
 
 // OCC selects the register budget: 0 = up to 64 registers (1,024-thread bound), 1 = 40 registers
 // (256-thread blocks, six per SM), trading spills to L1 for 50% more resident warps.
-template <int T, int OCC>
+// REAL: real-bias graphs (decimal group in slot 31); integer graphs run the instance without it.
+template <int T, int OCC, bool REAL>
 __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persistent(DevGraph G, WalkParams A) {
     const uint32_t lane = threadIdx.x & 31, tl = lane % T, team = lane / T;
     const uint32_t team_base = team * T;
@@ -418,7 +424,7 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
             continue;
         }
         if (have) {
-            const bool took = walk_step<T>(G, A, wid, pid, step, cur, prev, tl, team_mask, team_base, lane);
+            const bool took = walk_step<T, REAL>(G, A, wid, pid, step, cur, prev, tl, team_mask, team_base, lane);
             if (took) {
                 step++;
                 if (tl == 0) A.paths[wid * (uint64_t)A.stride + step] = cur;
@@ -432,6 +438,7 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
 }
 
 // The paper's step-by-step form (Section 6 (iii)): one launch per step, one thread per walker.
+template <bool REAL>
 __global__ void k_walk_step(DevGraph G, WalkParams A, uint32_t s) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t wid = tid; wid < A.nwalkers; wid += nt) {
@@ -455,7 +462,7 @@ __global__ void k_walk_step(DevGraph G, WalkParams A, uint32_t s) {
             if (cur == NONE32) continue;
             prev = A.s_prev[wid];
         }
-        const bool took = walk_step<1>(G, A, wid, pid, s, cur, prev, 0, 0, 0, 0);
+        const bool took = walk_step<1, REAL>(G, A, wid, pid, s, cur, prev, 0, 0, 0, 0);
         if (took) A.paths[wid * (uint64_t)A.stride + s + 1] = cur;
         if (!took || s + 1 == L) {
             finish_walker(A, wid, took ? s + 1 : s, 0, 1);
@@ -516,23 +523,28 @@ bingo_status edge_index_build(bingo_graph* g, cudaStream_t s) {
     return BINGO_OK;
 }
 
-static int g_occ_cache[2][3][33];
+static int g_occ_cache[2][2][3][33];
 
 template <int T, int OCC>
-static void* walk_kernel_ptr() { return (void*)k_walk_persistent<T, OCC>; }
-
-static void* walk_kernel(int lanes, int occ) {
-    if (occ) return lanes == 1 ? walk_kernel_ptr<1, 1>() : lanes == 4 ? walk_kernel_ptr<4, 1>() : walk_kernel_ptr<32, 1>();
-    return lanes == 1 ? walk_kernel_ptr<1, 0>() : lanes == 4 ? walk_kernel_ptr<4, 0>() : walk_kernel_ptr<32, 0>();
+static void* walk_kernel_ptr(bool real) {
+    return real ? (void*)k_walk_persistent<T, OCC, true> : (void*)k_walk_persistent<T, OCC, false>;
 }
 
-static int walk_blocks_per_sm(int lanes, int wpb, int occ) {
+static void* walk_kernel(int lanes, int occ, bool real) {
+    if (occ)
+        return lanes == 1 ? walk_kernel_ptr<1, 1>(real) : lanes == 4 ? walk_kernel_ptr<4, 1>(real)
+                                                                     : walk_kernel_ptr<32, 1>(real);
+    return lanes == 1 ? walk_kernel_ptr<1, 0>(real) : lanes == 4 ? walk_kernel_ptr<4, 0>(real)
+                                                                 : walk_kernel_ptr<32, 0>(real);
+}
+
+static int walk_blocks_per_sm(int lanes, int wpb, int occ, bool real) {
     const int li = lanes == 1 ? 0 : lanes == 4 ? 1 : 2;
     if (wpb < 1 || wpb > 32) return 1;
-    int& c = g_occ_cache[occ ? 1 : 0][li][wpb];
+    int& c = g_occ_cache[real ? 1 : 0][occ ? 1 : 0][li][wpb];
     if (c) return c;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel(lanes, occ), wpb * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel(lanes, occ, real), wpb * 32, 0);
     c = nb < 1 ? 1 : nb;
     return c;
 }
@@ -566,7 +578,8 @@ bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
         A.s_prev = A.s_cur + nwalkers;
         const unsigned blocks = (unsigned)std::min<uint64_t>((nwalkers + 255) / 256, (uint64_t)g->num_sms * 8);
         for (uint32_t st = 0; st < (max_steps ? max_steps : 1); st++) {
-            k_walk_step<<<blocks, 256, 0, s>>>(g->G, A, st);
+            if (g->G.fbits) k_walk_step<true><<<blocks, 256, 0, s>>>(g->G, A, st);
+            else k_walk_step<false><<<blocks, 256, 0, s>>>(g->G, A, st);
             g->launches++;
         }
         CK(cudaGetLastError(), "stepwise walk launch");
@@ -578,7 +591,8 @@ bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
     int wpb = (int)g->tune.warps_per_block;
     if (occ_mode && wpb > 8) wpb = 8;  // the 40-register variant is bounded to 256-thread blocks
     int bps = (int)g->tune.blocks_per_sm;
-    const int occ = walk_blocks_per_sm(lanes, wpb, occ_mode);
+    const bool real = g->G.fbits != 0;
+    const int occ = walk_blocks_per_sm(lanes, wpb, occ_mode, real);
     if (bps <= 0 || bps > occ) bps = occ;
     uint64_t blocks = (uint64_t)g->num_sms * bps;
     const uint64_t walkers_per_block = (uint64_t)wpb * (32 / lanes);
@@ -586,7 +600,7 @@ bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
     if (blocks > useful) blocks = useful;
     if (blocks == 0) blocks = 1;
     void* args[] = {(void*)&g->G, (void*)&A};
-    CK(cudaLaunchKernel(walk_kernel(lanes, occ_mode), dim3((unsigned)blocks), dim3(wpb * 32), args, 0, s),
+    CK(cudaLaunchKernel(walk_kernel(lanes, occ_mode, real), dim3((unsigned)blocks), dim3(wpb * 32), args, 0, s),
        "walk launch");
     g->launches++;
     CK(cudaGetLastError(), "walk launch");
