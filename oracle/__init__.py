@@ -89,6 +89,9 @@ def _p(a):
     return a.ctypes.data_as(t)
 
 
+ALL_REGULAR = 0xFFFFFFFF  # alpha value of the paper's BS baseline: every nonempty group regular
+
+
 def kind(cnt: int, d: int, alpha: int = 40, beta: int = 10) -> int:
     return _L().o_kind(cnt, d, alpha, beta)
 

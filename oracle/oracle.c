@@ -259,9 +259,13 @@ int o_apply(o_graph* g, const uint32_t* rec, uint64_t count, uint32_t max_bits, 
 
 /* Eq. group, evaluated in its printed order (first match wins), with percent
  * thresholds compared in integers: dense iff |G|/d > alpha%, one-element iff
- * |G| = 1, sparse iff |G|/d < beta% (and |G| != 1), regular otherwise. */
+ * |G| = 1, sparse iff |G|/d < beta% (and |G| != 1), regular otherwise.
+ * alpha = O_ALL_REGULAR turns group adaption off (every nonempty group regular). */
+#define O_ALL_REGULAR 0xFFFFFFFFu /* alpha value selecting the paper's BS baseline (Section 6.2,
+                                     Fig. Moptimization): every nonempty group in regular format */
 int o_kind(uint64_t cnt, uint64_t d, uint32_t alpha, uint32_t beta) {
     if (cnt == 0) return O_EMPTY;
+    if (alpha == O_ALL_REGULAR) return O_REGULAR;
     if (100 * cnt > (uint64_t)alpha * d) return O_DENSE;
     if (cnt == 1) return O_ONE;
     if (100 * cnt < (uint64_t)beta * d) return O_SPARSE;

@@ -379,3 +379,22 @@ def test_real_bias_validation():
     assert rc == 0 and st == (1, 0, 0)
     I, q, qsum = g.real_parts()
     assert [int(x) for x in I] == [1, 0] and [int(x) for x in q] == [128, 64] and int(qsum[0]) == 192
+
+
+def test_baseline_all_regular():
+    """Section 6.2 (Fig. Moptimization): the BS baseline keeps every group in regular format.  The
+    factorisation (counts, memberships) is unchanged, every nonempty group is regular, and the
+    sampler still draws w / sum w (Theorem 1 does not depend on the representation)."""
+    rng = np.random.default_rng(21)
+    configs = [tuple(int(x) for x in rng.integers(1, 64, size=int(rng.integers(1, 9)))) for _ in range(400)]
+    configs += [tuple([1] * 9 + [2, 6]), tuple([1] * 30 + [3, 3]), tuple([7] * 3 + [1] * 40 + [64, 128])]
+    g = _vertex_graph(configs)
+    for v, ws in enumerate(configs):
+        cnt_ga, kd_ga, sw = g.factor(v)
+        cnt, kd, sw2 = g.factor(v, O.ALL_REGULAR, 0)
+        assert (cnt == cnt_ga).all() and sw == sw2 == sum(ws)
+        assert all(int(kd[k]) == (O.REGULAR if cnt[k] else O.EMPTY) for k in range(32))
+        for i, w in enumerate(ws):
+            assert Fraction(*g.factored_prob(v, i, O.ALL_REGULAR, 0)) == Fraction(w, sum(ws))
+    # the last vertex has dense and one-element groups under Eq. group (and none under BS, above)
+    assert {int(x) for x in g.factor(len(configs) - 1)[1]} >= {O.DENSE, O.ONE}
