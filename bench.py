@@ -665,6 +665,145 @@ def run_serving(args):
     g.close()
 
 
+def _timed_walks(torch, B, g, starts, stride, nsteps, warmup, seed0, flush, stream):
+    """Median CUDA-event time of `nsteps` DeepWalk launches (after `warmup`), L2 flushed before each."""
+    nw = len(starts)
+    paths = torch.empty((nw, stride), dtype=torch.int32, device=starts.device)
+    plen = torch.empty(nw, dtype=torch.int32, device=starts.device)
+    pol = [B.policy(B.DEEPWALK, stride - 1)]
+    ms, steps = [], 0
+    for i in range(warmup + nsteps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.walk(starts, pol, seed0 + i, stride, paths, plen, mode=B.WALK_PERSISTENT | B.WALK_NO_PAD, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+            steps = int((plen.to(torch.int64) - 1).sum().item())
+    g.check(stream)
+    return float(np.median(ms)), steps
+
+
+def _timed_batches(torch, g, recs, warmup, flush, stream):
+    ms, conv = [], np.zeros((5, 5), dtype=np.int64)
+    for i, r in enumerate(recs):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = g.apply_updates(r, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+        conv += np.array(st["conversions"])
+    return float(np.median(ms)), conv
+
+
+def run_ablation(args):
+    """f1: real-valued biases with lambda (Section 4.3) against the integer graph of their integer
+    parts; f2: group adaption (Eq. group) against the all-regular baseline (Section 6.2).  Same
+    RMAT-20 graph, walkers and batch sizes as the main bench workload."""
+    import torch
+
+    import paper_2504_10233_gb300 as B
+
+    B.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    nb = args.warmup + args.steps
+    wl = W.make_workload("c2", nbatch=nb)
+    G = wl.graph
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    starts = t(W.walk_starts(G.n, wl.nwalkers, wl.walk_seed))
+    stride = wl.length + 1
+    sampler = ClockSampler(0)
+    if args.workload == "f1":
+        lam = 10.0
+        rng = np.random.default_rng(31)  # real biases uniform in [0.5, 100), the range of the float workload
+        breal = rng.uniform(0.5, 100.0, size=len(G.col)).astype(np.float32)
+        real = B.Graph(G.n, t(G.row_ptr), t(G.col), t(breal.view(np.uint32)), bias_format=B.BIAS_F32, lambda_=lam)
+        ex = real.export_state()  # integer parts of the real graph, in the same CSR order
+        integer = B.Graph(G.n, t(G.row_ptr), t(G.col), t(ex["bias"]), max_bits=32)
+        recs_r, recs_i = [], []
+        for b in wl.batches:
+            r = b.records().copy()
+            ins = r[:, 3] != 1
+            br = rng.uniform(0.5, 100.0, size=int(ins.sum())).astype(np.float32)
+            ri = r.copy()
+            r[ins, 2] = br.view(np.uint32)
+            ri[ins, 2] = np.floor(lam * br.astype(np.float64)).astype(np.uint32)
+            recs_r.append(t(r))
+            recs_i.append(t(ri))
+        sampler.start()
+        w_r, steps_r = _timed_walks(torch, B, real, starts, stride, args.steps, args.warmup, 7, flush, stream)
+        w_i, steps_i = _timed_walks(torch, B, integer, starts, stride, args.steps, args.warmup, 7, flush, stream)
+        u_r, _ = _timed_batches(torch, real, recs_r, args.warmup, flush, stream)
+        u_i, _ = _timed_batches(torch, integer, recs_i, args.warmup, flush, stream)
+        clocks = sampler.stop()
+        mr, mi = real.memory_report(), integer.memory_report()
+        state_r = sum(v for k, v in mr.items() if k != "pool_capacity")
+        state_i = sum(v for k, v in mi.items() if k != "pool_capacity")
+        ex = real.export_state()
+        cnt = ex["cnt"].astype(np.float64)
+        WI = (cnt[:, :31] * np.exp2(np.arange(31) + 8)).sum(axis=1)
+        share = np.where(WI + cnt[:, 31] > 0, cnt[:, 31] / np.maximum(WI + cnt[:, 31], 1), 0)
+        line = {"metric": "walk time, real-valued over integer biases (Section 4.3)", "value": w_r / w_i, "unit": "x",
+                "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                "dtype": "u32 integer parts + u8 decimal parts", "data": "synthetic",
+                "config": {"workload": "RMAT-20 (2^20 vertices, 2^24 edges), real biases uniform in [0.5, 100), "
+                                       "lambda = 10; integer twin: the same graph with biases floor(lambda b); "
+                                       "2^20 DeepWalk x 80; batches of 10^5 updates (50/50)",
+                           "l2": "flushed before every launch"},
+                "walk_ms": {"real": w_r, "integer": w_i},
+                "walk_steps_per_s": {"real": steps_r / (w_r / 1e3), "integer": steps_i / (w_i / 1e3)},
+                "update_ms_per_batch": {"real": u_r, "integer": u_i},
+                "state_bytes": {"real": state_r, "integer": state_i, "ratio": state_r / state_i},
+                "decimal_share_mean_over_vertices": float(share[ex["deg"] > 0].mean()),
+                "paper_context": "A100: 1.02x time, 1.08x memory (real vs integer biases)",
+                "clocks": clocks}
+    else:
+        ga = B.Graph(G.n, t(G.row_ptr), t(G.col), t(G.w), max_bits=G.max_bits)
+        mem_ga = ga.memory_report()
+        bsg = None
+        try:
+            bsg = B.Graph(G.n, t(G.row_ptr), t(G.col), t(G.w), max_bits=G.max_bits, all_regular=1)
+        except B.BingoError as e:  # the baseline may not fit where group adaption does
+            bs_err = str(e)
+        recs = [t(b.records()) for b in wl.batches]
+        sampler.start()
+        w_ga, steps = _timed_walks(torch, B, ga, starts, stride, args.steps, args.warmup, 7, flush, stream)
+        u_ga, conv = _timed_batches(torch, ga, recs, args.warmup, flush, stream)
+        mem_bs = w_bs = u_bs = None
+        if bsg is not None:
+            mem_bs = bsg.memory_report()
+            w_bs, _ = _timed_walks(torch, B, bsg, starts, stride, args.steps, args.warmup, 7, flush, stream)
+            u_bs, _ = _timed_batches(torch, bsg, recs, args.warmup, flush, stream)
+        clocks = sampler.stop()
+        grp = lambda m: m["regular_groups"] + m["sparse_groups"]
+        tot = lambda m: sum(v for k, v in m.items() if k not in ("pool_capacity", "edge_index"))
+        line = {"metric": "memory of the sampling state, all-regular baseline over group adaption (Section 6.2)",
+                "value": (tot(mem_bs) / tot(mem_ga)) if mem_bs else None, "unit": "x", "higher_is_better": True,
+                "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "u32/u64", "data": "synthetic",
+                "config": {"workload": "RMAT-20 (2^20 vertices, 2^24 edges), floor(Pareto 1.5) biases; 2^20 DeepWalk "
+                                       "x 80; batches of 10^5 updates (50/50)", "l2": "flushed before every launch"},
+                "memory_bytes": {"ga": mem_ga, "bs": mem_bs},
+                "group_memory_ratio": (grp(mem_bs) / max(1, grp(mem_ga))) if mem_bs else None,
+                "walk_ms": {"ga": w_ga, "bs": w_bs}, "walk_steps_per_s_ga": steps / (w_ga / 1e3),
+                "update_ms_per_batch": {"ga": u_ga, "bs": u_bs},
+                "ga_conversions_all_batches": conv.tolist(),
+                "paper_context": "A100: GA uses 14.6-22.2x less memory than BS and is 1.09x faster overall",
+                "clocks": clocks}
+        if bsg is None:
+            line["bs_unavailable"] = bs_err
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -692,6 +831,8 @@ def main():
         run_serving(args)
     elif args.workload == "c5":
         run_sweep(args)
+    elif args.workload in ("f1", "f2"):
+        run_ablation(args)
     else:
         run_ours(args)
 

@@ -84,7 +84,8 @@ typedef struct {
     uint32_t reg_variant;      /* walker register budget: 0 = 64 registers, 1 = 40 registers (more resident warps) */
     uint64_t pool_words;       /* device pool for adjacency and group blocks, in 4-byte words; 0 = auto */
     uint32_t bias_format;      /* BINGO_BIAS_U32 (default) or BINGO_BIAS_F32 */
-    uint32_t reserved0;
+    uint32_t all_regular;      /* 1: no group adaption, every nonempty group in regular format (the paper's
+                                  BS baseline, Section 6.2); 0 (default): Eq. group */
     double lambda;             /* BINGO_BIAS_F32: amortisation factor lambda > 0 (Section 4.3) */
 } bingo_config;
 

@@ -85,9 +85,14 @@ __host__ __device__ __forceinline__ uint32_t ref_of(uint64_t words) { return (ui
 __host__ __device__ __forceinline__ uint32_t capa_of(const VHdr& h) { return h.lcapa ? (1u << (h.lcapa - 1)) : 0u; }
 __host__ __device__ __forceinline__ uint32_t caps_of(const VHdr& h) { return h.lcaps ? (1u << (h.lcaps - 1)) : 0u; }
 
+// alpha value that turns group adaption off: every nonempty group regular (the BS baseline of the
+// group-adaption ablation, Section 6.2).
+constexpr uint32_t ALL_REGULAR = 0xFFFFFFFFu;
+
 // Eq. group (Section 5.1), in its printed order with strict percent comparisons.
 __host__ __device__ __forceinline__ uint32_t kind_of(uint32_t c, uint32_t d, uint32_t alpha, uint32_t beta) {
     if (c == 0) return K_EMPTY;
+    if (alpha == ALL_REGULAR) return K_REGULAR;
     const uint64_t c100 = 100ull * c;
     if (c100 > (uint64_t)alpha * d) return K_DENSE;
     if (c == 1) return K_ONE;

@@ -439,8 +439,8 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
     DevGraph& G = g->G;
     G.n = n;
     G.max_bits = c.max_bits;
-    G.alpha = c.alpha_pct;
-    G.beta = c.beta_pct;
+    G.alpha = c.all_regular ? ALL_REGULAR : c.alpha_pct;
+    G.beta = c.all_regular ? 0u : c.beta_pct;
     G.fbits = real ? FRAC_BITS : 0;
     G.lambda = real ? c.lambda : 0.0;
     G.vh = (VHot*)g->d_hdr;

@@ -868,8 +868,9 @@ __device__ __forceinline__ unsigned long long pool_bound(const DevGraph& G, uint
         const uint32_t c = cnt_ref(G, v, k);
         const uint32_t cmax = c + (((insbits >> k) & 1u) ? ni : 0u), cmin = c > nd ? c - nd : 0u;
         const uint32_t old = kind_of(c, d0, G.alpha, G.beta);
-        if (cmax < 2) continue;  // can never be a list kind (and is not one now)
-        const uint32_t lo2 = cmin > 2 ? cmin : 2;
+        const uint32_t min_list = G.alpha == ALL_REGULAR ? 1u : 2u;  // smallest count of a list kind
+        if (cmax < min_list) continue;  // can never be a list kind (and is not one now)
+        const uint32_t lo2 = cmin > min_list ? cmin : min_list;
         // sparse reachable: the smallest count >= 2 stays below beta% of the largest degree
         const bool can_sp = 100ull * lo2 < (uint64_t)G.beta * dmax;
         // regular reachable: [lo2, cmax] meets [ceil(beta dmin / 100), floor(alpha dmax / 100)]

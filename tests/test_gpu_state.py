@@ -325,3 +325,26 @@ def test_pool_exhaustion_rejects_batch_unchanged(B):
     ex = g.export_state()  # whatever streamed before the stop is complete and consistent
     from tests.gpu_helpers import check_layout_invariants
     check_layout_invariants(ex)
+
+
+def test_baseline_all_regular_parity_and_memory(B):
+    """The BS baseline of the group-adaption ablation (Section 6.2): every nonempty group regular.
+    Bit-exact against the oracle's BS mode through batches and streaming; group adaption (Eq. group)
+    needs less memory for group structures on the same graph."""
+    og = _stress_graph(12)
+    offs, dst, w, eid = og.edges()
+    bs = B.Graph(og.n, dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=12, all_regular=1)
+    ga = B.Graph(og.n, dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=12)
+    ex = bs.export_state()
+    assert_state_matches(ex, og, O.ALL_REGULAR, 0)
+    assert set(np.unique(ex["kind"]).tolist()) == {O.EMPTY, O.REGULAR}
+    mem_bs, mem_ga = bs.memory_report(), ga.memory_report()
+    assert mem_ga["regular_groups"] + mem_ga["sparse_groups"] < mem_bs["regular_groups"]
+    rng = np.random.default_rng(77)
+    for it in range(8):
+        rec = _stress_batch(rng, og, og.n, [1, 17, 300, 64][it % 4])
+        if it % 2:
+            apply_both(bs, og, rec, 12, stream=True)
+        else:
+            apply_both(bs, og, rec, 12)
+        assert_state_matches(bs.export_state(), og, O.ALL_REGULAR, 0)
