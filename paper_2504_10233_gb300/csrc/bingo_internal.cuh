@@ -2,7 +2,8 @@
 //
 // Device state of a graph (all in HBM):
 //   vh[v]   VHot, 64 bytes: header {adjacency block, degree d, nonempty-group mask, sparse-list
-//           block} and groups 0-5 as {|G_k|, ref} (Eq. wpk: W(p_k) = 2^k |G_k|); ref = destination of
+//           block (real-bias graphs: the decimal total Q_D, the sparse-list block moving to the
+//           cold part)} and groups 0-5 as {|G_k|, ref} (Eq. wpk: W(p_k) = 2^k |G_k|); ref = destination of
 //           the member of a one-element group, or the group block of a regular/sparse group, else 0.
 //           The hot array is n x 64 B, small enough to stay largely in L2.
 //   vc[v]   VCold, 224 bytes: groups 6-31 and the update-only fields (|S|, log2 capacities).
@@ -64,7 +65,7 @@ struct __align__(64) VHot {
     uint32_t adj;   // adjacency block, 32-byte units
     uint32_t deg;
     uint32_t mask;
-    uint32_t sref;  // sparse-list block, 32-byte units
+    uint32_t sref;  // sparse-list block, 32-byte units; real-bias graphs: the decimal total Q_D
     uint2 g[HOT_GROUPS];
 };
 struct __align__(32) VCold {
@@ -72,7 +73,8 @@ struct __align__(32) VCold {
     uint32_t nsp;
     uint8_t lcapa, lcaps;
     uint16_t pad;
-    uint32_t spare0, spare1;
+    uint32_t sref_real;  // real-bias graphs: the sparse-list block (32-byte units)
+    uint32_t spare1;
 };
 static_assert(sizeof(VHot) == 64, "VHot must be two sectors");
 static_assert(sizeof(VCold) == 224, "VCold must be seven sectors");
@@ -199,7 +201,7 @@ __device__ __forceinline__ VHdr load_hdr(const DevGraph& G, uint64_t v) {
     h.adj = words_of(a.adj);
     h.deg = a.deg;
     h.mask = a.mask;
-    h.sref = words_of(a.sref);
+    h.sref = words_of(G.fbits ? b.sref_real : a.sref);
     h.nsp = b.nsp;
     h.lcapa = b.lcapa;
     h.lcaps = b.lcaps;
@@ -212,12 +214,16 @@ __device__ __forceinline__ void store_hdr(const DevGraph& G, uint64_t v, const V
     a.adj = ref_of(h.adj);
     a.deg = h.deg;
     a.mask = h.mask;
-    a.sref = ref_of(h.sref);
+    if (G.fbits) b.sref_real = ref_of(h.sref);  // the hot word holds the decimal total (set_decimal_total)
+    else a.sref = ref_of(h.sref);
     b.nsp = h.nsp;
     b.lcapa = h.lcapa;
     b.lcaps = h.lcaps;
     b.pad = 0;
 }
+// Real-bias graphs: the decimal total lives in group slot 31 and, for the walker, in the hot line.
+__device__ __forceinline__ void set_decimal_total(const DevGraph& G, uint64_t v, uint32_t qd) { G.vh[v].sref = qd; }
+
 // {|G_k|, ref} of group k of vertex v
 __device__ __forceinline__ uint2& grp(const DevGraph& G, uint64_t v, uint32_t k) {
     return k < HOT_GROUPS ? G.vh[v].g[k] : G.vc[v].g[k - HOT_GROUPS];

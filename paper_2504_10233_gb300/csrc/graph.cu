@@ -105,6 +105,7 @@ __global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const
             h.lcaps = caps ? (uint8_t)(log2_u32(caps) + 1) : 0;
             h.pad = 0;
             store_hdr(G, v, h);
+            if (G.fbits) set_decimal_total(G, v, 0);  // k_build_fill sets it for vertices with edges
         }
     }
 }
@@ -147,7 +148,10 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
                 qs = __reduce_add_sync(FULL, qs);
                 if (lane == DEC_SLOT) gref = ref_of(next);
                 if (qs) h.mask |= 1u << DEC_SLOT;
-                if (lane == 0) cnt_ref(G, v, DEC_SLOT) = qs;
+                if (lane == 0) {
+                    cnt_ref(G, v, DEC_SLOT) = qs;
+                    set_decimal_total(G, v, qs);
+                }
                 next += dec_words(capa);
             }
         }
@@ -290,7 +294,8 @@ __global__ void k_export_dec(DevGraph G, const uint64_t* __restrict__ eoff, uint
         }
         qs = __reduce_add_sync(FULL, qs);
         const bool flag = ((h.mask >> DEC_SLOT) & 1u) != (qs != 0);
-        if (lane == 0 && (qs != cnt_ref(G, v, DEC_SLOT) || flag || (h.deg && !ref))) atomicAdd(bad, 1ull);
+        const bool hot = G.vh[v].sref != qs;
+        if (lane == 0 && (qs != cnt_ref(G, v, DEC_SLOT) || flag || hot || (h.deg && !ref))) atomicAdd(bad, 1ull);
     }
 }
 

@@ -726,6 +726,8 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     for (uint32_t k = rank; k < 32; k += T) {
         grp(G, v, k) = make_uint2(sh.cnt_new[k], (uint32_t)sh.gref_new[k]);
     }
+    if constexpr (REAL)
+        if (rank == 0) set_decimal_total(G, v, sh.cnt_new[DEC_SLOT]);
     if (rank == 0) {
         VHdr h;
         h.adj = adj;

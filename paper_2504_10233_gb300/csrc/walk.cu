@@ -137,11 +137,22 @@ __device__ __forceinline__ bool scan_pair(uint4 x, uint32_t i, uint64_t r, uint6
 // T = 1: one lane per walker.  Pairs 0-2 came with the header; the cold pairs 3..15 are read in
 // batches of four whose loads are issued together (predicated on the mask), keeping per-batch
 // sums; the batch holding k* is re-read (L1 hits) to find the group.
+// Real-bias graphs: the decimal total Q_D comes with the hot line (Sec0.sref), so for the totals pair
+// 15 is read only for group 30 (its slot-31 half taken as empty) and Q_D is added to the last batch;
+// pair 15 is read whole only when r falls in that batch.
+template <bool REAL>
+__device__ __forceinline__ uint4 ld_pair_tot(const DevGraph& G, uint32_t v, uint32_t i) {
+    uint4 x = ld_pair(G, v, i);
+    if (REAL && i == 15) x.z = 0;
+    return x;
+}
+
 template <bool REAL>
 __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status) {
-    const uint32_t pb = pair_bits(h.mask);
     constexpr uint32_t fb = REAL ? FRAC_BITS : 0u;
+    const uint32_t pbf = pair_bits(h.mask);                                  // pairs holding a nonempty slot
+    const uint32_t pb = REAL ? pair_bits(h.mask & ~(1u << DEC_SLOT)) : pbf;  // pairs read for the totals
     const uint64_t whot = pair_w(h.p0, 0, fb) + pair_w(h.p1, 1, fb) + pair_w(h.p2, 2, fb);
     uint64_t part[4];
     uint64_t tot = whot;
@@ -153,11 +164,12 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const uint32_t i = 3 + 4 * b + j;
-                x[j] = (i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair(G, v, i) : make_uint4(0, 0, 0, 0);
+                x[j] = (i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair_tot<REAL>(G, v, i) : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
             for (int j = 0; j < 4; j++) part[b] += pair_w(x[j], 3 + 4 * b + j, fb);
         }
+        if (REAL && b == 3) part[b] += h.sref;  // decimal total, slot 31 of pair 15
         tot += part[b];
     }
     const uint64_t r = below64(R, tot, status);
@@ -178,7 +190,7 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
 #pragma unroll
     for (int j = 0; j < 4; j++) {
         const uint32_t i = 3 + 4 * bs + j;
-        if (!found && i < 16 && ((pb >> (2 * i)) & 1u)) found = scan_pair(ld_pair(G, v, i), i, r, acc, ks, cs, ref, fb);
+        if (!found && i < 16 && ((pbf >> (2 * i)) & 1u)) found = scan_pair(ld_pair(G, v, i), i, r, acc, ks, cs, ref, fb);
     }
     if (!found) atomicOr(status, ST_STATE);
 }
@@ -253,10 +265,9 @@ __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, c
 // position costs one access.  Dense groups use rejection over the whole neighbour list, accepting a
 // slot whose bias has bit k* (Section 5.1).  Returns the destination vertex.
 // Decimal group of a real-bias vertex (Section 4.3, step (iii)): neighbour j with probability
-// q_j / Q_D.  Rejection over the d slots, a uniform slot accepted iff a uniform byte < q_j, four
-// candidates per round with their loads in flight; after DEC_ROUNDS rounds, inverse transform over
-// the decimal parts.  Either way the output law is q_j / Q_D, so the fallback keeps it exact.
-constexpr int DEC_ROUNDS = 4;
+// q_j / Q_D.  Rejection over the d slots, a uniform slot accepted iff a uniform byte < q_j; after
+// DEC_TRIES candidates, inverse transform over the decimal parts.  Either way the output law is
+// q_j / Q_D, so the fallback keeps it exact.
 // Inverse transform over the decimal parts: the first slot whose running sum of q exceeds r < Q_D.
 __device__ __noinline__ uint32_t decimal_its(const uint8_t* qb, const uint2* pairs, uint32_t d, uint32_t r) {
     uint32_t acc = 0;
@@ -266,21 +277,17 @@ __device__ __noinline__ uint32_t decimal_its(const uint8_t* qb, const uint2* pai
     }
     return NONE32;
 }
+// Decimal picks are rare (the decimal group carries a small share of the weight), so candidates go
+// one at a time: few registers on this path.
+constexpr int DEC_TRIES = 16;
 __device__ __forceinline__ uint32_t pick_decimal(const DevGraph& G, const Sec0& h, uint32_t qd, uint32_t ref,
                                                  StepRng& R, uint32_t* status) {
     if (words_of(ref) >= G.pool.words || qd == 0) { atomicOr(status, ST_STATE); return NONE32; }
     const uint8_t* qb = dec_bytes(G, ref);
     const uint2* pairs = adj_pairs(G, words_of(h.adj));
-    for (int t = 0; t < DEC_ROUNDS; t++) {
-        uint32_t j[4], q[4];
-        const uint32_t u = R.next();
-#pragma unroll
-        for (int c = 0; c < 4; c++) j[c] = below32(R, h.deg, status);
-#pragma unroll
-        for (int c = 0; c < 4; c++) q[c] = __ldg(qb + j[c]);
-#pragma unroll
-        for (int c = 0; c < 4; c++)
-            if (((u >> (8 * c)) & 255u) < q[c]) return __ldg(&pairs[j[c]].x);
+    for (int t = 0; t < DEC_TRIES; t++) {
+        const uint32_t j = below32(R, h.deg, status);
+        if ((R.next() & 255u) < __ldg(qb + j)) return __ldg(&pairs[j].x);
     }
     const uint32_t x = decimal_its(qb, pairs, h.deg, below32(R, qd, status));
     if (x == NONE32) atomicOr(status, ST_STATE);

@@ -207,7 +207,7 @@ def test_real_invalid_biases_rejected(B):
     assert_real_state_matches(g, og)
 
 
-def one_step_real(B, g, og, v, seed):
+def one_step_real(B, g, og, v, seed, n_samples=N_SAMPLES):
     offs, dst, _, _ = og.edges()
     I, q, _ = og.real_parts()
     a, c = int(offs[v]), int(offs[v + 1])
@@ -217,9 +217,9 @@ def one_step_real(B, g, og, v, seed):
     probs = np.bincount(inv, weights=ww)
     import torch
 
-    paths = torch.empty((N_SAMPLES, 2), dtype=torch.int32, device="cuda")
-    plen = torch.empty(N_SAMPLES, dtype=torch.int32, device="cuda")
-    g.walk(dev(np.full(N_SAMPLES, v, np.uint32)), [B.policy(B.DEEPWALK, 1)], seed, 2, paths, plen)
+    paths = torch.empty((n_samples, 2), dtype=torch.int32, device="cuda")
+    plen = torch.empty(n_samples, dtype=torch.int32, device="cuda")
+    g.walk(dev(np.full(n_samples, v, np.uint32)), [B.policy(B.DEEPWALK, 1)], seed, 2, paths, plen)
     g.check()
     got = paths.cpu().numpy().view(np.uint32)[:, 1].astype(np.int64)
     assert (plen.cpu().numpy() == 2).all()
@@ -236,7 +236,9 @@ def test_real_one_step_distribution(B):
     og = real_graph(8)
     g = make(B, og)
     for i, v in enumerate((0, 7, 8, 20, 41)):  # hubs, decimal-only vertices, plain vertices
-        one_step_real(B, g, og, v, 300 + i)
+        one_step_real(B, g, og, v, 310 + i)
+    # the decimal group's sampler alone, with 32x the samples (power to see a 0.1% bias in a bin)
+    one_step_real(B, g, og, 8, 320, n_samples=1 << 25)
     rng = np.random.default_rng(70)
     rec = real_batch(rng, og, og.n, 300)
     g.apply_updates(dev(rec))
