@@ -784,6 +784,20 @@ def run_ablation(args):
             mem_bs = bsg.memory_report()
             w_bs, _ = _timed_walks(torch, B, bsg, starts, stride, args.steps, args.warmup, 7, flush, stream)
             u_bs, _ = _timed_batches(torch, bsg, recs, args.warmup, flush, stream)
+        # alpha / beta sweep of Eq. group (percent thresholds) on the same graph and batches
+        sweep = []
+        for al, be in ((20, 10), (40, 10), (60, 10), (80, 10), (100, 10), (40, 0), (40, 5), (40, 20)):
+            gs = B.Graph(G.n, t(G.row_ptr), t(G.col), t(G.w), max_bits=G.max_bits, alpha_pct=al, beta_pct=be)
+            ms_ = gs.memory_report()
+            w_s, _ = _timed_walks(torch, B, gs, starts, stride, 3, 2, 7, flush, stream)
+            u_s, _ = _timed_batches(torch, gs, recs[:5], 2, flush, stream)
+            kinds = np.bincount(gs.export_state()["kind"].reshape(-1), minlength=5)
+            sweep.append({"alpha_pct": al, "beta_pct": be,
+                          "state_bytes": sum(v for k, v in ms_.items() if k not in ("pool_capacity", "edge_index")),
+                          "walk_ms": w_s, "update_ms_per_batch": u_s,
+                          "groups_by_kind": dict(zip(["empty", "dense", "one", "sparse", "regular"],
+                                                     [int(x) for x in kinds]))})
+            del gs
         clocks = sampler.stop()
         grp = lambda m: m["regular_groups"] + m["sparse_groups"]
         tot = lambda m: sum(v for k, v in m.items() if k not in ("pool_capacity", "edge_index"))
@@ -797,6 +811,7 @@ def run_ablation(args):
                 "walk_ms": {"ga": w_ga, "bs": w_bs}, "walk_steps_per_s_ga": steps / (w_ga / 1e3),
                 "update_ms_per_batch": {"ga": u_ga, "bs": u_bs},
                 "ga_conversions_all_batches": conv.tolist(),
+                "alpha_beta_sweep": sweep,
                 "paper_context": "A100: GA uses 14.6-22.2x less memory than BS and is 1.09x faster overall",
                 "clocks": clocks}
         if bsg is None:
