@@ -428,6 +428,63 @@ struct WarpTeam {
     }
 };
 
+// Block-wide collectives over shared scratch `sm` (>= 40 words).  Out of line: a block team calls
+// them from dozens of places, and inlining every copy made the update kernel's code far larger than
+// the instruction cache.
+static __device__ __noinline__ uint2 block_scan_excl(uint32_t* sm, uint32_t x) {  // {exclusive prefix, total}
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    uint32_t v = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, v, d);
+        if (lane >= (uint32_t)d) v += y;
+    }
+    if (lane == 31) sm[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < nw ? sm[lane] : 0, s = t;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, s, d);
+            if (lane >= (uint32_t)d) s += y;
+        }
+        if (lane < nw) sm[lane] = s - t;
+        if (lane == 31) sm[32] = s;
+    }
+    __syncthreads();
+    const uint2 r = make_uint2(sm[w] + v - x, sm[32]);
+    __syncthreads();
+    return r;
+}
+static __device__ __noinline__ uint32_t block_max(uint32_t* sm, uint32_t x) {
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x = ::max(x, __shfl_xor_sync(FULL, x, d));
+    if (lane == 0) sm[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < nw ? sm[lane] : 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) t = ::max(t, __shfl_xor_sync(FULL, t, d));
+        if (lane == 0) sm[32] = t;
+    }
+    __syncthreads();
+    const uint32_t r = sm[32];
+    __syncthreads();
+    return r;
+}
+static __device__ __noinline__ uint32_t block_or(uint32_t* sm, uint32_t x) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x |= __shfl_xor_sync(FULL, x, d);
+    if (threadIdx.x == 0) sm[33] = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicOr(&sm[33], x);
+    __syncthreads();
+    const uint32_t r = sm[33];
+    __syncthreads();
+    return r;
+}
+
 // Block team; needs `sm` = shared scratch of at least 40 words, private to the team.
 struct BlockTeam {
     uint32_t* sm;
@@ -435,66 +492,15 @@ struct BlockTeam {
     __device__ __forceinline__ uint32_t rank() const { return threadIdx.x; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
     __device__ __forceinline__ uint32_t scan_excl(uint32_t x, uint32_t& total) const {
-        const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-        uint32_t v = x;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            uint32_t y = __shfl_up_sync(FULL, v, d);
-            if (lane >= (uint32_t)d) v += y;
-        }
-        if (lane == 31) sm[w] = v;
-        __syncthreads();
-        if (w == 0) {
-            uint32_t t = lane < nw ? sm[lane] : 0, s = t;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                uint32_t y = __shfl_up_sync(FULL, s, d);
-                if (lane >= (uint32_t)d) s += y;
-            }
-            if (lane < nw) sm[lane] = s - t;
-            if (lane == 31) sm[32] = s;
-        }
-        __syncthreads();
-        const uint32_t r = sm[w] + v - x;
-        total = sm[32];
-        __syncthreads();
-        return r;
+        const uint2 r = block_scan_excl(sm, x);
+        total = r.y;
+        return r.x;
     }
     __device__ __forceinline__ uint32_t scan_pred(bool p, uint32_t& total) const { return scan_excl(p ? 1u : 0u, total); }
-    __device__ __forceinline__ uint32_t sum(uint32_t x) const {
-        uint32_t t;
-        scan_excl(x, t);
-        return t;
-    }
-    __device__ __forceinline__ uint32_t max(uint32_t x) const {
-        const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) x = ::max(x, __shfl_xor_sync(FULL, x, d));
-        if (lane == 0) sm[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            uint32_t t = lane < nw ? sm[lane] : 0;
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) t = ::max(t, __shfl_xor_sync(FULL, t, d));
-            if (lane == 0) sm[32] = t;
-        }
-        __syncthreads();
-        const uint32_t r = sm[32];
-        __syncthreads();
-        return r;
-    }
+    __device__ __forceinline__ uint32_t sum(uint32_t x) const { return block_scan_excl(sm, x).y; }
+    __device__ __forceinline__ uint32_t max(uint32_t x) const { return block_max(sm, x); }
     __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
-    __device__ __forceinline__ uint32_t or_all(uint32_t x) const {
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) x |= __shfl_xor_sync(FULL, x, d);
-        if (threadIdx.x == 0) sm[33] = 0;
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) atomicOr(&sm[33], x);
-        __syncthreads();
-        const uint32_t r = sm[33];
-        __syncthreads();
-        return r;
-    }
+    __device__ __forceinline__ uint32_t or_all(uint32_t x) const { return block_or(sm, x); }
 };
 #endif  // __CUDACC__
 

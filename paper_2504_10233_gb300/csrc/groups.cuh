@@ -13,7 +13,7 @@ namespace bingo {
 // positions ascending with j.  Returns the count.  load(j) reads what the test of element j needs;
 // the IT loads of a thread are issued before any test (indexes clamped into [0, n), the tail masked
 // afterwards), so they are in flight together instead of one dependent round trip per element.
-constexpr int COMPACT_IT = 8;
+constexpr int COMPACT_IT = 4;
 template <class Team, class Load, class Test, class Emit>
 __device__ __forceinline__ uint32_t team_compact_lt(const Team& t, uint32_t n, Load load, Test test, Emit emit) {
     uint32_t pos = 0;

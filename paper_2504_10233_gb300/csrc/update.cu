@@ -367,7 +367,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
             }
         }
         // Each thread takes RES_IT consecutive slots per iteration with their loads in flight together.
-        constexpr int RES_IT = 8;
+        constexpr int RES_IT = 4;
         for (uint32_t r = 0; r < (use_cand ? 0u : rounds); r++) {
             for (uint32_t j0 = rank * RES_IT; j0 < dtot; j0 += T * RES_IT) {
                 uint32_t x[RES_IT];

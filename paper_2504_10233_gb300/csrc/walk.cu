@@ -269,7 +269,7 @@ __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, c
 // DEC_TRIES candidates, inverse transform over the decimal parts.  Either way the output law is
 // q_j / Q_D, so the fallback keeps it exact.
 // Inverse transform over the decimal parts: the first slot whose running sum of q exceeds r < Q_D.
-__device__ __noinline__ uint32_t decimal_its(const uint8_t* qb, const uint2* pairs, uint32_t d, uint32_t r) {
+static __device__ __noinline__ uint32_t decimal_its(const uint8_t* qb, const uint2* pairs, uint32_t d, uint32_t r) {
     uint32_t acc = 0;
     for (uint32_t j = 0; j < d; j++) {
         acc += __ldg(qb + j);
