@@ -73,6 +73,7 @@ def _L():
                 "o_num_threads": (c.c_int, []),
                 "o_float_factor": (None, [c.c_uint64, DP, c.c_double, U32P, U64P, DP, DP]),
                 "o_set_lambda": (c.c_int, [c.c_void_p, c.c_double]),
+                "o_set_base4": (c.c_int, [c.c_void_p]),
                 "o_export_real": (None, [c.c_void_p, U32P, U32P, U64P]),
             }
             for name, (res, args) in sig.items():
@@ -159,6 +160,11 @@ class Graph:
         """Real-valued biases (Section 4.3): stored words are binary32 encodings, weights
         2^8 floor(lam b) + floor(frac(lam b) 2^8).  Returns the status (0 = ok)."""
         return int(_L().o_set_lambda(self._h, float(lam)))
+
+    def set_base4(self) -> int:
+        """Radix base 4 (Appendix): sub-group (i, v) of digit position i and value v in slot
+        3 i + v - 1, carrying v 4^i per member.  Returns the status (0 = ok)."""
+        return int(_L().o_set_base4(self._h))
 
     def real_parts(self):
         """(I u32[m], q u32[m], qsum u64[n]): integer and decimal parts per edge in the order of

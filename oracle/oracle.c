@@ -22,6 +22,10 @@
  *   - the factorised sampler's exact per-neighbour probability
  *     sum_k P(p_k) P(v_i | p_k) (Eqs. group_prob and pvp, Theorem 1), as a
  *     reduced fraction, for pinning Theorem 1 on small inputs;
+ *   - radix base 4 (Appendix, Fig. base4): one group per base-4 digit position i,
+ *     split into value sub-groups v = 1, 2, 3 (the edges whose digit i equals
+ *     v, each carrying v * 4^i); as a graph mode (o_set_base4), sub-group
+ *     (i, v) occupies group slot 3 i + v - 1;
  *   - floating-point biases with an amortisation factor lambda: integer part
  *     radix-decomposed, decimal parts in one extra group (Section 4.3), both
  *     for a single vertex (o_float_factor, real arithmetic) and as a graph
@@ -47,7 +51,7 @@ enum { O_DEEPWALK = 0, O_PPR = 1, O_NODE2VEC = 2 };
 
 typedef struct { uint32_t dst, w; uint64_t eid; } o_edge;
 typedef struct { o_edge* e; uint64_t len, cap; } o_adj;
-typedef struct { uint32_t n; o_adj* a; uint64_t next_eid; double lam; } o_graph;
+typedef struct { uint32_t n; o_adj* a; uint64_t next_eid; double lam; int base4; } o_graph;
 
 /* ------------------------------------------------------------------------------ real biases */
 
@@ -73,6 +77,16 @@ static int o_real_parts(uint32_t bits, double lam, uint32_t* I, uint32_t* q) {
     return (*I == 0 && *q == 0) ? 1 : 0;
 }
 
+/* ------------------------------------------------------------------------------ radix base 4 */
+
+/* Base-4 digit i of w: floor(w / 4^i) mod 4. */
+static inline uint32_t o_digit4(uint32_t w, int i) {
+    uint64_t p = 1;
+    for (int t = 0; t < i; t++) p *= 4;
+    return (uint32_t)((w / p) % 4);
+}
+#define O_B4_POSITIONS 10 /* base-4 mode: biases below 4^10, sub-groups 3 i + v - 1 < 30 */
+
 /* Integer part, the part of an edge that is radix-decomposed. */
 static inline uint32_t o_int_part(const o_graph* g, uint32_t w) {
     if (g->lam == 0.0) return w;
@@ -87,6 +101,24 @@ static inline uint64_t o_weight(const o_graph* g, uint32_t w) {
     uint32_t I, q;
     o_real_parts(w, g->lam, &I, &q);
     return ((uint64_t)I << O_FRAC_BITS) + q;
+}
+
+/* 1 iff an edge with stored word w belongs to group slot k: bit k of the (integer part of the)
+ * bias, or in base 4 the sub-group of digit position k / 3 with value k % 3 + 1. */
+static inline int o_in_slot(const o_graph* g, uint32_t w, int k) {
+    if (g->base4) return k < 3 * O_B4_POSITIONS && o_digit4(w, k / 3) == (uint32_t)(k % 3 + 1);
+    return (o_int_part(g, w) >> k) & 1u;
+}
+
+/* Weight one member of slot k carries: 2^k, 2^(k+8) for real biases (units of 2^-8), or
+ * v * 4^i for base-4 sub-group (i, v). */
+static inline uint64_t o_slot_unit(const o_graph* g, int k) {
+    if (g->base4) {
+        uint64_t p = 1;
+        for (int t = 0; t < k / 3; t++) p *= 4;
+        return (uint64_t)(k % 3 + 1) * p;
+    }
+    return (uint64_t)1 << (k + (g->lam != 0.0 ? O_FRAC_BITS : 0));
 }
 
 static inline uint32_t o_dec_part(const o_graph* g, uint32_t w) {
@@ -174,6 +206,17 @@ int o_set_lambda(o_graph* g, double lam) {
     return O_OK;
 }
 
+/* Switch the graph to radix base 4 (integer biases below 4^10).  O_INVALID if an edge's bias is
+ * too wide or the graph holds real biases. */
+int o_set_base4(o_graph* g) {
+    if (g->lam != 0.0) return O_INVALID;
+    for (uint32_t v = 0; v < g->n; v++)
+        for (uint64_t j = 0; j < g->a[v].len; j++)
+            if (g->a[v].e[j].w >= (1u << (2 * O_B4_POSITIONS))) return O_INVALID;
+    g->base4 = 1;
+    return O_OK;
+}
+
 /* Integer and decimal parts of every live edge, in the order of o_export_edges,
  * and the decimal total Q_D = sum of q per vertex. */
 void o_export_real(const o_graph* g, uint32_t* I, uint32_t* q, uint64_t* qsum) {
@@ -228,6 +271,7 @@ int o_apply(o_graph* g, const uint32_t* rec, uint64_t count, uint32_t max_bits, 
             }
             if (r[2] == 0) return O_INVALID;
             if (max_bits < 32 && (r[2] >> max_bits) != 0) return O_INVALID;
+            if (g->base4 && r[2] >= (1u << (2 * O_B4_POSITIONS))) return O_INVALID;
         }
     }
     uint64_t ins = 0, del = 0, nf = 0;
@@ -281,10 +325,9 @@ void o_factor(const o_graph* g, uint32_t v, uint32_t alpha, uint32_t beta, uint3
     uint64_t s = 0;
     for (int k = 0; k < 32; k++) cnt[k] = 0;
     for (uint64_t j = 0; j < a->len; j++) {
-        uint32_t w = o_int_part(g, a->e[j].w);
         s += o_weight(g, a->e[j].w);
         for (int k = 0; k < 32; k++)
-            if (w & (1u << k)) cnt[k]++;
+            if (o_in_slot(g, a->e[j].w, k)) cnt[k]++;
     }
     for (int k = 0; k < 32; k++) kind[k] = (uint8_t)o_kind(cnt[k], a->len, alpha, beta);
     *sumw = s;
@@ -304,7 +347,12 @@ void o_group_totals(const o_graph* g, uint32_t v, uint64_t* W) {
     const int sh = g->lam != 0.0 ? O_FRAC_BITS : 0;
     for (int k = 0; k < 32; k++) {
         uint64_t s = 0;
-        for (uint64_t j = 0; j < a->len; j++) s += (uint64_t)(o_int_part(g, a->e[j].w) & (1u << k)) << sh;
+        if (g->base4) {  /* sum of the digit values v * 4^i the members contribute */
+            for (uint64_t j = 0; j < a->len; j++)
+                if (o_in_slot(g, a->e[j].w, k)) s += o_slot_unit(g, k);
+        } else {
+            for (uint64_t j = 0; j < a->len; j++) s += (uint64_t)(o_int_part(g, a->e[j].w) & (1u << k)) << sh;
+        }
         W[k] = s;
     }
     if (sh) {
@@ -319,7 +367,8 @@ void o_group_totals(const o_graph* g, uint32_t v, uint64_t* W) {
 uint64_t o_members_count(const o_graph* g) {
     uint64_t t = 0;
     for (uint32_t v = 0; v < g->n; v++)
-        for (uint64_t j = 0; j < g->a[v].len; j++) t += (uint64_t)__builtin_popcount(o_int_part(g, g->a[v].e[j].w));
+        for (uint64_t j = 0; j < g->a[v].len; j++)
+            for (int k = 0; k < 32; k++) t += (uint64_t)o_in_slot(g, g->a[v].e[j].w, k);
     return t;
 }
 
@@ -330,7 +379,7 @@ void o_members_all(const o_graph* g, uint64_t* offs, uint64_t* eids) {
         for (int k = 0; k < 32; k++) {
             offs[32 * (uint64_t)v + k] = p;
             for (uint64_t j = 0; j < a->len; j++)
-                if (o_int_part(g, a->e[j].w) & (1u << k)) eids[p++] = a->e[j].eid;
+                if (o_in_slot(g, a->e[j].w, k)) eids[p++] = a->e[j].eid;
         }
     }
     offs[32 * (uint64_t)g->n] = p;
@@ -351,6 +400,8 @@ static unsigned __int128 gcd128(unsigned __int128 a, unsigned __int128 b) {
  * members by rejection on the whole neighbour list (Section 5.1): one trial
  * picks i with probability 1/d and succeeds with probability |G_k|/d, so the
  * conditional probability is (1/d) / (|G_k|/d), summed here as that ratio.
+ * Base 4 (Appendix): slot 3 i + v - 1 carries v * 4^i |S_iv|, so choosing it is choosing group
+ * 4^i and then its value sub-group v; the member is uniform within the sub-group.
  * Real biases (Section 4.3): the integer groups carry W(p_k) = 2^8 * 2^k |G_k|
  * (units of 2^-8) and the decimal group D carries Q_D = sum of the decimal parts
  * q_j; within D, neighbour i is drawn with probability q_i / Q_D (step (iii):
@@ -367,15 +418,14 @@ int o_factored_prob(const o_graph* g, uint32_t v, uint64_t i, uint32_t alpha, ui
     if (a->len == 0) return 1;
     const int sh = g->lam != 0.0 ? O_FRAC_BITS : 0;
     uint64_t W[32], tot = 0, QD = 0;
-    for (int k = 0; k < 32; k++) { W[k] = (uint64_t)cnt[k] << (k + sh); tot += W[k]; }
+    for (int k = 0; k < 32; k++) { W[k] = (uint64_t)cnt[k] * o_slot_unit(g, k); tot += W[k]; }
     if (sh) {
         for (uint64_t j = 0; j < a->len; j++) QD += o_dec_part(g, a->e[j].w);
         tot += QD;
     }
     unsigned __int128 pn = 0, pd = 1;
-    uint32_t wi = o_int_part(g, a->e[i].w);
     for (int k = 0; k < 32; k++) {
-        if (!(wi & (1u << k))) continue;
+        if (!o_in_slot(g, a->e[i].w, k)) continue;
         /* term = (W_k / tot) * q_k where q_k is the within-group probability */
         unsigned __int128 qn, qd;
         if (kind[k] == O_DENSE) { /* (1/d) / (cnt/d) */

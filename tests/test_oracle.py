@@ -398,3 +398,67 @@ def test_baseline_all_regular():
             assert Fraction(*g.factored_prob(v, i, O.ALL_REGULAR, 0)) == Fraction(w, sum(ws))
     # the last vertex has dense and one-element groups under Eq. group (and none under BS, above)
     assert {int(x) for x in g.factor(len(configs) - 1)[1]} >= {O.DENSE, O.ONE}
+
+
+# ----------------------------------------------------------------------------- radix base 4
+
+
+def _base4_graph(configs):
+    g = _vertex_graph(configs)
+    assert g.set_base4() == 0
+    return g
+
+
+def test_base4_figure_example():
+    """Appendix, Fig. base4: in group 4^0, neighbours 0 and 1 hold biases 2 and 3, so the group
+    splits into value sub-groups 2 = {0} and 3 = {1}; the group's weight is 2 + 3 = 5 and a
+    neighbour is drawn through group, sub-group, then uniformly inside the sub-group."""
+    g = _base4_graph([(2, 3)])
+    cnt, kd, sw = g.factor(0)
+    # slot 3 i + v - 1: (i = 0, v = 2) -> slot 1, (i = 0, v = 3) -> slot 2
+    assert [int(c) for c in cnt[:3]] == [0, 1, 1] and int(cnt[3:].sum()) == 0
+    W = g.group_totals(0)
+    assert int(W[1]) == 2 and int(W[2]) == 3 and int(W.sum()) == 5 == sw
+    assert [Fraction(*g.factored_prob(0, i)) for i in range(2)] == [Fraction(2, 5), Fraction(3, 5)]
+
+
+def test_base4_membership_by_digit_expansion():
+    """Each edge sits in one sub-group per nonzero base-4 digit (counted here from the base-4
+    numeral string), and the sub-group totals add up to the vertex's bias sum."""
+    rng = np.random.default_rng(31)
+    configs = [tuple(int(x) for x in rng.integers(1, 1 << 20, size=int(rng.integers(1, 9)))) for _ in range(200)]
+    g = _base4_graph(configs)
+    moffs, _ = g.members_all()
+    for v, ws in enumerate(configs):
+        nz = sum(sum(ch != "0" for ch in np.base_repr(w, 4)) for w in ws)
+        assert int(moffs[32 * v + 32] - moffs[32 * v]) == nz
+        assert int(g.group_totals(v).sum()) == sum(ws)
+        cnt, _, _ = g.factor(v)
+        positions = {k // 3 for k in range(32) if cnt[k]}
+        assert max(positions) + 1 == max(len(np.base_repr(w, 4)) for w in ws)  # K = number of base-4 digits
+
+
+def test_base4_theorem1_exact():
+    configs = [c for d in (1, 2, 3) for c in itertools.product(range(1, 16), repeat=d)]
+    rng = np.random.default_rng(32)
+    configs += [tuple(int(x) for x in rng.integers(1, 1 << 20, size=int(rng.integers(4, 9)))) for _ in range(500)]
+    configs += [tuple([1] * 9 + [2, 6]), tuple([3] * 30 + [12, 48]), tuple([7] * 3 + [1] * 40 + [64, 192])]
+    g = _base4_graph(configs)
+    kinds = set()
+    for v, ws in enumerate(configs):
+        kinds |= {int(x) for x in g.factor(v)[1]}
+        s = sum(ws)
+        for i, w in enumerate(ws):
+            assert Fraction(*g.factored_prob(v, i)) == Fraction(w, s), (ws, i)
+    assert {O.DENSE, O.ONE, O.SPARSE, O.REGULAR} <= kinds
+
+
+def test_base4_validation_and_updates():
+    g = O.Graph.from_edges(4, [(0, 1, (1 << 20) - 1)])
+    assert g.set_base4() == 0
+    assert g.apply(np.array([[0, 2, 1 << 20, 0]], dtype=np.uint32))[0] != 0
+    rc, st = g.apply(np.array([[0, 2, 6, 0], [0, 1, 0, 1]], dtype=np.uint32))
+    assert rc == 0 and st == (1, 1, 0)
+    cnt, _, sw = g.factor(0)
+    assert sw == 6 and int(cnt[1]) == 1 and int(cnt[3]) == 1 and int(cnt.sum()) == 2  # 6 = 2 + 1 * 4
+    assert O.Graph.from_edges(2, [(0, 1, 1 << 20)]).set_base4() != 0
