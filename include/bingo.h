@@ -87,6 +87,9 @@ typedef struct {
     uint32_t all_regular;      /* 1: no group adaption, every nonempty group in regular format (the paper's
                                   BS baseline, Section 6.2); 0 (default): Eq. group */
     double lambda;             /* BINGO_BIAS_F32: amortisation factor lambda > 0 (Section 4.3) */
+    uint32_t radix_base;       /* 2 (default; 0 means 2) or 4: one group per base-4 digit position, split into
+                                  value sub-groups (Appendix, Fig. base4); base 4 needs integer biases < 2^20 */
+    uint32_t reserved1;
 } bingo_config;
 
 /* One update record, 16 bytes. */
@@ -141,6 +144,14 @@ void bingo_default_config(bingo_config* cfg);
  * list (with an exact inverse-transform fallback).  Requirements: b finite and
  * >= 0, lambda b < 2^31, 256 I + q >= 1 (no zero weights), degree < 2^24.
  * max_bits is ignored for real biases.
+ * Radix base 4 (cfg->radix_base = 4, Appendix "arbitrary radix bases"): the
+ * bias w < 2^20 is split into base-4 digits; group 4^i is kept as value
+ * sub-groups v = 1, 2, 3 (the edges whose digit i equals v, each carrying
+ * v 4^i), stored in group slot 3 i + v - 1 (slots 0..29) with the same kinds
+ * (Eq. group), member lists and updates as base-2 groups; the sampler draws
+ * sub-group (i, v) with probability v 4^i |S_iv| / sum w (group, then
+ * sub-group) and a member uniformly.  cnt[] of bingo_export_state is indexed
+ * by slot; bias[] holds the biases.
  * Errors: BINGO_E_INVALID (bad ids or biases; nothing allocated), BINGO_E_OOM, BINGO_E_CUDA.
  * Synchronises `stream` before returning.  *out receives the new graph.
  */

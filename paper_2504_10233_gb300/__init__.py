@@ -42,7 +42,8 @@ class bingo_config(c.Structure):
     _fields_ = [("alpha_pct", c.c_uint32), ("beta_pct", c.c_uint32), ("max_bits", c.c_uint32),
                 ("lanes_per_walker", c.c_uint32), ("warps_per_block", c.c_uint32), ("blocks_per_sm", c.c_uint32),
                 ("update_chunk", c.c_uint32), ("reg_variant", c.c_uint32), ("pool_words", c.c_uint64),
-                ("bias_format", c.c_uint32), ("all_regular", c.c_uint32), ("lambda_", c.c_double)]
+                ("bias_format", c.c_uint32), ("all_regular", c.c_uint32), ("lambda_", c.c_double),
+                ("radix_base", c.c_uint32), ("reserved1", c.c_uint32)]
 
 
 class bingo_update_stats(c.Structure):

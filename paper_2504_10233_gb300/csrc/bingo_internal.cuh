@@ -183,6 +183,7 @@ struct DevGraph {
     uint32_t alpha, beta;
     uint32_t fbits;   // 0: integer biases; FRAC_BITS: real biases (slot 31 = decimal group)
     double lambda;    // real biases: amortisation factor
+    uint32_t base4;   // 1: radix base 4, the stored bias word is the sub-group mask (b4_mask)
     VHot* vh;
     VCold* vc;
     Pool pool;
@@ -263,6 +264,33 @@ __device__ __forceinline__ uint32_t int_part(const DevGraph& G, uint32_t bits) {
 __device__ __forceinline__ uint64_t slot_w(uint32_t c, uint32_t k, uint32_t fbits) {
     return (fbits && k == DEC_SLOT) ? (uint64_t)c : ((uint64_t)c << (k + fbits));
 }
+// Weight modes of the walker: integer base 2, real biases, integer base 4.
+enum : int { WM_INT = 0, WM_REAL = 1, WM_B4 = 2 };
+template <int WM>
+__device__ __forceinline__ uint64_t slot_weight(uint32_t c, uint32_t k) {
+    if constexpr (WM == WM_B4) return (uint64_t)c * ((uint64_t)(k % 3 + 1) << (2 * (k / 3)));
+    else return slot_w(c, k, WM == WM_REAL ? FRAC_BITS : 0u);
+}
+// ---- radix base 4 (Appendix): sub-group (digit position i, value v) is slot 3 i + v - 1.
+constexpr uint32_t B4_POSITIONS = 10;  // biases below 4^10 = 2^20: slots 0..29
+// Sub-group mask of a bias: bit 3 i + v - 1 for every nonzero base-4 digit v at position i.  Stored
+// in place of the bias, so membership of slot k stays a bit test, as in base 2.
+__host__ __device__ __forceinline__ uint32_t b4_mask(uint32_t w) {
+    uint32_t m = 0;
+    for (uint32_t i = 0; i < B4_POSITIONS; i++) {
+        const uint32_t d = (w >> (2 * i)) & 3u;
+        if (d) m |= 1u << (3 * i + d - 1);
+    }
+    return m;
+}
+// The bias a sub-group mask stands for.
+__host__ __device__ __forceinline__ uint32_t b4_value(uint32_t m) {
+    uint32_t w = 0;
+    for (uint32_t k = 0; k < 3 * B4_POSITIONS; k++)
+        if ((m >> k) & 1u) w += (k % 3 + 1) << (2 * (k / 3));
+    return w;
+}
+
 // Kind of group slot k (Eq. group); the decimal slot of a real-bias graph has none.
 __device__ __forceinline__ uint32_t slot_kind(const DevGraph& G, uint32_t c, uint32_t d, uint32_t k) {
     return (G.fbits && k == DEC_SLOT) ? (uint32_t)K_EMPTY : kind_of(c, d, G.alpha, G.beta);

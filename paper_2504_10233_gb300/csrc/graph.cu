@@ -56,6 +56,12 @@ __global__ void k_split_biases(const uint32_t* __restrict__ bits, uint64_t m, do
     if (bad) atomicOr(status, ST_INVALID);
 }
 
+// Radix base 4: every bias replaced by its sub-group mask (slot 3 i + v - 1 per nonzero digit).
+__global__ void k_b4_masks(const uint32_t* __restrict__ w, uint64_t m, uint32_t* __restrict__ out) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = tid; j < m; j += nt) out[j] = b4_mask(w[j]);
+}
+
 // Per vertex: d, |G_k| (Eq. dwi / wpk by ballot over 32-edge chunks), mask, kinds (Eq. group),
 // |S| and the words its blocks need.  One warp per vertex.
 __global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const uint32_t* __restrict__ bias,
@@ -223,7 +229,7 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
             for (uint32_t j = lane; j < d; j += 32) {
                 const uint2 e = pairs[j];
                 odst[eoff[v] + j] = e.x;
-                obias[eoff[v] + j] = e.y;
+                obias[eoff[v] + j] = G.base4 ? b4_value(e.y) : e.y;
                 oeid[eoff[v] + j] = eids[j];
             }
         }
@@ -393,6 +399,13 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
         set_error("invalid bias format %u / lambda %g", c.bias_format, c.lambda);
         return BINGO_E_INVALID;
     }
+    if (c.radix_base == 0) c.radix_base = 2;
+    const bool base4 = c.radix_base == 4;
+    if ((c.radix_base != 2 && !base4) || (base4 && real)) {
+        set_error("invalid radix base %u (2, or 4 with integer biases)", c.radix_base);
+        return BINGO_E_INVALID;
+    }
+    if (base4 && c.max_bits > 2 * B4_POSITIONS) c.max_bits = 2 * B4_POSITIONS;  // biases below 4^10
     cudaStream_t s = (cudaStream_t)stream;
     bingo_graph* g = new bingo_graph();
     g->cfg = c;
@@ -429,6 +442,12 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
     }
     k_validate_csr<<<grid_for(g, (m > n ? m : n), 256), 256, 0, s>>>(n, m, rp, cl, bs, c.max_bits, real, status);
     g->launches++;
+    if (base4 && m) {  // factorise the sub-group masks from here on (validation saw the biases)
+        if (!cu(ensure(bint, sizeof(uint32_t) * m), "sub-group masks")) { release_stage(); return fail(st); }
+        k_b4_masks<<<grid_for(g, m, 256), 256, 0, s>>>(bs, m, (uint32_t*)bint.p);
+        g->launches++;
+        bs = (const uint32_t*)bint.p;
+    }
     uint32_t hst = 0;
     if (!cu(cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, s), "status read") ||
         !cu(cudaStreamSynchronize(s), "validate")) { release_stage(); return fail(st); }
@@ -448,6 +467,7 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
     G.beta = c.all_regular ? 0u : c.beta_pct;
     G.fbits = real ? FRAC_BITS : 0;
     G.lambda = real ? c.lambda : 0.0;
+    G.base4 = base4 ? 1u : 0u;
     G.vh = (VHot*)g->d_hdr;
     G.vc = (VCold*)g->d_cold;
     G.pool.status = status;

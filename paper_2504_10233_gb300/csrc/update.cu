@@ -825,7 +825,8 @@ __global__ void k_key_count(const uint64_t* total, uint64_t* nkeys) { *nkeys = *
 __global__ void k_seg_flags(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t cap,
                             const uint64_t* __restrict__ nkeys_dev, uint32_t bn, const uint4* __restrict__ ups,
                             const uint64_t* __restrict__ pscan, const unsigned long long* __restrict__ eid_base,
-                            uint32_t fbits, double lambda, uint64_t* __restrict__ flag, uint4* __restrict__ rec) {
+                            uint32_t fbits, double lambda, uint32_t base4, uint64_t* __restrict__ flag,
+                            uint4* __restrict__ rec) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t nkeys = nkeys_dev ? *nkeys_dev : cap;
     for (uint64_t i = tid; i < cap; i += nt) {
@@ -838,6 +839,7 @@ __global__ void k_seg_flags(const uint64_t* __restrict__ keys, const uint32_t* _
             const uint64_t eid = *eid_base + (pscan[r] >> 32);
             uint32_t I = u.z, q = 0;
             if (fbits) split_real_bias(u.z, lambda, I, q);
+            if (base4) I = b4_mask(u.z);
             rec[i] = make_uint4((uint32_t)eid, u.y, I, ((uint32_t)(eid >> 32) & 0xFFFFFFu) | (q << 24));
         }
     }
@@ -1137,6 +1139,7 @@ __global__ void __launch_bounds__(STREAM_TEAMS * 32) k_stream_apply(DevGraph G, 
             // reserve this record's worst-case pool growth so no allocation inside it can fail
             uint32_t I = u.z, qd = 0;
             if (REAL && ni) split_real_bias(u.z, G.lambda, I, qd);
+            if (G.base4 && ni) I = b4_mask(u.z);
             const VHdr h = load_hdr(G, u.x);
             if (REAL && h.deg + ni >= REAL_MAX_DEG) {
                 if (t.rank() == 0) atomicOr(G.pool.status, ST_INVALID);
@@ -1326,7 +1329,7 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     A.count = cap;
     A.count_dev = ctl + CTL_SCR + 8;
     A.n = g->n;
-    A.max_bits = g->cfg.max_bits;
+    A.max_bits = g->G.base4 ? std::min<uint32_t>(g->cfg.max_bits, 2 * B4_POSITIONS) : g->cfg.max_bits;
     A.fbits = g->G.fbits;
     A.lambda = g->G.lambda;
     A.bn = bits_for(g->n);
@@ -1357,7 +1360,7 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
     k_seg_flags<<<grid_cap(g, kc, 256), 256, 0, s>>>(skeys, svals, kc, nkeys_dev, A.bn, A.ups, A.pscan,
                                                      (const unsigned long long*)(ctl + CTL_SCR + 9), A.fbits,
-                                                     A.lambda, flag, (uint4*)g->s_rec.p);
+                                                     A.lambda, g->G.base4, flag, (uint4*)g->s_rec.p);
     CK(scan_excl_u64(flag, segid, kc, nseg_dev, g->s_tmp, s, &g->launches), "segment scan");
     k_seg_write<<<grid_cap(g, kc, 256), 256, 0, s>>>(flag, segid, kc, nkeys_dev, seg_start);
     g->launches += 2;
@@ -1492,7 +1495,7 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     A.count = count;
     A.count_dev = nullptr;
     A.n = g->n;
-    A.max_bits = g->cfg.max_bits;
+    A.max_bits = g->G.base4 ? std::min<uint32_t>(g->cfg.max_bits, 2 * B4_POSITIONS) : g->cfg.max_bits;
     A.fbits = g->G.fbits;
     A.lambda = g->G.lambda;
     A.bn = bits_for(g->n);
@@ -1517,7 +1520,7 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     uint32_t* seg_start = (uint32_t*)(segid + count);
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
     k_seg_flags<<<grid_cap(g, count, 256), 256, 0, s>>>(skeys, svals, count, nullptr, A.bn, A.ups, A.pscan, nullptr,
-                                                        0u, 0.0, flag, nullptr);
+                                                        0u, 0.0, 0u, flag, nullptr);
     CK(scan_excl_u64(flag, segid, count, nseg_dev, g->s_tmp, s, &g->launches), "stream segments");
     k_seg_write<<<grid_cap(g, count, 256), 256, 0, s>>>(flag, segid, count, nullptr, seg_start);
     SegArgs S;

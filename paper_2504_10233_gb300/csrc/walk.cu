@@ -112,10 +112,11 @@ __device__ __forceinline__ uint4 ld_pair(const DevGraph& G, uint32_t v, uint32_t
     if (i < HOT_GROUPS / 2) return ld_hot(reinterpret_cast<const uint4*>(G.vh + v) + 1 + i);
     return __ldg(reinterpret_cast<const uint4*>(G.vc + v) + (i - HOT_GROUPS / 2));
 }
-// fb = 0 for integer biases; for real biases every integer group counts 2^fb times and slot 31 (the
-// second half of pair 15) carries the decimal total itself.
-__device__ __forceinline__ uint64_t pair_w(uint4 x, uint32_t i, uint32_t fb) {
-    return slot_w(x.x, 2 * i, fb) + slot_w(x.z, 2 * i + 1, fb);
+// WM: the weight mode (slot_weight): integer base 2, real biases (every integer group counts 2^8
+// times and slot 31, the second half of pair 15, carries the decimal total itself), or base 4.
+template <int WM>
+__device__ __forceinline__ uint64_t pair_w(uint4 x, uint32_t i) {
+    return slot_weight<WM>(x.x, 2 * i) + slot_weight<WM>(x.z, 2 * i + 1);
 }
 // pairs with at least one nonempty group, as bits 2i of the result
 __device__ __forceinline__ uint32_t pair_bits(uint32_t mask) { return (mask | (mask >> 1)) & 0x55555555u; }
@@ -125,11 +126,12 @@ __device__ __forceinline__ uint32_t pair_bits(uint32_t mask) { return (mask | (m
 // i.e. group k with probability W(p_k) / sum W (Eq. group_prob); they differ only in how a team
 // of T lanes shares the vertex record.  Outputs k*, |G_k*| and the group's ref.
 
+template <int WM>
 __device__ __forceinline__ bool scan_pair(uint4 x, uint32_t i, uint64_t r, uint64_t& acc, uint32_t& ks, uint32_t& cs,
-                                          uint32_t& ref, uint32_t fb) {
-    const uint64_t lo = acc + slot_w(x.x, 2 * i, fb);
+                                          uint32_t& ref) {
+    const uint64_t lo = acc + slot_weight<WM>(x.x, 2 * i);
     if (r < lo) { ks = 2 * i; cs = x.x; ref = x.y; return true; }
-    acc = lo + slot_w(x.z, 2 * i + 1, fb);
+    acc = lo + slot_weight<WM>(x.z, 2 * i + 1);
     if (r < acc) { ks = 2 * i + 1; cs = x.z; ref = x.w; return true; }
     return false;
 }
@@ -140,20 +142,20 @@ __device__ __forceinline__ bool scan_pair(uint4 x, uint32_t i, uint64_t r, uint6
 // Real-bias graphs: the decimal total Q_D comes with the hot line (Sec0.sref), so for the totals pair
 // 15 is read only for group 30 (its slot-31 half taken as empty) and Q_D is added to the last batch;
 // pair 15 is read whole only when r falls in that batch.
-template <bool REAL>
+template <int WM>
 __device__ __forceinline__ uint4 ld_pair_tot(const DevGraph& G, uint32_t v, uint32_t i) {
     uint4 x = ld_pair(G, v, i);
-    if (REAL && i == 15) x.z = 0;
+    if (WM == WM_REAL && i == 15) x.z = 0;
     return x;
 }
 
-template <bool REAL>
+template <int WM>
 __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status) {
-    constexpr uint32_t fb = REAL ? FRAC_BITS : 0u;
+    constexpr bool REAL = WM == WM_REAL;
     const uint32_t pbf = pair_bits(h.mask);                                  // pairs holding a nonempty slot
     const uint32_t pb = REAL ? pair_bits(h.mask & ~(1u << DEC_SLOT)) : pbf;  // pairs read for the totals
-    const uint64_t whot = pair_w(h.p0, 0, fb) + pair_w(h.p1, 1, fb) + pair_w(h.p2, 2, fb);
+    const uint64_t whot = pair_w<WM>(h.p0, 0) + pair_w<WM>(h.p1, 1) + pair_w<WM>(h.p2, 2);
     uint64_t part[4];
     uint64_t tot = whot;
 #pragma unroll
@@ -164,19 +166,19 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const uint32_t i = 3 + 4 * b + j;
-                x[j] = (i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair_tot<REAL>(G, v, i) : make_uint4(0, 0, 0, 0);
+                x[j] = (i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair_tot<WM>(G, v, i) : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
-            for (int j = 0; j < 4; j++) part[b] += pair_w(x[j], 3 + 4 * b + j, fb);
+            for (int j = 0; j < 4; j++) part[b] += pair_w<WM>(x[j], 3 + 4 * b + j);
         }
         if (REAL && b == 3) part[b] += h.sref;  // decimal total, slot 31 of pair 15
         tot += part[b];
     }
     const uint64_t r = below64(R, tot, status);
     uint64_t acc = 0;
-    if (scan_pair(h.p0, 0, r, acc, ks, cs, ref, fb)) return;
-    if (scan_pair(h.p1, 1, r, acc, ks, cs, ref, fb)) return;
-    if (scan_pair(h.p2, 2, r, acc, ks, cs, ref, fb)) return;
+    if (scan_pair<WM>(h.p0, 0, r, acc, ks, cs, ref)) return;
+    if (scan_pair<WM>(h.p1, 1, r, acc, ks, cs, ref)) return;
+    if (scan_pair<WM>(h.p2, 2, r, acc, ks, cs, ref)) return;
     int bs = 3;
 #pragma unroll
     for (int b = 0; b < 3; b++) {
@@ -190,14 +192,14 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
 #pragma unroll
     for (int j = 0; j < 4; j++) {
         const uint32_t i = 3 + 4 * bs + j;
-        if (!found && i < 16 && ((pbf >> (2 * i)) & 1u)) found = scan_pair(ld_pair(G, v, i), i, r, acc, ks, cs, ref, fb);
+        if (!found && i < 16 && ((pbf >> (2 * i)) & 1u)) found = scan_pair<WM>(ld_pair(G, v, i), i, r, acc, ks, cs, ref);
     }
     if (!found) atomicOr(status, ST_STATE);
 }
 
 // T = 4: lane t of the team owns pairs [4t, 4t+4) (groups 8t..8t+7); a two-level shuffle prefix
 // over the team and a ballot find the lane holding k*, which searches its pairs again.
-template <bool REAL>
+template <int WM>
 __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status,
                                                uint32_t tl, uint32_t team_mask, uint32_t team_base) {
@@ -205,7 +207,7 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
     uint64_t s = 0;
     for (uint32_t m = mine; m; m &= m - 1) {
         const uint32_t i = 4 * tl + ((__ffs(m) - 1) >> 1);
-        s += pair_w(ld_pair(G, v, i), i, REAL ? FRAC_BITS : 0u);
+        s += pair_w<WM>(ld_pair(G, v, i), i);
     }
     uint64_t incl = s;
 #pragma unroll
@@ -225,9 +227,9 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
         for (uint32_t m = mine; m && !found; m &= m - 1) {
             const uint32_t i = 4 * tl + ((__ffs(m) - 1) >> 1);
             const uint4 x = ld_pair(G, v, i);
-            acc += slot_w(x.x, 2 * i, REAL ? FRAC_BITS : 0u);
+            acc += slot_weight<WM>(x.x, 2 * i);
             if (r < acc) { k_l = 2 * i; c_l = x.x; r_l = x.y; found = true; break; }
-            acc += slot_w(x.z, 2 * i + 1, REAL ? FRAC_BITS : 0u);
+            acc += slot_weight<WM>(x.z, 2 * i + 1);
             if (r < acc) { k_l = 2 * i + 1; c_l = x.z; r_l = x.w; found = true; }
         }
     }
@@ -238,14 +240,14 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
 
 // T = 32: lane k owns group k; a warp-wide shuffle prefix of W_k = 2^k |G_k| and a ballot of
 // (prefix > r) give k* as the first set bit.
-template <bool REAL>
+template <int WM>
 __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                 uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status,
                                                 uint32_t lane) {
     uint2 gk = make_uint2(0, 0);
     if ((h.mask >> lane) & 1u)
         gk = __ldg(lane < HOT_GROUPS ? &G.vh[v].g[lane] : &G.vc[v].g[lane - HOT_GROUPS]);
-    uint64_t incl = slot_w(gk.x, lane, REAL ? FRAC_BITS : 0u);
+    uint64_t incl = slot_weight<WM>(gk.x, lane);
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const uint64_t y = __shfl_up_sync(FULL, incl, d);
@@ -294,10 +296,10 @@ __device__ __forceinline__ uint32_t pick_decimal(const DevGraph& G, const Sec0& 
     return x;
 }
 
-template <bool REAL>
+template <int WM>
 __device__ __forceinline__ uint32_t pick_member(const DevGraph& G, const Sec0& h, uint32_t ks, uint32_t cs,
                                                 uint32_t ref, StepRng& R, uint32_t* status) {
-    if constexpr (REAL)
+    if constexpr (WM == WM_REAL)
         if (ks == DEC_SLOT) return pick_decimal(G, h, cs, ref, R, status);
     const uint32_t kd = kind_of(cs, h.deg, G.alpha, G.beta);
     if (kd == K_DENSE) {
@@ -327,7 +329,7 @@ __device__ __forceinline__ uint32_t pick_member(const DevGraph& G, const Sec0& h
 }
 
 // One step of a walker at `cur`.  Returns false if the walk ends here (PPR stop, no out-edge, error).
-template <int T, bool REAL>
+template <int T, int WM>
 __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A, uint64_t wid, uint32_t pid,
                                           uint32_t step, uint32_t& cur, uint32_t& prev, uint32_t tl,
                                           uint32_t team_mask, uint32_t team_base, uint32_t lane) {
@@ -345,10 +347,10 @@ __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A
     if (h.deg == 0) return false;
     for (int attempt = 0; attempt < MAX_N2V_TRIES; attempt++) {
         uint32_t ks, cs, ref;
-        if constexpr (T == 1) select_group_1<REAL>(G, cur, h, R, ks, cs, ref, A.status);
-        else if constexpr (T == 4) select_group_4<REAL>(G, cur, h, R, ks, cs, ref, A.status, tl, team_mask, team_base);
-        else select_group_32<REAL>(G, cur, h, R, ks, cs, ref, A.status, lane);
-        const uint32_t x = pick_member<REAL>(G, h, ks, cs, ref, R, A.status);
+        if constexpr (T == 1) select_group_1<WM>(G, cur, h, R, ks, cs, ref, A.status);
+        else if constexpr (T == 4) select_group_4<WM>(G, cur, h, R, ks, cs, ref, A.status, tl, team_mask, team_base);
+        else select_group_32<WM>(G, cur, h, R, ks, cs, ref, A.status, lane);
+        const uint32_t x = pick_member<WM>(G, h, ks, cs, ref, R, A.status);
         if (x >= G.n) {
             if (x != NONE32) atomicOr(A.status, ST_STATE);
             return false;
@@ -386,8 +388,9 @@ __device__ __forceinline__ void finish_walker(const WalkParams& A, uint64_t wid,
 
 // OCC selects the register budget: 0 = up to 64 registers (1,024-thread bound), 1 = 40 registers
 // (256-thread blocks, six per SM), trading spills to L1 for 50% more resident warps.
-// REAL: real-bias graphs (decimal group in slot 31); integer graphs run the instance without it.
-template <int T, int OCC, bool REAL>
+// WM: the graph's weight mode; each mode runs its own instance (integer graphs carry no code for the
+// decimal group or the base-4 weights).
+template <int T, int OCC, int WM>
 __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persistent(DevGraph G, WalkParams A) {
     const uint32_t lane = threadIdx.x & 31, tl = lane % T, team = lane / T;
     const uint32_t team_base = team * T;
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
             continue;
         }
         if (have) {
-            const bool took = walk_step<T, REAL>(G, A, wid, pid, step, cur, prev, tl, team_mask, team_base, lane);
+            const bool took = walk_step<T, WM>(G, A, wid, pid, step, cur, prev, tl, team_mask, team_base, lane);
             if (took) {
                 step++;
                 if (tl == 0) A.paths[wid * (uint64_t)A.stride + step] = cur;
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
 }
 
 // The paper's step-by-step form (Section 6 (iii)): one launch per step, one thread per walker.
-template <bool REAL>
+template <int WM>
 __global__ void k_walk_step(DevGraph G, WalkParams A, uint32_t s) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t wid = tid; wid < A.nwalkers; wid += nt) {
@@ -469,7 +472,7 @@ __global__ void k_walk_step(DevGraph G, WalkParams A, uint32_t s) {
             if (cur == NONE32) continue;
             prev = A.s_prev[wid];
         }
-        const bool took = walk_step<1, REAL>(G, A, wid, pid, s, cur, prev, 0, 0, 0, 0);
+        const bool took = walk_step<1, WM>(G, A, wid, pid, s, cur, prev, 0, 0, 0, 0);
         if (took) A.paths[wid * (uint64_t)A.stride + s + 1] = cur;
         if (!took || s + 1 == L) {
             finish_walker(A, wid, took ? s + 1 : s, 0, 1);
@@ -530,28 +533,32 @@ bingo_status edge_index_build(bingo_graph* g, cudaStream_t s) {
     return BINGO_OK;
 }
 
-static int g_occ_cache[2][2][3][33];
+static int g_occ_cache[3][2][3][33];
+
+static int weight_mode(const bingo_graph* g) { return g->G.fbits ? WM_REAL : g->G.base4 ? WM_B4 : WM_INT; }
 
 template <int T, int OCC>
-static void* walk_kernel_ptr(bool real) {
-    return real ? (void*)k_walk_persistent<T, OCC, true> : (void*)k_walk_persistent<T, OCC, false>;
+static void* walk_kernel_ptr(int wm) {
+    return wm == WM_REAL ? (void*)k_walk_persistent<T, OCC, WM_REAL>
+           : wm == WM_B4 ? (void*)k_walk_persistent<T, OCC, WM_B4>
+                         : (void*)k_walk_persistent<T, OCC, WM_INT>;
 }
 
-static void* walk_kernel(int lanes, int occ, bool real) {
+static void* walk_kernel(int lanes, int occ, int wm) {
     if (occ)
-        return lanes == 1 ? walk_kernel_ptr<1, 1>(real) : lanes == 4 ? walk_kernel_ptr<4, 1>(real)
-                                                                     : walk_kernel_ptr<32, 1>(real);
-    return lanes == 1 ? walk_kernel_ptr<1, 0>(real) : lanes == 4 ? walk_kernel_ptr<4, 0>(real)
-                                                                 : walk_kernel_ptr<32, 0>(real);
+        return lanes == 1 ? walk_kernel_ptr<1, 1>(wm) : lanes == 4 ? walk_kernel_ptr<4, 1>(wm)
+                                                                   : walk_kernel_ptr<32, 1>(wm);
+    return lanes == 1 ? walk_kernel_ptr<1, 0>(wm) : lanes == 4 ? walk_kernel_ptr<4, 0>(wm)
+                                                               : walk_kernel_ptr<32, 0>(wm);
 }
 
-static int walk_blocks_per_sm(int lanes, int wpb, int occ, bool real) {
+static int walk_blocks_per_sm(int lanes, int wpb, int occ, int wm) {
     const int li = lanes == 1 ? 0 : lanes == 4 ? 1 : 2;
     if (wpb < 1 || wpb > 32) return 1;
-    int& c = g_occ_cache[real ? 1 : 0][occ ? 1 : 0][li][wpb];
+    int& c = g_occ_cache[wm][occ ? 1 : 0][li][wpb];
     if (c) return c;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel(lanes, occ, real), wpb * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel(lanes, occ, wm), wpb * 32, 0);
     c = nb < 1 ? 1 : nb;
     return c;
 }
@@ -585,8 +592,10 @@ bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
         A.s_prev = A.s_cur + nwalkers;
         const unsigned blocks = (unsigned)std::min<uint64_t>((nwalkers + 255) / 256, (uint64_t)g->num_sms * 8);
         for (uint32_t st = 0; st < (max_steps ? max_steps : 1); st++) {
-            if (g->G.fbits) k_walk_step<true><<<blocks, 256, 0, s>>>(g->G, A, st);
-            else k_walk_step<false><<<blocks, 256, 0, s>>>(g->G, A, st);
+            const int wm = weight_mode(g);
+            if (wm == WM_REAL) k_walk_step<WM_REAL><<<blocks, 256, 0, s>>>(g->G, A, st);
+            else if (wm == WM_B4) k_walk_step<WM_B4><<<blocks, 256, 0, s>>>(g->G, A, st);
+            else k_walk_step<WM_INT><<<blocks, 256, 0, s>>>(g->G, A, st);
             g->launches++;
         }
         CK(cudaGetLastError(), "stepwise walk launch");
@@ -598,8 +607,8 @@ bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
     int wpb = (int)g->tune.warps_per_block;
     if (occ_mode && wpb > 8) wpb = 8;  // the 40-register variant is bounded to 256-thread blocks
     int bps = (int)g->tune.blocks_per_sm;
-    const bool real = g->G.fbits != 0;
-    const int occ = walk_blocks_per_sm(lanes, wpb, occ_mode, real);
+    const int wm = weight_mode(g);
+    const int occ = walk_blocks_per_sm(lanes, wpb, occ_mode, wm);
     if (bps <= 0 || bps > occ) bps = occ;
     uint64_t blocks = (uint64_t)g->num_sms * bps;
     const uint64_t walkers_per_block = (uint64_t)wpb * (32 / lanes);
@@ -607,7 +616,7 @@ bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
     if (blocks > useful) blocks = useful;
     if (blocks == 0) blocks = 1;
     void* args[] = {(void*)&g->G, (void*)&A};
-    CK(cudaLaunchKernel(walk_kernel(lanes, occ_mode, real), dim3((unsigned)blocks), dim3(wpb * 32), args, 0, s),
+    CK(cudaLaunchKernel(walk_kernel(lanes, occ_mode, wm), dim3((unsigned)blocks), dim3(wpb * 32), args, 0, s),
        "walk launch");
     g->launches++;
     CK(cudaGetLastError(), "walk launch");

@@ -22,8 +22,20 @@ def _segments(lengths):
     return starts
 
 
-def gpu_canonical(ex):
-    """Edges sorted by (vertex, eid) and group memberships sorted by (vertex, k, eid)."""
+def b4_slots(w):
+    """Radix base 4: slot mask of each bias (bit 3 i + v - 1 for every nonzero base-4 digit v at
+    position i), from the digits of the base-4 numeral."""
+    out = np.zeros(len(w), dtype=np.uint64)
+    for j, x in enumerate(np.asarray(w, dtype=np.int64)):
+        for i, ch in enumerate(reversed(np.base_repr(int(x), 4))):
+            if ch != "0":
+                out[j] |= np.uint64(1) << np.uint64(3 * i + int(ch) - 1)
+    return out
+
+
+def gpu_canonical(ex, memb=None):
+    """Edges sorted by (vertex, eid) and group memberships sorted by (vertex, k, eid).  memb: per
+    edge slot mask when it is not the bias itself (radix base 4)."""
     deg = ex["deg"].astype(np.int64)
     n = len(deg)
     eoff = _segments(deg)
@@ -33,7 +45,7 @@ def gpu_canonical(ex):
     edges = (vslot[order], ex["dst"][order], ex["bias"][order], eid[order])
     # groups: (v, k, eid) for every membership
     kind = ex["kind"]
-    w = ex["bias"].astype(np.uint64)
+    w = (ex["bias"] if memb is None else memb).astype(np.uint64)
     vs, ks, es = [], [], []
     # dense groups: filter the adjacency by bit k
     for k in range(32):
@@ -72,8 +84,9 @@ def oracle_canonical(og: O.Graph):
     return (v, dst, w, eid), (gv, gk, meids.astype(np.uint64))
 
 
-def check_layout_invariants(ex):
+def check_layout_invariants(ex, memb=None):
     """Member lists compact and consistent with their inverted indexes; sparse lists exact."""
+    wbits = (ex["bias"] if memb is None else memb).astype(np.uint64)
     deg = ex["deg"].astype(np.int64)
     n = len(deg)
     kind = ex["kind"]
@@ -105,7 +118,7 @@ def check_layout_invariants(ex):
     np.bitwise_or.at(spmask, sv, (np.uint64(1) << sk.astype(np.uint64)))
     eoff = _segments(deg)
     vslot = np.repeat(np.arange(n, dtype=np.int64), deg)
-    in_s = (ex["bias"].astype(np.uint64) & spmask[vslot]) != 0
+    in_s = (wbits & spmask[vslot]) != 0
     exp_cnt = np.bincount(vslot[in_s], minlength=n)
     assert (exp_cnt == spl).all(), "sparse list size != edges in sparse groups"
     sv2 = np.repeat(np.arange(n, dtype=np.int64), spl)
@@ -116,12 +129,13 @@ def check_layout_invariants(ex):
     ov, ok = np.nonzero(kind == O.ONE)
     os_ = ex["one_slot"][ov, ok].astype(np.int64)
     assert (os_ < deg[ov]).all()
-    assert (((ex["bias"][eoff[ov] + os_].astype(np.uint64) >> ok.astype(np.uint64)) & np.uint64(1)) == 1).all()
+    assert (((wbits[eoff[ov] + os_] >> ok.astype(np.uint64)) & np.uint64(1)) == 1).all()
 
 
-def assert_state_matches(ex, og: O.Graph, alpha=40, beta=10):
+def assert_state_matches(ex, og: O.Graph, alpha=40, beta=10, base4=False):
     """Bit-exact factorisation state (edges, |G_k|, kinds, memberships) + layout invariants."""
-    (gv, gd, gw, ge), (Gv, Gk, Ge) = gpu_canonical(ex)
+    memb = b4_slots(ex["bias"]) if base4 else None
+    (gv, gd, gw, ge), (Gv, Gk, Ge) = gpu_canonical(ex, memb)
     (ov, od, ow, oe), (Ov, Ok, Oe) = oracle_canonical(og)
     assert len(ge) == len(oe), f"edge count {len(ge)} != oracle {len(oe)}"
     assert (gv == ov).all() and (gd == od).all() and (gw == ow).all() and (ge == oe).all(), "adjacency differs"
@@ -130,7 +144,7 @@ def assert_state_matches(ex, og: O.Graph, alpha=40, beta=10):
     assert (ex["kind"] == kd).all(), "group kinds differ"
     assert len(Ge) == len(Oe), f"membership count {len(Ge)} != oracle {len(Oe)}"
     assert (Gv == Ov).all() and (Gk == Ok).all() and (Ge == Oe).all(), "group memberships differ"
-    check_layout_invariants(ex)
+    check_layout_invariants(ex, memb)
 
 
 def edge_keys(og: O.Graph):

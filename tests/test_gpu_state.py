@@ -348,3 +348,22 @@ def test_baseline_all_regular_parity_and_memory(B):
         else:
             apply_both(bs, og, rec, 12)
         assert_state_matches(bs.export_state(), og, O.ALL_REGULAR, 0)
+
+
+def test_radix_base4_parity(B):
+    """Radix base 4 (Appendix): value sub-groups per base-4 digit, in slots 3 i + v - 1.  Bit-exact
+    against the oracle's base-4 mode through creation, batches and streaming records."""
+    og = _stress_graph(13)
+    assert og.set_base4() == 0
+    offs, dst, w, eid = og.edges()
+    g = B.Graph(og.n, dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=12, radix_base=4)
+    ex = g.export_state()
+    assert_state_matches(ex, og, base4=True)
+    assert set(np.unique(ex["kind"]).tolist()) >= {O.DENSE, O.ONE, O.REGULAR}
+    rng = np.random.default_rng(88)
+    for it in range(8):
+        rec = _stress_batch(rng, og, og.n, [1, 17, 300, 64][it % 4])
+        apply_both(g, og, rec, 12, stream=bool(it % 2))
+        assert_state_matches(g.export_state(), og, base4=True)
+    with pytest.raises(B.BingoError):
+        B.Graph(og.n, dev(offs.astype(np.uint64)), dev(dst), dev(np.full_like(w, 1 << 20)), radix_base=4)

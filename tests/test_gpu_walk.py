@@ -354,3 +354,26 @@ def test_server_results_same_alone_and_in_the_mix(B):
     after, stats2 = serve([3], updates=upd)
     assert after[3][2] >= 1 and stats2.updates_applied == len(upd)
     assert_steps_live(og, after[3][0], after[3][1])
+
+
+def test_radix_base4_one_step_and_team_width(B):
+    """Radix base 4: group 4^i then value sub-group v (weight v 4^i |S_iv|), then a uniform member;
+    one-step frequencies match w / sum w, and every team width draws the same paths."""
+    wl = W.make_workload("c2", scale=14, m=1 << 18, nbatch=1, batch=1000)
+    G = wl.graph
+    w = np.minimum(G.w, (1 << 20) - 1).astype(np.uint32)
+    g = B.Graph(G.n, dev(G.row_ptr), dev(G.col), dev(w), max_bits=20, radix_base=4)
+    og = O.Graph(G.n, G.row_ptr, G.col, w)
+    assert og.set_base4() == 0
+    offs, _, _, _ = og.edges()
+    deg = np.diff(offs.astype(np.int64))
+    for i, v in enumerate(np.argsort(-deg)[[0, 5, 50, 500]]):
+        one_step_check(B, g, og, int(v), 600 + i)
+    starts = W.walk_starts(G.n, 20000, 3)
+    out = []
+    for lanes in (1, 4, 32):
+        g.set_walk_config(lanes, 8)
+        out.append(run_walk(B, g, starts, [B.policy(B.DEEPWALK, 20)], 9, 21))
+    for p, l in out[1:]:
+        assert (p == out[0][0]).all() and (l == out[0][1]).all()
+    assert_steps_live(og, *out[0])
