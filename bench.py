@@ -99,6 +99,33 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------- roofline model
 
+WALK_SOURCES = ["paper_2504_10233_gb300/csrc/walk.cu", "paper_2504_10233_gb300/csrc/bingo_internal.cuh"]
+
+
+def walk_source_digest() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in WALK_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str):
+    """DRAM bytes (read + write) per walker launch from the committed ncu capture of this workload,
+    or None when the walker sources changed since the capture (the digest no longer matches)."""
+    path = os.path.join(ROOT, "profiles", "walk_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(workload)
+    if not ent or ent.get("sources_sha256_16") != walk_source_digest():
+        return None
+    return float(ent["dram_bytes_per_launch"])
+
 def expected_bytes_per_vertex(ex, alpha=40, beta=10):
     """Algorithmic bytes of one sampled step from each vertex, averaged over the group choice:
     header sector 32 + count line 32*ceil(4*K_v/32) + the group's pick (regular: member sector 32,
@@ -323,7 +350,8 @@ def run_ours(args):
     pk, pk_src = peaks()
     achieved = abytes / (walk_ms[-1] / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": args.traffic,
+            "frac": achieved / pk["hbm_gbs"],
+            "traffic": args.traffic if args.traffic is not None else measured_traffic(args.workload),
             "kernel": "k_walk_persistent", "peak_source": f"{pk_src} hbm_gbs (copy bandwidth)",
             "bytes_per_step": abytes / max(1, int((l_np.astype(np.int64) - 1).sum()))}
 
@@ -705,8 +733,9 @@ def _timed_batches(torch, g, recs, warmup, flush, stream):
 
 def run_ablation(args):
     """f1: real-valued biases with lambda (Section 4.3) against the integer graph of their integer
-    parts; f2: group adaption (Eq. group) against the all-regular baseline (Section 6.2).  Same
-    RMAT-20 graph, walkers and batch sizes as the main bench workload."""
+    parts; f2: group adaption (Eq. group) against the all-regular baseline (Section 6.2); f3: radix
+    base 4 against base 2 (Appendix).  Same RMAT-20 graph, walkers and batch sizes as the main bench
+    workload."""
     import torch
 
     import paper_2504_10233_gb300 as B
@@ -766,6 +795,38 @@ def run_ablation(args):
                 "state_bytes": {"real": state_r, "integer": state_i, "ratio": state_r / state_i},
                 "decimal_share_mean_over_vertices": float(share[ex["deg"] > 0].mean()),
                 "paper_context": "A100: 1.02x time, 1.08x memory (real vs integer biases)",
+                "clocks": clocks}
+    elif args.workload == "f3":
+        w20 = np.minimum(G.w, (1 << 20) - 1).astype(np.uint32)  # base 4 takes biases below 4^10
+        recs = []
+        for b in wl.batches:
+            r = b.records().copy()
+            r[:, 2] = np.minimum(r[:, 2], (1 << 20) - 1)
+            recs.append(t(r))
+        g2 = B.Graph(G.n, t(G.row_ptr), t(G.col), t(w20), max_bits=20)
+        g4 = B.Graph(G.n, t(G.row_ptr), t(G.col), t(w20), max_bits=20, radix_base=4)
+        sampler.start()
+        w_2, steps = _timed_walks(torch, B, g2, starts, stride, args.steps, args.warmup, 7, flush, stream)
+        w_4, _ = _timed_walks(torch, B, g4, starts, stride, args.steps, args.warmup, 7, flush, stream)
+        u_2, _ = _timed_batches(torch, g2, recs, args.warmup, flush, stream)
+        u_4, _ = _timed_batches(torch, g4, recs, args.warmup, flush, stream)
+        clocks = sampler.stop()
+        tot = lambda m: sum(v for k, v in m.items() if k not in ("pool_capacity", "edge_index"))
+        m2, m4 = g2.memory_report(), g4.memory_report()
+        e2, e4 = g2.export_state(), g4.export_state()
+        ne = lambda e: int((e["cnt"] > 0).sum())
+        line = {"metric": "radix base 4 over base 2: state memory, walk time, update time (Appendix)",
+                "value": tot(m4) / tot(m2), "unit": "x (memory)", "higher_is_better": False,
+                "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "u32/u64", "data": "synthetic",
+                "config": {"workload": "RMAT-20 (2^20 vertices, 2^24 edges), floor(Pareto 1.5) biases clipped below "
+                                       "2^20; 2^20 DeepWalk x 80; batches of 10^5 updates (50/50)",
+                           "l2": "flushed before every launch"},
+                "memory_bytes": {"base2": m2, "base4": m4},
+                "nonempty_groups": {"base2": ne(e2), "base4": ne(e4)},
+                "member_entries": {"base2": int(e2["sizes"]["list_entries"]), "base4": int(e4["sizes"]["list_entries"])},
+                "walk_ms": {"base2": w_2, "base4": w_4}, "walk_steps_per_s_base4": steps / (w_4 / 1e3),
+                "update_ms_per_batch": {"base2": u_2, "base4": u_4},
+                "paper_context": "not evaluated in the paper (larger bases reduce K; nested structures are hard on GPUs)",
                 "clocks": clocks}
     else:
         ga = B.Graph(G.n, t(G.row_ptr), t(G.col), t(G.w), max_bits=G.max_bits)
@@ -846,7 +907,7 @@ def main():
         run_serving(args)
     elif args.workload == "c5":
         run_sweep(args)
-    elif args.workload in ("f1", "f2"):
+    elif args.workload in ("f1", "f2", "f3"):
         run_ablation(args)
     else:
         run_ours(args)
