@@ -207,12 +207,25 @@ struct SegScratch {
     unsigned long long* best; // [nd]
 };
 
+constexpr uint32_t PRE_MULT = 4;             // candidate region per deletion key
+constexpr uint32_t PRE_CHUNK = 256 * 8;
+constexpr uint32_t PRE_MIN_DEG = 1u << 16;   // vertices this large are scanned by the whole grid
+constexpr uint32_t NO_PRE = 0xFFFFFFFFu;
+
+// Deletion candidates among the pre-existing slots [0, d0), collected for a big segment by the
+// grid-wide pre-pass (k_cand_scan); list == nullptr when there is none.
+struct PreCand {
+    const uint32_t* list = nullptr;
+    uint32_t count = 0, cap = 0;
+};
+
 // Apply one vertex's segment (ni insertions then nd deletions).  Returns false if the graph ran out of pool.
 // REAL: real-bias graphs (decimal parts follow their edges, slot 31 holds the decimal total).
 template <bool REAL, class Team, class Src>
 __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint32_t v, uint32_t ni, uint32_t nd,
                               Src B, const SegScratch& X, unsigned long long* stats, uint32_t* sdel_buf,
-                              uint32_t sdel_cap, uint32_t* cand_buf = nullptr, uint32_t cand_cap = 0) {
+                              uint32_t sdel_cap, uint32_t* cand_buf = nullptr, uint32_t cand_cap = 0,
+                              PreCand pre = PreCand()) {
     const uint32_t rank = t.rank(), T = t.size();
     const VHdr h0 = load_hdr(G, v);
     const uint32_t d0 = h0.deg, capa0 = capa_of(h0), caps0 = caps_of(h0);
@@ -323,21 +336,35 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
         uint32_t ncand = 0;
         bool use_cand = cand_buf != nullptr;
         if (use_cand) {
-            ncand = team_compact_lt(
-                t, dtot, [&](uint32_t j) { return make_uint2(pairs[j].x, (uint32_t)(eids[j] >> 32)); },
-                [&](uint2 xe, uint32_t) {
-                    if (xe.y & (uint32_t)(DEAD_BIT >> 32)) return false;
-                    const uint32_t x = xe.x;
-                    uint32_t lo = 0, hi = nd;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (B.del_dst(mid) < x) lo = mid + 1; else hi = mid;
-                    }
-                    return lo < nd && B.del_dst(lo) == x;
-                },
-                [&](uint32_t j, uint32_t pos) {
-                    if (pos < cand_cap) cand_buf[pos] = j;
-                });
+            auto is_cand = [&](uint2 xe, uint32_t) {
+                if (xe.y & (uint32_t)(DEAD_BIT >> 32)) return false;
+                const uint32_t x = xe.x;
+                uint32_t lo = 0, hi = nd;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (B.del_dst(mid) < x) lo = mid + 1; else hi = mid;
+                }
+                return lo < nd && B.del_dst(lo) == x;
+            };
+            if (pre.list && pre.count <= pre.cap) {
+                // the pre-pass scanned [0, d0); only the appended slots are left to test
+                const uint32_t n0 = pre.count;
+                if (n0 <= cand_cap)
+                    for (uint32_t i = rank; i < n0; i += T) cand_buf[i] = pre.list[i];
+                const uint32_t n1 = team_compact_lt(
+                    t, ni, [&](uint32_t j) { return make_uint2(pairs[d0 + j].x, (uint32_t)(eids[d0 + j] >> 32)); },
+                    is_cand,
+                    [&](uint32_t j, uint32_t pos) {
+                        if (n0 + pos < cand_cap) cand_buf[n0 + pos] = d0 + j;
+                    });
+                ncand = n0 + n1;
+            } else {
+                ncand = team_compact_lt(
+                    t, dtot, [&](uint32_t j) { return make_uint2(pairs[j].x, (uint32_t)(eids[j] >> 32)); }, is_cand,
+                    [&](uint32_t j, uint32_t pos) {
+                        if (pos < cand_cap) cand_buf[pos] = j;
+                    });
+            }
             use_cand = ncand <= cand_cap;
             t.sync();
         }
@@ -911,6 +938,12 @@ struct SegArgs {
     unsigned long long* queue;    // [0] next small segment, [1] next big segment (k_apply work queues)
     uint4* rec;                   // per key: the insertion record {edge id low, dst, bias, edge id high}
     uint4* seginfo;               // per segment: {v, first key, ni, nd}
+    uint32_t* gcand;              // big segments: deletion candidates from the pre-pass, region PRE_MULT * (first
+                                  // deletion key) .. + PRE_MULT * nd
+    uint32_t* gcand_cnt;          // per segment: candidates found (may exceed the region: then unused);
+                                  // NO_PRE for segments the pre-pass does not scan
+    uint32_t* huge_list;          // segments scanned by the pre-pass
+    unsigned long long* nhuge;
     uint64_t eid_base;
     const unsigned long long* eid_base_dev;  // when set, the edge-id base is read on the device
     uint32_t* holes;
@@ -944,6 +977,9 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
         for (uint32_t i = a; i < lo; i++) insbits |= S.rec[i].z;
         bound += pool_bound(G, v, h, ni, b - lo, insbits);
         const bool big = dtot > 4096 || (b - a) > 256;
+        const bool huge = h.deg >= PRE_MIN_DEG && b > lo;  // hub with deletions: grid-wide candidate scan
+        S.gcand_cnt[sidx] = huge ? 0u : NO_PRE;
+        if (huge) S.huge_list[atomicAdd(S.nhuge, 1ull)] = (uint32_t)sidx;
         if (big) S.big_list[atomicAdd(&S.counts[1], 1ull)] = (uint32_t)sidx;
         else S.small_list[atomicAdd(&S.counts[0], 1ull)] = (uint32_t)sidx;
     }
@@ -955,6 +991,58 @@ __global__ void k_oom_check(DevGraph G, const unsigned long long* counts, unsign
     if (top + counts[2] > G.pool.words) atomicOr(G.pool.status, ST_OOM);
     queue[0] = 0;
     queue[1] = 0;
+}
+
+// Grid-wide pre-pass for the big segments (hubs): the pre-existing slots [0, d0) whose destination
+// is deleted in the segment, found by every block at once instead of by the segment's single team
+// (an O(d) scan per touched hub).  Candidate order is irrelevant: resolution takes minima of edge ids.
+constexpr uint32_t PRE_SMEM_KEYS = 4096;  // deletion destinations staged per block
+__global__ void __launch_bounds__(256) k_cand_scan(DevGraph G, SegArgs S) {
+    __shared__ uint32_t sk[PRE_SMEM_KEYS];
+    if (*(volatile uint32_t*)G.pool.status & ST_STOP) return;  // block-uniform: read once below
+    const unsigned long long nhuge = *S.nhuge;
+    const uint64_t dmask = (1ull << S.B.bn) - 1;
+    for (unsigned long long i = 0; i < nhuge; i++) {
+        const uint32_t sidx = S.huge_list[i];
+        const uint4 info = S.seginfo[sidx];
+        const uint32_t nd = info.w;
+        const uint32_t v = info.x, first = info.y + info.z;
+        const VHdr h = load_hdr(G, v);
+        const uint32_t d0 = h.deg;
+        if (nd == 0 || blockIdx.x * PRE_CHUNK >= d0) continue;  // block-uniform
+        const uint2* pairs = adj_pairs(G, h.adj);
+        const uint64_t* dk = S.sorted_keys + first;
+        const bool staged = nd <= PRE_SMEM_KEYS;
+        __syncthreads();  // the previous segment's keys are no longer read
+        if (staged)
+            for (uint32_t k = threadIdx.x; k < nd; k += blockDim.x) sk[k] = (uint32_t)(dk[k] & dmask);
+        __syncthreads();
+        uint32_t* out = S.gcand + (uint64_t)PRE_MULT * first;
+        const uint32_t cap = PRE_MULT * nd;
+        for (uint32_t c0 = blockIdx.x * PRE_CHUNK; c0 < d0; c0 += gridDim.x * PRE_CHUNK) {
+            uint32_t x[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint32_t j = c0 + q * 256 + threadIdx.x;
+                x[q] = j < d0 ? pairs[j].x : NONE32;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint32_t j = c0 + q * 256 + threadIdx.x;
+                if (j >= d0) continue;
+                uint32_t lo = 0, hi = nd;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    const uint32_t kv = staged ? sk[mid] : (uint32_t)(dk[mid] & dmask);
+                    if (kv < x[q]) lo = mid + 1; else hi = mid;
+                }
+                if (lo < nd && (staged ? sk[lo] : (uint32_t)(dk[lo] & dmask)) == x[q]) {
+                    const uint32_t pos = atomicAdd(S.gcand_cnt + sidx, 1u);
+                    if (pos < cap) out[pos] = j;
+                }
+            }
+        }
+    }
 }
 
 // Per-team scratch in shared memory for segments of at most SMALL_X insertions and deletions, so the
@@ -969,7 +1057,7 @@ template <bool REAL, class Team>
 __device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, const SegArgs& S, SegSh& sh, uint32_t sidx,
                                             uint32_t* sdel_buf, uint32_t sdel_cap, uint32_t* cand_buf,
                                             uint32_t cand_cap, SmallScratch* sx = nullptr,
-                                            unsigned long long* stats = nullptr) {
+                                            unsigned long long* stats = nullptr, bool pre_scanned = false) {
     const uint4 info = S.seginfo[sidx];
     const uint32_t v = info.x, a = info.y, ni = info.z, nd = info.w;
     BatchSrc src;
@@ -993,7 +1081,14 @@ __device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, co
         X.best = S.best + a + ni;
     }
     src.sdel = nullptr;
-    apply_segment<REAL>(t, G, sh, v, ni, nd, src, X, stats ? stats : S.stats, sdel_buf, sdel_cap, cand_buf, cand_cap);
+    PreCand pre;
+    if (pre_scanned && nd && S.gcand_cnt[sidx] != NO_PRE) {
+        pre.list = S.gcand + (uint64_t)PRE_MULT * (a + ni);
+        pre.count = S.gcand_cnt[sidx];
+        pre.cap = PRE_MULT * nd;
+    }
+    apply_segment<REAL>(t, G, sh, v, ni, nd, src, X, stats ? stats : S.stats, sdel_buf, sdel_cap, cand_buf, cand_cap,
+                        pre);
 }
 
 constexpr uint32_t SMALL_SDEL = 64;    // staged deletion destinations per warp team
@@ -1041,7 +1136,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) k_apply(DevGraph G, SegArgs 
             __syncthreads();
             if (i >= nbig) break;
             run_segment<REAL>(t, G, S, smem.big.sh, S.big_list[i], smem.big.sdel, BIG_SDEL, smem.big.cand, BIG_CAND, nullptr,
-                        bstats);
+                        bstats, true);
         }
     }
     __syncthreads();  // shared memory changes from the big-segment to the warp-team layout
@@ -1305,6 +1400,8 @@ static bingo_status update_capacity(bingo_graph* g, uint64_t count) {
     CK(ensure(g->s_best, 8 * kc + 64), "update scratch");
     CK(ensure(g->s_rec, 16 * kc), "update scratch");
     CK(ensure(g->s_seginfo, 16 * kc + 16), "update scratch");
+    CK(ensure(g->s_gcand, 4ull * PRE_MULT * kc), "update scratch");
+    CK(ensure(g->s_gcand_cnt, 8 * kc + 32), "update scratch");
     CK(ensure(g->s_tmp, std::max(radix_sort_tmp_bytes(kc), scan_tmp_bytes(kc))), "update scratch");
     if (!g->apply_blocks) {
         int per_sm = 0;
@@ -1380,6 +1477,11 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     S.eid_base_dev = (const unsigned long long*)(ctl + CTL_SCR + 9);
     S.rec = (uint4*)g->s_rec.p;
     S.seginfo = (uint4*)g->s_seginfo.p;
+    S.gcand = (uint32_t*)g->s_gcand.p;
+    S.gcand_cnt = (uint32_t*)g->s_gcand_cnt.p;
+    S.huge_list = S.gcand_cnt + kc + 4;
+    S.nhuge = (unsigned long long*)(ctl + CTL_SCR + 13);
+    CK(cudaMemsetAsync(S.nhuge, 0, 8, s), "pre-pass count reset");
     S.holes = (uint32_t*)g->s_aux.p;
     S.surv = S.holes + kc;
     S.slot_scratch = S.surv + kc;
@@ -1388,9 +1490,10 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     k_seg_classify<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S);
     S.queue = (unsigned long long*)(ctl + CTL_SCR + 11);
     k_oom_check<<<1, 1, 0, s>>>(g->G, counts, S.queue);
+    k_cand_scan<<<(unsigned)g->num_sms * 4, 256, 0, s>>>(g->G, S);
     if (g->G.fbits) k_apply<true><<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
     else k_apply<false><<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
-    g->launches += 3;
+    g->launches += 4;
     if (g->G.eh_mask) {
         k_eh_apply<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S, kc, nkeys_dev);
         g->launches++;
