@@ -367,3 +367,35 @@ def test_radix_base4_parity(B):
         assert_state_matches(g.export_state(), og, base4=True)
     with pytest.raises(B.BingoError):
         B.Graph(og.n, dev(offs.astype(np.uint64)), dev(dst), dev(np.full_like(w, 1 << 20)), radix_base=4)
+
+
+def test_hub_prepass_deletions(B):
+    """A hub past the grid-wide pre-pass threshold (d >= 2^16): deletions of duplicated edges, repeated
+    deletions of one destination, deletions of edges inserted in the same batch and misses, all
+    resolved to the earliest live copy as the oracle does."""
+    n = 4096
+    rng = np.random.default_rng(91)
+    hub_d = 70000
+    edges = [(0, int(x), int(w)) for x, w in zip(rng.integers(1, 2000, hub_d), rng.integers(1, 1 << 10, hub_d))]
+    edges += [(1 + (j % 50), int(rng.integers(0, n)), 3) for j in range(2000)]
+    og = O.Graph.from_edges(n, edges)
+    offs, dst, w, eid = og.edges()
+    g = B.Graph(n, dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=10)
+    for it in range(4):
+        rec = []
+        hub_dst = dst[int(offs[0]):int(offs[1])]
+        for _ in range(400):  # deletions of live hub edges (destinations repeat: duplicates exist)
+            rec.append([0, int(hub_dst[int(rng.integers(0, len(hub_dst)))]), 0, 1])
+        for _ in range(100):  # insert-then-delete in one batch, and misses
+            x = int(rng.integers(2000, 3000))
+            rec.append([0, x, int(rng.integers(1, 1 << 10)), 0])
+            rec.append([0, x, 0, 1])
+            rec.append([0, int(rng.integers(3000, n)), 0, 1])
+        for _ in range(300):
+            rec.append([0, int(rng.integers(1, 2000)), int(rng.integers(1, 1 << 10)), 0])
+        rec = np.array(rec, dtype=np.uint32)
+        rec = rec[rng.permutation(len(rec))]
+        st = apply_both(g, og, rec, 10)
+        assert st["not_found"] > 0 and st["deleted"] > 0
+        offs, dst, w, eid = og.edges()
+        assert_state_matches(g.export_state(), og)
