@@ -361,12 +361,16 @@ def run_ours(args):
     h_plen = torch.empty(nw, dtype=torch.int32).pin_memory()
     h_recs = [torch.from_numpy(np.ascontiguousarray(b.records())).pin_memory() for b in wl.batches]
     e2e_steps, e2e_t = 0, 0.0
-    for i in range(0 if args.no_e2e else min(args.steps, 3)):
+    n_e2e = 0 if args.no_e2e else min(args.steps, 3)
+    for i in range(n_e2e + (1 if n_e2e else 0)):  # the first pass is an untimed warm-up (staging buffers)
         flush.fill_(i)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.apply_updates(h_recs[i % len(h_recs)], stream=stream)  # host records: H2D inside the call
-        g.walk(h_starts, pol, seed0 + 1000 + i, stride, h_paths, h_plen, mode=mode, stream=stream)
+        # padded form: the call writes every entry of the host rows, so nothing is uploaded first
+        g.walk(h_starts, pol, seed0 + 1000 + i, stride, h_paths, h_plen, mode=B.WALK_PERSISTENT, stream=stream)
+        if i == 0:
+            continue
         e2e_t += time.perf_counter() - t0
         e2e_steps += int((h_plen.numpy().astype(np.int64) - 1).sum())
     e2e_t = max_over_ranks(e2e_t, dev)
