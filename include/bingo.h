@@ -80,7 +80,8 @@ typedef struct {
     uint32_t lanes_per_walker; /* group-selection team width: 1, 4 or 32; 0 = tuned default */
     uint32_t warps_per_block;  /* walker kernel block size in warps; 0 = tuned default */
     uint32_t blocks_per_sm;    /* walker kernel persistent blocks per SM; 0 = tuned default */
-    uint32_t update_chunk;     /* segments above this many adjacency slots use a whole block; 0 = default */
+    uint32_t update_chunk;     /* vertex segments above this many adjacency slots (or above 256 records) are applied
+                                  by a whole 512-thread block instead of one warp; 0 = 4096 */
     uint32_t reg_variant;      /* walker register budget: 0 = 64 registers, 1 = 40 registers (more resident warps) */
     uint64_t pool_words;       /* device pool for adjacency and group blocks, in 4-byte words; 0 = auto */
     uint32_t bias_format;      /* BINGO_BIAS_U32 (default) or BINGO_BIAS_F32 */
@@ -311,6 +312,20 @@ bingo_status bingo_memory_report(bingo_graph* g, uint64_t out[6]);
  */
 bingo_status bingo_autotune(bingo_graph* g, uint64_t nwalkers, const uint32_t* starts, uint32_t length, void* stream,
                             bingo_config* out_cfg);
+
+/*
+ * Autotune the update pipeline's update_chunk (the adjacency size above which a vertex's
+ * segment is applied by a whole block rather than one warp) on the caller's own records,
+ * which ARE applied: they are split into consecutive equal slices, one per candidate setting
+ * and round, applied in order as separate batches (each slice's insertions before its
+ * deletions, every slice seeing the earlier ones), and the setting with the least time per
+ * record is kept in the graph's config.  ups: bingo_update[count], host or device.  stats
+ * (nullable) receives the sums over all slices; out_cfg (nullable) the resulting config.
+ * Errors as bingo_apply_updates; on an error the slices applied so far stay applied.
+ * Synchronises `stream`.  The paper has no counterpart (it fixes its kernel shapes).
+ */
+bingo_status bingo_autotune_updates(bingo_graph* g, const bingo_update* ups, uint64_t count, void* stream,
+                                    bingo_update_stats* stats, bingo_config* out_cfg);
 
 /* Current configuration of the graph (host pointer). */
 bingo_status bingo_get_config(bingo_graph* g, bingo_config* out);

@@ -98,6 +98,7 @@ SIGNATURES = {
     "bingo_export_decimal": (c.c_int, [VP, VP]),
     "bingo_memory_report": (c.c_int, [VP, c.POINTER(c.c_uint64)]),
     "bingo_autotune": (c.c_int, [VP, c.c_uint64, VP, c.c_uint32, VP, c.POINTER(bingo_config)]),
+    "bingo_autotune_updates": (c.c_int, [VP, VP, c.c_uint64, VP, c.POINTER(bingo_update_stats), c.POINTER(bingo_config)]),
     "bingo_get_config": (c.c_int, [VP, c.POINTER(bingo_config)]),
     "bingo_set_walk_config": (c.c_int, [VP, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32]),
     "bingo_kernel_launches": (c.c_uint64, [VP]),
@@ -244,6 +245,15 @@ def bingo_memory_report(h):
     return dict(zip(keys, [int(x) for x in out]))
 
 
+def bingo_autotune_updates(h, records, stream=None):
+    """Tune update_chunk on these records, which are applied (as consecutive slices)."""
+    cfg = bingo_config()
+    st = bingo_update_stats()
+    n = int(records.shape[0]) if hasattr(records, "shape") else len(records)
+    _err(load().bingo_autotune_updates(h, _ptr(records), n, _stream(stream), c.byref(st), c.byref(cfg)))
+    return st.as_dict(), cfg
+
+
 def bingo_autotune(h, nwalkers, starts, length, stream=None):
     cfg = bingo_config()
     _err(load().bingo_autotune(h, nwalkers, _ptr(starts), length, _stream(stream), c.byref(cfg)))
@@ -355,6 +365,9 @@ class Graph:
 
     def autotune(self, starts, length, stream=None):
         return bingo_autotune(self.h, len(starts), starts, length, stream)
+
+    def autotune_updates(self, records, stream=None):
+        return bingo_autotune_updates(self.h, records, stream)
 
     def set_walk_config(self, lanes, warps_per_block, blocks_per_sm=0, reg_variant=0):
         bingo_set_walk_config(self.h, lanes, warps_per_block, blocks_per_sm, reg_variant)

@@ -936,6 +936,7 @@ struct SegArgs {
     uint32_t* big_list;
     unsigned long long* counts;   // [0] small, [1] big, [2] pool bound
     unsigned long long* queue;    // [0] next small segment, [1] next big segment (k_apply work queues)
+    uint32_t big_slots;           // segments above this many adjacency slots run on a block team
     uint4* rec;                   // per key: the insertion record {edge id low, dst, bias, edge id high}
     uint4* seginfo;               // per segment: {v, first key, ni, nd}
     uint32_t* gcand;              // big segments: deletion candidates from the pre-pass, region PRE_MULT * (first
@@ -976,7 +977,7 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
         uint32_t insbits = 0;
         for (uint32_t i = a; i < lo; i++) insbits |= S.rec[i].z;
         bound += pool_bound(G, v, h, ni, b - lo, insbits);
-        const bool big = dtot > 4096 || (b - a) > 256;
+        const bool big = dtot > S.big_slots || (b - a) > 256;
         const bool huge = h.deg >= PRE_MIN_DEG && b > lo;  // hub with deletions: grid-wide candidate scan
         S.gcand_cnt[sidx] = huge ? 0u : NO_PRE;
         if (huge) S.huge_list[atomicAdd(S.nhuge, 1ull)] = (uint32_t)sidx;
@@ -1091,6 +1092,7 @@ __device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, co
                         pre);
 }
 
+constexpr uint32_t DEFAULT_UPDATE_CHUNK = 4096;  // best of 1,024 .. 16,384 on RMAT-20 with 10^5-update batches
 constexpr uint32_t SMALL_SDEL = 64;    // staged deletion destinations per warp team
 constexpr uint32_t SMALL_CAND = 64;    // resolution candidates per warp team
 constexpr uint32_t BIG_SDEL = 4096;    // per block team
@@ -1477,6 +1479,7 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     S.eid_base_dev = (const unsigned long long*)(ctl + CTL_SCR + 9);
     S.rec = (uint4*)g->s_rec.p;
     S.seginfo = (uint4*)g->s_seginfo.p;
+    S.big_slots = g->cfg.update_chunk ? g->cfg.update_chunk : DEFAULT_UPDATE_CHUNK;
     S.gcand = (uint32_t*)g->s_gcand.p;
     S.gcand_cnt = (uint32_t*)g->s_gcand_cnt.p;
     S.huge_list = S.gcand_cnt + kc + 4;
@@ -1649,6 +1652,73 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     } else if (st == BINGO_OK) {
         g->eh_distinct += stats ? stats->inserted : count;
     }
+    return st;
+}
+
+bingo_status bingo_autotune_updates(bingo_graph* g, const bingo_update* ups, uint64_t count, void* stream,
+                                    bingo_update_stats* stats, bingo_config* out_cfg) {
+    if (!g || (count && !ups)) { set_error("autotune: bad arguments"); return BINGO_E_INVALID; }
+    static const uint32_t cand[] = {1024, 2048, 4096, 8192, 16384};
+    constexpr int NC = 5, ROUNDS = 2;
+    cudaStream_t s = (cudaStream_t)stream;
+    bingo_update_stats total;
+    memset(&total, 0, sizeof(total));
+    auto add = [&](const bingo_update_stats& x) {
+        total.inserted += x.inserted;
+        total.deleted += x.deleted;
+        total.not_found += x.not_found;
+        total.vertices_touched += x.vertices_touched;
+        total.groups_rebuilt += x.groups_rebuilt;
+        for (int a = 0; a < 5; a++)
+            for (int b = 0; b < 5; b++) total.conversions[a][b] += x.conversions[a][b];
+    };
+    const uint64_t slice = count / (NC * ROUNDS);
+    bingo_status st = BINGO_OK;
+    if (slice == 0) {  // too few records to compare settings: apply them as one batch
+        st = bingo_apply_updates(g, ups, count, stream, &total);
+    } else {
+        // the slices share one capacity (the largest slice), so only the setting changes between them
+        if ((st = update_capacity(g, count - slice * (NC * ROUNDS - 1))) != BINGO_OK) return st;
+        double per_rec[NC] = {0};
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        const uint32_t saved = g->cfg.update_chunk;
+        uint64_t off = 0;
+        for (int r = 0; r < ROUNDS && st == BINGO_OK; r++) {
+            for (int c = 0; c < NC && st == BINGO_OK; c++) {
+                const bool last = r == ROUNDS - 1 && c == NC - 1;
+                const uint64_t n = last ? count - off : slice;
+                if (g->cfg.update_chunk != cand[c]) {
+                    g->cfg.update_chunk = cand[c];
+                    if (g->upd_graph) cudaGraphExecDestroy(g->upd_graph);  // the setting is baked into the graph
+                    g->upd_graph = nullptr;
+                }
+                bingo_update_stats one;
+                cudaEventRecord(e0, s);
+                st = bingo_apply_updates(g, ups + off, n, stream, &one);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (st == BINGO_OK) {
+                    add(one);
+                    per_rec[c] += ms / (double)n;
+                }
+                off += n;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        int best = 0;
+        for (int c = 1; c < NC; c++)
+            if (per_rec[c] < per_rec[best]) best = c;
+        g->cfg.update_chunk = st == BINGO_OK ? cand[best] : saved;
+        if (g->upd_graph) cudaGraphExecDestroy(g->upd_graph);
+        g->upd_graph = nullptr;
+    }
+    if (stats) *stats = total;
+    if (out_cfg && st == BINGO_OK) st = bingo_get_config(g, out_cfg);
     return st;
 }
 

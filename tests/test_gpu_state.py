@@ -399,3 +399,27 @@ def test_hub_prepass_deletions(B):
         assert st["not_found"] > 0 and st["deleted"] > 0
         offs, dst, w, eid = og.edges()
         assert_state_matches(g.export_state(), og)
+
+
+def test_update_autotune_applies_slices_in_order(B):
+    """bingo_autotune_updates applies the records as ten consecutive slices (five settings, two
+    rounds) and keeps one of the candidate update_chunk settings; the state equals the oracle's
+    after the same slices."""
+    og = _stress_graph(21)
+    offs, dst, w, eid = og.edges()
+    g = B.Graph(og.n, dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=12)
+    rng = np.random.default_rng(22)
+    rec = _stress_batch(rng, og, og.n, 1003)
+    st, cfg = g.autotune_updates(dev(rec))
+    assert cfg.update_chunk in (1024, 2048, 4096, 8192, 16384)
+    sl = len(rec) // 10
+    tot = [0, 0, 0]
+    for k in range(10):
+        part = rec[k * sl: (k + 1) * sl] if k < 9 else rec[9 * sl:]
+        rc, s = og.apply(part, 12)
+        assert rc == 0
+        tot = [a + b for a, b in zip(tot, s)]
+    assert (st["inserted"], st["deleted"], st["not_found"]) == tuple(tot)
+    assert_state_matches(g.export_state(), og)
+    apply_both(g, og, _stress_batch(rng, og, og.n, 200), 12)  # the kept setting serves later batches
+    assert_state_matches(g.export_state(), og)
