@@ -280,3 +280,48 @@ def test_real_walks_live_and_team_independent(B):
     for p, l in out[1:]:
         assert (p == out[0][0]).all() and (l == out[0][1]).all()
     assert_steps_live(og, *out[0])
+
+
+def test_real_server_matches_direct_walk(B):
+    """The serving loop on a real-bias graph: a request's paths equal a direct walk with its seed,
+    alone or merged with others; real-bias updates go through the server's epochs."""
+    import ctypes
+
+    og = real_graph(10)
+    g = make(B, og)
+    L = B.load()
+    pol = B.policy(B.DEEPWALK, 12)
+    rng = np.random.default_rng(90)
+    reqs = [(rng.integers(0, og.n, size=k).astype(np.uint32), 70 + i) for i, k in enumerate([3, 200, 1500])]
+    h = ctypes.c_void_p()
+    cfg = B.bingo_server_config()
+    assert L.bingo_server_create(g.h, ctypes.byref(cfg), ctypes.byref(h)) == 0
+    tickets = []
+    for st, seed in reqs:
+        t = ctypes.c_uint64()
+        assert L.bingo_server_submit_walk(h, st.ctypes.data, len(st), ctypes.byref(pol), seed, ctypes.byref(t)) == 0
+        tickets.append(t.value)
+    out = []
+    for (st, _), t in zip(reqs, tickets):
+        p = np.zeros((len(st), 13), np.uint32)
+        l = np.zeros(len(st), np.uint32)
+        ep = ctypes.c_uint64()
+        assert L.bingo_server_wait(h, t, 60000, p.ctypes.data, l.ctypes.data, ctypes.byref(ep)) == 0
+        out.append((p, l))
+    upd = real_batch(rng, og, og.n, 100)
+    ep = ctypes.c_uint64()
+    assert L.bingo_server_submit_updates(h, upd.ctypes.data, len(upd), ctypes.byref(ep)) == 0
+    assert L.bingo_server_drain(h, 60000) == 0
+    L.bingo_server_destroy(h)
+    import torch
+
+    for (st, seed), (p, l) in zip(reqs, out):
+        paths = torch.empty((len(st), 13), dtype=torch.int32, device="cuda")
+        plen = torch.empty(len(st), dtype=torch.int32, device="cuda")
+        # the updates were applied after these requests: compare against a fresh graph of the old state
+        g0 = make(B, real_graph(10))
+        g0.walk(dev(st), [pol], seed, 13, paths, plen)
+        g0.check()
+        assert (paths.cpu().numpy().view(np.uint32) == p).all() and (plen.cpu().numpy().view(np.uint32) == l).all()
+    og.apply(upd)
+    assert_real_state_matches(g, og)
