@@ -887,8 +887,24 @@ __global__ void k_seg_write(const uint64_t* __restrict__ flag, const uint64_t* _
 // words) for every group that can reach a list kind (Eq. group) other than its current kind, the
 // blocks of every group that can be sparse when the set of sparse groups can change (they are
 // rebuilt together), and a sparse list.
+// The 32 group counts of vertex v, read as whole 16-byte pairs with every load in flight at once.
+__device__ __forceinline__ void load_counts(const DevGraph& G, uint32_t v, uint32_t* cnt) {
+    const uint4* hot = reinterpret_cast<const uint4*>(G.vh + v) + 1;
+    const uint4* cold = reinterpret_cast<const uint4*>(G.vc + v);
+    uint4 x[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) x[i] = i < (int)HOT_GROUPS / 2 ? hot[i] : cold[i - HOT_GROUPS / 2];
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        cnt[2 * i] = x[i].x;
+        cnt[2 * i + 1] = x[i].z;
+    }
+}
+
 __device__ __forceinline__ unsigned long long pool_bound(const DevGraph& G, uint32_t v, const VHdr& h, uint32_t ni,
                                                          uint32_t nd, uint32_t insbits) {
+    uint32_t cnts[32];
+    load_counts(G, v, cnts);
     const uint32_t d0 = h.deg, dmin = d0 + ni >= nd ? d0 + ni - nd : 0, dmax = d0 + ni;
     const bool grows = dmax > capa_of(h);
     const uint32_t capa1 = grows ? capa_for(dmax) : capa_of(h);
@@ -896,7 +912,7 @@ __device__ __forceinline__ unsigned long long pool_bound(const DevGraph& G, uint
     bool sp_set_may_change = false, any_old_sp = false;
     const uint32_t nslots = G.fbits ? DEC_SLOT : 32u;  // the decimal slot is never a list
     for (uint32_t k = 0; k < nslots; k++) {
-        const uint32_t c = cnt_ref(G, v, k);
+        const uint32_t c = cnts[k];
         const uint32_t cmax = c + (((insbits >> k) & 1u) ? ni : 0u), cmin = c > nd ? c - nd : 0u;
         const uint32_t old = kind_of(c, d0, G.alpha, G.beta);
         const uint32_t min_list = G.alpha == ALL_REGULAR ? 1u : 2u;  // smallest count of a list kind
