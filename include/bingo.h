@@ -73,6 +73,16 @@ enum {
     BINGO_BIAS_F32 = 1  /* real biases with amortisation factor lambda (Section 4.3), see bingo_create */
 };
 
+/* Internal vertex numbering (bingo_config.vertex_order).  Not part of the paper's method: the graph
+ * may renumber its vertices by descending out-degree (ties by id) so that the vertex records
+ * walks visit most sit together in memory.  Ids are translated at every call and each vertex
+ * keeps its adjacency in the caller's CSR order, so the graph (edges, edge ids, group contents)
+ * is the same under either numbering, and so are walks on a freshly created graph or after
+ * insertions and streaming updates.  A batch that deletes edges applies a vertex's deletions in
+ * the order of their internal destination ids, which can leave the slots inside the vertex
+ * ordered differently; walks are then equal in distribution, not draw for draw. */
+enum { BINGO_ORDER_AUTO = 0, BINGO_ORDER_CALLER = 1, BINGO_ORDER_DEGREE = 2 };
+
 typedef struct {
     uint32_t alpha_pct;        /* Eq. group alpha, percent (paper: 40) */
     uint32_t beta_pct;         /* Eq. group beta, percent (paper: 10) */
@@ -90,7 +100,9 @@ typedef struct {
     double lambda;             /* BINGO_BIAS_F32: amortisation factor lambda > 0 (Section 4.3) */
     uint32_t radix_base;       /* 2 (default; 0 means 2) or 4: one group per base-4 digit position, split into
                                   value sub-groups (Appendix, Fig. base4); base 4 needs integer biases < 2^20 */
-    uint32_t reserved1;
+    uint32_t vertex_order;     /* internal vertex numbering: BINGO_ORDER_AUTO (0; by degree when n <= 2^23),
+                                  BINGO_ORDER_CALLER (the caller's ids) or BINGO_ORDER_DEGREE; every call still
+                                  takes and returns the caller's ids (see BINGO_ORDER_*) */
 } bingo_config;
 
 /* One update record, 16 bytes. */

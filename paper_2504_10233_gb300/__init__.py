@@ -26,6 +26,7 @@ OP_INSERT, OP_DELETE, OP_SET_BIAS = 0, 1, 2
 WALK_PERSISTENT, WALK_STEPWISE, WALK_NO_PAD = 0, 1, 0x100
 SERVER_NO_MERGE = 1
 BIAS_U32, BIAS_F32 = 0, 1
+ORDER_AUTO, ORDER_CALLER, ORDER_DEGREE = 0, 1, 2
 PAD = 0xFFFFFFFF
 
 c = ctypes
@@ -43,7 +44,7 @@ class bingo_config(c.Structure):
                 ("lanes_per_walker", c.c_uint32), ("warps_per_block", c.c_uint32), ("blocks_per_sm", c.c_uint32),
                 ("update_chunk", c.c_uint32), ("reg_variant", c.c_uint32), ("pool_words", c.c_uint64),
                 ("bias_format", c.c_uint32), ("all_regular", c.c_uint32), ("lambda_", c.c_double),
-                ("radix_base", c.c_uint32), ("reserved1", c.c_uint32)]
+                ("radix_base", c.c_uint32), ("vertex_order", c.c_uint32)]
 
 
 class bingo_update_stats(c.Structure):

@@ -80,6 +80,8 @@ struct bingo_graph {
     // owned device allocations
     void* d_hdr = nullptr;      // VHot[n]
     void* d_cold = nullptr;     // VCold[n]
+    void* d_order = nullptr;    // internal -> caller vertex id [n] (degree numbering), else null
+    void* d_perm = nullptr;     // caller -> internal vertex id [n]
     void* d_pool = nullptr;
     void* d_ctl = nullptr;      // control words: top, npending, leaked, status, queue, counters
     void* d_fcount = nullptr;

@@ -65,7 +65,7 @@ struct __align__(64) VHot {
     uint32_t adj;   // adjacency block, 32-byte units
     uint32_t deg;
     uint32_t mask;
-    uint32_t sref;  // sparse-list block, 32-byte units; real-bias graphs: the decimal total Q_D
+    uint32_t word;  // real-bias graphs: the decimal total Q_D; otherwise the caller's id of this vertex
     uint2 g[HOT_GROUPS];
 };
 struct __align__(32) VCold {
@@ -73,7 +73,7 @@ struct __align__(32) VCold {
     uint32_t nsp;
     uint8_t lcapa, lcaps;
     uint16_t pad;
-    uint32_t sref_real;  // real-bias graphs: the sparse-list block (32-byte units)
+    uint32_t sref;       // sparse-list block, 32-byte units
     uint32_t spare1;
 };
 static_assert(sizeof(VHot) == 64, "VHot must be two sectors");
@@ -184,6 +184,11 @@ struct DevGraph {
     uint32_t fbits;   // 0: integer biases; FRAC_BITS: real biases (slot 31 = decimal group)
     double lambda;    // real biases: amortisation factor
     uint32_t base4;   // 1: radix base 4, the stored bias word is the sub-group mask (b4_mask)
+    // Internal vertex numbering: vertices are renumbered by descending out-degree (ties by id), so the
+    // records of the vertices walks visit most sit together in HBM and L2.  order[i] = caller's id of
+    // internal vertex i, perm[v] = internal id of the caller's vertex v; both null = identity.
+    const uint32_t* order;
+    const uint32_t* perm;
     VHot* vh;
     VCold* vc;
     Pool pool;
@@ -202,7 +207,7 @@ __device__ __forceinline__ VHdr load_hdr(const DevGraph& G, uint64_t v) {
     h.adj = words_of(a.adj);
     h.deg = a.deg;
     h.mask = a.mask;
-    h.sref = words_of(G.fbits ? b.sref_real : a.sref);
+    h.sref = words_of(b.sref);
     h.nsp = b.nsp;
     h.lcapa = b.lcapa;
     h.lcaps = b.lcaps;
@@ -215,15 +220,20 @@ __device__ __forceinline__ void store_hdr(const DevGraph& G, uint64_t v, const V
     a.adj = ref_of(h.adj);
     a.deg = h.deg;
     a.mask = h.mask;
-    if (G.fbits) b.sref_real = ref_of(h.sref);  // the hot word holds the decimal total (set_decimal_total)
-    else a.sref = ref_of(h.sref);
+    b.sref = ref_of(h.sref);  // the hot word is set once at build (caller's id) or by set_decimal_total
     b.nsp = h.nsp;
     b.lcapa = h.lcapa;
     b.lcaps = h.lcaps;
     b.pad = 0;
 }
 // Real-bias graphs: the decimal total lives in group slot 31 and, for the walker, in the hot line.
-__device__ __forceinline__ void set_decimal_total(const DevGraph& G, uint64_t v, uint32_t qd) { G.vh[v].sref = qd; }
+__device__ __forceinline__ void set_decimal_total(const DevGraph& G, uint64_t v, uint32_t qd) { G.vh[v].word = qd; }
+
+// ids at or above n pass through unchanged (callers reject them)
+__device__ __forceinline__ uint32_t to_internal(const DevGraph& G, uint32_t v) {
+    return (G.perm && v < G.n) ? __ldg(G.perm + v) : v;
+}
+__device__ __forceinline__ uint32_t to_caller(const DevGraph& G, uint32_t v) { return G.order ? __ldg(G.order + v) : v; }
 
 // {|G_k|, ref} of group k of vertex v
 __device__ __forceinline__ uint2& grp(const DevGraph& G, uint64_t v, uint32_t k) {

@@ -70,8 +70,9 @@ __global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t v = warp; v < G.n; v += nwarps) {
-        const uint64_t a = rp[v];
-        const uint32_t d = (uint32_t)(rp[v + 1] - a);
+        const uint32_t ov = G.order ? G.order[v] : (uint32_t)v;  // the caller's row of internal vertex v
+        const uint64_t a = rp[ov];
+        const uint32_t d = (uint32_t)(rp[ov + 1] - a);
         uint32_t c = 0;  // lane k: |G_k|
         for (uint32_t b = 0; b < d; b += 32) {
             const uint32_t w = (b + lane < d) ? bias[a + b + lane] : 0u;
@@ -112,6 +113,7 @@ __global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const
             h.pad = 0;
             store_hdr(G, v, h);
             if (G.fbits) set_decimal_total(G, v, 0);  // k_build_fill sets it for vertices with edges
+            else G.vh[v].word = G.order ? G.order[v] : (uint32_t)v;  // read by the walker for path entries
         }
     }
 }
@@ -127,7 +129,7 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
     for (uint64_t v = warp; v < G.n; v += nwarps) {
         VHdr h = load_hdr(G, v);
         const uint32_t d = h.deg, capa = capa_of(h), caps = caps_of(h);
-        const uint64_t a = rp[v];
+        const uint64_t a = rp[G.order ? G.order[v] : (uint32_t)v];  // edge ids stay the caller's CSR positions
         uint64_t next = base + offs[v];
         const uint32_t c = cnt_ref(G, v, lane);
         const uint32_t kd = kind_of(c, d, G.alpha, G.beta);
@@ -140,7 +142,7 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
             uint2* pairs = adj_pairs(G, h.adj);
             uint64_t* eids = adj_eids(G, h.adj, capa);
             for (uint32_t j = lane; j < d; j += 32) {
-                pairs[j] = make_uint2(col[a + j], bias[a + j]);
+                pairs[j] = make_uint2(G.perm ? G.perm[col[a + j]] : col[a + j], bias[a + j]);
                 eids[j] = a + j;
             }
             next += 4ull * capa;
@@ -191,6 +193,29 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
     }
 }
 
+// ---- internal numbering ----------------------------------------------------------------------------------
+
+// BINGO_ORDER_AUTO renumbers graphs up to 2^23 vertices: the order table (4 bytes a vertex, read once
+// per walk step to translate the path entry) then takes at most a quarter of L2.
+constexpr uint32_t ORDER_AUTO_MAX_N = 1u << 23;
+
+// Sort keys of the degree numbering: a stable ascending sort of (2^32 - 1 - out-degree) orders the
+// vertices by descending out-degree, ties by the caller's id.
+__global__ void k_order_keys(uint32_t n, const uint64_t* __restrict__ rp, uint64_t* __restrict__ keys,
+                             uint32_t* __restrict__ vals) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = tid; v < n; v += nt) {
+        const uint64_t d = rp[v + 1] - rp[v];
+        keys[v] = 0xFFFFFFFFull - (d < 0xFFFFFFFFull ? d : 0xFFFFFFFFull);
+        vals[v] = (uint32_t)v;
+    }
+}
+
+__global__ void k_order_perm(uint32_t n, const uint32_t* __restrict__ order, uint32_t* __restrict__ perm) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = tid; i < n; i += nt) perm[order[i]] = (uint32_t)i;
+}
+
 // ---- export ----------------------------------------------------------------------------------------------
 
 __global__ void k_export_sizes(DevGraph G, uint64_t* __restrict__ deg64, uint64_t* __restrict__ glen64,
@@ -198,14 +223,15 @@ __global__ void k_export_sizes(DevGraph G, uint64_t* __restrict__ deg64, uint64_
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t v = warp; v < G.n; v += nwarps) {
+    for (uint64_t ve = warp; ve < G.n; ve += nwarps) {  // the caller's vertex order
+        const uint64_t v = G.perm ? G.perm[ve] : ve;
         const VHdr h = load_hdr(G, v);
         const uint32_t c = cnt_ref(G, v, lane);
         const uint32_t kd = slot_kind(G, c, h.deg, lane);
-        glen64[v * 32 + lane] = is_list(kd) ? c : 0;
+        glen64[ve * 32 + lane] = is_list(kd) ? c : 0;
         if (lane == 0) {
-            deg64[v] = h.deg;
-            nsp64[v] = h.sref ? h.nsp : 0;
+            deg64[ve] = h.deg;
+            nsp64[ve] = h.sref ? h.nsp : 0;
         }
     }
 }
@@ -220,7 +246,8 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t v = warp; v < G.n; v += nwarps) {
+    for (uint64_t ve = warp; ve < G.n; ve += nwarps) {  // the caller's vertex order and ids
+        const uint64_t v = G.perm ? G.perm[ve] : ve;
         const VHdr h = load_hdr(G, v);
         const uint32_t d = h.deg, capa = capa_of(h), caps = caps_of(h);
         if (d) {
@@ -228,16 +255,16 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
             const uint64_t* eids = adj_eids(G, h.adj, capa);
             for (uint32_t j = lane; j < d; j += 32) {
                 const uint2 e = pairs[j];
-                odst[eoff[v] + j] = e.x;
-                obias[eoff[v] + j] = G.base4 ? b4_value(e.y) : e.y;
-                oeid[eoff[v] + j] = eids[j];
+                odst[eoff[ve] + j] = G.order ? G.order[e.x] : e.x;
+                obias[eoff[ve] + j] = G.base4 ? b4_value(e.y) : e.y;
+                oeid[eoff[ve] + j] = eids[j];
             }
         }
         const uint32_t c = cnt_ref(G, v, lane);
         const uint32_t kd = slot_kind(G, c, d, lane);
         const uint32_t gr = gref_ref(G, v, lane);
-        okind[v * 32 + lane] = (uint8_t)kd;
-        ocnt[v * 32 + lane] = c;
+        okind[ve * 32 + lane] = (uint8_t)kd;
+        ocnt[ve * 32 + lane] = c;
         uint32_t one_slot = NONE32;
         if (kd == K_ONE) {  // the stored reference is the destination; locate the member's slot
             const uint2* pairs = adj_pairs(G, h.adj);
@@ -245,7 +272,7 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
                 if ((pairs[j].y >> lane) & 1u) { one_slot = j; break; }
             if (one_slot == NONE32 || pairs[one_slot].x != gr) atomicAdd(bad, 1ull);
         }
-        oone[v * 32 + lane] = one_slot;
+        oone[ve * 32 + lane] = one_slot;
         const uint32_t listm = __ballot_sync(FULL, is_list(kd));
         for (uint32_t m = listm; m; m &= m - 1) {
             const uint32_t k = __ffs(m) - 1;
@@ -256,7 +283,7 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
             const uint32_t* mdst = G.pool.base + g;
             const uint32_t* mem = mdst + icap;
             const uint32_t* inv = mem + icap;
-            const uint64_t o = goff[v * 32 + k];
+            const uint64_t o = goff[ve * 32 + k];
             const uint2* pairs = adj_pairs(G, h.adj);
             const uint32_t* S = h.sref ? G.pool.base + h.sref : nullptr;
             for (uint32_t i = lane; i < ck; i += 32) {
@@ -274,8 +301,8 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
             const uint32_t* Sinv = S + capa;
             for (uint32_t i = lane; i < h.nsp; i += 32) {
                 const uint32_t x = S[i];
-                osp[soff[v] + i] = x;
-                ospinv[soff[v] + i] = x < capa ? Sinv[x] : NONE32;
+                osp[soff[ve] + i] = x;
+                ospinv[soff[ve] + i] = x < capa ? Sinv[x] : NONE32;
             }
         }
     }
@@ -287,20 +314,21 @@ __global__ void k_export_dec(DevGraph G, const uint64_t* __restrict__ eoff, uint
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t v = warp; v < G.n; v += nwarps) {
+    for (uint64_t ve = warp; ve < G.n; ve += nwarps) {
+        const uint64_t v = G.perm ? G.perm[ve] : ve;
         const VHdr h = load_hdr(G, v);
         const uint32_t ref = gref_ref(G, v, DEC_SLOT);
         uint32_t qs = 0;
         if (h.deg && ref) {
             const uint8_t* qb = dec_bytes(G, ref);
             for (uint32_t j = lane; j < h.deg; j += 32) {
-                oq[eoff[v] + j] = qb[j];
+                oq[eoff[ve] + j] = qb[j];
                 qs += qb[j];
             }
         }
         qs = __reduce_add_sync(FULL, qs);
         const bool flag = ((h.mask >> DEC_SLOT) & 1u) != (qs != 0);
-        const bool hot = G.vh[v].sref != qs;
+        const bool hot = G.vh[v].word != qs;
         if (lane == 0 && (qs != cnt_ref(G, v, DEC_SLOT) || flag || hot || (h.deg && !ref))) atomicAdd(bad, 1ull);
     }
 }
@@ -343,7 +371,7 @@ static void free_graph(bingo_graph* g) {
     if (!g) return;
     if (g->upd_graph) cudaGraphExecDestroy(g->upd_graph);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
-    void* ptrs[] = {g->d_hdr, g->d_cold, g->d_pool, g->d_ctl, g->d_fcount, g->d_fstack, g->d_pending, g->d_eh};
+    void* ptrs[] = {g->d_hdr, g->d_cold, g->d_order, g->d_perm, g->d_pool, g->d_ctl, g->d_fcount, g->d_fstack, g->d_pending, g->d_eh};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     Buf* bufs[] = {&g->s_in, &g->s_keys, &g->s_keys2, &g->s_vals, &g->s_vals2, &g->s_tmp, &g->s_seg,
@@ -397,6 +425,10 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
     const bool real = c.bias_format == BINGO_BIAS_F32;
     if (c.bias_format > BINGO_BIAS_F32 || (real && !(c.lambda > 0.0 && c.lambda < 1e300))) {
         set_error("invalid bias format %u / lambda %g", c.bias_format, c.lambda);
+        return BINGO_E_INVALID;
+    }
+    if (c.vertex_order > BINGO_ORDER_DEGREE) {
+        set_error("invalid vertex order %u", c.vertex_order);
         return BINGO_E_INVALID;
     }
     if (c.radix_base == 0) c.radix_base = 2;
@@ -475,8 +507,34 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
     G.pool.npending = (unsigned long long*)(ctl + CTL_NPENDING);
     G.pool.leaked = (unsigned long long*)(ctl + CTL_LEAKED);
 
+    G.order = nullptr;
+    G.perm = nullptr;
     Buf words, offs, tot;
     auto release_all = [&]() { release(words); release(offs); release(tot); release_stage(); };
+    if (n >= 1 && (c.vertex_order == BINGO_ORDER_DEGREE ||
+                   (c.vertex_order == BINGO_ORDER_AUTO && n >= 2 && n <= ORDER_AUTO_MAX_N))) {
+        // internal numbering by descending out-degree (read from row_ptr, which validation accepted)
+        Buf k1, k2, v2;
+        auto release_sort = [&]() { release(k1); release(k2); release(v2); };
+        if (!cu(cudaMalloc(&g->d_order, sizeof(uint32_t) * (size_t)n), "vertex order") ||
+            !cu(cudaMalloc(&g->d_perm, sizeof(uint32_t) * (size_t)n), "vertex permutation") ||
+            !cu(ensure(k1, sizeof(uint64_t) * n), "order keys") || !cu(ensure(k2, sizeof(uint64_t) * n), "order keys") ||
+            !cu(ensure(v2, sizeof(uint32_t) * n), "order values")) { release_sort(); release_all(); return fail(st); }
+        k_order_keys<<<grid_for(g, n, 256), 256, 0, s>>>(n, rp, (uint64_t*)k1.p, (uint32_t*)g->d_order);
+        g->launches++;
+        bool alt = false;
+        if (!cu(radix_sort_pairs((uint64_t*)k1.p, (uint32_t*)g->d_order, (uint64_t*)k2.p, (uint32_t*)v2.p, n, 32,
+                                 g->s_tmp, s, &alt, &g->launches), "vertex order sort") ||
+            (alt && !cu(cudaMemcpyAsync(g->d_order, v2.p, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s),
+                        "vertex order copy"))) { release_sort(); release_all(); return fail(st); }
+        k_order_perm<<<grid_for(g, n, 256), 256, 0, s>>>(n, (const uint32_t*)g->d_order, (uint32_t*)g->d_perm);
+        g->launches++;
+        if (!cu(cudaStreamSynchronize(s), "vertex order")) { release_sort(); release_all(); return fail(st); }
+        release_sort();
+        G.order = (const uint32_t*)g->d_order;
+        G.perm = (const uint32_t*)g->d_perm;
+    }
+    g->cfg.vertex_order = G.order ? BINGO_ORDER_DEGREE : BINGO_ORDER_CALLER;
     if (!cu(ensure(words, sizeof(uint64_t) * n), "build words") || !cu(ensure(offs, sizeof(uint64_t) * n), "build offsets") ||
         !cu(ensure(tot, 64), "build total")) { release_all(); return fail(st); }
     const unsigned wblocks = grid_for(g, (uint64_t)n * 32, 256);

@@ -796,7 +796,10 @@ struct BatchArgs {
     uint64_t* packed;     // per record: nkeys (low 32) | is_insert (high 32)
     uint64_t* pscan;      // exclusive scan of packed
     uint32_t* status;
+    const uint32_t* perm; // caller -> internal vertex ids, or null (identity)
 };
+
+__device__ __forceinline__ uint32_t batch_id(const BatchArgs& A, uint32_t v) { return A.perm ? __ldg(A.perm + v) : v; }
 
 __device__ __forceinline__ uint64_t live_count(const BatchArgs& A) { return A.count_dev ? *A.count_dev : A.count; }
 
@@ -831,14 +834,14 @@ __global__ void k_make_keys(BatchArgs A) {
         const uint4 u = A.ups[i];
         if (u.x >= A.n || u.y >= A.n || u.w > 2) continue;
         uint64_t pos = A.pscan[i] & 0xFFFFFFFFull;
-        const uint64_t sk = (uint64_t)u.x << (A.bn + 1);
+        const uint64_t sk = (uint64_t)batch_id(A, u.x) << (A.bn + 1);
         if (u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS) {
             A.keys[pos] = sk;
             A.vals[pos] = (uint32_t)i;
             pos++;
         }
         if (u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS) {
-            A.keys[pos] = sk | (1ull << A.bn) | u.y;
+            A.keys[pos] = sk | (1ull << A.bn) | batch_id(A, u.y);
             A.vals[pos] = (uint32_t)i;
         }
     }
@@ -852,8 +855,8 @@ __global__ void k_key_count(const uint64_t* total, uint64_t* nkeys) { *nkeys = *
 __global__ void k_seg_flags(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t cap,
                             const uint64_t* __restrict__ nkeys_dev, uint32_t bn, const uint4* __restrict__ ups,
                             const uint64_t* __restrict__ pscan, const unsigned long long* __restrict__ eid_base,
-                            uint32_t fbits, double lambda, uint32_t base4, uint64_t* __restrict__ flag,
-                            uint4* __restrict__ rec) {
+                            uint32_t fbits, double lambda, uint32_t base4, const uint32_t* __restrict__ perm,
+                            uint64_t* __restrict__ flag, uint4* __restrict__ rec) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t nkeys = nkeys_dev ? *nkeys_dev : cap;
     for (uint64_t i = tid; i < cap; i += nt) {
@@ -867,7 +870,7 @@ __global__ void k_seg_flags(const uint64_t* __restrict__ keys, const uint32_t* _
             uint32_t I = u.z, q = 0;
             if (fbits) split_real_bias(u.z, lambda, I, q);
             if (base4) I = b4_mask(u.z);
-            rec[i] = make_uint4((uint32_t)eid, u.y, I, ((uint32_t)(eid >> 32) & 0xFFFFFFu) | (q << 24));
+            rec[i] = make_uint4((uint32_t)eid, perm ? perm[u.y] : u.y, I, ((uint32_t)(eid >> 32) & 0xFFFFFFu) | (q << 24));
         }
     }
 }
@@ -1185,7 +1188,7 @@ __global__ void k_eh_apply(DevGraph G, SegArgs S, uint64_t cap, const uint64_t* 
         const uint32_t src = (uint32_t)(key >> (S.B.bn + 1));
         const uint4 u = S.B.ups[S.sorted_vals[i]];
         if (del && S.slot_scratch[i] == NONE32) continue;
-        const unsigned long long k = ((unsigned long long)src << 32) | u.y;
+        const unsigned long long k = ((unsigned long long)src << 32) | to_internal(G, u.y);
         uint64_t p = eh_hash(k) & G.eh_mask;
         for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
             if (!del) {
@@ -1246,7 +1249,9 @@ __global__ void __launch_bounds__(STREAM_TEAMS * 32) k_stream_apply(DevGraph G, 
         for (uint32_t r = a; r < b; r++) {
             if (*G.pool.status & ST_STOP) return;
             const uint32_t rec = S.sorted_vals[r];
-            const uint4 u = S.B.ups[rec];
+            uint4 u = S.B.ups[rec];
+            u.x = to_internal(G, u.x);
+            u.y = to_internal(G, u.y);
             const uint32_t ni = (u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
             const uint32_t nd = (u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
             // reserve this record's worst-case pool growth so no allocation inside it can fail
@@ -1453,6 +1458,7 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     A.packed = (uint64_t*)g->s_rank.p;
     A.pscan = A.packed + cap;
     A.status = (uint32_t*)(ctl + CTL_STATUS);
+    A.perm = g->G.perm;
     uint64_t* total = (uint64_t*)(ctl + CTL_SCR + 4);  // low 32 bits: key count; high: insertions
     uint64_t* nkeys_dev = (uint64_t*)(ctl + CTL_SCR + 10);
     k_expand<<<grid_cap(g, cap, 256), 256, 0, s>>>(A);
@@ -1475,7 +1481,7 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
     k_seg_flags<<<grid_cap(g, kc, 256), 256, 0, s>>>(skeys, svals, kc, nkeys_dev, A.bn, A.ups, A.pscan,
                                                      (const unsigned long long*)(ctl + CTL_SCR + 9), A.fbits,
-                                                     A.lambda, g->G.base4, flag, (uint4*)g->s_rec.p);
+                                                     A.lambda, g->G.base4, A.perm, flag, (uint4*)g->s_rec.p);
     CK(scan_excl_u64(flag, segid, kc, nseg_dev, g->s_tmp, s, &g->launches), "segment scan");
     k_seg_write<<<grid_cap(g, kc, 256), 256, 0, s>>>(flag, segid, kc, nkeys_dev, seg_start);
     g->launches += 2;
@@ -1626,6 +1632,7 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     A.packed = (uint64_t*)g->s_rank.p;
     A.pscan = A.packed + count;
     A.status = (uint32_t*)(ctl + CTL_STATUS);
+    A.perm = g->G.perm;
     uint64_t* total = (uint64_t*)(ctl + CTL_SCR + 4);
     k_expand<<<grid_cap(g, count, 256), 256, 0, s>>>(A);  // validation + insertion flags
     CK(scan_excl_u64(A.packed, A.pscan, count, total, g->s_tmp, s, &g->launches), "stream scan");
@@ -1642,7 +1649,7 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     uint32_t* seg_start = (uint32_t*)(segid + count);
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
     k_seg_flags<<<grid_cap(g, count, 256), 256, 0, s>>>(skeys, svals, count, nullptr, A.bn, A.ups, A.pscan, nullptr,
-                                                        0u, 0.0, 0u, flag, nullptr);
+                                                        0u, 0.0, 0u, nullptr, flag, nullptr);
     CK(scan_excl_u64(flag, segid, count, nseg_dev, g->s_tmp, s, &g->launches), "stream segments");
     k_seg_write<<<grid_cap(g, count, 256), 256, 0, s>>>(flag, segid, count, nullptr, seg_start);
     SegArgs S;

@@ -91,7 +91,8 @@ __device__ __forceinline__ uint4 ld_hot(const uint4* q) {
 
 // Hot part of a vertex record: the header and groups 0-5 (pairs 0-2), one 64-byte line.
 struct Sec0 {
-    uint32_t adj, deg, mask, sref;
+    uint32_t adj, deg, mask;
+    uint32_t word;  // real-bias graphs: the decimal total Q_D; otherwise the caller's id of the vertex
     uint4 p0, p1, p2;
 };
 __device__ __forceinline__ Sec0 ld_sec0(const DevGraph& G, uint32_t v) {
@@ -101,7 +102,7 @@ __device__ __forceinline__ Sec0 ld_sec0(const DevGraph& G, uint32_t v) {
     s.adj = a.x;
     s.deg = a.y;
     s.mask = a.z;
-    s.sref = a.w;
+    s.word = a.w;
     s.p0 = ld_hot(q + 1);
     s.p1 = ld_hot(q + 2);
     s.p2 = ld_hot(q + 3);
@@ -139,7 +140,7 @@ __device__ __forceinline__ bool scan_pair(uint4 x, uint32_t i, uint64_t r, uint6
 // T = 1: one lane per walker.  Pairs 0-2 came with the header; the cold pairs 3..15 are read in
 // batches of four whose loads are issued together (predicated on the mask), keeping per-batch
 // sums; the batch holding k* is re-read (L1 hits) to find the group.
-// Real-bias graphs: the decimal total Q_D comes with the hot line (Sec0.sref), so for the totals pair
+// Real-bias graphs: the decimal total Q_D comes with the hot line (Sec0.word), so for the totals pair
 // 15 is read only for group 30 (its slot-31 half taken as empty) and Q_D is added to the last batch;
 // pair 15 is read whole only when r falls in that batch.
 template <int WM>
@@ -171,7 +172,7 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
 #pragma unroll
             for (int j = 0; j < 4; j++) part[b] += pair_w<WM>(x[j], 3 + 4 * b + j);
         }
-        if (REAL && b == 3) part[b] += h.sref;  // decimal total, slot 31 of pair 15
+        if (REAL && b == 3) part[b] += h.word;  // decimal total, slot 31 of pair 15
         tot += part[b];
     }
     const uint64_t r = below64(R, tot, status);
@@ -332,7 +333,7 @@ __device__ __forceinline__ uint32_t pick_member(const DevGraph& G, const Sec0& h
 template <int T, int WM>
 __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A, uint64_t wid, uint32_t pid,
                                           uint32_t step, uint32_t& cur, uint32_t& prev, uint32_t tl,
-                                          uint32_t team_mask, uint32_t team_base, uint32_t lane) {
+                                          uint32_t team_mask, uint32_t team_base, uint32_t lane, uint32_t& hword) {
     const bingo_policy* P = A.pols + pid;
     const uint32_t kind = __ldg(&P->kind);
     StepRng R;
@@ -342,8 +343,10 @@ __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A
         walker_stream(A, wid, pid, key, lid);
         R.init(key, lid, step);
     }
+    hword = NONE32;
     if (kind == BINGO_PPR && R.next() < __ldg(&P->ppr_stop_u32)) return false;
     const Sec0 h = ld_sec0(G, cur);
+    hword = h.word;
     if (h.deg == 0) return false;
     for (int attempt = 0; attempt < MAX_N2V_TRIES; attempt++) {
         uint32_t ks, cs, ref;
@@ -386,6 +389,17 @@ __device__ __forceinline__ void finish_walker(const WalkParams& A, uint64_t wid,
         for (uint32_t t = steps + 1 + tl; t < A.stride; t += T) row[t] = NONE32;
 }
 
+// 4-byte asynchronous copy from global to shared memory: no register waits for the value.
+__device__ __forceinline__ void async_id_fetch(uint32_t sh, const uint32_t* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sh), "l"(src) : "memory");
+}
+// Waits for this thread's copies, then reads the word.
+__device__ __forceinline__ uint32_t async_id_take(uint32_t sh) {
+    uint32_t v;
+    asm volatile("cp.async.wait_all;\n\tld.shared.u32 %0, [%1];" : "=r"(v) : "r"(sh) : "memory");
+    return v;
+}
+
 // OCC selects the register budget: 0 = up to 64 registers (1,024-thread bound), 1 = 40 registers
 // (256-thread blocks, six per SM), trading spills to L1 for 50% more resident warps.
 // WM: the graph's weight mode; each mode runs its own instance (integer graphs carry no code for the
@@ -397,6 +411,12 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
     const uint32_t team_mask = (T == 32) ? FULL : (((1u << T) - 1u) << team_base);
     uint64_t wid = 0;
     uint32_t pid = 0, cur = 0, prev = NONE32, step = 0, L = 0;
+    // Real-bias graphs (whose hot word is the decimal total) under an internal numbering: the
+    // caller's id of each vertex reached is fetched by an asynchronous copy into this thread's
+    // shared-memory word and stored to the path one step later, so the translation overlaps the
+    // next step instead of stalling the warp.
+    __shared__ uint32_t path_id[OCC ? 256 : 1024];
+    const uint32_t path_sh = (uint32_t)__cvta_generic_to_shared(path_id + threadIdx.x);
     bool have = false, drained = false;
     for (;;) {
         if (!drained) {
@@ -422,6 +442,7 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
                     step = 0;
                     have = true;
                     if (tl == 0) A.paths[wid * (uint64_t)A.stride] = cur;
+                    cur = to_internal(G, cur);
                     if (L == 0) {
                         finish_walker(A, wid, 0, tl, T);
                         have = false;
@@ -434,10 +455,30 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
             continue;
         }
         if (have) {
-            const bool took = walk_step<T, WM>(G, A, wid, pid, step, cur, prev, tl, team_mask, team_base, lane);
-            if (took) {
+            uint32_t hword;
+            const bool took = walk_step<T, WM>(G, A, wid, pid, step, cur, prev, tl, team_mask, team_base, lane, hword);
+            uint32_t* row = A.paths + wid * (uint64_t)A.stride;
+            if constexpr (WM != WM_REAL) {
+                // Path entry `step` is the vertex this step started from, whose hot line carries the
+                // caller's id; it is read there (no extra load) except when the walk stopped before
+                // reading it, and for the last vertex of a walk.
+                if (step && tl == 0) row[step] = hword != NONE32 ? hword : to_caller(G, cur);
+                if (took) {
+                    step++;
+                    if (step == L && tl == 0) row[step] = to_caller(G, cur);
+                }
+            } else if (G.order) {
+                if (step && tl == 0) row[step] = async_id_take(path_sh);  // the id fetched last step
+                if (took) {
+                    step++;
+                    if (tl == 0) {
+                        async_id_fetch(path_sh, G.order + cur);
+                        if (step == L) row[step] = async_id_take(path_sh);
+                    }
+                }
+            } else if (took) {
                 step++;
-                if (tl == 0) A.paths[wid * (uint64_t)A.stride + step] = cur;
+                if (tl == 0) row[step] = cur;
             }
             if (!took || step == L) {
                 finish_walker(A, wid, step, tl, T);
@@ -462,6 +503,7 @@ __global__ void k_walk_step(DevGraph G, WalkParams A, uint32_t s) {
             prev = NONE32;
             if (cur >= G.n) { L = 0; atomicOr(A.status, ST_INVALID); }
             A.paths[wid * (uint64_t)A.stride] = cur;
+            cur = to_internal(G, cur);
             if (L == 0) {
                 finish_walker(A, wid, 0, 0, 1);
                 A.s_cur[wid] = NONE32;
@@ -472,8 +514,9 @@ __global__ void k_walk_step(DevGraph G, WalkParams A, uint32_t s) {
             if (cur == NONE32) continue;
             prev = A.s_prev[wid];
         }
-        const bool took = walk_step<1, WM>(G, A, wid, pid, s, cur, prev, 0, 0, 0, 0);
-        if (took) A.paths[wid * (uint64_t)A.stride + s + 1] = cur;
+        uint32_t hword;
+        const bool took = walk_step<1, WM>(G, A, wid, pid, s, cur, prev, 0, 0, 0, 0, hword);
+        if (took) A.paths[wid * (uint64_t)A.stride + s + 1] = to_caller(G, cur);
         if (!took || s + 1 == L) {
             finish_walker(A, wid, took ? s + 1 : s, 0, 1);
             A.s_cur[wid] = NONE32;
