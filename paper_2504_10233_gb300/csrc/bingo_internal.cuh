@@ -1,12 +1,12 @@
 // Internal device structures and primitives of the radix-factorised sampler.
 //
 // Device state of a graph (all in HBM):
-//   vh[v]   VHot, 64 bytes: header {adjacency block, degree d, nonempty-group mask, sparse-list
-//           block (real-bias graphs: the decimal total Q_D, the sparse-list block moving to the
-//           cold part)} and groups 0-5 as {|G_k|, ref} (Eq. wpk: W(p_k) = 2^k |G_k|); ref = destination of
-//           the member of a one-element group, or the group block of a regular/sparse group, else 0.
-//           The hot array is n x 64 B, small enough to stay largely in L2.
-//   vc[v]   VCold, 224 bytes: groups 6-31 and the update-only fields (|S|, log2 capacities).
+//   vh[v]   VHot, 64 bytes: header {adjacency block, degree d, nonempty-group mask, the caller's id
+//           of v (path entries)} and groups 0-5 as {|G_k|, ref} (Eq. wpk: W(p_k) = 2^k |G_k|); ref =
+//           destination of the member of a one-element group, or the group block of a regular/sparse
+//           group, else 0.  The hot array is n x 64 B, small enough to stay largely in L2.
+//   vc[v]   VCold, 256 bytes: one sector {the total weight of groups 6-31, the update-only fields
+//           (|S|, log2 capacities, sparse-list block)}, then groups 6-31.
 //   pool    u32 words holding every variable-size block, in power-of-two sizes (offsets stored in
 //           32-byte units):
 //             adjacency   4*capA words: capA x {dst, bias} (8 B, AoS) then capA x u64 edge id
@@ -24,6 +24,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "bingo.h"
@@ -65,19 +66,22 @@ struct __align__(64) VHot {
     uint32_t adj;   // adjacency block, 32-byte units
     uint32_t deg;
     uint32_t mask;
-    uint32_t word;  // real-bias graphs: the decimal total Q_D; otherwise the caller's id of this vertex
+    uint32_t word;  // the caller's id of this vertex (path entries of walks)
     uint2 g[HOT_GROUPS];
 };
 struct __align__(32) VCold {
-    uint2 g[32 - HOT_GROUPS];
+    uint64_t wcold;      // sum of the weights of groups 6-31: with the hot groups, the vertex total
     uint32_t nsp;
     uint8_t lcapa, lcaps;
     uint16_t pad;
     uint32_t sref;       // sparse-list block, 32-byte units
-    uint32_t spare1;
+    uint32_t spare[3];
+    uint2 g[32 - HOT_GROUPS];
+    uint32_t tail[4];
 };
 static_assert(sizeof(VHot) == 64, "VHot must be two sectors");
-static_assert(sizeof(VCold) == 224, "VCold must be seven sectors");
+static_assert(sizeof(VCold) == 256, "VCold must be eight sectors");
+static_assert(offsetof(VCold, g) == 32, "cold groups start at the second sector");
 
 constexpr uint64_t POOL_UNIT_WORDS = 8;  // offsets are stored in 32-byte units
 constexpr uint64_t MAX_POOL_WORDS = (1ull << 32) * POOL_UNIT_WORDS;
@@ -189,6 +193,7 @@ struct DevGraph {
     // internal vertex i, perm[v] = internal id of the caller's vertex v; both null = identity.
     const uint32_t* order;
     const uint32_t* perm;
+
     VHot* vh;
     VCold* vc;
     Pool pool;
@@ -220,14 +225,12 @@ __device__ __forceinline__ void store_hdr(const DevGraph& G, uint64_t v, const V
     a.adj = ref_of(h.adj);
     a.deg = h.deg;
     a.mask = h.mask;
-    b.sref = ref_of(h.sref);  // the hot word is set once at build (caller's id) or by set_decimal_total
+    b.sref = ref_of(h.sref);  // the hot word (caller's id) is set once, at build
     b.nsp = h.nsp;
     b.lcapa = h.lcapa;
     b.lcaps = h.lcaps;
     b.pad = 0;
 }
-// Real-bias graphs: the decimal total lives in group slot 31 and, for the walker, in the hot line.
-__device__ __forceinline__ void set_decimal_total(const DevGraph& G, uint64_t v, uint32_t qd) { G.vh[v].word = qd; }
 
 // ids at or above n pass through unchanged (callers reject them)
 __device__ __forceinline__ uint32_t to_internal(const DevGraph& G, uint32_t v) {
@@ -280,6 +283,16 @@ template <int WM>
 __device__ __forceinline__ uint64_t slot_weight(uint32_t c, uint32_t k) {
     if constexpr (WM == WM_B4) return (uint64_t)c * ((uint64_t)(k % 3 + 1) << (2 * (k / 3)));
     else return slot_w(c, k, WM == WM_REAL ? FRAC_BITS : 0u);
+}
+// The graph's slot weight, its weight mode taken at run time (update and build kernels).
+__device__ __forceinline__ uint64_t graph_slot_weight(const DevGraph& G, uint32_t c, uint32_t k) {
+    return G.base4 ? slot_weight<WM_B4>(c, k) : slot_w(c, k, G.fbits);
+}
+// VCold.wcold of a vertex from its 32 slot counts.
+__device__ __forceinline__ uint64_t cold_total(const DevGraph& G, const uint32_t* cnt) {
+    uint64_t w = 0;
+    for (uint32_t k = HOT_GROUPS; k < 32; k++) w += graph_slot_weight(G, cnt[k], k);
+    return w;
 }
 // ---- radix base 4 (Appendix): sub-group (digit position i, value v) is slot 3 i + v - 1.
 constexpr uint32_t B4_POSITIONS = 10;  // biases below 4^10 = 2^20: slots 0..29

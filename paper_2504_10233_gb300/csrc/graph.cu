@@ -112,8 +112,7 @@ __global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const
             h.lcaps = caps ? (uint8_t)(log2_u32(caps) + 1) : 0;
             h.pad = 0;
             store_hdr(G, v, h);
-            if (G.fbits) set_decimal_total(G, v, 0);  // k_build_fill sets it for vertices with edges
-            else G.vh[v].word = G.order ? G.order[v] : (uint32_t)v;  // read by the walker for path entries
+            G.vh[v].word = G.order ? G.order[v] : (uint32_t)v;  // read by the walker for path entries
         }
     }
 }
@@ -156,10 +155,7 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
                 qs = __reduce_add_sync(FULL, qs);
                 if (lane == DEC_SLOT) gref = ref_of(next);
                 if (qs) h.mask |= 1u << DEC_SLOT;
-                if (lane == 0) {
-                    cnt_ref(G, v, DEC_SLOT) = qs;
-                    set_decimal_total(G, v, qs);
-                }
+                if (lane == 0) cnt_ref(G, v, DEC_SLOT) = qs;
                 next += dec_words(capa);
             }
         }
@@ -189,14 +185,21 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
         }
         gref_ref(G, v, lane) = gref;
         __syncwarp();
-        if (lane == 0) store_hdr(G, v, h);
+        // total weight of the cold groups (the decimal slot's count was written above)
+        uint64_t wc = lane >= HOT_GROUPS ? graph_slot_weight(G, cnt_ref(G, v, lane), lane) : 0ull;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(FULL, wc, o);
+        if (lane == 0) {
+            store_hdr(G, v, h);
+            G.vc[v].wcold = wc;
+        }
     }
 }
 
 // ---- internal numbering ----------------------------------------------------------------------------------
 
-// BINGO_ORDER_AUTO renumbers graphs up to 2^23 vertices: the order table (4 bytes a vertex, read once
-// per walk step to translate the path entry) then takes at most a quarter of L2.
+// BINGO_ORDER_AUTO renumbers graphs up to 2^23 vertices: the order table (4 bytes a vertex, read
+// to translate walk starts and last vertices) then takes at most a quarter of L2.
 constexpr uint32_t ORDER_AUTO_MAX_N = 1u << 23;
 
 // Sort keys of the degree numbering: a stable ascending sort of (2^32 - 1 - out-degree) orders the
@@ -263,6 +266,11 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
         const uint32_t c = cnt_ref(G, v, lane);
         const uint32_t kd = slot_kind(G, c, d, lane);
         const uint32_t gr = gref_ref(G, v, lane);
+        // the walker's cached cold total and the caller's id in the hot line
+        uint64_t wc = lane >= HOT_GROUPS ? graph_slot_weight(G, c, lane) : 0ull;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(FULL, wc, o);
+        if (lane == 0 && (wc != G.vc[v].wcold || G.vh[v].word != (uint32_t)ve)) atomicAdd(bad, 1ull);
         okind[ve * 32 + lane] = (uint8_t)kd;
         ocnt[ve * 32 + lane] = c;
         uint32_t one_slot = NONE32;
@@ -328,8 +336,7 @@ __global__ void k_export_dec(DevGraph G, const uint64_t* __restrict__ eoff, uint
         }
         qs = __reduce_add_sync(FULL, qs);
         const bool flag = ((h.mask >> DEC_SLOT) & 1u) != (qs != 0);
-        const bool hot = G.vh[v].word != qs;
-        if (lane == 0 && (qs != cnt_ref(G, v, DEC_SLOT) || flag || hot || (h.deg && !ref))) atomicAdd(bad, 1ull);
+        if (lane == 0 && (qs != cnt_ref(G, v, DEC_SLOT) || flag || (h.deg && !ref))) atomicAdd(bad, 1ull);
     }
 }
 

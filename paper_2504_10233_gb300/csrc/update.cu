@@ -753,9 +753,8 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     for (uint32_t k = rank; k < 32; k += T) {
         grp(G, v, k) = make_uint2(sh.cnt_new[k], (uint32_t)sh.gref_new[k]);
     }
-    if constexpr (REAL)
-        if (rank == 0) set_decimal_total(G, v, sh.cnt_new[DEC_SLOT]);
     if (rank == 0) {
+        G.vc[v].wcold = cold_total(G, sh.cnt_new);
         VHdr h;
         h.adj = adj;
         h.deg = d1;
@@ -893,7 +892,7 @@ __global__ void k_seg_write(const uint64_t* __restrict__ flag, const uint64_t* _
 // The 32 group counts of vertex v, read as whole 16-byte pairs with every load in flight at once.
 __device__ __forceinline__ void load_counts(const DevGraph& G, uint32_t v, uint32_t* cnt) {
     const uint4* hot = reinterpret_cast<const uint4*>(G.vh + v) + 1;
-    const uint4* cold = reinterpret_cast<const uint4*>(G.vc + v);
+    const uint4* cold = reinterpret_cast<const uint4*>(G.vc[v].g);
     uint4 x[16];
 #pragma unroll
     for (int i = 0; i < 16; i++) x[i] = i < (int)HOT_GROUPS / 2 ? hot[i] : cold[i - HOT_GROUPS / 2];

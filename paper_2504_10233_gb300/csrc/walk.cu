@@ -92,7 +92,7 @@ __device__ __forceinline__ uint4 ld_hot(const uint4* q) {
 // Hot part of a vertex record: the header and groups 0-5 (pairs 0-2), one 64-byte line.
 struct Sec0 {
     uint32_t adj, deg, mask;
-    uint32_t word;  // real-bias graphs: the decimal total Q_D; otherwise the caller's id of the vertex
+    uint32_t word;  // the caller's id of the vertex
     uint4 p0, p1, p2;
 };
 __device__ __forceinline__ Sec0 ld_sec0(const DevGraph& G, uint32_t v) {
@@ -111,7 +111,7 @@ __device__ __forceinline__ Sec0 ld_sec0(const DevGraph& G, uint32_t v) {
 // Groups 2i and 2i+1 of vertex v as {c_2i, ref_2i, c_2i+1, ref_2i+1} (16-byte aligned).
 __device__ __forceinline__ uint4 ld_pair(const DevGraph& G, uint32_t v, uint32_t i) {
     if (i < HOT_GROUPS / 2) return ld_hot(reinterpret_cast<const uint4*>(G.vh + v) + 1 + i);
-    return __ldg(reinterpret_cast<const uint4*>(G.vc + v) + (i - HOT_GROUPS / 2));
+    return __ldg(reinterpret_cast<const uint4*>(G.vc[v].g) + (i - HOT_GROUPS / 2));
 }
 // WM: the weight mode (slot_weight): integer base 2, real biases (every integer group counts 2^8
 // times and slot 31, the second half of pair 15, carries the decimal total itself), or base 4.
@@ -137,65 +137,39 @@ __device__ __forceinline__ bool scan_pair(uint4 x, uint32_t i, uint64_t r, uint6
     return false;
 }
 
-// T = 1: one lane per walker.  Pairs 0-2 came with the header; the cold pairs 3..15 are read in
-// batches of four whose loads are issued together (predicated on the mask), keeping per-batch
-// sums; the batch holding k* is re-read (L1 hits) to find the group.
-// Real-bias graphs: the decimal total Q_D comes with the hot line (Sec0.word), so for the totals pair
-// 15 is read only for group 30 (its slot-31 half taken as empty) and Q_D is added to the last batch;
-// pair 15 is read whole only when r falls in that batch.
-template <int WM>
-__device__ __forceinline__ uint4 ld_pair_tot(const DevGraph& G, uint32_t v, uint32_t i) {
-    uint4 x = ld_pair(G, v, i);
-    if (WM == WM_REAL && i == 15) x.z = 0;
-    return x;
-}
-
+// T = 1: one lane per walker.  Pairs 0-2 came with the header and the total weight of groups
+// 6-31 comes from the cold record's first sector (VCold.wcold, read when the mask shows a cold
+// group), so r is drawn without reading the cold groups.  They are read, in batches of four pairs whose loads are issued together
+// (predicated on the mask), only when r falls beyond the hot groups.
 template <int WM>
 __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status) {
-    constexpr bool REAL = WM == WM_REAL;
-    const uint32_t pbf = pair_bits(h.mask);                                  // pairs holding a nonempty slot
-    const uint32_t pb = REAL ? pair_bits(h.mask & ~(1u << DEC_SLOT)) : pbf;  // pairs read for the totals
+    const uint32_t pb = pair_bits(h.mask);  // pairs holding a nonempty slot
     const uint64_t whot = pair_w<WM>(h.p0, 0) + pair_w<WM>(h.p1, 1) + pair_w<WM>(h.p2, 2);
-    uint64_t part[4];
-    uint64_t tot = whot;
-#pragma unroll
-    for (int b = 0; b < 4; b++) {
-        part[b] = 0;
-        if ((pb >> (8 * b + 6)) & 0x55u) {
-            uint4 x[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const uint32_t i = 3 + 4 * b + j;
-                x[j] = (i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair_tot<WM>(G, v, i) : make_uint4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j++) part[b] += pair_w<WM>(x[j], 3 + 4 * b + j);
-        }
-        if (REAL && b == 3) part[b] += h.word;  // decimal total, slot 31 of pair 15
-        tot += part[b];
-    }
-    const uint64_t r = below64(R, tot, status);
+    uint64_t wcold = 0;
+    if (h.mask >> HOT_GROUPS) wcold = __ldg(&G.vc[v].wcold);
+    const uint64_t r = below64(R, whot + wcold, status);
     uint64_t acc = 0;
     if (scan_pair<WM>(h.p0, 0, r, acc, ks, cs, ref)) return;
     if (scan_pair<WM>(h.p1, 1, r, acc, ks, cs, ref)) return;
     if (scan_pair<WM>(h.p2, 2, r, acc, ks, cs, ref)) return;
-    int bs = 3;
+#pragma unroll 1
+    for (uint32_t i0 = 3; i0 < 16; i0 += 4) {
+        if (!((pb >> (2 * i0)) & 0x55u)) continue;
+        uint4 x[4];
 #pragma unroll
-    for (int b = 0; b < 3; b++) {
-        if (bs == 3 && r < acc + part[b]) bs = b;
-        else if (bs == 3) acc += part[b];
+        for (uint32_t j = 0; j < 4; j++) {
+            const uint32_t i = i0 + j;
+            x[j] = (i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair(G, v, i) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < 4; j++)
+            if (scan_pair<WM>(x[j], i0 + j, r, acc, ks, cs, ref)) return;
     }
     ks = 31;
     cs = 0;
     ref = 0;
-    bool found = false;
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        const uint32_t i = 3 + 4 * bs + j;
-        if (!found && i < 16 && ((pbf >> (2 * i)) & 1u)) found = scan_pair<WM>(ld_pair(G, v, i), i, r, acc, ks, cs, ref);
-    }
-    if (!found) atomicOr(status, ST_STATE);
+    atomicOr(status, ST_STATE);  // r beyond every group: the cached total disagrees with the counts
 }
 
 // T = 4: lane t of the team owns pairs [4t, 4t+4) (groups 8t..8t+7); a two-level shuffle prefix
@@ -389,17 +363,6 @@ __device__ __forceinline__ void finish_walker(const WalkParams& A, uint64_t wid,
         for (uint32_t t = steps + 1 + tl; t < A.stride; t += T) row[t] = NONE32;
 }
 
-// 4-byte asynchronous copy from global to shared memory: no register waits for the value.
-__device__ __forceinline__ void async_id_fetch(uint32_t sh, const uint32_t* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sh), "l"(src) : "memory");
-}
-// Waits for this thread's copies, then reads the word.
-__device__ __forceinline__ uint32_t async_id_take(uint32_t sh) {
-    uint32_t v;
-    asm volatile("cp.async.wait_all;\n\tld.shared.u32 %0, [%1];" : "=r"(v) : "r"(sh) : "memory");
-    return v;
-}
-
 // OCC selects the register budget: 0 = up to 64 registers (1,024-thread bound), 1 = 40 registers
 // (256-thread blocks, six per SM), trading spills to L1 for 50% more resident warps.
 // WM: the graph's weight mode; each mode runs its own instance (integer graphs carry no code for the
@@ -411,12 +374,6 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
     const uint32_t team_mask = (T == 32) ? FULL : (((1u << T) - 1u) << team_base);
     uint64_t wid = 0;
     uint32_t pid = 0, cur = 0, prev = NONE32, step = 0, L = 0;
-    // Real-bias graphs (whose hot word is the decimal total) under an internal numbering: the
-    // caller's id of each vertex reached is fetched by an asynchronous copy into this thread's
-    // shared-memory word and stored to the path one step later, so the translation overlaps the
-    // next step instead of stalling the warp.
-    __shared__ uint32_t path_id[OCC ? 256 : 1024];
-    const uint32_t path_sh = (uint32_t)__cvta_generic_to_shared(path_id + threadIdx.x);
     bool have = false, drained = false;
     for (;;) {
         if (!drained) {
@@ -458,27 +415,13 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
             uint32_t hword;
             const bool took = walk_step<T, WM>(G, A, wid, pid, step, cur, prev, tl, team_mask, team_base, lane, hword);
             uint32_t* row = A.paths + wid * (uint64_t)A.stride;
-            if constexpr (WM != WM_REAL) {
-                // Path entry `step` is the vertex this step started from, whose hot line carries the
-                // caller's id; it is read there (no extra load) except when the walk stopped before
-                // reading it, and for the last vertex of a walk.
-                if (step && tl == 0) row[step] = hword != NONE32 ? hword : to_caller(G, cur);
-                if (took) {
-                    step++;
-                    if (step == L && tl == 0) row[step] = to_caller(G, cur);
-                }
-            } else if (G.order) {
-                if (step && tl == 0) row[step] = async_id_take(path_sh);  // the id fetched last step
-                if (took) {
-                    step++;
-                    if (tl == 0) {
-                        async_id_fetch(path_sh, G.order + cur);
-                        if (step == L) row[step] = async_id_take(path_sh);
-                    }
-                }
-            } else if (took) {
+            // Path entry `step` is the vertex this step started from, whose hot line carries the
+            // caller's id; it is read there (no extra load) except when the walk stopped before
+            // reading it, and for the last vertex of a walk.
+            if (step && tl == 0) row[step] = hword != NONE32 ? hword : to_caller(G, cur);
+            if (took) {
                 step++;
-                if (tl == 0) row[step] = cur;
+                if (step == L && tl == 0) row[step] = to_caller(G, cur);
             }
             if (!took || step == L) {
                 finish_walker(A, wid, step, tl, T);
