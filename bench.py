@@ -297,7 +297,7 @@ def run_ours(args):
     mode = B.WALK_PERSISTENT | B.WALK_NO_PAD
     if args.autotune:
         with torch.cuda.stream(stream):
-            g.autotune(starts[: min(nw, 1 << 18)], wl.length, stream=stream)
+            g.autotune(starts, wl.length, stream=stream)  # every walker: the tuned shape fits the whole launch
     seed0 = replica_seed(wl.walk_seed, rank)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -377,6 +377,27 @@ def run_ours(args):
     e2e = {"value": sum_over_ranks(float(e2e_steps), dev) / e2e_t if e2e_t > 0 else None, "unit": "steps/s",
            "h2d_bytes_per_step": int(h_starts.numel() * 4 + h_recs[0].numel() * 4),
            "d2h_bytes_per_step": int(h_paths.numel() * 4 + h_plen.numel() * 4)}
+    if n_e2e:
+        # context for the end-to-end number: one plain device-to-pinned-host copy of the path buffer
+        c0, c1 = ev(), ev()
+        with torch.cuda.stream(stream):
+            c0.record(stream)
+            h_paths.copy_(paths, non_blocking=True)
+            c1.record(stream)
+        torch.cuda.synchronize()
+        e2e["d2h_copy_gbs"] = h_paths.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
+        # the same copy split into four parts on four streams (several copy engines)
+        cs = [torch.cuda.Stream(device=dev) for _ in range(4)]
+        parts = np.linspace(0, nw, 5).astype(int)
+        c0, ends = ev(), [ev() for _ in cs]
+        c0.record(stream)
+        for k, sk in enumerate(cs):
+            sk.wait_event(c0)
+            with torch.cuda.stream(sk):
+                h_paths[parts[k]:parts[k + 1]].copy_(paths[parts[k]:parts[k + 1]], non_blocking=True)
+                ends[k].record(sk)
+        torch.cuda.synchronize()
+        e2e["d2h_copy_gbs_4streams"] = h_paths.numel() * 4 / (max(c0.elapsed_time(x) for x in ends) / 1e3) / 1e9
 
     # streaming: the same kind of records applied as batches of one (Section 4.2), device buffers
     streaming = None

@@ -225,7 +225,13 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
  *   mode        BINGO_WALK_PERSISTENT or BINGO_WALK_STEPWISE
  * A vertex without out-edges ends the walk.  Results depend only on (graph
  * state, seed, walker index) — not on the launch shape or the mode.
- * Asynchronous on `stream` when every pointer is a device pointer.
+ * Asynchronous on `stream` when every pointer is a device pointer.  Any array
+ * may instead be a host pointer: inputs are staged to the device and outputs
+ * copied back, and the call synchronises `stream`.  With host outputs and at
+ * least 2^17 walkers, the persistent form downloads the rows in id-ordered
+ * chunks (at most 32) on a library-owned copy stream while the walk runs: the
+ * walker that completes a chunk flags it in host-mapped memory, and the
+ * calling thread starts that chunk's copy.  Results are the same either way.
  */
 bingo_status bingo_walk(bingo_graph* g, uint64_t nwalkers, const uint32_t* starts, const uint32_t* lengths,
                         const uint8_t* policy_ids, const bingo_policy* policies, uint32_t npolicies, uint64_t seed,

@@ -2,6 +2,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "bingo_host.h"
@@ -41,6 +42,92 @@ bingo_status check_policies(const bingo_policy* pols, uint32_t npol, uint32_t st
             return BINGO_E_INVALID;
         }
         *max_len = std::max(*max_len, p.max_len);
+    }
+    return BINGO_OK;
+}
+
+// Host-output walk whose download overlaps the walk.  The one persistent launch counts finished
+// walkers per id-ordered chunk (walkers are taken from the queue in id order, so chunks finish
+// roughly in order), and the walker that completes a chunk writes this call's sequence number into
+// the chunk's flag in host-mapped pinned memory.  This thread issues each chunk's download as soon
+// as its flag shows, on WALK_IO_STREAMS copy streams in turn, so copies run while later chunks
+// still walk.  Once the kernel has ended (its event completes; every loop in it
+// is bounded) the remaining chunks are downloaded without looking at their flags, so the host never
+// waits on a flag alone.  The caller's stream waits for the last download.
+bingo_status walk_host_io_overlap(bingo_graph* g, WalkReq q, uint32_t* paths, uint32_t* path_len,
+                                  bool host_paths, bool host_plen, cudaStream_t s) {
+    for (int k = 0; k < WALK_IO_STREAMS; k++) {
+        if (!g->io_copy[k]) CK(cudaStreamCreateWithFlags(&g->io_copy[k], cudaStreamNonBlocking), "download stream");
+        if (!g->io_done[k]) CK(cudaEventCreateWithFlags(&g->io_done[k], cudaEventDisableTiming), "walk event");
+    }
+    if (!g->io_kernel) CK(cudaEventCreateWithFlags(&g->io_kernel, cudaEventDisableTiming), "walk event");
+    if (!g->io_flags) {
+        void* h = nullptr;
+        CK(cudaHostAlloc(&h, sizeof(uint32_t) * WALK_IO_MAX_CHUNKS, cudaHostAllocMapped), "chunk flags");
+        memset(h, 0, sizeof(uint32_t) * WALK_IO_MAX_CHUNKS);
+        void* d = nullptr;
+        const cudaError_t e = cudaHostGetDevicePointer(&d, h, 0);
+        if (e != cudaSuccess) { cudaFreeHost(h); return cuda_fail(e, "chunk flags"); }
+        g->io_flags = (volatile uint32_t*)h;
+        g->io_flags_dev = (uint32_t*)d;
+    }
+    const uint64_t n = q.nwalkers, stride = q.stride;
+    uint32_t shift = WALK_IO_MIN_SHIFT;
+    while (((n + (1ull << shift) - 1) >> shift) > WALK_IO_MAX_CHUNKS) shift++;
+    const uint32_t nch = (uint32_t)((n + (1ull << shift) - 1) >> shift);
+    CK(ensure(g->w_chunk_done, sizeof(uint32_t) * WALK_IO_MAX_CHUNKS), "chunk counters");
+    CK(cudaMemsetAsync(g->w_chunk_done.p, 0, sizeof(uint32_t) * nch, s), "chunk counters");
+    if (++g->io_seq == 0) g->io_seq = 1;  // flags hold earlier calls' numbers, never this one's
+    q.chunk_done = (uint32_t*)g->w_chunk_done.p;
+    q.host_flags = g->io_flags_dev;
+    q.chunk_shift = shift;
+    q.io_seq = g->io_seq;
+    bingo_status st = walk_launch(g, q, s);
+    if (st != BINGO_OK) return st;
+    CK(cudaEventRecord(g->io_kernel, s), "walk event");
+    // on a failed call below, wait for the copies already issued so that none lands after the return
+    auto fail = [&](cudaError_t e, const char* what) {
+        for (cudaStream_t c : g->io_copy) cudaStreamSynchronize(c);
+        return cuda_fail(e, what);
+    };
+    // after the kernel: every copy stream orders its remaining downloads behind it
+    auto after_kernel = [&]() {
+        for (cudaStream_t c : g->io_copy) {
+            const cudaError_t w = cudaStreamWaitEvent(c, g->io_kernel, 0);
+            if (w != cudaSuccess) return w;
+        }
+        return cudaSuccess;
+    };
+    bool kernel_done = false;
+    for (uint32_t c = 0; c < nch; c++) {
+        while (!kernel_done && g->io_flags[c] != g->io_seq) {
+            const cudaError_t e = cudaEventQuery(g->io_kernel);
+            if (e == cudaSuccess) {
+                kernel_done = true;
+                const cudaError_t w = after_kernel();
+                if (w != cudaSuccess) return fail(w, "walk event");
+            } else if (e != cudaErrorNotReady) {
+                return fail(e, "walk");
+            } else {
+                std::this_thread::yield();
+            }
+        }
+        const uint64_t lo = (uint64_t)c << shift, cnt = std::min<uint64_t>(1ull << shift, n - lo);
+        cudaStream_t cs = g->io_copy[c % WALK_IO_STREAMS];
+        cudaError_t e = cudaSuccess;
+        if (host_paths)
+            e = cudaMemcpyAsync(paths + lo * stride, q.paths + lo * stride, 4 * cnt * stride, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess && host_plen)
+            e = cudaMemcpyAsync(path_len + lo, q.plen + lo, 4 * cnt, cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) return fail(e, "paths download");
+    }
+    if (!kernel_done) {
+        const cudaError_t w = after_kernel();
+        if (w != cudaSuccess) return fail(w, "walk event");
+    }
+    for (int k = 0; k < WALK_IO_STREAMS; k++) {
+        CK(cudaEventRecord(g->io_done[k], g->io_copy[k]), "walk event");
+        CK(cudaStreamWaitEvent(s, g->io_done[k], 0), "walk event");
     }
     return BINGO_OK;
 }
@@ -115,10 +202,15 @@ bingo_status bingo_walk(bingo_graph* g, uint64_t nwalkers, const uint32_t* start
     q.pad = pad;
     q.max_steps = lengths ? stride - 1 : max_len;
     q.queue = (unsigned long long*)((uint64_t*)g->d_ctl + CTL_QUEUE);
-    st = walk_launch(g, q, s);
-    if (st != BINGO_OK) return st;
-    if (host_paths) CK(cudaMemcpyAsync(paths, dpaths, 4ull * nwalkers * stride, cudaMemcpyDeviceToHost, s), "paths download");
-    if (host_plen) CK(cudaMemcpyAsync(path_len, dplen, 4ull * nwalkers, cudaMemcpyDeviceToHost, s), "lengths download");
+    if ((host_paths || host_plen) && base_mode == BINGO_WALK_PERSISTENT && nwalkers >= WALK_IO_MIN) {
+        st = walk_host_io_overlap(g, q, paths, path_len, host_paths, host_plen, s);
+        if (st != BINGO_OK) return st;
+    } else {
+        st = walk_launch(g, q, s);
+        if (st != BINGO_OK) return st;
+        if (host_paths) CK(cudaMemcpyAsync(paths, dpaths, 4ull * nwalkers * stride, cudaMemcpyDeviceToHost, s), "paths download");
+        if (host_plen) CK(cudaMemcpyAsync(path_len, dplen, 4ull * nwalkers, cudaMemcpyDeviceToHost, s), "lengths download");
+    }
     if (host_io || host_paths || host_plen) {
         CK(cudaStreamSynchronize(s), "walk");
         uint32_t status = 0;

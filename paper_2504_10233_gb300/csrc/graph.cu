@@ -378,12 +378,18 @@ static void free_graph(bingo_graph* g) {
     if (!g) return;
     if (g->upd_graph) cudaGraphExecDestroy(g->upd_graph);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    for (cudaStream_t c : g->io_copy)
+        if (c) cudaStreamDestroy(c);
+    for (cudaEvent_t e : g->io_done)
+        if (e) cudaEventDestroy(e);
+    if (g->io_kernel) cudaEventDestroy(g->io_kernel);
+    if (g->io_flags) cudaFreeHost((void*)g->io_flags);
     void* ptrs[] = {g->d_hdr, g->d_cold, g->d_order, g->d_perm, g->d_pool, g->d_ctl, g->d_fcount, g->d_fstack, g->d_pending, g->d_eh};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     Buf* bufs[] = {&g->s_in, &g->s_keys, &g->s_keys2, &g->s_vals, &g->s_vals2, &g->s_tmp, &g->s_seg,
                    &g->s_rank, &g->s_best, &g->s_aux, &g->s_walk, &g->s_stage, &g->s_rec, &g->s_seginfo, &g->s_gcand, &g->s_gcand_cnt,
-                   &g->w_starts, &g->w_len, &g->w_pid, &g->w_paths, &g->w_plen};
+                   &g->w_starts, &g->w_len, &g->w_pid, &g->w_paths, &g->w_plen, &g->w_pols, &g->w_chunk_done};
     for (Buf* b : bufs) release(*b);
     delete g;
 }

@@ -47,6 +47,10 @@ struct WalkParams {
     const uint64_t* req_off;
     const uint64_t* req_key;
     uint32_t nreq;
+    // completion notices for downloads that overlap the walk (chunk_done null = off)
+    uint32_t* chunk_done;
+    uint32_t* host_flags;
+    uint32_t chunk_shift, io_seq;
     // stepwise state
     uint32_t* s_cur;
     uint32_t* s_prev;
@@ -355,12 +359,29 @@ __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A
     return false;
 }
 
+// Completion notice of walker `wid`, whose row and length are written: the walker that completes its
+// id chunk publishes io_seq in the chunk's host-mapped flag, after which the host may start a copy
+// engine on the chunk while the walk goes on.  Each lane fences its own stores at system scope (the
+// copy engine is the reader) before the team's count.
+__device__ __forceinline__ void notify_done(const WalkParams& A, uint64_t wid, uint32_t tl, uint32_t team_mask) {
+    __threadfence_system();
+    __syncwarp(team_mask);
+    if (tl != 0) return;
+    const uint64_t c = wid >> A.chunk_shift, lo = c << A.chunk_shift;
+    const uint64_t size = A.nwalkers - lo < (1ull << A.chunk_shift) ? A.nwalkers - lo : (1ull << A.chunk_shift);
+    if (atomicAdd(A.chunk_done + c, 1u) + 1 == size) {
+        __threadfence_system();
+        *(volatile uint32_t*)(A.host_flags + c) = A.io_seq;
+    }
+}
+
 __device__ __forceinline__ void finish_walker(const WalkParams& A, uint64_t wid, uint32_t steps, uint32_t tl,
-                                              uint32_t T) {
+                                              uint32_t T, uint32_t team_mask) {
     uint32_t* row = A.paths + wid * (uint64_t)A.stride;
     if (tl == 0) A.plen[wid] = steps + 1;
     if (A.flags & WF_PAD)
         for (uint32_t t = steps + 1 + tl; t < A.stride; t += T) row[t] = NONE32;
+    if (A.chunk_done) notify_done(A, wid, tl, team_mask);
 }
 
 // OCC selects the register budget: 0 = up to 64 registers (1,024-thread bound), 1 = 40 registers
@@ -401,7 +422,7 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
                     if (tl == 0) A.paths[wid * (uint64_t)A.stride] = cur;
                     cur = to_internal(G, cur);
                     if (L == 0) {
-                        finish_walker(A, wid, 0, tl, T);
+                        finish_walker(A, wid, 0, tl, T, team_mask);
                         have = false;
                     }
                 }
@@ -424,7 +445,7 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
                 if (step == L && tl == 0) row[step] = to_caller(G, cur);
             }
             if (!took || step == L) {
-                finish_walker(A, wid, step, tl, T);
+                finish_walker(A, wid, step, tl, T, team_mask);
                 have = false;
             }
         }
@@ -448,7 +469,7 @@ __global__ void k_walk_step(DevGraph G, WalkParams A, uint32_t s) {
             A.paths[wid * (uint64_t)A.stride] = cur;
             cur = to_internal(G, cur);
             if (L == 0) {
-                finish_walker(A, wid, 0, 0, 1);
+                finish_walker(A, wid, 0, 0, 1, 1u << (threadIdx.x & 31));
                 A.s_cur[wid] = NONE32;
                 continue;
             }
@@ -461,7 +482,7 @@ __global__ void k_walk_step(DevGraph G, WalkParams A, uint32_t s) {
         const bool took = walk_step<1, WM>(G, A, wid, pid, s, cur, prev, 0, 0, 0, 0, hword);
         if (took) A.paths[wid * (uint64_t)A.stride + s + 1] = to_caller(G, cur);
         if (!took || s + 1 == L) {
-            finish_walker(A, wid, took ? s + 1 : s, 0, 1);
+            finish_walker(A, wid, took ? s + 1 : s, 0, 1, 1u << (threadIdx.x & 31));
             A.s_cur[wid] = NONE32;
         } else {
             A.s_cur[wid] = cur;
@@ -571,6 +592,10 @@ bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
     A.req_off = q.req_off;
     A.req_key = q.req_key;
     A.nreq = q.nreq;
+    A.chunk_done = q.chunk_done;
+    A.host_flags = q.host_flags;
+    A.chunk_shift = q.chunk_shift;
+    A.io_seq = q.io_seq;
     if (nwalkers == 0) return BINGO_OK;
     if (mode == BINGO_WALK_STEPWISE) {
         CK(ensure(g->s_walk, 8 * nwalkers), "walk state");

@@ -274,6 +274,44 @@ def test_padding_flag_and_host_buffers(B):
     assert (p3[idx] == 0x12345678).all() and (p3[~idx] == p1[~idx]).all()
 
 
+def test_host_buffer_walk_in_chunks_equals_device_walk(B):
+    """Host-output walks of >= 2^17 walkers download id-ordered chunks of rows while the walk runs,
+    each as soon as its last walker finished; every row must equal the device-buffer walk."""
+    import torch
+
+    wl = W.make_workload("c2", scale=14, m=1 << 18, nbatch=1, batch=1000)
+    G = wl.graph
+    g = graph_of(B, G)
+    n, stride = 300_001, 23  # 19 chunks of 2^14 walkers, the last one ragged (5,089)
+    starts = W.walk_starts(G.n, n, 5)
+    lengths = (np.arange(n) % 23).astype(np.uint32)  # includes zero-length walks
+    pids = (np.arange(n) % 2).astype(np.uint8)
+    pols = [B.policy(B.DEEPWALK, 22), B.policy(B.PPR, 22, 0.15)]
+    p1, l1 = run_walk(B, g, starts, pols, 9, stride, lengths=lengths, pids=pids)
+    assert (l1 == np.minimum(lengths, 22) + 1).sum() > n // 4  # many walks run to their length
+    # pageable host inputs and outputs
+    p2 = np.zeros((n, stride), np.uint32)
+    l2 = np.zeros(n, np.uint32)
+    g.walk(starts, pols, 9, stride, p2, l2, lengths=lengths, policy_ids=pids)
+    assert (p2 == p1).all() and (l2 == l1).all()
+    # pinned host outputs, device inputs
+    p3 = torch.zeros((n, stride), dtype=torch.int32).pin_memory()
+    l3 = torch.zeros(n, dtype=torch.int32).pin_memory()
+    g.walk(dev(starts), pols, 9, stride, p3, l3, lengths=dev(lengths), policy_ids=dev(pids))
+    assert (p3.numpy().view(np.uint32) == p1).all() and (l3.numpy().view(np.uint32) == l1).all()
+    # device paths, host lengths only
+    p4 = torch.zeros((n, stride), dtype=torch.int32, device="cuda")
+    l4 = np.zeros(n, np.uint32)
+    g.walk(starts, pols, 9, stride, p4, l4, lengths=lengths, policy_ids=pids)
+    assert (p4.cpu().numpy().view(np.uint32) == p1).all() and (l4 == l1).all()
+    # no padding: entries beyond path_len keep the caller's values through the chunked round trip
+    p5 = np.full((n, stride), 0x12345678, dtype=np.uint32)
+    g.walk(starts, pols, 9, stride, p5, l2, lengths=lengths, policy_ids=pids, mode=B.WALK_NO_PAD)
+    idx = np.arange(stride)[None, :] >= l1[:, None].astype(np.int64)
+    assert (p5[idx] == 0x12345678).all() and (p5[~idx] == p1[~idx]).all()
+    g.check()
+
+
 def test_invalid_walk_arguments(B):
     wl = W.make_workload("c1")
     G = wl.graph
