@@ -892,9 +892,19 @@ def run_ablation(args):
                           "groups_by_kind": dict(zip(["empty", "dense", "one", "sparse", "regular"],
                                                      [int(x) for x in kinds]))})
             del gs
-        clocks = sampler.stop()
         grp = lambda m: m["regular_groups"] + m["sparse_groups"]
         tot = lambda m: sum(v for k, v in m.items() if k not in ("pool_capacity", "edge_index"))
+        # the group-adaption tuner (bingo_autotune_adaption): its pick with no memory limit, and within the
+        # state size of the paper's thresholds (alpha 40, beta 10)
+        tuned = {}
+        for label, budget in (("no_budget", 0), ("within_paper_default_state", tot(mem_ga))):
+            tg = B.Graph.tuned(G.n, t(G.row_ptr), t(G.col), t(G.w), starts, wl.length, state_budget_bytes=budget,
+                               max_bits=G.max_bits)
+            w_t, _ = _timed_walks(torch, B, tg, starts, stride, 3, 2, 7, flush, stream)
+            tuned[label] = {"alpha_pct": tg.cfg.alpha_pct, "beta_pct": tg.cfg.beta_pct,
+                            "state_bytes": tot(tg.memory_report()), "walk_ms": w_t}
+            tg.close()
+        clocks = sampler.stop()
         line = {"metric": "memory of the sampling state, all-regular baseline over group adaption (Section 6.2)",
                 "value": (tot(mem_bs) / tot(mem_ga)) if mem_bs else None, "unit": "x", "higher_is_better": True,
                 "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "u32/u64", "data": "synthetic",
@@ -906,6 +916,7 @@ def run_ablation(args):
                 "update_ms_per_batch": {"ga": u_ga, "bs": u_bs},
                 "ga_conversions_all_batches": conv.tolist(),
                 "alpha_beta_sweep": sweep,
+                "adaption_autotune": tuned,
                 "paper_context": "A100: GA uses 14.6-22.2x less memory than BS and is 1.09x faster overall",
                 "clocks": clocks}
         if bsg is None:

@@ -345,6 +345,31 @@ bingo_status bingo_autotune(bingo_graph* g, uint64_t nwalkers, const uint32_t* s
 bingo_status bingo_autotune_updates(bingo_graph* g, const bingo_update* ups, uint64_t count, void* stream,
                                     bingo_update_stats* stats, bingo_config* out_cfg);
 
+/*
+ * Choose the group-adaption thresholds of Eq. group (alpha, beta; Section 5.1)
+ * for a graph.  The paper fixes alpha = 40, beta = 10 and reports the memory
+ * and time of adaption against keeping every group regular (Section 6.2,
+ * Fig. Moptimization); which point of that trade-off is best depends on the
+ * graph and the hardware, so this call measures it.  The graph is built from
+ * the CSR (arguments as bingo_create; host or device pointers) under every
+ * candidate alpha in {20, 40, 70, 100} (100: no group is ever dense) x beta in
+ * {0, 10} (0: no group is ever sparse), with cfg's other fields.  Candidates
+ * whose state (bingo_memory_report [0] + [1] + [2] + [3]) exceeds
+ * state_budget_bytes (0 = no limit) are dropped; on each of the others a trial
+ * walk of `nwalkers` DeepWalk walkers of `length` steps from `starts` (host or
+ * device) is timed (one warm-up, two timed launches), and the graph with the
+ * least walk time is returned in *out; the others are destroyed.  Kinds stay a
+ * pure function of (|G_k|, d, alpha, beta), so every candidate samples
+ * exactly.  out_cfg (nullable) receives the chosen config (alpha_pct,
+ * beta_pct).  Errors: as bingo_create; BINGO_E_OOM if no candidate fits the
+ * budget or the device; BINGO_E_INVALID for cfg->all_regular (nothing to
+ * tune).  Synchronises `stream`.
+ */
+bingo_status bingo_autotune_adaption(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t* col,
+                                     const uint32_t* bias, const bingo_config* cfg, uint64_t state_budget_bytes,
+                                     uint64_t nwalkers, const uint32_t* starts, uint32_t length, void* stream,
+                                     bingo_graph** out, bingo_config* out_cfg);
+
 /* Current configuration of the graph (host pointer). */
 bingo_status bingo_get_config(bingo_graph* g, bingo_config* out);
 bingo_status bingo_set_walk_config(bingo_graph* g, uint32_t lanes_per_walker, uint32_t warps_per_block,

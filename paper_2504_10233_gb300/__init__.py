@@ -100,6 +100,8 @@ SIGNATURES = {
     "bingo_memory_report": (c.c_int, [VP, c.POINTER(c.c_uint64)]),
     "bingo_autotune": (c.c_int, [VP, c.c_uint64, VP, c.c_uint32, VP, c.POINTER(bingo_config)]),
     "bingo_autotune_updates": (c.c_int, [VP, VP, c.c_uint64, VP, c.POINTER(bingo_update_stats), c.POINTER(bingo_config)]),
+    "bingo_autotune_adaption": (c.c_int, [c.c_uint32, c.c_uint64, VP, VP, VP, c.POINTER(bingo_config), c.c_uint64,
+                                          c.c_uint64, VP, c.c_uint32, VP, c.POINTER(VP), c.POINTER(bingo_config)]),
     "bingo_get_config": (c.c_int, [VP, c.POINTER(bingo_config)]),
     "bingo_set_walk_config": (c.c_int, [VP, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32]),
     "bingo_kernel_launches": (c.c_uint64, [VP]),
@@ -261,6 +263,18 @@ def bingo_autotune(h, nwalkers, starts, length, stream=None):
     return cfg
 
 
+def bingo_autotune_adaption(n, row_ptr, col, bias, cfg, state_budget_bytes, starts, length, stream=None):
+    """Build the graph under each candidate (alpha, beta) and keep the fastest within the budget;
+    returns (handle, chosen config)."""
+    h = VP()
+    out = bingo_config()
+    _err(load().bingo_autotune_adaption(n, int(len(col)), _ptr(row_ptr), _ptr(col), _ptr(bias),
+                                        c.byref(cfg) if cfg is not None else None, int(state_budget_bytes),
+                                        int(len(starts)), _ptr(starts), length, _stream(stream), c.byref(h),
+                                        c.byref(out)))
+    return h, out
+
+
 def bingo_get_config(h):
     cfg = bingo_config()
     _err(load().bingo_get_config(h, c.byref(cfg)))
@@ -329,6 +343,16 @@ class Graph:
         self.n = int(n)
         self.cfg = default_config(max_bits=max_bits, **cfg)
         self.h = bingo_create(self.n, row_ptr, col, bias, self.cfg, stream)
+
+    @classmethod
+    def tuned(cls, n, row_ptr, col, bias, starts, length, state_budget_bytes=0, max_bits=32, stream=None, **cfg):
+        """A graph whose group-adaption thresholds were chosen by bingo_autotune_adaption."""
+        self = cls.__new__(cls)
+        self.n = int(n)
+        base = default_config(max_bits=max_bits, **cfg)
+        self.h, self.cfg = bingo_autotune_adaption(self.n, row_ptr, col, bias, base, state_budget_bytes, starts,
+                                                   length, stream)
+        return self
 
     def close(self):
         if getattr(self, "h", None):

@@ -315,4 +315,124 @@ bingo_status bingo_autotune(bingo_graph* g, uint64_t nwalkers, const uint32_t* s
     return best < 1e30f ? BINGO_OK : BINGO_E_CUDA;
 }
 
+// Group-adaption tuner: build the graph under each candidate (alpha, beta) of Eq. group, keep the
+// candidates whose state fits the budget, time a trial walk on each and return the fastest.
+bingo_status bingo_autotune_adaption(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t* col,
+                                     const uint32_t* bias, const bingo_config* cfg, uint64_t state_budget_bytes,
+                                     uint64_t nwalkers, const uint32_t* starts, uint32_t length, void* stream,
+                                     bingo_graph** out, bingo_config* out_cfg) {
+    if (!out || !starts || nwalkers == 0 || length == 0) { set_error("autotune_adaption: bad arguments"); return BINGO_E_INVALID; }
+    *out = nullptr;
+    bingo_config base;
+    if (cfg) base = *cfg; else bingo_default_config(&base);
+    if (base.all_regular) { set_error("autotune_adaption: all_regular graphs have no adaption to tune"); return BINGO_E_INVALID; }
+    cudaStream_t s = (cudaStream_t)stream;
+    // stage host inputs once for every candidate build and walk
+    Buf brp, bcol, bbias, bst, bpaths, bplen;
+    auto cleanup = [&]() { release(brp); release(bcol); release(bbias); release(bst); release(bpaths); release(bplen); };
+    auto stage = [&](const void* src, size_t bytes, Buf& b, const void** dst) -> cudaError_t {
+        if (!src || bytes == 0 || is_device_ptr(src)) { *dst = src; return cudaSuccess; }
+        cudaError_t e = ensure(b, bytes);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, s);
+        *dst = b.p;
+        return e;
+    };
+    const uint64_t* drp;
+    const uint32_t *dcol, *dbias, *dst_;
+    cudaError_t e = stage(row_ptr, 8ull * ((uint64_t)n + 1), brp, (const void**)&drp);
+    if (e == cudaSuccess) e = stage(col, 4ull * m, bcol, (const void**)&dcol);
+    if (e == cudaSuccess) e = stage(bias, 4ull * m, bbias, (const void**)&dbias);
+    if (e == cudaSuccess) e = stage(starts, 4ull * nwalkers, bst, (const void**)&dst_);
+    const uint32_t stride = length + 1;
+    if (e == cudaSuccess) e = ensure(bpaths, 4ull * nwalkers * stride);
+    if (e == cudaSuccess) e = ensure(bplen, 4ull * nwalkers);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "autotune_adaption staging"); }
+    static const uint32_t alphas[] = {20, 40, 70, 100};  // 100: no group is ever dense
+    static const uint32_t betas[] = {0, 10};             // 0: no group is ever sparse
+    bingo_policy pol;
+    memset(&pol, 0, sizeof(pol));
+    pol.kind = BINGO_DEEPWALK;
+    pol.max_len = length;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    bingo_graph* best = nullptr;
+    float best_ms = 0.f;
+    bingo_status st = BINGO_OK, last_fail = BINGO_OK;
+    bool over_budget = false;
+    for (uint32_t ai = 0; ai < 4 && st == BINGO_OK; ai++) {
+        for (uint32_t bi = 0; bi < 2 && st == BINGO_OK; bi++) {
+            bingo_config c = base;
+            c.alpha_pct = alphas[ai];
+            c.beta_pct = betas[bi];
+            bingo_graph* g = nullptr;
+            bingo_status cs = bingo_create(n, m, drp, dcol, dbias, &c, stream, &g);
+            if (cs == BINGO_E_OOM) { last_fail = cs; continue; }  // this candidate does not fit the device
+            if (cs != BINGO_OK) { st = cs; break; }
+            uint64_t rep[6];
+            cs = bingo_memory_report(g, rep);
+            if (cs != BINGO_OK) { bingo_destroy(g); st = cs; break; }
+            if (state_budget_bytes && rep[0] + rep[1] + rep[2] + rep[3] > state_budget_bytes) {
+                over_budget = true;
+                bingo_destroy(g);
+                continue;
+            }
+            if ((e = ensure(g->w_pols, sizeof(bingo_policy))) != cudaSuccess ||
+                (e = cudaMemcpyAsync(g->w_pols.p, &pol, sizeof(pol), cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+                bingo_destroy(g);
+                st = cuda_fail(e, "autotune_adaption policy");
+                break;
+            }
+            WalkReq q;
+            q.nwalkers = nwalkers;
+            q.starts = dst_;
+            q.dev_pols = (const bingo_policy*)g->w_pols.p;
+            q.npol = 1;
+            q.stride = stride;
+            q.paths = (uint32_t*)bpaths.p;
+            q.plen = (uint32_t*)bplen.p;
+            q.mode = BINGO_WALK_PERSISTENT;
+            q.pad = false;
+            q.max_steps = length;
+            q.queue = (unsigned long long*)((uint64_t*)g->d_ctl + CTL_QUEUE);
+            float tsum = 0.f;
+            for (int rep_i = 0; rep_i < 3 && cs == BINGO_OK; rep_i++) {  // one warm-up, two timed
+                q.seed = 4321 + rep_i;
+                cudaEventRecord(e0, s);
+                cs = walk_launch(g, q, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) cs = cuda_fail(cudaGetLastError(), "autotune_adaption walk");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep_i > 0) tsum += ms;
+            }
+            if (cs == BINGO_OK) cs = bingo_check(g, stream);
+            if (cs != BINGO_OK) { bingo_destroy(g); st = cs; break; }
+            if (!best || tsum < best_ms) {
+                if (best) bingo_destroy(best);
+                best = g;
+                best_ms = tsum;
+            } else {
+                bingo_destroy(g);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cleanup();
+    if (st != BINGO_OK) {
+        if (best) bingo_destroy(best);
+        return st;
+    }
+    if (!best) {
+        if (over_budget) set_error("autotune_adaption: no (alpha, beta) candidate fits %llu bytes of state",
+                                   (unsigned long long)state_budget_bytes);
+        else set_error("autotune_adaption: no candidate could be built (%d)", (int)last_fail);
+        return BINGO_E_OOM;
+    }
+    *out = best;
+    if (out_cfg) bingo_get_config(best, out_cfg);
+    return BINGO_OK;
+}
+
 }  // extern "C"

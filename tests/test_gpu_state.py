@@ -423,3 +423,37 @@ def test_update_autotune_applies_slices_in_order(B):
     assert_state_matches(g.export_state(), og)
     apply_both(g, og, _stress_batch(rng, og, og.n, 200), 12)  # the kept setting serves later batches
     assert_state_matches(g.export_state(), og)
+
+
+def test_adaption_autotune_choice_parity_and_budget(B):
+    """bingo_autotune_adaption returns one of its (alpha, beta) candidates, in exactly the state a plain
+    create with that pair gives (oracle parity under the chosen thresholds, before and after a batch);
+    only candidates within the state budget can be chosen, and a budget below every candidate is
+    BINGO_E_OOM."""
+    wl = W.make_workload("c2", scale=14, m=1 << 18, nbatch=1, batch=1000)
+    G = wl.graph
+    starts = W.walk_starts(G.n, 1 << 15, 0)
+    og = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    mem = {}
+    for a in (20, 40, 70, 100):
+        for b in (0, 10):
+            g = make(B, G, alpha_pct=a, beta_pct=b)
+            r = g.memory_report()
+            mem[(a, b)] = r["adjacency"] + r["vertex_records"] + r["regular_groups"] + r["sparse_groups"]
+            g.close()
+    assert len(set(mem.values())) > 1  # the candidates really differ in memory
+    t = B.Graph.tuned(G.n, dev(G.row_ptr), dev(G.col), dev(G.w), dev(starts), 20, max_bits=G.max_bits)
+    pick = (t.cfg.alpha_pct, t.cfg.beta_pct)
+    assert pick in mem
+    assert_state_matches(t.export_state(), og, alpha=pick[0], beta=pick[1])
+    apply_both(t, og, wl.batches[0].records(), G.max_bits)
+    assert_state_matches(t.export_state(), og, alpha=pick[0], beta=pick[1])
+    t.close()
+    budget = min(mem.values())  # host inputs this time
+    t = B.Graph.tuned(G.n, G.row_ptr, G.col, G.w, starts, 20, state_budget_bytes=budget, max_bits=G.max_bits)
+    assert mem[(t.cfg.alpha_pct, t.cfg.beta_pct)] <= budget
+    t.close()
+    with pytest.raises(B.BingoError) as ei:
+        B.Graph.tuned(G.n, dev(G.row_ptr), dev(G.col), dev(G.w), dev(starts), 20, state_budget_bytes=budget - 1,
+                      max_bits=G.max_bits)
+    assert ei.value.status == B.E_OOM
