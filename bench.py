@@ -160,6 +160,49 @@ def walk_bytes(per_vertex, paths, plen):
     return float(per_vertex[src].sum())
 
 
+def update_bytes(ex0, ex1, rec):
+    """Algorithmic bytes of one update batch, from the exported state before (ex0) and after (ex1) it:
+    per record its 16 bytes and a sort by source (two passes of 16 bytes read + 16 written); per
+    insertion the adjacency slot (32) and, for every set bit k whose group (v, k) is a member list
+    (regular or sparse) after the batch, the member entry and its inverted-index entry (32 + 32);
+    per deletion that finds its edge the locating probe (32), the adjacency slot (32), one compaction
+    move (32), and for every set bit of the removed edge whose group was a list before the batch the
+    entry, its inverted entry, the tail read and the patch (4 x 32); per touched vertex its count line
+    read and written (2 x 32 ceil(4 K_v / 32), K_v = highest nonempty group + 1 after the batch)."""
+    rec = np.asarray(rec, dtype=np.uint32).reshape(-1, 4)
+    src = rec[:, 0].astype(np.int64)
+    op = rec[:, 3]
+    ins, dele = op != 1, op != 0
+    nbytes = 16.0 * len(rec) + 64.0 * float(ins.sum() + dele.sum())
+    sh = np.arange(32, dtype=np.uint64)
+    # insertions
+    k1 = ex1["kind"]
+    listk1 = (k1 == 3) | (k1 == 4)
+    bits = ((rec[ins, 2].astype(np.uint64)[:, None] >> sh[None, :]) & np.uint64(1)).astype(bool)
+    nbytes += 32.0 * float(ins.sum()) + 64.0 * float((bits & listk1[src[ins]]).sum())
+    # deletions: the earliest live copy of (src, dst) before the batch
+    deg0 = ex0["deg"].astype(np.int64)
+    v0 = np.repeat(np.arange(len(deg0), dtype=np.uint64), deg0)
+    key0 = (v0 << np.uint64(32)) | ex0["dst"].astype(np.uint64)
+    order = np.lexsort((ex0["eid"], key0))
+    key0s, bias0s = key0[order], ex0["bias"][order]
+    first = np.ones(len(key0s), dtype=bool)
+    first[1:] = key0s[1:] != key0s[:-1]
+    key0s, bias0s = key0s[first], bias0s[first]
+    dk = (src[dele].astype(np.uint64) << np.uint64(32)) | rec[dele, 1].astype(np.uint64)
+    pos = np.minimum(np.searchsorted(key0s, dk), max(len(key0s) - 1, 0))
+    found = (key0s[pos] == dk) if len(key0s) else np.zeros(len(dk), dtype=bool)
+    listk0 = (ex0["kind"] == 3) | (ex0["kind"] == 4)
+    dbits = ((bias0s[pos[found]].astype(np.uint64)[:, None] >> sh[None, :]) & np.uint64(1)).astype(bool)
+    nbytes += 96.0 * float(found.sum()) + 128.0 * float((dbits & listk0[src[dele][found]]).sum())
+    # touched vertices
+    tv = np.unique(src)
+    mask1 = ex1["cnt"][tv] > 0
+    kv = np.where(mask1.any(axis=1), 32 - np.argmax(mask1[:, ::-1], axis=1), 0)
+    nbytes += float((2.0 * 32.0 * np.ceil(4.0 * kv / 32.0)).sum())
+    return nbytes
+
+
 # ------------------------------------------------------------------------------------- distributed helpers
 
 def dist_env():
@@ -281,7 +324,8 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     B.load()
     nsteps = args.warmup + args.steps
-    wl = W.make_workload(args.workload, nbatch=nsteps + 1)  # the last batch feeds the streaming measurement
+    # after the timed steps: one more batch for the update byte model, and the last feeds the streaming measurement
+    wl = W.make_workload(args.workload, nbatch=nsteps + 2)
     G = wl.graph
     stream = torch.cuda.Stream(device=dev)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -354,6 +398,16 @@ def run_ours(args):
             "traffic": args.traffic if args.traffic is not None else measured_traffic(args.workload),
             "kernel": "k_walk_persistent", "peak_source": f"{pk_src} hbm_gbs (copy bandwidth)",
             "bytes_per_step": abytes / max(1, int((l_np.astype(np.int64) - 1).sum()))}
+
+    # the update roofline: the byte model over one further batch of the same stream (state exported before
+    # and after it, outside the timed region) divided by the mean time of the timed batches
+    g.apply_updates(recs[nsteps], stream=stream)
+    ub = update_bytes(ex, g.export_state(), wl.batches[nsteps].records())
+    upd_achieved = ub / (float(np.mean(upd_ms)) / 1e3) / 1e9
+    upd_roof = {"bound": "hbm", "achieved": upd_achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": upd_achieved / pk["hbm_gbs"], "kernel": "update pipeline (one captured graph per batch)",
+                "bytes_per_update": ub / len(wl.batches[nsteps]),
+                "model": "per record, sort, locate, adjacency slot, list-group entries, count lines"}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     h_starts = torch.from_numpy(W.walk_starts(G.n, nw, wl.walk_seed)).pin_memory()
@@ -434,7 +488,7 @@ def run_ours(args):
                            "walk_config": {"lanes_per_walker": g.config().lanes_per_walker,
                                            "warps_per_block": g.config().warps_per_block,
                                            "reg_variant": g.config().reg_variant}},
-                "updated_edges_per_s": upd_rate, "walk_steps_per_s": walk_rate,
+                "updated_edges_per_s": upd_rate, "update_roofline": upd_roof, "walk_steps_per_s": walk_rate,
                 "update_ms_per_step": float(np.mean(upd_ms)), "walk_ms_per_step": float(np.mean(walk_ms)),
                 "wall_s_timed": wall, "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
                 "roofline": roof, "cpu_baseline": cpu, "streaming": streaming}
