@@ -274,6 +274,15 @@ WORKLOAD_TEXT = {
 }
 
 
+METRIC_MAIN = "sampled walk steps/s (update batch + walk per step); updated edges/s; p50/p99 latency in the serving bench"
+
+
+def main_config(args, wl):
+    """The workload part of the main line's config, shared by both arms."""
+    return {"workload": WORKLOAD_TEXT.get(args.workload, args.workload), "walkers": wl.nwalkers,
+            "length": wl.length, "updates_per_step": len(wl.batches[0])}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle (the only reference this paper has), bounded sample per step."""
     import oracle as O
@@ -297,12 +306,12 @@ def run_reference(args):
             total_steps += float((plen.astype(np.int64) - 1).sum())
             total_t += dt
     v = total_steps / total_t
-    line = {"impl": "reference", "metric": "sampled walk steps/s (update batch + walk per step)", "value": v,
+    line = {"impl": "reference", "metric": METRIC_MAIN, "value": v,
             "unit": "steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT.get(args.workload, args.workload),
-                       "sample": f"{nw} walkers per step (bounded sample on host cores)"},
+            "config": dict(main_config(args, wl), sample=f"{nw} of the {wl.nwalkers} walkers per step (bounded "
+                                                          f"sample on host cores), every update of the batch"),
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"per step: one batch of updates applied to the oracle, then {nw} walkers x "
                                        f"{wl.length}"},
@@ -477,13 +486,11 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(G, wl.batches[0], wl.length, 77, args.cpu_seconds)
     if rank == 0:
-        line = {"metric": "sampled walk steps/s (update batch + walk per step); updated edges/s; p50/p99 latency "
-                          "in the serving bench",
+        line = {"metric": METRIC_MAIN,
                 "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
-                "config": {"workload": WORKLOAD_TEXT.get(args.workload, args.workload), "walkers": nw,
-                           "length": wl.length, "updates_per_step": len(wl.batches[0]),
+                "config": {**main_config(args, wl),
                            "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); state > L2",
                            "walk_config": {"lanes_per_walker": g.config().lanes_per_walker,
                                            "warps_per_block": g.config().warps_per_block,
