@@ -154,8 +154,9 @@ def edge_keys(og: O.Graph):
     return np.unique((src << np.uint64(32)) | dst.astype(np.uint64))
 
 
-def assert_steps_live(og: O.Graph, paths: np.ndarray, plen: np.ndarray, keys=None):
-    """Every consecutive pair of every path is a live edge of the oracle graph; padding is 0xFFFFFFFF."""
+def assert_steps_live(og: O.Graph, paths: np.ndarray, plen: np.ndarray, keys=None, padded=True):
+    """Every consecutive pair of every path is a live edge of the oracle graph; padding is 0xFFFFFFFF
+    (padded=False: entries past path_len are the caller's and are not looked at)."""
     keys = edge_keys(og) if keys is None else keys
     L = paths.shape[1]
     idx = np.arange(L - 1)[None, :]
@@ -167,5 +168,6 @@ def assert_steps_live(og: O.Graph, paths: np.ndarray, plen: np.ndarray, keys=Non
     pos = np.minimum(pos, len(keys) - 1)
     ok = keys[pos] == q
     assert ok.all(), f"{int((~ok).sum())} steps are not live edges"
-    pad = np.arange(L)[None, :] >= plen.astype(np.int64)[:, None]
-    assert (paths[pad] == 0xFFFFFFFF).all(), "padding is not 0xFFFFFFFF"
+    if padded:
+        pad = np.arange(L)[None, :] >= plen.astype(np.int64)[:, None]
+        assert (paths[pad] == 0xFFFFFFFF).all(), "padding is not 0xFFFFFFFF"

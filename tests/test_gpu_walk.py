@@ -165,6 +165,38 @@ def test_every_step_is_a_live_edge(B, name):
         assert_steps_live(og, paths, plen)
 
 
+def test_c2_full_size_walk_in_the_bench_launch(B):
+    """The bench workload at full size (RMAT-20, 2^24 edges, 2^20 DeepWalk walkers x 80) after one
+    10^5-update batch, in the launch bench.py times (tuned shape, persistent form, no padding):
+    every step is a live edge of the oracle graph, lengths are in range and the start is entry 0;
+    and the one-step law at the highest-degree vertex (binned) holds at this size."""
+    import torch
+
+    wl = W.make_workload("c2", nbatch=1)
+    G = wl.graph
+    g = graph_of(B, G)
+    og = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    rec = wl.batches[0].records()
+    g.apply_updates(dev(rec))
+    og.apply(rec, G.max_bits)
+    starts = W.walk_starts(G.n, wl.nwalkers, wl.walk_seed)
+    ds = dev(starts)
+    g.autotune(ds, wl.length)
+    stride = wl.length + 1
+    paths = torch.full((wl.nwalkers, stride), -3, dtype=torch.int32, device="cuda")
+    plen = torch.zeros(wl.nwalkers, dtype=torch.int32, device="cuda")
+    g.walk(ds, [B.policy(B.DEEPWALK, wl.length)], 1, stride, paths, plen, mode=B.WALK_PERSISTENT | B.WALK_NO_PAD)
+    g.check()
+    p = paths.cpu().numpy().view(np.uint32)
+    l = plen.cpu().numpy().view(np.uint32)
+    assert (l >= 1).all() and (l <= stride).all() and (p[:, 0] == starts).all()
+    assert int((l.astype(np.int64) - 1).sum()) > 20_000_000  # the walk really ran at scale
+    assert_steps_live(og, p, l, padded=False)
+    offs, _, _, _ = og.edges()
+    hub = int(np.argmax(np.diff(offs.astype(np.int64))))
+    one_step_check(B, g, og, hub, 9)
+
+
 def _mixed_policies(B):
     return [B.policy(B.DEEPWALK, 20), B.policy(B.PPR, 30, 0.15), B.policy(B.NODE2VEC, 25, n2v_pq=(2.0, 0.5))]
 
