@@ -344,6 +344,38 @@ def test_host_buffer_walk_in_chunks_equals_device_walk(B):
     g.check()
 
 
+def test_bounded_rejection_loop_reports_timeout(B):
+    """Every device loop is bounded.  A node2vec policy that accepts no candidate (all thresholds 0)
+    exhausts the rejection loop of every second step: the walk ends after its first-order step, the
+    device status reads BINGO_E_TIMEOUT through bingo_check, the status is then clear, and the graph
+    keeps walking correctly."""
+    import torch
+
+    wl = W.make_workload("c1")
+    G = wl.graph
+    g = graph_of(B, G)
+    og = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    pol = B.policy(B.NODE2VEC, 5, n2v_pq=(2.0, 0.5))
+    for i in range(3):
+        pol.n2v_accept[i] = 0
+    n = 256
+    starts = W.walk_starts(G.n, n, 0)
+    paths = torch.empty((n, 6), dtype=torch.int32, device="cuda")
+    plen = torch.empty(n, dtype=torch.int32, device="cuda")
+    g.walk(dev(starts), [pol], 1, 6, paths, plen)
+    with pytest.raises(B.BingoError) as ei:
+        g.check()
+    assert ei.value.status == B.E_TIMEOUT
+    p = paths.cpu().numpy().view(np.uint32)
+    l = plen.cpu().numpy().view(np.uint32)
+    assert (l <= 2).all() and (l == 2).sum() > n // 2  # the first-order step, then the loop gave up
+    assert_steps_live(og, p, l)
+    g.check()  # the status was cleared
+    p2, l2 = run_walk(B, g, starts, [B.policy(B.DEEPWALK, 5)], 2, 6)
+    assert (l2 == 6).all()
+    assert_steps_live(og, p2, l2)
+
+
 def test_invalid_walk_arguments(B):
     wl = W.make_workload("c1")
     G = wl.graph
