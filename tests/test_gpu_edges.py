@@ -155,3 +155,27 @@ def test_widest_base4_biases(B):
     assert_state_matches(ex, og, base4=True)
     assert (ex["bias"][:6] == w[:6]).all()
     one_step(B, g, 0, probs_of(edges, 0), 21)
+
+
+def test_calls_with_nothing_to_do(B):
+    """Zero walkers, an empty update batch and an empty streaming call are valid no-ops through every
+    walk entry point and both buffer kinds, and leave the state exactly as created."""
+    import torch
+
+    edges = [(0, 1, 3), (1, 2, 5), (2, 0, 7), (2, 1, 1)]
+    og = O.Graph.from_edges(3, edges)
+    offs, dst, w, _ = og.edges()
+    g = B.Graph(3, dev(offs.astype(np.uint64)), dev(dst), dev(w))
+    pol = [B.policy(B.DEEPWALK, 4)]
+    none_dev = torch.empty((0, 5), dtype=torch.int32, device="cuda")
+    g.walk(torch.empty(0, dtype=torch.int32, device="cuda"), pol, 0, 5, none_dev,
+           torch.empty(0, dtype=torch.int32, device="cuda"))
+    g.walk(np.zeros(0, np.uint32), pol, 0, 5, np.zeros((0, 5), np.uint32), np.zeros(0, np.uint32))
+    g.walk(np.zeros(0, np.uint32), pol, 0, 5, np.zeros((0, 5), np.uint32), np.zeros(0, np.uint32),
+           mode=B.WALK_STEPWISE)
+    g.check()
+    st = g.apply_updates(torch.empty((0, 4), dtype=torch.int32, device="cuda"))
+    assert (st["inserted"], st["deleted"], st["not_found"]) == (0, 0, 0)
+    st = g.stream_updates(np.zeros((0, 4), np.uint32))
+    assert (st["inserted"], st["deleted"], st["not_found"]) == (0, 0, 0)
+    assert_state_matches(g.export_state(), og)
