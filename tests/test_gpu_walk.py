@@ -145,6 +145,39 @@ def test_hub_one_step_binned(B):
     one_step_check(B, g, og, 0, 77)
 
 
+def test_group_selection_law_at_a_hub(B):
+    """Group selection on its own (Eq. group_prob): with power-of-two biases each edge lies in exactly
+    one group, and with distinct destinations each sampled neighbour names its edge, so 10^6 one-step
+    samples from a hub whose groups take every kind (dense, regular, sparse, one-element) give the
+    group frequencies, which must match W_k / sum_j W_j, W_k = 2^k |G_k| (TV <= 0.01, chi-square
+    p > 1e-3; at most 32 categories)."""
+    n = 1 << 15
+    rng = np.random.default_rng(12)
+    d = 20000
+    ks = np.concatenate([np.zeros(9000), np.full(4000, 3), rng.integers(5, 16, size=d - 13001), [19]]).astype(np.int64)
+    rng.shuffle(ks)
+    dsts = rng.permutation(n)[:d]
+    edges = [(0, int(x), 1 << int(k)) for x, k in zip(dsts, ks)] + [(v, (v + 1) % n, 1) for v in range(1, n)]
+    og = O.Graph.from_edges(n, edges)
+    offs, dst, w, _ = og.edges()
+    g = B.Graph(n, dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=20)
+    ex = g.export_state()
+    assert {O.DENSE, O.REGULAR, O.SPARSE, O.ONE} <= set(ex["kind"][0][ex["cnt"][0] > 0].tolist())
+    paths, plen = run_walk(B, g, np.zeros(N_SAMPLES, np.uint32), [B.policy(B.DEEPWALK, 1)], 21, 2)
+    assert (plen == 2).all()
+    group_of = np.full(n, -1, dtype=np.int64)
+    group_of[dsts] = ks
+    got = group_of[paths[:, 1].astype(np.int64)]
+    assert (got >= 0).all(), "sampled a non-neighbour"
+    cnt = np.bincount(ks, minlength=20).astype(np.float64)
+    W_k = cnt * np.exp2(np.arange(20))
+    live = cnt > 0
+    counts = np.bincount(got, minlength=20).astype(np.float64)[live]
+    probs = (W_k / W_k.sum())[live]
+    assert tv(counts, probs) <= 0.01
+    assert chisq_p(counts, probs) > 1e-3
+
+
 @pytest.mark.parametrize("name", ["c1", "c2s"])
 def test_every_step_is_a_live_edge(B, name):
     wl = W.make_workload("c1") if name == "c1" else W.make_workload("c2", scale=15, m=1 << 19, nbatch=2, batch=20000)
