@@ -294,7 +294,7 @@ def run_reference(args):
     G = wl.graph
     og = O.Graph(G.n, G.row_ptr, G.col, G.w)
     pol = O.policy(O.DEEPWALK, wl.length)
-    nw = args.ref_walkers
+    nw = min(args.ref_walkers, wl.nwalkers)
     total_steps, total_t = 0.0, 0.0
     for i in range(args.warmup + args.steps):
         st = W.walk_starts(G.n, nw, 1000 + i)
