@@ -61,3 +61,14 @@ def test_walk_bytes_per_vertex_and_sum():
     paths = np.array([[0, 1, 0xFFFFFFFF], [0, 1, 0xFFFFFFFF], [1, 0xFFFFFFFF, 0xFFFFFFFF]], np.uint32)
     plen = np.array([2, 2, 1], np.uint32)
     assert np.isclose(bench.walk_bytes(per, paths, plen), 2 * want)
+
+
+def test_cpu_baseline_leg_reports_a_bounded_sample():
+    """The oracle timing of the bench line on a small graph: a positive rate in steps/s, the threads
+    used, and a description of the sample it timed."""
+    import workloads as W
+
+    wl = W.make_workload("c1")
+    cb = bench.cpu_baseline(wl.graph, wl.batches[0], wl.length, 77, target_s=0.2)
+    assert cb["kind"] == "oracle" and cb["unit"] == "steps/s" and cb["value"] > 0 and cb["cores"] >= 1
+    assert "DeepWalk walkers x 80" in cb["sample"]
