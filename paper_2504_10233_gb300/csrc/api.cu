@@ -50,10 +50,10 @@ bingo_status check_policies(const bingo_policy* pols, uint32_t npol, uint32_t st
 // walkers per id-ordered chunk (walkers are taken from the queue in id order, so chunks finish
 // roughly in order), and the walker that completes a chunk writes this call's sequence number into
 // the chunk's flag in host-mapped pinned memory.  This thread issues each chunk's download as soon
-// as its flag shows, on WALK_IO_STREAMS copy streams in turn, so copies run while later chunks
-// still walk.  Once the kernel has ended (its event completes; every loop in it
-// is bounded) the remaining chunks are downloaded without looking at their flags, so the host never
-// waits on a flag alone.  The caller's stream waits for the last download.
+// as its flag shows, on WALK_IO_STREAMS copy streams in turn, so copies run while later chunks still
+// walk.  Once the kernel has ended (its event completes; every loop in it is bounded) the remaining
+// chunks are downloaded without looking at their flags, so the host never waits on a flag alone.
+// The caller's stream waits for the last download.
 bingo_status walk_host_io_overlap(bingo_graph* g, WalkReq q, uint32_t* paths, uint32_t* path_len,
                                   bool host_paths, bool host_plen, cudaStream_t s) {
     for (int k = 0; k < WALK_IO_STREAMS; k++) {
