@@ -275,6 +275,52 @@ def bingo_autotune_adaption(n, row_ptr, col, bias, cfg, state_budget_bytes, star
     return h, out
 
 
+def state_sizes(h) -> dict:
+    """bingo_state_sizes_get as a dict (n, m, list_entries, sparse_entries, pool words, next edge id)."""
+    sz = bingo_state_sizes()
+    _err(load().bingo_state_sizes_get(h, c.byref(sz)))
+    return {f: int(getattr(sz, f)) for f, _ in bingo_state_sizes._fields_}
+
+
+def _size_class(x: int) -> int:
+    return max(0, int(x) - 1).bit_length()  # ceil(log2 x): graphs within a factor of two share a class
+
+
+def walk_tune_key(graph, length: int, device: str) -> str:
+    """Cache key of a tuned walker launch: the device, the graph's size class and weight format, the walk length."""
+    cfg = graph.config()
+    m = graph.state_sizes()["m"]
+    return (f"{device}|n2^{_size_class(graph.n)}|m2^{_size_class(m)}|bits{cfg.max_bits}|fmt{cfg.bias_format}"
+            f"|base{cfg.radix_base or 2}|L{int(length)}")
+
+
+def cached_walk_tune(graph, starts, length: int, cache_path: str, device: str, stream=None) -> dict:
+    """The walker launch shape (lanes per walker, warps per block, blocks per SM, register variant) from a
+    JSON cache keyed by walk_tune_key; on a miss bingo_autotune measures it on `starts` and the result is
+    stored (the file is replaced atomically).  Returns the shape and whether it came from the cache."""
+    import json
+
+    key = walk_tune_key(graph, length, device)
+    data = {"version": 1, "entries": {}}
+    if os.path.exists(cache_path):
+        with open(cache_path) as fh:
+            data = json.load(fh)
+    fields = ("lanes_per_walker", "warps_per_block", "blocks_per_sm", "reg_variant")
+    hit = data.get("entries", {}).get(key)
+    if hit is not None:
+        graph.set_walk_config(hit["lanes_per_walker"], hit["warps_per_block"], hit["blocks_per_sm"],
+                              hit["reg_variant"])
+        return dict(hit, cached=True)
+    cfg = graph.autotune(starts, length, stream=stream)
+    entry = {f: int(getattr(cfg, f)) for f in fields}
+    data.setdefault("entries", {})[key] = entry
+    tmp = f"{cache_path}.tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, cache_path)
+    return dict(entry, cached=False)
+
+
 def bingo_get_config(h):
     cfg = bingo_config()
     _err(load().bingo_get_config(h, c.byref(cfg)))
@@ -399,6 +445,12 @@ class Graph:
 
     def config(self):
         return bingo_get_config(self.h)
+
+    def state_sizes(self) -> dict:
+        return state_sizes(self.h)
+
+    def cached_walk_tune(self, starts, length, cache_path, device, stream=None) -> dict:
+        return cached_walk_tune(self, starts, length, cache_path, device, stream)
 
     def kernel_launches(self) -> int:
         return bingo_kernel_launches(self.h)
