@@ -14,7 +14,7 @@ import pytest
 import oracle as O
 import workloads as W
 from tests.conftest import golden
-from tests.stats import chisq_p, tv
+from tests.stats import binned, chisq_p, tv
 
 KIND = {"empty": O.EMPTY, "dense": O.DENSE, "one": O.ONE, "sparse": O.SPARSE, "regular": O.REGULAR}
 
@@ -235,6 +235,60 @@ def test_oracle_sampler_statistics():
         probs = w[a:b].astype(np.float64)
         assert tv(counts, probs) < 0.01
         assert chisq_p(counts, probs) > 1e-3
+
+
+def _one_step_counts(g, starts, seed, pol):
+    """Destination of the first step of o_walk from every start (length-1 walks)."""
+    paths, plen = g.walk(starts, [pol], seed=seed)
+    assert (plen == 2).all(), "every start has out-edges, so every length-1 walk takes its step"
+    return paths[:, 1]
+
+
+def test_oracle_walk_first_order_law():
+    """o_walk's first-order next hop (inverse transform over the walk's per-vertex u64 prefix
+    sums, the path every DeepWalk and PPR step and node2vec's first step take) against the
+    transition probability w_i / sum w of Section 2.1.  Several start vertices share one call,
+    including the first and last vertex of the graph, so each reads its own slice of the walk's
+    prefix-sum table.  Hubs with d > 1,000 are binned in edge order with exact bin masses (TV on
+    256 bins, chi-square on 1,000), and a hub with 31-bit biases has a total above 2^32."""
+    wl = W.make_workload("c1")
+    G = wl.graph
+    g = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    offs, dst, w, eid = g.edges()
+    vs = [0, 17, 511, G.n - 1]
+    N = 1_000_000
+    starts = np.repeat(np.array(vs, dtype=np.uint32), N)
+    for kind, n_pol in ((O.DEEPWALK, O.policy(O.DEEPWALK, 1)), (O.NODE2VEC, O.policy(O.NODE2VEC, 1, 0, (1 << 30, 1 << 31, 1 << 32)))):
+        x = _one_step_counts(g, starts, 11 + kind, n_pol)
+        for i, v in enumerate(vs):
+            a, b = int(offs[v]), int(offs[v + 1])
+            cats, inv = np.unique(dst[a:b], return_inverse=True)  # duplicates merged by summing weight
+            probs = np.bincount(inv, weights=w[a:b].astype(np.float64), minlength=len(cats))
+            xs = x[i * N:(i + 1) * N]
+            assert np.isin(xs, cats).all()
+            counts = np.bincount(np.searchsorted(cats, xs), minlength=len(cats))
+            assert tv(counts, probs) < 0.01, (kind, v)
+            assert chisq_p(counts, probs) > 1e-3, (kind, v)
+
+    # hubs: distinct destinations, so a sampled destination names its edge
+    rng = np.random.default_rng(5)
+    d = 5000
+    n = d + 3
+    hub_w = [rng.integers(1, 1 << 20, size=d), rng.integers(1, 1 << 31, size=d)]
+    edges = []
+    for h, ws in enumerate(hub_w):
+        edges += [(h, 3 + j, int(ws[j])) for j in range(d)]
+    edges += [(2, 0, 1), (2, 1, 3)] + [(3 + j, 2, 1) for j in range(d)]
+    g = O.Graph.from_edges(n, edges)
+    assert sum(int(x) for x in hub_w[1]) > 1 << 32
+    starts = np.repeat(np.array([0, 1], dtype=np.uint32), N)
+    x = _one_step_counts(g, starts, 23, O.policy(O.DEEPWALK, 1))
+    for h, ws in enumerate(hub_w):
+        counts = np.bincount(x[h * N:(h + 1) * N].astype(np.int64) - 3, minlength=d)
+        assert counts.sum() == N and len(counts) == d
+        probs = ws.astype(np.float64)
+        assert tv(*binned(counts, probs, 256)) < 0.01, h
+        assert chisq_p(*binned(counts, probs, 1000)) > 1e-3, h
 
 
 def test_ppr_length_truncated_geometric():
