@@ -52,6 +52,10 @@ def _L():
             lib = c.CDLL(_LIB)
             sig = {
                 "o_create": (c.c_void_p, [c.c_uint32, U64P, U32P, U32P]),
+                "o_create_ids": (c.c_void_p, [c.c_uint32, U64P, U32P, U32P, U64P, c.c_uint64]),
+                "o_apply_ids": (c.c_int, [c.c_void_p, U32P, c.c_uint64, c.c_uint32, U64P, U64P]),
+                "o_edges_of": (None, [c.c_void_p, U32P, c.c_uint64, U64P, U32P, U32P, U64P]),
+                "o_degree_sum": (c.c_uint64, [c.c_void_p, U32P, c.c_uint64]),
                 "o_destroy": (None, [c.c_void_p]),
                 "o_num_edges": (c.c_uint64, [c.c_void_p]),
                 "o_degree": (c.c_uint32, [c.c_void_p, c.c_uint32]),
@@ -122,6 +126,21 @@ class Graph:
             raise MemoryError("oracle graph")
 
     @classmethod
+    def from_csr_ids(cls, n: int, row_ptr, col, w, eid, next_eid: int):
+        """Oracle graph from CSR rows whose edges carry explicit ids (ascending within each row); later
+        insertions continue from next_eid.  Used to hold only some sources' rows of a larger graph."""
+        self = cls.__new__(cls)
+        self.n = int(n)
+        rp = np.ascontiguousarray(row_ptr, dtype=np.uint64)
+        co = np.ascontiguousarray(col, dtype=np.uint32)
+        ww = np.ascontiguousarray(w, dtype=np.uint32)
+        ee = np.ascontiguousarray(eid, dtype=np.uint64)
+        self._h = _L().o_create_ids(self.n, _p(rp), _p(co), _p(ww), _p(ee), int(next_eid))
+        if not self._h:
+            raise MemoryError("oracle graph")
+        return self
+
+    @classmethod
     def from_edges(cls, n, edges):
         """edges: iterable of (src, dst, w) in edge-id order (stable by source)."""
         e = sorted(enumerate(edges), key=lambda t: (t[1][0], t[0]))
@@ -155,6 +174,27 @@ class Graph:
         st = np.zeros(3, dtype=np.uint64)
         rc = _L().o_apply(self._h, _p(r), r.shape[0], max_bits, _p(st))
         return rc, tuple(int(x) for x in st)
+
+    def apply_ids(self, records: np.ndarray, ins_ids, max_bits: int = 32):
+        """apply() with the edge id of every insertion given (ins_ids[i] for record i; ignored for
+        deletions).  Returns (status, (inserted, deleted, not_found))."""
+        r = np.ascontiguousarray(records, dtype=np.uint32).reshape(-1, 4)
+        ids = np.ascontiguousarray(ins_ids, dtype=np.uint64)
+        assert len(ids) == r.shape[0]
+        st = np.zeros(3, dtype=np.uint64)
+        rc = _L().o_apply_ids(self._h, _p(r), r.shape[0], max_bits, _p(ids), _p(st))
+        return rc, tuple(int(x) for x in st)
+
+    def edges_of(self, ids):
+        """(offs u64[k+1], dst, w, eid) of the listed vertices (row i = ids[i]), ascending eid."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        m = int(_L().o_degree_sum(self._h, _p(ids), len(ids)))
+        offs = np.empty(len(ids) + 1, dtype=np.uint64)
+        dst = np.empty(max(m, 1), dtype=np.uint32)
+        w = np.empty(max(m, 1), dtype=np.uint32)
+        eid = np.empty(max(m, 1), dtype=np.uint64)
+        _L().o_edges_of(self._h, _p(ids), len(ids), _p(offs), _p(dst), _p(w), _p(eid))
+        return offs, dst[:m], w[:m], eid[:m]
 
     def set_lambda(self, lam: float) -> int:
         """Real-valued biases (Section 4.3): stored words are binary32 encodings, weights

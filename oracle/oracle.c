@@ -164,6 +164,20 @@ o_graph* o_create(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, cons
     return g;
 }
 
+/* The same with explicit edge ids: edge j of the CSR has id eid[j] (ascending within each row), and
+ * later insertions continue from next_eid.  A graph holding only some sources' rows keeps the ids
+ * those edges have in the whole graph (sampled-vertex parity: Section 5.2's batch semantics are per
+ * source, so a source's edges depend only on its own rows and records). */
+o_graph* o_create_ids(uint32_t n, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
+                      const uint64_t* eid, uint64_t next_eid) {
+    o_graph* g = o_create(n, row_ptr, col, w);
+    if (!g) return NULL;
+    for (uint32_t v = 0; v < n; v++)
+        for (uint64_t j = 0; j < g->a[v].len; j++) g->a[v].e[j].eid = eid[row_ptr[v] + j];
+    g->next_eid = next_eid;
+    return g;
+}
+
 void o_destroy(o_graph* g) {
     if (!g) return;
     for (uint32_t v = 0; v < g->n; v++) free(g->a[v].e);
@@ -259,7 +273,21 @@ int o_has_edge(const o_graph* g, uint32_t u, uint32_t x) {
  * the graph unchanged.
  * stats (nullable) = {inserted, deleted, not_found}.
  */
-int o_apply(o_graph* g, const uint32_t* rec, uint64_t count, uint32_t max_bits, uint64_t* stats) {
+typedef struct { uint32_t src; uint64_t idx; } o_del;
+static int o_del_cmp(const void* a, const void* b) {
+    const o_del* x = (const o_del*)a;
+    const o_del* y = (const o_del*)b;
+    if (x->src != y->src) return x->src < y->src ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+/* As o_apply, with the id of every insertion given: record i, if it inserts (op 0 or 2), adds edge
+ * id ins_eid[i].  Ids must exceed every id of the record's source and increase in batch order per
+ * source (o_apply passes next_eid, next_eid + 1, ... in batch order).  The deletions of different
+ * sources touch different lists, so they are applied source by source (sources in parallel); each
+ * source's deletions run in batch order. */
+int o_apply_ids(o_graph* g, const uint32_t* rec, uint64_t count, uint32_t max_bits, const uint64_t* ins_eid,
+                uint64_t* stats) {
     for (uint64_t i = 0; i < count; i++) {
         const uint32_t* r = rec + 4 * i;
         if (r[0] >= g->n || r[1] >= g->n || r[3] > 2) return O_INVALID;
@@ -274,18 +302,33 @@ int o_apply(o_graph* g, const uint32_t* rec, uint64_t count, uint32_t max_bits, 
             if (g->base4 && r[2] >= (1u << (2 * O_B4_POSITIONS))) return O_INVALID;
         }
     }
-    uint64_t ins = 0, del = 0, nf = 0;
+    uint64_t ins = 0, del = 0, nf = 0, ndel = 0;
     for (uint64_t i = 0; i < count; i++) {
         const uint32_t* r = rec + 4 * i;
         if (r[3] == 0 || r[3] == 2) {
-            o_edge x = {r[1], r[2], g->next_eid++};
+            o_edge x = {r[1], r[2], ins_eid[i]};
             if (adj_push(&g->a[r[0]], x) != O_OK) return O_NOMEM;
+            if (ins_eid[i] >= g->next_eid) g->next_eid = ins_eid[i] + 1;
             ins++;
         }
+        if (r[3] == 1 || r[3] == 2) ndel++;
     }
-    for (uint64_t i = 0; i < count; i++) {
-        const uint32_t* r = rec + 4 * i;
-        if (r[3] == 1 || r[3] == 2) {
+    o_del* dl = (o_del*)malloc(sizeof(o_del) * (ndel ? ndel : 1));
+    if (!dl) return O_NOMEM;
+    uint64_t t = 0;
+    for (uint64_t i = 0; i < count; i++)
+        if (rec[4 * i + 3] == 1 || rec[4 * i + 3] == 2) { dl[t].src = rec[4 * i]; dl[t].idx = i; t++; }
+    qsort(dl, ndel, sizeof(o_del), o_del_cmp); /* by source, then batch order */
+    uint64_t nrun = 0;
+    uint64_t* run = (uint64_t*)malloc(sizeof(uint64_t) * (ndel + 1));
+    if (!run) { free(dl); return O_NOMEM; }
+    for (uint64_t i = 0; i < ndel; i++)
+        if (i == 0 || dl[i].src != dl[i - 1].src) run[nrun++] = i;
+    run[nrun] = ndel;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : del, nf)
+    for (int64_t q = 0; q < (int64_t)nrun; q++) {
+        for (uint64_t i = run[q]; i < run[q + 1]; i++) {
+            const uint32_t* r = rec + 4 * dl[i].idx;
             o_adj* a = &g->a[r[0]];
             uint64_t j = 0;
             while (j < a->len && a->e[j].dst != r[1]) j++; /* ascending id: first hit is earliest */
@@ -295,8 +338,43 @@ int o_apply(o_graph* g, const uint32_t* rec, uint64_t count, uint32_t max_bits, 
             del++;
         }
     }
+    free(run);
+    free(dl);
     if (stats) { stats[0] = ins; stats[1] = del; stats[2] = nf; }
     return O_OK;
+}
+
+int o_apply(o_graph* g, const uint32_t* rec, uint64_t count, uint32_t max_bits, uint64_t* stats) {
+    uint64_t* ids = (uint64_t*)malloc(sizeof(uint64_t) * (count ? count : 1));
+    if (!ids) return O_NOMEM;
+    uint64_t next = g->next_eid;
+    for (uint64_t i = 0; i < count; i++) ids[i] = (rec[4 * i + 3] == 0 || rec[4 * i + 3] == 2) ? next++ : 0;
+    const int rc = o_apply_ids(g, rec, count, max_bits, ids, stats);
+    free(ids);
+    return rc;
+}
+
+/* Export the live edges of the listed vertices (row i = ids[i]) in ascending edge-id order;
+ * offs has count+1 entries. */
+void o_edges_of(const o_graph* g, const uint32_t* ids, uint64_t count, uint64_t* offs, uint32_t* dst, uint32_t* w,
+                uint64_t* eid) {
+    uint64_t p = 0;
+    for (uint64_t i = 0; i < count; i++) {
+        const o_adj* a = &g->a[ids[i]];
+        offs[i] = p;
+        for (uint64_t j = 0; j < a->len; j++, p++) {
+            dst[p] = a->e[j].dst;
+            w[p] = a->e[j].w;
+            eid[p] = a->e[j].eid;
+        }
+    }
+    offs[count] = p;
+}
+
+uint64_t o_degree_sum(const o_graph* g, const uint32_t* ids, uint64_t count) {
+    uint64_t s = 0;
+    for (uint64_t i = 0; i < count; i++) s += g->a[ids[i]].len;
+    return s;
 }
 
 /* ------------------------------------------------------------------------------ factorisation */

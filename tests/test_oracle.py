@@ -109,6 +109,82 @@ def test_update_semantics():
             assert got == exp, (b["why"], v)
 
 
+def _batch_by_definition(lists, next_eid, rec):
+    """Section 5.2's batch semantics written out: every insertion in batch order (new ids continue
+    the count), then every deletion in batch order, each removing the live copy of (src, dst) with
+    the smallest edge id; a bias change is one insertion plus one deletion."""
+    for s_, d_, b_, op in rec:
+        if op in (0, 2):
+            lists[s_].append((d_, b_, next_eid))
+            next_eid += 1
+    nf = 0
+    for s_, d_, b_, op in rec:
+        if op in (1, 2):
+            hit = [e for e in lists[s_] if e[0] == d_]
+            if not hit:
+                nf += 1
+                continue
+            lists[s_].remove(min(hit, key=lambda e: e[2]))
+    return next_eid, nf
+
+
+def test_batch_semantics_brute_force():
+    """Random tiny multigraphs with many duplicate (src, dst) pairs and batches mixing all three
+    operations: the oracle's adjacency equals the semantics written out in plain Python."""
+    rng = np.random.default_rng(17)
+    for trial in range(40):
+        n = 5
+        edges = [(int(rng.integers(0, n)), int(rng.integers(0, 3)), int(rng.integers(1, 16))) for _ in range(25)]
+        g = O.Graph.from_edges(n, edges)
+        lists = {v: [] for v in range(n)}
+        for eid_, (_, (s_, d_, b_)) in enumerate(sorted(enumerate(edges), key=lambda t: (t[1][0], t[0]))):
+            lists[s_].append((d_, b_, eid_))  # edge ids follow the CSR order
+        nxt = len(edges)
+        for _ in range(3):
+            rec = [(int(rng.integers(0, n)), int(rng.integers(0, 3)), int(rng.integers(1, 16)), int(rng.integers(0, 3)))
+                   for _ in range(int(rng.integers(1, 30)))]
+            rc, st = g.apply(np.array(rec, dtype=np.uint32))
+            nxt, nf = _batch_by_definition(lists, nxt, rec)
+            assert rc == 0 and st[2] == nf
+            offs, dst, w, eid = g.edges()
+            for v in range(n):
+                got = [(int(dst[j]), int(w[j]), int(eid[j])) for j in range(int(offs[v]), int(offs[v + 1]))]
+                assert got == lists[v], (trial, v)
+
+
+def test_sampled_sources_replay_equals_full_replay():
+    """A graph holding only some sources' rows, with their edge ids, that replays only those sources'
+    records with the insertion ids they have in the whole batch ends with the same edges as the whole
+    graph (batch semantics are per source, Section 5.2)."""
+    wl = W.make_workload("c1")
+    G = wl.graph
+    full = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    rp = G.row_ptr.astype(np.int64)
+    eid_all = np.arange(rp[-1], dtype=np.uint64)
+    same = O.Graph.from_csr_ids(G.n, G.row_ptr, G.col, G.w, eid_all, rp[-1])
+    assert all((a == b).all() for a, b in zip(same.edges(), full.edges()))
+    S = np.array([0, 3, 17, 200, 511, G.n - 1], dtype=np.uint32)
+    deg = rp[S + 1] - rp[S]
+    sub_rp = np.zeros(G.n + 1, dtype=np.uint64)
+    sub_rp[S.astype(np.int64) + 1] = deg
+    sub_rp = np.cumsum(sub_rp).astype(np.uint64)
+    rows = np.concatenate([np.arange(rp[v], rp[v + 1]) for v in S])
+    sub = O.Graph.from_csr_ids(G.n, sub_rp, G.col[rows], G.w[rows], rows.astype(np.uint64), rp[-1])
+    rec = wl.batches[0].records()
+    # duplicate deletions and bias changes of sampled sources too
+    extra = np.array([[int(S[1]), int(G.col[rp[S[1]]]), 0, 1]] * 3 + [[int(S[2]), int(G.col[rp[S[2]]]), 9, 2]],
+                     dtype=np.uint32)
+    rec = np.concatenate([rec, extra])
+    nxt = full.m
+    ins = (rec[:, 3] == 0) | (rec[:, 3] == 2)
+    ids = (nxt + np.cumsum(ins) - 1).astype(np.uint64)
+    assert full.apply(rec)[0] == 0
+    sel = np.isin(rec[:, 0], S)
+    assert sub.apply_ids(rec[sel], ids[sel])[0] == 0
+    a, b = full.edges_of(S), sub.edges_of(S)
+    assert all((x == y).all() for x, y in zip(a, b))
+
+
 def test_philox_known_answers():
     for vec in golden("philox_kat.json")["vectors"]:
         out = W.philox4x32_10([int(x, 16) for x in vec["ctr"]], [int(x, 16) for x in vec["key"]])
