@@ -129,6 +129,23 @@ typedef struct {
                                 uniform u32 < n2v_accept[dist]; values in [0, 2^32] = f(dist) / max f * 2^32 */
 } bingo_policy;
 
+/*
+ * Fill a walk policy (Section 2.2; Section 6.1 evaluation settings) from its
+ * real-valued parameters, so that callers need not derive the u32 thresholds:
+ *   PPR: ppr_stop_u32 = round(ppr_stop * 2^32), saturated at 2^32 - 1;
+ *        ppr_stop in [0, 1].
+ *   node2vec (Eq. node2vec): f(dist) = 1/p, 1, 1/q at distance 0, 1, 2;
+ *        n2v_accept[d] = round(f(d) / max f * 2^32), so a candidate at
+ *        distance d is accepted with probability f(d) / max f (exact when the
+ *        ratios are dyadic, e.g. p = 2, q = 0.5 gives 2^30, 2^31, 2^32);
+ *        p, q > 0 and finite.
+ *   DeepWalk: no parameters (ppr_stop, p, q ignored).
+ * Errors: BINGO_E_INVALID for an unknown kind, out-of-range parameters or a
+ * NULL out.  Host only; no device work.
+ */
+bingo_status bingo_policy_make(uint32_t kind, uint32_t max_len, double ppr_stop, double n2v_p, double n2v_q,
+                               bingo_policy* out);
+
 /* Library and build info. */
 const char* bingo_version(void);
 /* Thread-local message describing the last non-OK status on this thread. */
@@ -275,6 +292,31 @@ bingo_status bingo_walk_noalloc(bingo_graph* g, uint64_t nwalkers, const uint32_
  */
 bingo_status bingo_check(bingo_graph* g, void* stream);
 
+/*
+ * The walker's random numbers, evaluated on the device by the same code the
+ * walk kernels run, so that the generator can be checked against published
+ * known-answer vectors and other implementations.  The paper does not fix a
+ * generator; walks use Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3", SC'11).
+ *
+ * bingo_philox4x32_10: out[4i..4i+3] = Philox4x32-10(counter ctr[4i..4i+3],
+ *   key key[2i..2i+1]) for i < count (count <= 2^26).  Host pointers.
+ * bingo_walker_draws: the draws of walker `walker` at step `step` of a walk
+ *   with Philox key `seed` (key words: seed low, seed high), in the order the
+ *   walker consumes them: the u32 outputs of counters (walker low, walker
+ *   high, step, 0), (.., 1), ..., four words per counter in output order
+ *   (range 0); or, with range >= 1, successive exact uniform integers in
+ *   [0, range) drawn from that stream by Lemire's multiply-shift with
+ *   rejection (32-bit draws for range < 2^32, else two words, high first).
+ *   count <= 2^20; out is a host uint64[count].
+ * Both allocate scratch device memory on the current device and synchronise
+ * it.  Errors: BINGO_E_INVALID (bad sizes or NULL), BINGO_E_TIMEOUT (a
+ * bounded draw ran out of retries, probability below 2^-60), BINGO_E_CUDA.
+ */
+bingo_status bingo_philox4x32_10(uint64_t count, const uint32_t* ctr, const uint32_t* key, uint32_t* out);
+bingo_status bingo_walker_draws(uint64_t seed, uint64_t walker, uint32_t step, uint64_t range, uint32_t count,
+                                uint64_t* out);
+
 /* Sizes needed by bingo_export_state (host pointer). */
 typedef struct {
     uint64_t n;            /* vertices */
@@ -307,6 +349,29 @@ bingo_status bingo_state_sizes_get(bingo_graph* g, bingo_state_sizes* out);
 bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, uint32_t* bias, uint64_t* eid,
                                 uint32_t* cnt, uint8_t* kind, uint32_t* one_slot, uint32_t* glen, uint32_t* members,
                                 uint32_t* member_inv, uint32_t* sp_len, uint32_t* sp_list, uint32_t* sp_inv);
+
+/*
+ * The same export restricted to a list of vertices, for checking the state of
+ * graphs whose whole export does not fit host memory (parity on sampled
+ * vertices; per-source batch semantics, Section 5.2, make a source's state
+ * depend only on its own initial edges and records).
+ *   ids    uint32[count] caller vertex ids (host or device), each < n;
+ *          duplicates allowed; 1 <= count <= 2^31
+ *   sizes  host uint64[3]: {edges, list entries, sparse-list entries} of the
+ *          listed vertices (the sizes of dst/bias/eid, members/member_inv and
+ *          sp_list/sp_inv below)
+ * bingo_export_vertices fills the arrays of bingo_export_state with row i
+ * describing vertex ids[i]: deg[count], cnt/kind/one_slot/glen[32 count],
+ * sp_len[count], and the variable-length arrays concatenated in row order.
+ * Every output is a nullable host pointer.  Errors: BINGO_E_INVALID (an id
+ * >= n, count out of range), BINGO_E_STATE (an inconsistent stored
+ * destination), BINGO_E_CUDA.  Synchronises the device.
+ */
+bingo_status bingo_export_vertices_sizes(bingo_graph* g, const uint32_t* ids, uint64_t count, uint64_t sizes[3]);
+bingo_status bingo_export_vertices(bingo_graph* g, const uint32_t* ids, uint64_t count, uint32_t* deg, uint32_t* dst,
+                                   uint32_t* bias, uint64_t* eid, uint32_t* cnt, uint8_t* kind, uint32_t* one_slot,
+                                   uint32_t* glen, uint32_t* members, uint32_t* member_inv, uint32_t* sp_len,
+                                   uint32_t* sp_list, uint32_t* sp_inv);
 
 /*
  * Real-bias graphs (BINGO_BIAS_F32, Section 4.3): the decimal part q of every live

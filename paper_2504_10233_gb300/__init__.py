@@ -113,6 +113,12 @@ SIGNATURES = {
     "bingo_server_wait": (c.c_int, [VP, c.c_uint64, c.c_uint32, VP, VP, c.POINTER(c.c_uint64)]),
     "bingo_server_drain": (c.c_int, [VP, c.c_uint32]),
     "bingo_server_stats_get": (c.c_int, [VP, c.POINTER(bingo_server_stats)]),
+    "bingo_export_vertices_sizes": (c.c_int, [VP, VP, c.c_uint64, c.POINTER(c.c_uint64)]),
+    "bingo_export_vertices": (c.c_int, [VP, VP, c.c_uint64] + [VP] * 13),
+    "bingo_policy_make": (c.c_int, [c.c_uint32, c.c_uint32, c.c_double, c.c_double, c.c_double,
+                                    c.POINTER(bingo_policy)]),
+    "bingo_philox4x32_10": (c.c_int, [c.c_uint64, VP, VP, VP]),
+    "bingo_walker_draws": (c.c_int, [c.c_uint64, c.c_uint64, c.c_uint32, c.c_uint64, c.c_uint32, VP]),
 }
 
 _lock = threading.Lock()
@@ -167,20 +173,33 @@ def _stream(s):
 
 
 def policy(kind: int, max_len: int, ppr_stop: float | int = 0, n2v_pq=None) -> bingo_policy:
-    """Walk policy.  ppr_stop: probability (float) or u32 threshold (int).  n2v_pq = (p, q) for node2vec."""
+    """Walk policy through bingo_policy_make.  ppr_stop: probability (float) or u32 threshold (int).
+    n2v_pq = (p, q) for node2vec."""
     p = bingo_policy()
-    p.kind, p.max_len, p.reserved = kind, max_len, 0
-    if isinstance(ppr_stop, float):
-        ppr_stop = int(round(ppr_stop * 2 ** 32))
-    p.ppr_stop_u32 = int(ppr_stop)
-    if n2v_pq is not None:
-        pp, qq = n2v_pq
-        f = [1.0 / pp, 1.0, 1.0 / qq]
-        mf = max(f)
-        for i in range(3):
-            # exact for the dyadic ratios used here (1/4, 1/2, 1); general ratios round to the nearest u32 step
-            p.n2v_accept[i] = int(round(f[i] / mf * 2 ** 32))
+    pp, qq = n2v_pq if n2v_pq is not None else (1.0, 1.0)
+    prob = float(ppr_stop) if isinstance(ppr_stop, float) else 0.0
+    _err(load().bingo_policy_make(kind, max_len, prob, float(pp), float(qq), c.byref(p)))
+    if not isinstance(ppr_stop, float):
+        p.ppr_stop_u32 = int(ppr_stop)
     return p
+
+
+def bingo_philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 evaluated on the device by the walker's own code: ctr u32[count, 4], key u32[count, 2]."""
+    ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    key = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
+    assert len(ctr) == len(key)
+    out = np.zeros_like(ctr)
+    _err(load().bingo_philox4x32_10(len(ctr), _ptr(ctr), _ptr(key), _ptr(out)))
+    return out
+
+
+def bingo_walker_draws(seed: int, walker: int, step: int, count: int, range_: int = 0) -> np.ndarray:
+    """The draws walker `walker` makes at step `step` under key `seed` (raw u32 words, or bounded in
+    [0, range_) when range_ >= 1), evaluated on the device."""
+    out = np.zeros(count, dtype=np.uint64)
+    _err(load().bingo_walker_draws(int(seed), int(walker), int(step), int(range_), int(count), _ptr(out)))
+    return out
 
 
 def default_config(max_bits: int = 32, **kw) -> bingo_config:
@@ -364,6 +383,35 @@ def bingo_export_state(h):
     return out
 
 
+def bingo_export_vertices(h, ids):
+    """The state of the listed caller vertices (row i = ids[i]) in the layout of bingo_export_state."""
+    L = load()
+    ids = np.ascontiguousarray(np.asarray(ids, dtype=np.uint32))
+    k = len(ids)
+    sz = (c.c_uint64 * 3)()
+    _err(L.bingo_export_vertices_sizes(h, _ptr(ids), k, sz))
+    m, le, se = int(sz[0]), int(sz[1]), int(sz[2])
+    out = {
+        "deg": np.zeros(k, np.uint32), "dst": np.zeros(max(m, 1), np.uint32), "bias": np.zeros(max(m, 1), np.uint32),
+        "eid": np.zeros(max(m, 1), np.uint64), "cnt": np.zeros(32 * k, np.uint32), "kind": np.zeros(32 * k, np.uint8),
+        "one_slot": np.zeros(32 * k, np.uint32), "glen": np.zeros(32 * k, np.uint32),
+        "members": np.zeros(max(le, 1), np.uint32), "member_inv": np.zeros(max(le, 1), np.uint32),
+        "sp_len": np.zeros(k, np.uint32), "sp_list": np.zeros(max(se, 1), np.uint32),
+        "sp_inv": np.zeros(max(se, 1), np.uint32),
+    }
+    order = ["deg", "dst", "bias", "eid", "cnt", "kind", "one_slot", "glen", "members", "member_inv", "sp_len",
+             "sp_list", "sp_inv"]
+    _err(L.bingo_export_vertices(h, _ptr(ids), k, *[_ptr(out[x]) for x in order]))
+    for x in ("dst", "bias", "eid"):
+        out[x] = out[x][:m]
+    out["members"], out["member_inv"] = out["members"][:le], out["member_inv"][:le]
+    out["sp_list"], out["sp_inv"] = out["sp_list"][:se], out["sp_inv"][:se]
+    for x in ("cnt", "kind", "one_slot", "glen"):
+        out[x] = out[x].reshape(k, 32)
+    out["ids"] = ids
+    return out
+
+
 def bingo_export_decimal(h):
     """Decimal parts (units of 2^-8) of every live edge of a real-bias graph, in export order."""
     L = load()
@@ -427,6 +475,9 @@ class Graph:
 
     def export_state(self):
         return bingo_export_state(self.h)
+
+    def export_vertices(self, ids):
+        return bingo_export_vertices(self.h, ids)
 
     def export_decimal(self):
         return bingo_export_decimal(self.h)

@@ -1,4 +1,5 @@
 // C-ABI entry points for walks, the walker autotuner and device-status checks.
+#include <math.h>
 #include <string.h>
 
 #include <algorithm>
@@ -17,9 +18,6 @@ using namespace bingo;
 
 namespace bingo {
 bingo_status edge_index_build(bingo_graph* g, cudaStream_t s);
-}
-
-namespace {
 
 bingo_status check_policies(const bingo_policy* pols, uint32_t npol, uint32_t stride, bool have_lengths,
                             bool* need_n2v, uint32_t* max_len) {
@@ -45,6 +43,21 @@ bingo_status check_policies(const bingo_policy* pols, uint32_t npol, uint32_t st
     }
     return BINGO_OK;
 }
+
+bingo_status check_device(const bingo_graph* g, const char* who) {
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    if (dev != g->device) {
+        set_error("%s: the current device is %d but the graph lives on device %d", who, dev, g->device);
+        return BINGO_E_INVALID;
+    }
+    return BINGO_OK;
+}
+
+}  // namespace bingo
+
+namespace {
 
 // Host-output walk whose download overlaps the walk.  The one persistent launch counts finished
 // walkers per id-ordered chunk (walkers are taken from the queue in id order, so chunks finish
@@ -132,6 +145,23 @@ bingo_status walk_host_io_overlap(bingo_graph* g, WalkReq q, uint32_t* paths, ui
     return BINGO_OK;
 }
 
+// Philox4x32-10 of the walker on `count` (counter, key) tuples.
+__global__ void k_philox_eval(uint64_t count, const uint4* ctr, const uint2* key, uint4* out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = philox4x32_10(ctr[i], key[i]);
+}
+
+// The draws one walker makes at one step, in the order the walker consumes them: its raw u32
+// stream (range 0), or successive exact uniform integers in [0, range) (the bounded draws of group
+// selection and member picks).
+__global__ void k_walker_draws(uint2 key, uint64_t walker, uint32_t step, uint64_t range, uint32_t count,
+                               uint64_t* out, uint32_t* status) {
+    if (blockIdx.x || threadIdx.x) return;
+    StepRng R;
+    R.init(key, walker, step);
+    for (uint32_t i = 0; i < count; i++) out[i] = range ? below64(R, range, status) : (uint64_t)R.next();
+}
+
 }  // namespace
 
 extern "C" {
@@ -141,6 +171,8 @@ bingo_status bingo_walk(bingo_graph* g, uint64_t nwalkers, const uint32_t* start
                         uint32_t stride, uint32_t* paths, uint32_t* path_len, uint32_t mode, void* stream) {
     if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
     if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
+    bingo_status st = check_device(g, "walk");
+    if (st != BINGO_OK) return st;
     const uint32_t base_mode = mode & 0xFF;
     const bool pad = !(mode & 0x100);
     if (base_mode > BINGO_WALK_STEPWISE) { set_error("unknown walk mode %u", mode); return BINGO_E_INVALID; }
@@ -148,7 +180,7 @@ bingo_status bingo_walk(bingo_graph* g, uint64_t nwalkers, const uint32_t* start
     if (stride == 0) { set_error("stride must be >= 1"); return BINGO_E_INVALID; }
     bool need_n2v = false;
     uint32_t max_len = 0;
-    bingo_status st = check_policies(policies, npolicies, stride, lengths != nullptr, &need_n2v, &max_len);
+    st = check_policies(policies, npolicies, stride, lengths != nullptr, &need_n2v, &max_len);
     if (st != BINGO_OK) return st;
     if (nwalkers == 0) return BINGO_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -432,6 +464,74 @@ bingo_status bingo_autotune_adaption(uint32_t n, uint64_t m, const uint64_t* row
     }
     *out = best;
     if (out_cfg) bingo_get_config(best, out_cfg);
+    return BINGO_OK;
+}
+
+bingo_status bingo_policy_make(uint32_t kind, uint32_t max_len, double ppr_stop, double n2v_p, double n2v_q,
+                               bingo_policy* out) {
+    if (!out || kind > BINGO_NODE2VEC) { set_error("policy_make: bad kind or NULL output"); return BINGO_E_INVALID; }
+    memset(out, 0, sizeof(*out));
+    out->kind = kind;
+    out->max_len = max_len;
+    if (kind == BINGO_PPR) {
+        if (!(ppr_stop >= 0.0 && ppr_stop <= 1.0)) { set_error("policy_make: PPR stop %g outside [0, 1]", ppr_stop); return BINGO_E_INVALID; }
+        const double t = nearbyint(ppr_stop * 4294967296.0);
+        out->ppr_stop_u32 = t >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)t;
+    }
+    if (kind == BINGO_NODE2VEC) {
+        if (!(n2v_p > 0.0 && n2v_q > 0.0 && isfinite(n2v_p) && isfinite(n2v_q))) {
+            set_error("policy_make: node2vec p = %g, q = %g must be positive and finite", n2v_p, n2v_q);
+            return BINGO_E_INVALID;
+        }
+        // f(dist) of Eq. node2vec: 1/p at distance 0, 1 at distance 1, 1/q at distance 2
+        const double f[3] = {1.0 / n2v_p, 1.0, 1.0 / n2v_q};
+        const double mf = std::max(f[0], std::max(f[1], f[2]));
+        for (int d = 0; d < 3; d++) {
+            const double t = nearbyint(f[d] / mf * 4294967296.0);
+            out->n2v_accept[d] = t >= 4294967296.0 ? (1ull << 32) : (uint64_t)t;
+        }
+    }
+    return BINGO_OK;
+}
+
+bingo_status bingo_philox4x32_10(uint64_t count, const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+    if (count == 0) return BINGO_OK;
+    if (!ctr || !key || !out || count > (1ull << 26)) { set_error("philox4x32_10: bad arguments"); return BINGO_E_INVALID; }
+    Buf b;
+    CK(ensure(b, 40 * count), "philox4x32_10 buffers");
+    uint4* dc = (uint4*)b.p;
+    uint4* dout = dc + count;
+    uint2* dk = (uint2*)(dout + count);
+    cudaError_t e = cudaMemcpy(dc, ctr, 16 * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dk, key, 8 * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_philox_eval<<<(unsigned)std::min<uint64_t>((count + 255) / 256, 1024), 256>>>(count, dc, dk, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, 16 * count, cudaMemcpyDeviceToHost);
+    release(b);
+    return e == cudaSuccess ? BINGO_OK : cuda_fail(e, "philox4x32_10");
+}
+
+bingo_status bingo_walker_draws(uint64_t seed, uint64_t walker, uint32_t step, uint64_t range, uint32_t count,
+                                uint64_t* out) {
+    if (count == 0) return BINGO_OK;
+    if (!out || count > (1u << 20)) { set_error("walker_draws: bad arguments"); return BINGO_E_INVALID; }
+    Buf b;
+    CK(ensure(b, 8ull * count + 8), "walker_draws buffers");
+    uint32_t* dstatus = (uint32_t*)((uint64_t*)b.p + count);
+    cudaError_t e = cudaMemset(dstatus, 0, 4);
+    if (e == cudaSuccess) {
+        k_walker_draws<<<1, 32>>>(make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), walker, step, range, count,
+                                  (uint64_t*)b.p, dstatus);
+        e = cudaGetLastError();
+    }
+    uint32_t status = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(out, b.p, 8ull * count, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&status, dstatus, 4, cudaMemcpyDeviceToHost);
+    release(b);
+    if (e != cudaSuccess) return cuda_fail(e, "walker_draws");
+    if (status) { set_error("walker_draws: a bounded draw ran out of retries"); return BINGO_E_TIMEOUT; }
     return BINGO_OK;
 }
 

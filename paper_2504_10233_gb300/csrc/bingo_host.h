@@ -65,6 +65,24 @@ struct WalkReq {
 
 bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s);
 
+// Validate a host array of walk policies (kinds, node2vec thresholds <= 2^32, max_len + 1 <= stride
+// unless per-walker lengths are given); reports whether any is node2vec and the longest max_len.
+// Shared by every walk entry point so that they accept exactly the same inputs.
+bingo_status check_policies(const bingo_policy* pols, uint32_t npol, uint32_t stride, bool have_lengths,
+                            bool* need_n2v, uint32_t* max_len);
+
+// BINGO_E_INVALID unless the calling thread's current device is the graph's: every launch and every
+// device pointer of a call belongs to the device that was current when the graph was created.
+bingo_status check_device(const bingo_graph* g, const char* who);
+
+// Launch every walker kernel instance of the graph's weight mode once, over zero walkers, on `s`:
+// this loads each instance (lazy module loading would otherwise load it at its first real launch)
+// and sizes the context's local-memory reservation for it, both of which can allocate device memory.
+cudaError_t walk_preload(bingo_graph* g, cudaStream_t s);
+// Resolve, on the current device, the address of the allocation-free walk's fixed scratch array
+// (loading its module); later calls on that device reuse it.
+bingo_status noalloc_prepare(void);
+
 // Host-output walks of at least WALK_IO_MIN walkers download their rows in id-ordered chunks
 // (at most WALK_IO_MAX_CHUNKS) while the walk runs.
 constexpr uint64_t WALK_IO_MIN = 1ull << 17;

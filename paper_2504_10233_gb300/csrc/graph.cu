@@ -221,25 +221,29 @@ __global__ void k_order_perm(uint32_t n, const uint32_t* __restrict__ order, uin
 
 // ---- export ----------------------------------------------------------------------------------------------
 
-__global__ void k_export_sizes(DevGraph G, uint64_t* __restrict__ deg64, uint64_t* __restrict__ glen64,
+// Export row i is the caller's vertex ids[i] (ids null: vertex i), for i < count.
+__global__ void k_export_sizes(DevGraph G, const uint32_t* __restrict__ ids, uint64_t count,
+                               uint64_t* __restrict__ deg64, uint64_t* __restrict__ glen64,
                                uint64_t* __restrict__ nsp64) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t ve = warp; ve < G.n; ve += nwarps) {  // the caller's vertex order
+    for (uint64_t i = warp; i < count; i += nwarps) {
+        const uint64_t ve = ids ? ids[i] : i;  // the caller's id
         const uint64_t v = G.perm ? G.perm[ve] : ve;
         const VHdr h = load_hdr(G, v);
         const uint32_t c = cnt_ref(G, v, lane);
         const uint32_t kd = slot_kind(G, c, h.deg, lane);
-        glen64[ve * 32 + lane] = is_list(kd) ? c : 0;
+        glen64[i * 32 + lane] = is_list(kd) ? c : 0;
         if (lane == 0) {
-            deg64[ve] = h.deg;
-            nsp64[ve] = h.sref ? h.nsp : 0;
+            deg64[i] = h.deg;
+            nsp64[i] = h.sref ? h.nsp : 0;
         }
     }
 }
 
-__global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, const uint64_t* __restrict__ goff,
+__global__ void k_export_fill(DevGraph G, const uint32_t* __restrict__ ids, uint64_t count,
+                              const uint64_t* __restrict__ eoff, const uint64_t* __restrict__ goff,
                               const uint64_t* __restrict__ soff, uint32_t* __restrict__ odst,
                               uint32_t* __restrict__ obias, uint64_t* __restrict__ oeid, uint8_t* __restrict__ okind,
                               uint32_t* __restrict__ oone, uint32_t* __restrict__ ocnt, uint32_t* __restrict__ omem,
@@ -249,7 +253,8 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t ve = warp; ve < G.n; ve += nwarps) {  // the caller's vertex order and ids
+    for (uint64_t i = warp; i < count; i += nwarps) {
+        const uint64_t ve = ids ? ids[i] : i;  // the caller's id
         const uint64_t v = G.perm ? G.perm[ve] : ve;
         const VHdr h = load_hdr(G, v);
         const uint32_t d = h.deg, capa = capa_of(h), caps = caps_of(h);
@@ -258,9 +263,9 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
             const uint64_t* eids = adj_eids(G, h.adj, capa);
             for (uint32_t j = lane; j < d; j += 32) {
                 const uint2 e = pairs[j];
-                odst[eoff[ve] + j] = G.order ? G.order[e.x] : e.x;
-                obias[eoff[ve] + j] = G.base4 ? b4_value(e.y) : e.y;
-                oeid[eoff[ve] + j] = eids[j];
+                odst[eoff[i] + j] = G.order ? G.order[e.x] : e.x;
+                obias[eoff[i] + j] = G.base4 ? b4_value(e.y) : e.y;
+                oeid[eoff[i] + j] = eids[j];
             }
         }
         const uint32_t c = cnt_ref(G, v, lane);
@@ -271,8 +276,8 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
 #pragma unroll
         for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(FULL, wc, o);
         if (lane == 0 && (wc != G.vc[v].wcold || G.vh[v].word != (uint32_t)ve)) atomicAdd(bad, 1ull);
-        okind[ve * 32 + lane] = (uint8_t)kd;
-        ocnt[ve * 32 + lane] = c;
+        okind[i * 32 + lane] = (uint8_t)kd;
+        ocnt[i * 32 + lane] = c;
         uint32_t one_slot = NONE32;
         if (kd == K_ONE) {  // the stored reference is the destination; locate the member's slot
             const uint2* pairs = adj_pairs(G, h.adj);
@@ -280,7 +285,7 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
                 if ((pairs[j].y >> lane) & 1u) { one_slot = j; break; }
             if (one_slot == NONE32 || pairs[one_slot].x != gr) atomicAdd(bad, 1ull);
         }
-        oone[ve * 32 + lane] = one_slot;
+        oone[i * 32 + lane] = one_slot;
         const uint32_t listm = __ballot_sync(FULL, is_list(kd));
         for (uint32_t m = listm; m; m &= m - 1) {
             const uint32_t k = __ffs(m) - 1;
@@ -291,26 +296,26 @@ __global__ void k_export_fill(DevGraph G, const uint64_t* __restrict__ eoff, con
             const uint32_t* mdst = G.pool.base + g;
             const uint32_t* mem = mdst + icap;
             const uint32_t* inv = mem + icap;
-            const uint64_t o = goff[ve * 32 + k];
+            const uint64_t o = goff[i * 32 + k];
             const uint2* pairs = adj_pairs(G, h.adj);
             const uint32_t* S = h.sref ? G.pool.base + h.sref : nullptr;
-            for (uint32_t i = lane; i < ck; i += 32) {
-                const uint32_t x = mem[i];
-                omem[o + i] = x;
-                ominv[o + i] = x < icap ? inv[x] : NONE32;
+            for (uint32_t t = lane; t < ck; t += 32) {
+                const uint32_t x = mem[t];
+                omem[o + t] = x;
+                ominv[o + t] = x < icap ? inv[x] : NONE32;
                 // the stored destination must be the member's edge destination
                 uint32_t slot = x;
                 if (kk == K_SPARSE) slot = (S && x < h.nsp) ? S[x] : NONE32;
-                if (slot >= d || pairs[slot].x != mdst[i]) atomicAdd(bad, 1ull);
+                if (slot >= d || pairs[slot].x != mdst[t]) atomicAdd(bad, 1ull);
             }
         }
         if (h.sref) {
             const uint32_t* S = G.pool.base + h.sref;
             const uint32_t* Sinv = S + capa;
-            for (uint32_t i = lane; i < h.nsp; i += 32) {
-                const uint32_t x = S[i];
-                osp[soff[ve] + i] = x;
-                ospinv[soff[ve] + i] = x < capa ? Sinv[x] : NONE32;
+            for (uint32_t t = lane; t < h.nsp; t += 32) {
+                const uint32_t x = S[t];
+                osp[soff[i] + t] = x;
+                ospinv[soff[i] + t] = x < capa ? Sinv[x] : NONE32;
             }
         }
     }
@@ -600,6 +605,11 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
     g->launches++;
     if (!cu(cudaGetLastError(), "build fill") || !cu(cudaStreamSynchronize(s), "build fill")) { release_all(); return fail(st); }
     release_all();
+    // load the walker kernels of this weight format and resolve the allocation-free walk's scratch
+    // now, so that no later walk call triggers a lazy module load (which can allocate device memory)
+    if (!cu(walk_preload(g, s), "walker kernels preload") || !cu(cudaStreamSynchronize(s), "walker kernels preload"))
+        return fail(st);
+    if ((st = noalloc_prepare()) != BINGO_OK) return fail(st);
     g->m_live = m;
     g->next_eid = m;
     g->tune.lanes = c.lanes_per_walker ? c.lanes_per_walker : 1;
@@ -650,8 +660,11 @@ struct ExportPlan {
     }
 };
 
-static bingo_status export_plan(bingo_graph* g, ExportPlan& P, uint64_t totals[3]) {
-    const uint64_t n = g->n;
+// Sizes and offsets of the export rows: row i is the caller's vertex ids[i] (device array; null =
+// every vertex in id order), i < n.
+static bingo_status export_plan(bingo_graph* g, ExportPlan& P, uint64_t totals[3], const uint32_t* ids = nullptr,
+                                uint64_t count = ~0ull) {
+    const uint64_t n = ids ? count : g->n;
     CK(ensure(P.deg64, 8 * n), "export");
     CK(ensure(P.eoff, 8 * n), "export");
     CK(ensure(P.glen, 8 * 32 * n), "export");
@@ -660,7 +673,7 @@ static bingo_status export_plan(bingo_graph* g, ExportPlan& P, uint64_t totals[3
     CK(ensure(P.soff, 8 * n), "export");
     CK(ensure(P.tot, 64), "export");
     cudaStream_t s = 0;
-    k_export_sizes<<<grid_for(g, n * 32, 256), 256, 0, s>>>(g->G, (uint64_t*)P.deg64.p, (uint64_t*)P.glen.p,
+    k_export_sizes<<<grid_for(g, n * 32, 256), 256, 0, s>>>(g->G, ids, n, (uint64_t*)P.deg64.p, (uint64_t*)P.glen.p,
                                                             (uint64_t*)P.nsp.p);
     uint64_t* tot = (uint64_t*)P.tot.p;
     CK(scan_excl_u64((uint64_t*)P.deg64.p, (uint64_t*)P.eoff.p, n, tot + 0, g->s_tmp, s, &g->launches), "export scan");
@@ -722,16 +735,20 @@ bingo_status bingo_export_decimal(bingo_graph* g, uint8_t* q) {
     return BINGO_OK;
 }
 
-bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, uint32_t* bias, uint64_t* eid,
-                                uint32_t* cnt, uint8_t* kind, uint32_t* one_slot, uint32_t* glen, uint32_t* members,
-                                uint32_t* member_inv, uint32_t* sp_len, uint32_t* sp_list, uint32_t* sp_inv) {
-    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+}  // extern "C"
+
+// Export rows i < count of the caller's vertices ids[i] (device array; null = every vertex, count = n)
+// to host buffers, each nullable.
+static bingo_status export_rows(bingo_graph* g, const uint32_t* ids, uint64_t count, uint32_t* deg, uint32_t* dst,
+                                uint32_t* bias, uint64_t* eid, uint32_t* cnt, uint8_t* kind, uint32_t* one_slot,
+                                uint32_t* glen, uint32_t* members, uint32_t* member_inv, uint32_t* sp_len,
+                                uint32_t* sp_list, uint32_t* sp_inv) {
     CK(cudaDeviceSynchronize(), "sync");
     ExportPlan P;
     uint64_t t[3];
-    bingo_status st = export_plan(g, P, t);
+    bingo_status st = export_plan(g, P, t, ids, count);
     if (st != BINGO_OK) { P.release_all(); return st; }
-    const uint64_t n = g->n, m = t[0], L = t[1], S = t[2];
+    const uint64_t n = ids ? count : g->n, m = t[0], L = t[1], S = t[2];
     Buf o;
     // device staging: dst, bias (u32 m each), eid (u64 m), kind (u8 32n), one and cnt (u32 32n each), mem/minv (L),
     // sp/spinv (S)
@@ -751,7 +768,7 @@ bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, ui
     uint8_t* okind = (uint8_t*)p; p += 32 * n;
     unsigned long long* obad = (unsigned long long*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
     cudaMemset(obad, 0, 8);
-    k_export_fill<<<grid_for(g, n * 32, 256), 256>>>(g->G, (uint64_t*)P.eoff.p, (uint64_t*)P.goff.p,
+    k_export_fill<<<grid_for(g, n * 32, 256), 256>>>(g->G, ids, n, (uint64_t*)P.eoff.p, (uint64_t*)P.goff.p,
                                                      (uint64_t*)P.soff.p, odst, obias, oeid, okind, oone, ocnt, omem,
                                                      ominv, osp, ospinv, obad);
     e = cudaDeviceSynchronize();
@@ -795,6 +812,65 @@ bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, ui
         return BINGO_E_STATE;
     }
     return BINGO_OK;
+}
+
+// Upload and validate a host or device list of the caller's vertex ids.
+static bingo_status stage_ids(bingo_graph* g, const uint32_t* ids, uint64_t count, Buf& b, const uint32_t** out) {
+    if (!ids || count == 0 || count > (1ull << 31)) { set_error("export_vertices: need 1..2^31 vertex ids"); return BINGO_E_INVALID; }
+    std::vector<uint32_t> h;
+    const uint32_t* hp = ids;
+    if (is_device_ptr(ids)) {
+        h.resize(count);
+        CK(cudaMemcpy(h.data(), ids, 4 * count, cudaMemcpyDeviceToHost), "export_vertices ids");
+        hp = h.data();
+    }
+    for (uint64_t i = 0; i < count; i++)
+        if (hp[i] >= g->n) { set_error("export_vertices: id %u at %llu is >= n", hp[i], (unsigned long long)i); return BINGO_E_INVALID; }
+    CK(ensure(b, 4 * count), "export_vertices ids");
+    CK(cudaMemcpy(b.p, hp, 4 * count, cudaMemcpyHostToDevice), "export_vertices ids");
+    *out = (const uint32_t*)b.p;
+    return BINGO_OK;
+}
+
+extern "C" {
+
+bingo_status bingo_export_state(bingo_graph* g, uint32_t* deg, uint32_t* dst, uint32_t* bias, uint64_t* eid,
+                                uint32_t* cnt, uint8_t* kind, uint32_t* one_slot, uint32_t* glen, uint32_t* members,
+                                uint32_t* member_inv, uint32_t* sp_len, uint32_t* sp_list, uint32_t* sp_inv) {
+    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+    return export_rows(g, nullptr, g->n, deg, dst, bias, eid, cnt, kind, one_slot, glen, members, member_inv, sp_len,
+                       sp_list, sp_inv);
+}
+
+bingo_status bingo_export_vertices_sizes(bingo_graph* g, const uint32_t* ids, uint64_t count, uint64_t sizes[3]) {
+    if (!g || !sizes) { set_error("NULL argument"); return BINGO_E_INVALID; }
+    CK(cudaDeviceSynchronize(), "sync");
+    Buf b;
+    const uint32_t* dids = nullptr;
+    bingo_status st = stage_ids(g, ids, count, b, &dids);
+    if (st == BINGO_OK) {
+        ExportPlan P;
+        st = export_plan(g, P, sizes, dids, count);
+        P.release_all();
+    }
+    release(b);
+    return st;
+}
+
+bingo_status bingo_export_vertices(bingo_graph* g, const uint32_t* ids, uint64_t count, uint32_t* deg, uint32_t* dst,
+                                   uint32_t* bias, uint64_t* eid, uint32_t* cnt, uint8_t* kind, uint32_t* one_slot,
+                                   uint32_t* glen, uint32_t* members, uint32_t* member_inv, uint32_t* sp_len,
+                                   uint32_t* sp_list, uint32_t* sp_inv) {
+    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+    CK(cudaDeviceSynchronize(), "sync");
+    Buf b;
+    const uint32_t* dids = nullptr;
+    bingo_status st = stage_ids(g, ids, count, b, &dids);
+    if (st == BINGO_OK)
+        st = export_rows(g, dids, count, deg, dst, bias, eid, cnt, kind, one_slot, glen, members, member_inv, sp_len,
+                         sp_list, sp_inv);
+    release(b);
+    return st;
 }
 
 bingo_status bingo_memory_report(bingo_graph* g, uint64_t out[6]) {

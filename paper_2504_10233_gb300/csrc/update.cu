@@ -1534,6 +1534,10 @@ bingo_status bingo_apply_updates(bingo_graph* g, const bingo_update* ups, uint64
                                  bingo_update_stats* stats) {
     if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
     if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
+    {
+        const bingo_status ds = check_device(g, "apply_updates");
+        if (ds != BINGO_OK) return ds;
+    }
     if (count && !ups) { set_error("NULL update array"); return BINGO_E_INVALID; }
     if (count >= 0x3FFFFFFFull) { set_error("batch too large"); return BINGO_E_INVALID; }
     if (g->next_eid + count >= (1ull << 56)) { set_error("edge id space exhausted"); return BINGO_E_INVALID; }
@@ -1594,6 +1598,10 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
                                   bingo_update_stats* stats) {
     if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
     if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
+    {
+        const bingo_status ds = check_device(g, "stream_updates");
+        if (ds != BINGO_OK) return ds;
+    }
     if (count && !ups) { set_error("NULL update array"); return BINGO_E_INVALID; }
     if (count >= 0x7FFFFFFFull) { set_error("too many records"); return BINGO_E_INVALID; }
     if (g->next_eid + count >= (1ull << 56)) { set_error("edge id space exhausted"); return BINGO_E_INVALID; }

@@ -198,6 +198,13 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
     const uint64_t r = below64(R, tot, status);
     const uint64_t excl = incl - s;
     const uint32_t b = __ballot_sync(team_mask, r < incl && r >= excl) & team_mask;
+    if (b == 0) {  // r beyond every group: the counts disagree with the mask (never with a consistent state)
+        ks = 31;
+        cs = 0;
+        ref = 0;
+        if (tl == 0) atomicOr(status, ST_STATE);
+        return;
+    }
     const uint32_t owner = __ffs(b) - 1;
     uint32_t k_l = 0, c_l = 0, r_l = 0;
     if (lane_id() == owner) {
@@ -235,6 +242,13 @@ __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, c
     const uint64_t tot = __shfl_sync(FULL, incl, 31);
     const uint64_t r = below64(R, tot, status);
     const uint32_t b = __ballot_sync(FULL, r < incl);
+    if (b == 0) {  // only when the total is zero, which a vertex with out-edges never has
+        ks = 31;
+        cs = 0;
+        ref = 0;
+        if (lane == 0) atomicOr(status, ST_STATE);
+        return;
+    }
     ks = __ffs(b) - 1;
     cs = __shfl_sync(FULL, gk.x, ks);
     ref = __shfl_sync(FULL, gk.y, ks);
@@ -280,6 +294,7 @@ __device__ __forceinline__ uint32_t pick_member(const DevGraph& G, const Sec0& h
                                                 uint32_t ref, StepRng& R, uint32_t* status) {
     if constexpr (WM == WM_REAL)
         if (ks == DEC_SLOT) return pick_decimal(G, h, cs, ref, R, status);
+    if (cs == 0) return NONE32;  // no group was selected (the selection flagged ST_STATE)
     const uint32_t kd = kind_of(cs, h.deg, G.alpha, G.beta);
     if (kd == K_DENSE) {
         const uint2* pairs = adj_pairs(G, words_of(h.adj));
@@ -568,6 +583,33 @@ static int walk_blocks_per_sm(int lanes, int wpb, int occ, int wm) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk_kernel(lanes, occ, wm), wpb * 32, 0);
     c = nb < 1 ? 1 : nb;
     return c;
+}
+
+// Every walker instance of the graph's weight mode is launched once over zero walkers: the launch
+// loads its module (lazy loading) and grows the context's local-memory reservation to the kernel's
+// frame, so no later walk launch does either (both can allocate device memory).
+cudaError_t walk_preload(bingo_graph* g, cudaStream_t s) {
+    const int wm = weight_mode(g);
+    WalkParams A;
+    memset(&A, 0, sizeof(A));
+    A.queue = (unsigned long long*)((uint64_t*)g->d_ctl + CTL_QUEUE);
+    A.status = (uint32_t*)((uint64_t*)g->d_ctl + CTL_STATUS);
+    A.stride = 1;
+    A.npol = 1;
+    void* args[] = {(void*)&g->G, (void*)&A};
+    for (int occ = 0; occ < 2; occ++)
+        for (int lanes : {1, 4, 32}) {
+            const cudaError_t e = cudaLaunchKernel(walk_kernel(lanes, occ, wm), dim3(1), dim3(32), args, 0, s);
+            if (e != cudaSuccess) return e;
+            g->launches++;
+        }
+    if (wm == WM_REAL) k_walk_step<WM_REAL><<<1, 32, 0, s>>>(g->G, A, 0);
+    else if (wm == WM_B4) k_walk_step<WM_B4><<<1, 32, 0, s>>>(g->G, A, 0);
+    else k_walk_step<WM_INT><<<1, 32, 0, s>>>(g->G, A, 0);
+    g->launches++;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), s);
 }
 
 // Launch the walk on device buffers (all pointers device).  Pre: policies validated.
