@@ -56,6 +56,7 @@ def _L():
                 "o_apply_ids": (c.c_int, [c.c_void_p, U32P, c.c_uint64, c.c_uint32, U64P, U64P]),
                 "o_edges_of": (None, [c.c_void_p, U32P, c.c_uint64, U64P, U32P, U32P, U64P]),
                 "o_degree_sum": (c.c_uint64, [c.c_void_p, U32P, c.c_uint64]),
+                "o_count_edges": (None, [c.c_void_p, U32P, U32P, c.c_uint64, U32P]),
                 "o_destroy": (None, [c.c_void_p]),
                 "o_num_edges": (c.c_uint64, [c.c_void_p]),
                 "o_degree": (c.c_uint32, [c.c_void_p, c.c_uint32]),
@@ -75,6 +76,7 @@ def _L():
                                   c.c_uint64, U32P, U32P]),
                 "o_sample_many": (None, [c.c_void_p, c.c_uint32, c.c_uint64, c.c_uint64, U64P]),
                 "o_num_threads": (c.c_int, []),
+                "o_set_threads": (None, [c.c_int]),
                 "o_float_factor": (None, [c.c_uint64, DP, c.c_double, U32P, U64P, DP, DP]),
                 "o_set_lambda": (c.c_int, [c.c_void_p, c.c_double]),
                 "o_set_base4": (c.c_int, [c.c_void_p]),
@@ -103,6 +105,11 @@ def kind(cnt: int, d: int, alpha: int = 40, beta: int = 10) -> int:
 
 def num_threads() -> int:
     return _L().o_num_threads()
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on."""
+    _L().o_set_threads(int(n))
 
 
 def policy(kind_: int, max_len: int, ppr_stop_u32: int = 0, n2v_accept=(0, 0, 0)) -> OPolicy:
@@ -184,6 +191,14 @@ class Graph:
         st = np.zeros(3, dtype=np.uint64)
         rc = _L().o_apply_ids(self._h, _p(r), r.shape[0], max_bits, _p(ids), _p(st))
         return rc, tuple(int(x) for x in st)
+
+    def count_edges(self, us, xs):
+        """Live copies of every (us[i], xs[i])."""
+        us = np.ascontiguousarray(us, dtype=np.uint32)
+        xs = np.ascontiguousarray(xs, dtype=np.uint32)
+        out = np.zeros(len(us), dtype=np.uint32)
+        _L().o_count_edges(self._h, _p(us), _p(xs), len(us), _p(out))
+        return out
 
     def edges_of(self, ids):
         """(offs u64[k+1], dst, w, eid) of the listed vertices (row i = ids[i]), ascending eid."""

@@ -281,11 +281,20 @@ static int o_del_cmp(const void* a, const void* b) {
     return x->idx < y->idx ? -1 : (x->idx > y->idx);
 }
 
+static int o_u32_cmp(const void* a, const void* b) {
+    const uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+    return x < y ? -1 : (x > y);
+}
+
 /* As o_apply, with the id of every insertion given: record i, if it inserts (op 0 or 2), adds edge
  * id ins_eid[i].  Ids must exceed every id of the record's source and increase in batch order per
- * source (o_apply passes next_eid, next_eid + 1, ... in batch order).  The deletions of different
- * sources touch different lists, so they are applied source by source (sources in parallel); each
- * source's deletions run in batch order. */
+ * source (o_apply passes next_eid, next_eid + 1, ... in batch order).
+ * Deletions (Section 5.2): each removes the live copy of (src, dst) with the smallest edge id, in
+ * batch order.  Deletions of different sources touch different lists and deletions of different
+ * destinations of one source touch different copies, so a source whose batch deletes destination x
+ * r times loses the r earliest live copies of x (all of them if it has fewer; the rest are not
+ * found).  Each source is therefore applied in one pass over its list in edge-id order, dropping
+ * an edge while its destination still has deletions left (sources in parallel). */
 int o_apply_ids(o_graph* g, const uint32_t* rec, uint64_t count, uint32_t max_bits, const uint64_t* ins_eid,
                 uint64_t* stats) {
     for (uint64_t i = 0; i < count; i++) {
@@ -314,31 +323,49 @@ int o_apply_ids(o_graph* g, const uint32_t* rec, uint64_t count, uint32_t max_bi
         if (r[3] == 1 || r[3] == 2) ndel++;
     }
     o_del* dl = (o_del*)malloc(sizeof(o_del) * (ndel ? ndel : 1));
-    if (!dl) return O_NOMEM;
+    uint32_t* dd = (uint32_t*)malloc(sizeof(uint32_t) * (ndel ? ndel : 1));
+    uint64_t* run = (uint64_t*)malloc(sizeof(uint64_t) * (ndel + 1));
+    if (!dl || !dd || !run) { free(dl); free(dd); free(run); return O_NOMEM; }
     uint64_t t = 0;
     for (uint64_t i = 0; i < count; i++)
         if (rec[4 * i + 3] == 1 || rec[4 * i + 3] == 2) { dl[t].src = rec[4 * i]; dl[t].idx = i; t++; }
-    qsort(dl, ndel, sizeof(o_del), o_del_cmp); /* by source, then batch order */
+    qsort(dl, ndel, sizeof(o_del), o_del_cmp); /* by source */
     uint64_t nrun = 0;
-    uint64_t* run = (uint64_t*)malloc(sizeof(uint64_t) * (ndel + 1));
-    if (!run) { free(dl); return O_NOMEM; }
-    for (uint64_t i = 0; i < ndel; i++)
+    for (uint64_t i = 0; i < ndel; i++) {
         if (i == 0 || dl[i].src != dl[i - 1].src) run[nrun++] = i;
+        dd[i] = rec[4 * dl[i].idx + 1];
+    }
     run[nrun] = ndel;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : del, nf)
     for (int64_t q = 0; q < (int64_t)nrun; q++) {
-        for (uint64_t i = run[q]; i < run[q + 1]; i++) {
-            const uint32_t* r = rec + 4 * dl[i].idx;
-            o_adj* a = &g->a[r[0]];
-            uint64_t j = 0;
-            while (j < a->len && a->e[j].dst != r[1]) j++; /* ascending id: first hit is earliest */
-            if (j == a->len) { nf++; continue; }
-            memmove(a->e + j, a->e + j + 1, sizeof(o_edge) * (a->len - j - 1));
-            a->len--;
-            del++;
+        /* this source's deleted destinations, sorted; left[k] deletions of dd[a + k] remain */
+        const uint64_t a = run[q], k = run[q + 1] - run[q];
+        uint32_t* xs = dd + a;
+        qsort(xs, k, sizeof(uint32_t), o_u32_cmp);
+        uint32_t* left = (uint32_t*)calloc(k, sizeof(uint32_t));
+        uint64_t nu = 0;
+        for (uint64_t j = 0; j < k; j++) {
+            if (nu && xs[nu - 1] == xs[j]) { left[nu - 1]++; continue; }
+            xs[nu] = xs[j];
+            left[nu++] = 1;
         }
+        o_adj* A = &g->a[dl[a].src];
+        uint64_t w = 0;
+        for (uint64_t j = 0; j < A->len; j++) {  /* ascending edge id */
+            uint64_t lo = 0, hi = nu;
+            while (lo < hi) {
+                const uint64_t mid = (lo + hi) / 2;
+                if (xs[mid] < A->e[j].dst) lo = mid + 1; else hi = mid;
+            }
+            if (lo < nu && xs[lo] == A->e[j].dst && left[lo]) { left[lo]--; del++; continue; }
+            A->e[w++] = A->e[j];
+        }
+        A->len = w;
+        for (uint64_t j = 0; j < nu; j++) nf += left[j];
+        free(left);
     }
     free(run);
+    free(dd);
     free(dl);
     if (stats) { stats[0] = ins; stats[1] = del; stats[2] = nf; }
     return O_OK;
@@ -369,6 +396,47 @@ void o_edges_of(const o_graph* g, const uint32_t* ids, uint64_t count, uint64_t*
         }
     }
     offs[count] = p;
+}
+
+/* Live copies of (us[i], xs[i]) for i < count: each source's list is sorted once by destination
+ * (a copy) and searched for its queries (sources in parallel). */
+typedef struct { uint32_t u; uint64_t i; } o_query;
+static int o_query_cmp(const void* a, const void* b) {
+    const o_query* x = (const o_query*)a;
+    const o_query* y = (const o_query*)b;
+    if (x->u != y->u) return x->u < y->u ? -1 : 1;
+    return x->i < y->i ? -1 : (x->i > y->i);
+}
+void o_count_edges(const o_graph* g, const uint32_t* us, const uint32_t* xs, uint64_t count, uint32_t* out) {
+    o_query* q = (o_query*)malloc(sizeof(o_query) * (count ? count : 1));
+    uint64_t* run = (uint64_t*)malloc(sizeof(uint64_t) * (count + 1));
+    for (uint64_t i = 0; i < count; i++) { q[i].u = us[i]; q[i].i = i; }
+    qsort(q, count, sizeof(o_query), o_query_cmp);
+    uint64_t nrun = 0;
+    for (uint64_t i = 0; i < count; i++)
+        if (i == 0 || q[i].u != q[i - 1].u) run[nrun++] = i;
+    run[nrun] = count;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < (int64_t)nrun; r++) {
+        const uint32_t u = q[run[r]].u;
+        const o_adj* A = u < g->n ? &g->a[u] : NULL;
+        const uint64_t d = A ? A->len : 0;
+        uint32_t* row = (uint32_t*)malloc(sizeof(uint32_t) * (d ? d : 1));
+        for (uint64_t j = 0; j < d; j++) row[j] = A->e[j].dst;
+        qsort(row, d, sizeof(uint32_t), o_u32_cmp);
+        for (uint64_t t = run[r]; t < run[r + 1]; t++) {
+            const uint32_t x = xs[q[t].i];
+            uint64_t lo = 0, hi = d;
+            while (lo < hi) { const uint64_t mid = (lo + hi) / 2; if (row[mid] < x) lo = mid + 1; else hi = mid; }
+            uint64_t b = lo;
+            hi = d;
+            while (b < hi) { const uint64_t mid = (b + hi) / 2; if (row[mid] <= x) b = mid + 1; else hi = mid; }
+            out[q[t].i] = (uint32_t)(b - lo);
+        }
+        free(row);
+    }
+    free(run);
+    free(q);
 }
 
 uint64_t o_degree_sum(const o_graph* g, const uint32_t* ids, uint64_t count) {
@@ -678,6 +746,16 @@ void o_sample_many(const o_graph* g, uint32_t v, uint64_t count, uint64_t seed, 
         out[t] = its_search(c, a->len, o_below(&r, s));
     }
     free(c);
+}
+
+/* Threads for the OpenMP loops (walkers, per-source deletions); the bench times the oracle at one
+ * thread and at all host cores. */
+void o_set_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 int o_num_threads(void) {

@@ -185,6 +185,26 @@ def test_sampled_sources_replay_equals_full_replay():
     assert all((x == y).all() for x, y in zip(a, b))
 
 
+def test_count_edges_equals_has_edge():
+    """The batched live-copy count against the plain list scan (o_has_edge) and a count of the
+    exported adjacency, on c1 after its batch."""
+    wl = W.make_workload("c1")
+    G = wl.graph
+    g = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    g.apply(wl.batches[0].records(), G.max_bits)
+    offs, dst, _, _ = g.edges()
+    rng = np.random.default_rng(9)
+    us = rng.integers(0, G.n, 20000).astype(np.uint32)
+    xs = rng.integers(0, G.n, 20000).astype(np.uint32)
+    live = np.repeat(np.arange(G.n), np.diff(offs.astype(np.int64)))
+    us[:5000], xs[:5000] = live[:5000], dst[:5000]  # pairs that exist
+    got = g.count_edges(us, xs)
+    for u, x, c in zip(us[::7], xs[::7], got[::7]):
+        seg = dst[int(offs[u]):int(offs[u + 1])]
+        assert c == int((seg == x).sum()) and (c > 0) == g.has_edge(int(u), int(x))
+    assert (got[:5000] > 0).all()
+
+
 def test_philox_known_answers():
     for vec in golden("philox_kat.json")["vectors"]:
         out = W.philox4x32_10([int(x, 16) for x in vec["ctr"]], [int(x, 16) for x in vec["key"]])
