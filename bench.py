@@ -45,7 +45,9 @@ def peaks():
 # ------------------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms from before the warm-up (starting the
+    sampler costs seconds, which must not fall in the timed region); stop() keeps the samples read
+    inside the timed window [mark_start(), mark_end()]."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -55,6 +57,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -68,12 +71,20 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        if self.t1 is not None:  # one more sample period so the window's last sample is read
+            while time.perf_counter() < self.t1 + 0.25:
+                time.sleep(0.05)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -81,7 +92,13 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lo = self.t0 if self.t0 is not None else -1e300
+        hi = (self.t1 + 0.25) if self.t1 is not None else 1e300
+        inside = [ln for ts, ln in self.lines if lo <= ts <= hi]
+        if not inside and self.lines:  # a window shorter than the sampling period: the nearest sample
+            mid = 0.5 * (lo + hi) if self.t0 is not None and self.t1 is not None else self.lines[-1][0]
+            inside = [min(self.lines, key=lambda x: abs(x[0] - mid))[1]]
+        for ln in inside:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 8:
                 continue
@@ -160,7 +177,21 @@ def walk_bytes(per_vertex, paths, plen):
     return float(per_vertex[src].sum())
 
 
-def update_bytes(ex0, ex1, rec):
+def sample_steps(plen, k, seed):
+    """k steps drawn uniformly (with replacement) from all sampled steps of a launch: (walker, t) with
+    t < plen - 1; the step leaves from path entry t."""
+    steps = np.maximum(plen.astype(np.int64) - 1, 0)
+    cum = np.cumsum(steps)
+    tot = int(cum[-1]) if len(cum) else 0
+    if tot == 0:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64), 0
+    u = np.random.default_rng(seed).integers(0, tot, size=k)
+    w = np.searchsorted(cum, u, side="right")
+    t = u - (cum[w] - steps[w])
+    return w, t, tot
+
+
+def update_bytes(ex0, ex1, rec, ids=None):
     """Algorithmic bytes of one update batch, from the exported state before (ex0) and after (ex1) it:
     per record its 16 bytes and a sort by source (two passes of 16 bytes read + 16 written); per
     insertion the adjacency slot (32) and, for every set bit k whose group (v, k) is a member list
@@ -168,9 +199,16 @@ def update_bytes(ex0, ex1, rec):
     per deletion that finds its edge the locating probe (32), the adjacency slot (32), one compaction
     move (32), and for every set bit of the removed edge whose group was a list before the batch the
     entry, its inverted entry, the tail read and the patch (4 x 32); per touched vertex its count line
-    read and written (2 x 32 ceil(4 K_v / 32), K_v = highest nonempty group + 1 after the batch)."""
+    read and written (2 x 32 ceil(4 K_v / 32), K_v = highest nonempty group + 1 after the batch).
+    ids: when the exports hold only some vertices (bingo_export_vertices), the sorted vertex of each
+    row; they must include every source of the batch."""
     rec = np.asarray(rec, dtype=np.uint32).reshape(-1, 4)
     src = rec[:, 0].astype(np.int64)
+    if ids is not None:
+        ids = np.asarray(ids, dtype=np.int64)
+        row = np.searchsorted(ids, src)
+        assert (ids[np.minimum(row, len(ids) - 1)] == src).all(), "every source needs an exported row"
+        src = row
     op = rec[:, 3]
     ins, dele = op != 1, op != 0
     nbytes = 16.0 * len(rec) + 64.0 * float(ins.sum() + dele.sum())
@@ -239,49 +277,110 @@ def replica_seed(base: int, rank: int) -> int:
     return base + 0x9E3779B97F4A7C15 * rank & 0xFFFFFFFFFFFFFFFF
 
 
-# ------------------------------------------------------------------------------------- CPU baseline
+# ------------------------------------------------------------------------------------- workloads of the main line
 
-def cpu_baseline(G, batch, length, seed, target_s=15.0):
-    """The oracle as it stands, on a bounded sample: the first update batch applied, then as many
-    DeepWalk walkers as fit in about target_s seconds (calibrated on a small run)."""
-    import oracle as O
+SWEEP_SIZES = [10 ** e for e in range(3, 8)]
+SWEEP_REPS = 3  # per size: one untimed batch (capacity growth and graph capture happen there), two timed
 
-    og = O.Graph(G.n, G.row_ptr, G.col, G.w)
-    og.apply(batch.records(), G.max_bits)
-    pol = O.policy(O.DEEPWALK, length)
-    nw = 4096
-    st = W.walk_starts(G.n, nw, seed)
-    t0 = time.perf_counter()
-    _, plen = og.walk(st, [pol], seed)
-    dt = time.perf_counter() - t0
-    rate = max(float((plen.astype(np.int64) - 1).sum()) / max(dt, 1e-9), 1.0)
-    nw = int(min(1 << 22, max(nw, target_s * rate / max(length * 0.5, 1))))
-    st = W.walk_starts(G.n, nw, seed + 1)
-    t0 = time.perf_counter()
-    _, plen = og.walk(st, [pol], seed + 1)
-    dt = time.perf_counter() - t0
-    steps = float((plen.astype(np.int64) - 1).sum())
-    return {"value": steps / dt, "unit": "steps/s", "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{nw} DeepWalk walkers x {length} (uniform starts) on the same graph after its first "
-                      f"update batch; inverse-CDF over exact u64 prefix sums; {steps:.0f} steps in {dt:.1f} s"}
-
-
-# ------------------------------------------------------------------------------------- arms
-
-WORKLOAD_TEXT = {
-    "c2": "RMAT-20 (2^20 vertices, 2^24 edges, a=.57 b=.19 c=.19), floor(Pareto 1.5) biases <= 2^20; "
-          "per step: 10^5 updates (50/50) then 2^20 DeepWalk walkers x 80",
+MAIN = {
+    # RMAT-26 + 64 hubs, uniform 31-bit biases: per step a 10^6-record batch, then 16M PPR walkers
+    "c5": dict(policy="ppr", length=100, ppr_stop=0.15, batch=10 ** 6, sweep=True,
+               text="RMAT-26 (2^26 vertices, 2^30 edges) + 64 hubs x 10^6 extra out-edges, uniform biases in "
+                    "[1, 2^31); per step: 10^6 updates (50/50, hold-out protocol) then 16M PPR walkers "
+                    "(stop 0.15, cap 100)"),
+    # ER 1,024 / 16,384, biases U[1, 255]: per step a batch of 1,024 inserts + 1,024 deletes, then 1,024
+    # DeepWalk walkers x 80 (a correctness workload: its state fits L2)
+    "c1": dict(policy="deepwalk", length=80, ppr_stop=0.0, batch=2048, sweep=False,
+               text="ER directed (1,024 vertices, 16,384 edges), biases U[1, 255]; per step: 1,024 inserts + 1,024 "
+                    "deletes then 1,024 DeepWalk walkers x 80"),
+    # RMAT-20, floor(Pareto 1.5) biases: per step a 10^5-record batch, then 2^20 DeepWalk walkers x 80
+    "c2": dict(policy="deepwalk", length=80, ppr_stop=0.0, batch=10 ** 5, sweep=False,
+               text="RMAT-20 (2^20 vertices, 2^24 edges, a=.57 b=.19 c=.19), floor(Pareto 1.5) biases <= 2^20; "
+                    "per step: 10^5 updates (50/50) then 2^20 DeepWalk walkers x 80"),
 }
 
+POLICY_NAME = {"deepwalk": "DeepWalk", "ppr": "PPR (stop 0.15; x = cap)"}
 
 METRIC_MAIN = "sampled walk steps/s (update batch + walk per step); updated edges/s; p50/p99 latency in the serving bench"
 
 
-def main_config(args, wl):
-    """The workload part of the main line's config, shared by both arms."""
-    return {"workload": WORKLOAD_TEXT.get(args.workload, args.workload), "walkers": wl.nwalkers,
-            "length": wl.length, "updates_per_step": len(wl.batches[0])}
+def main_workload(name, nsteps):
+    """The workload and its per-step batches (plus, for c5, the records of the batch-size sweep): one
+    stream of hold-out-protocol records cut into consecutive batches."""
+    spec = MAIN[name]
+    extra = SWEEP_REPS * sum(SWEEP_SIZES) if spec["sweep"] else 0
+    if name in ("c1", "c2"):
+        wl = W.make_workload(name, nbatch=nsteps)
+        return wl, [b.records() for b in wl.batches], None
+    wl = W.make_workload(name, nbatch=1, batch=nsteps * spec["batch"] + extra)
+    rec = wl.batches[0].records()
+    b = spec["batch"]
+    return wl, [rec[i * b:(i + 1) * b] for i in range(nsteps)], rec[nsteps * b:]
 
+
+def main_config(args, wl, name=None):
+    """The workload part of the main line's config, shared by both arms."""
+    name = name or args.workload
+    spec = MAIN[name]
+    return {"workload": spec["text"], "walkers": wl.nwalkers, "length": spec["length"], "policy": spec["policy"],
+            "updates_per_step": spec["batch"]}
+
+
+def _oracle_policy(O, name):
+    spec = MAIN[name]
+    if spec["policy"] == "ppr":
+        return O.policy(O.PPR, spec["length"], int(round(spec["ppr_stop"] * 2 ** 32)))
+    return O.policy(O.DEEPWALK, spec["length"])
+
+
+# ------------------------------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(G, batch, length, seed, target_s=15.0, name="c2", one_thread_s=None):
+    """The oracle as it stands, on a bounded sample: the first update batch applied, then as many
+    walkers of the workload's policy as fit in about target_s seconds (calibrated on a small run), on
+    all host cores; with one_thread_s, the same at one thread on a sample sized for about that long."""
+    import oracle as O
+
+    og = O.Graph(G.n, G.row_ptr, G.col, G.w)
+    rec = batch.records() if hasattr(batch, "records") else batch
+    t0 = time.perf_counter()
+    og.apply(rec, G.max_bits)
+    t_apply = time.perf_counter() - t0
+    pol = _oracle_policy(O, name)
+    cores = O.num_threads()
+
+    def timed(nw, seed_):
+        st = W.walk_starts(G.n, nw, seed_)
+        t0 = time.perf_counter()
+        _, plen = og.walk(st, [pol], seed_)
+        return float((plen.astype(np.int64) - 1).sum()), time.perf_counter() - t0
+
+    def sized(budget_s, seed_):
+        steps, dt = timed(4096, seed_)
+        rate = max(steps / max(dt, 1e-9), 1.0)
+        nw = int(min(1 << 24, max(4096, budget_s * rate / max(length * 0.5, 1))))
+        steps, dt = timed(nw, seed_ + 1)
+        return nw, steps, dt
+
+    nw, steps, dt = sized(target_s, seed)
+    out = {"value": steps / dt, "unit": "steps/s", "cores": cores, "kind": "oracle",
+           "sample": f"{nw} {POLICY_NAME[MAIN[name]['policy']]} walkers x {length} (uniform starts) on the same graph after its "
+                     f"first update batch; inverse transform over exact u64 prefix sums (rebuilt by every walk call); "
+                     f"{steps:.0f} steps in {dt:.1f} s",
+           "updated_edges_per_s": len(rec) / t_apply, "update_sample": f"the first batch, {len(rec)} records"}
+    if one_thread_s:
+        O.set_threads(1)
+        try:
+            nw1, steps1, dt1 = sized(one_thread_s, seed + 7)
+        finally:
+            O.set_threads(cores)
+        out["one_thread"] = {"value": steps1 / dt1, "unit": "steps/s", "cores": 1,
+                             "sample": f"{nw1} walkers, {steps1:.0f} steps in {dt1:.1f} s"}
+    del og
+    return out
+
+
+# ------------------------------------------------------------------------------------- arms
 
 def run_reference(args):
     """Reference arm: the CPU oracle (the only reference this paper has), bounded sample per step."""
@@ -290,16 +389,16 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    wl = W.make_workload(args.workload, nbatch=args.steps + args.warmup)
+    wl, batches, _ = main_workload(args.workload, args.steps + args.warmup)
     G = wl.graph
     og = O.Graph(G.n, G.row_ptr, G.col, G.w)
-    pol = O.policy(O.DEEPWALK, wl.length)
+    pol = _oracle_policy(O, args.workload)
     nw = min(args.ref_walkers, wl.nwalkers)
     total_steps, total_t = 0.0, 0.0
     for i in range(args.warmup + args.steps):
         st = W.walk_starts(G.n, nw, 1000 + i)
         t0 = time.perf_counter()
-        og.apply(wl.batches[i].records(), G.max_bits)
+        og.apply(batches[i], G.max_bits)
         _, plen = og.walk(st, [pol], 1000 + i)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
@@ -313,10 +412,232 @@ def run_reference(args):
             "config": dict(main_config(args, wl), sample=f"{nw} of the {wl.nwalkers} walkers per step (bounded "
                                                           f"sample on host cores), every update of the batch"),
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": O.num_threads(), "kind": "oracle",
-                             "sample": f"per step: one batch of updates applied to the oracle, then {nw} walkers x "
-                                       f"{wl.length}"},
+                             "sample": f"per step: one batch of updates applied to the oracle, then {nw} walkers "
+                                       f"(cap {MAIN[args.workload]['length']})"},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _ev(torch):
+    return torch.cuda.Event(enable_timing=True)
+
+
+def _policies(B, name):
+    spec = MAIN[name]
+    if spec["policy"] == "ppr":
+        return [B.policy(B.PPR, spec["length"], spec["ppr_stop"])]
+    return [B.policy(B.DEEPWALK, spec["length"])]
+
+
+def walk_roofline(B, g, torch, paths, plen, walk_ms, pk, pk_src, traffic, nsample=10 ** 6):
+    """Algorithmic bytes of a walk launch from the per-step model: the mean model bytes of a step over
+    a uniform sample of the launch's steps (each counted from the exported state of the vertex it
+    leaves) times the launch's step count; over the launch's CUDA-event time."""
+    plen_h = plen.cpu().numpy().view(np.uint32)
+    w, t, tot = sample_steps(plen_h, nsample, 12345)
+    wi = torch.from_numpy(w).to(paths.device)
+    ti = torch.from_numpy(t).to(paths.device)
+    src = paths[wi, ti].cpu().numpy().view(np.uint32)
+    ids, row = np.unique(src, return_inverse=True)
+    exv = g.export_vertices(ids)
+    per = expected_bytes_per_vertex(exv)
+    bps = float(per[row].mean())
+    abytes = bps * tot
+    achieved = abytes / (walk_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": "k_walk_persistent",
+            "peak_source": f"{pk_src} hbm_gbs (copy bandwidth)", "bytes_per_step": bps, "steps_per_launch": tot,
+            "model": f"per-step model bytes averaged over {len(w)} uniformly sampled steps of the launch "
+                     f"({len(ids)} distinct vertices exported) x the launch's steps"}
+
+
+def update_roofline(g, rec_dev, rec, upd_ms_mean, pk, stream):
+    """The update byte model over one further batch of the stream (the touched vertices exported before
+    and after it, outside the timed region) over the mean time of the timed batches."""
+    ids = np.unique(rec[:, 0])
+    ex0 = g.export_vertices(ids)
+    g.apply_updates(rec_dev, stream=stream)
+    ex1 = g.export_vertices(ids)
+    ub = update_bytes(ex0, ex1, rec, ids=ids)
+    ach = ub / (upd_ms_mean / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+            "kernel": "update pipeline (one captured graph per batch)", "bytes_per_update": ub / len(rec),
+            "model": "per record, sort, locate, adjacency slot, list-group entries, count lines"}
+
+
+def run_main(args, name, dev, rank, ws, local, secondary=False):
+    """One main-workload run: W warm-up and K timed steps (update batch + walk), rooflines, end to end
+    through the C ABI with host buffers; for the headline also streaming, the batch sweep and the
+    oracle baseline.  Returns the line's fields."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2504_10233_gb300 as B
+
+    spec = MAIN[name]
+    nsteps = args.warmup + args.steps
+    t_setup = time.perf_counter()
+    # after the timed steps: one more batch for the update byte model and one for the end-to-end warm-up
+    wl, batches, sweep_rec = main_workload(name, nsteps + 2 + min(args.steps, 3))
+    t_gen = time.perf_counter() - t_setup
+    G = wl.graph
+    stream = torch.cuda.Stream(device=dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    t0 = time.perf_counter()
+    g = B.Graph(G.n, t(G.row_ptr), t(G.col), t(G.w), max_bits=G.max_bits)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    t_create = time.perf_counter() - t0
+    nw, L = wl.nwalkers, spec["length"]
+    stride = L + 1
+    starts = t(W.walk_starts(G.n, nw, wl.walk_seed))
+    paths = torch.empty((nw, stride), dtype=torch.int32, device=dev)
+    plen = torch.empty(nw, dtype=torch.int32, device=dev)
+    pol = _policies(B, name)
+    recs = [t(b) for b in batches]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    mode = B.WALK_PERSISTENT | B.WALK_NO_PAD
+    if args.autotune:
+        with torch.cuda.stream(stream):
+            g.autotune(starts, L, stream=stream)  # every walker: the tuned shape fits the whole launch
+    seed0 = replica_seed(wl.walk_seed, rank)
+
+    upd_ms, walk_ms, tot_steps, tot_upd = [], [], 0, 0
+    launches0 = None
+    sampler = ClockSampler(local)
+    if not secondary:
+        sampler.start()
+        time.sleep(0.5)  # the sampler's start-up stays out of the timed region
+    for i in range(nsteps):
+        timed = i >= args.warmup
+        if timed and launches0 is None:
+            if ws > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            launches0 = g.kernel_launches()
+            sampler.mark_start()
+            t_wall0 = time.perf_counter()
+        flush.fill_(i)  # L2 flush between steps (outside the events)
+        torch.cuda.synchronize()
+        e0, e1, e2 = _ev(torch), _ev(torch), _ev(torch)
+        e0.record(stream)
+        g.apply_updates(recs[i], stream=stream)
+        e1.record(stream)
+        g.walk(starts, pol, seed0 + i, stride, paths, plen, mode=mode, stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if timed:
+            upd_ms.append(e0.elapsed_time(e1))
+            walk_ms.append(e1.elapsed_time(e2))
+            tot_steps += int((plen.to(torch.int64) - 1).sum().item())
+            tot_upd += len(batches[i])
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall0
+    sampler.mark_end()
+    clocks = sampler.stop() if not secondary else None
+    launches = g.kernel_launches() - launches0
+    g.check(stream)
+    step_ms = [a + b for a, b in zip(upd_ms, walk_ms)]
+    t_total = max_over_ranks(sum(step_ms) / 1e3, dev)
+    all_steps = sum_over_ranks(float(tot_steps), dev)
+    value = all_steps / t_total
+    walk_rate = tot_steps / (sum(walk_ms) / 1e3)
+    upd_rate = tot_upd / (sum(upd_ms) / 1e3)
+    pk, pk_src = peaks()
+    traffic = args.traffic if args.traffic is not None else measured_traffic(name)
+    roof = walk_roofline(B, g, torch, paths, plen, walk_ms[-1], pk, pk_src, traffic)
+    upd_roof = update_roofline(g, recs[nsteps], batches[nsteps], float(np.mean(upd_ms)), pk, stream)
+
+    # end to end through the public API with host buffers (pinned): the batch's records and the walk
+    # starts go up, the lengths and the packed paths (bingo_walk_packed: no padding) come back
+    h_starts = torch.from_numpy(W.walk_starts(G.n, nw, wl.walk_seed)).pin_memory()
+    h_len = torch.empty(nw, dtype=torch.int32).pin_memory()
+    h_vert = torch.empty(nw * stride, dtype=torch.int32).pin_memory()
+    h_recs = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory() for b in batches[nsteps + 1:]]
+    e2e_steps, e2e_t, d2h = 0, 0.0, []
+    n_e2e = 0 if args.no_e2e else len(h_recs) - 1
+    for i in range(n_e2e + (1 if n_e2e else 0)):  # the first pass is an untimed warm-up (staging buffers)
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.apply_updates(h_recs[i], stream=stream)  # host records: H2D inside the call
+        tot = g.walk_packed(h_starts, pol, seed0 + 1000 + i, L, h_len, h_vert, stream=stream)
+        if i == 0:
+            continue
+        e2e_t += time.perf_counter() - t0
+        e2e_steps += tot - nw
+        d2h.append(4 * nw + 4 * tot)
+    e2e_t = max_over_ranks(e2e_t, dev)
+    e2e = {"value": sum_over_ranks(float(e2e_steps), dev) / e2e_t if e2e_t > 0 else None, "unit": "steps/s",
+           "h2d_bytes_per_step": int(h_starts.numel() * 4 + h_recs[0].numel() * 4),
+           "d2h_bytes_per_step": int(np.mean(d2h)) if d2h else 0,
+           "api": "bingo_apply_updates (host records) + bingo_walk_packed (host starts, lengths and packed paths)"}
+    out = {"value": value, "ms_per_step": 1e3 * t_total / args.steps, "walk_steps_per_s": walk_rate,
+           "updated_edges_per_s": upd_rate, "update_ms_per_step": float(np.mean(upd_ms)),
+           "walk_ms_per_step": float(np.mean(walk_ms)), "wall_s_timed": wall, "clocks": clocks, "e2e": e2e,
+           "gpu_launches": int(launches), "roofline": roof, "update_roofline": upd_roof,
+           "config": {**main_config(args, wl, name),
+                      "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); state > L2",
+                      "setup_s": {"generate": t_gen, "create": t_create},
+                      "walk_config": {"lanes_per_walker": g.config().lanes_per_walker,
+                                      "warps_per_block": g.config().warps_per_block,
+                                      "reg_variant": g.config().reg_variant}}}
+    del h_vert, h_len, h_starts, paths, plen
+    if not secondary and not args.no_e2e:
+        # streaming: records of the same stream applied as batches of one (Section 4.2), device buffers
+        srec = t(batches[-1][: args.stream_records])
+        torch.cuda.synchronize()
+        e0, e1 = _ev(torch), _ev(torch)
+        e0.record(stream)
+        g.stream_updates(srec, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        one_ms = []
+        for j in range(30):  # single-record calls: the latency of one streamed update through the API
+            t0 = time.perf_counter()
+            g.stream_updates(srec[j: j + 1], stream=stream)
+            one_ms.append(1e3 * (time.perf_counter() - t0))
+        sps = int(srec.shape[0]) / (e0.elapsed_time(e1) / 1e3)
+        out["streaming"] = {"records": int(srec.shape[0]), "updates_per_s": sps,
+                            "single_record_call_ms_median": float(np.median(one_ms)),
+                            "batched_over_streaming": upd_rate / sps}
+    if not secondary and sweep_rec is not None:
+        out["batch_sweep"] = update_sweep(g, torch, t, sweep_rec, stream)
+    if not secondary:
+        out["memory_bytes"] = g.memory_report()
+    g.close()
+    del recs, starts, g
+    torch.cuda.empty_cache()
+    if rank == 0 and ws == 1 and not secondary and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(G, batches[0], L, 77, args.cpu_seconds, name=name,
+                                           one_thread_s=args.cpu_seconds / 2)
+    return out
+
+
+def update_sweep(g, torch, t, rec, stream):
+    """Update batches of 10^3 .. 10^7 records (50/50) applied in place, consecutive slices of the same
+    stream; per size the median of the timed batches after one untimed one."""
+    off, sweep = 0, []
+    for sz in SWEEP_SIZES:
+        ms_rep, nf = [], 0
+        for rep in range(SWEEP_REPS):
+            r = t(rec[off: off + sz])
+            off += sz
+            torch.cuda.synchronize()
+            e0, e1 = _ev(torch), _ev(torch)
+            e0.record(stream)
+            st = g.apply_updates(r, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                ms_rep.append(e0.elapsed_time(e1))
+                nf += st["not_found"]
+        ms = float(np.median(ms_rep))
+        sweep.append({"batch": sz, "ms": ms, "updated_edges_per_s": sz / (ms / 1e3), "not_found": nf,
+                      "timed_batches": len(ms_rep)})
+    return sweep
 
 
 def run_ours(args):
@@ -332,175 +653,19 @@ def run_ours(args):
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
     B.load()
-    nsteps = args.warmup + args.steps
-    # after the timed steps: one more batch for the update byte model, and the last feeds the streaming measurement
-    wl = W.make_workload(args.workload, nbatch=nsteps + 2)
-    G = wl.graph
-    stream = torch.cuda.Stream(device=dev)
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    g = B.Graph(G.n, t(G.row_ptr), t(G.col), t(G.w), max_bits=G.max_bits)
-    nw = wl.nwalkers
-    stride = wl.length + 1
-    starts = t(W.walk_starts(G.n, nw, wl.walk_seed))
-    paths = torch.empty((nw, stride), dtype=torch.int32, device=dev)
-    plen = torch.empty(nw, dtype=torch.int32, device=dev)
-    pol = [B.policy(B.DEEPWALK, wl.length)]
-    recs = [t(b.records()) for b in wl.batches]
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    mode = B.WALK_PERSISTENT | B.WALK_NO_PAD
-    if args.autotune:
-        with torch.cuda.stream(stream):
-            g.autotune(starts, wl.length, stream=stream)  # every walker: the tuned shape fits the whole launch
-    seed0 = replica_seed(wl.walk_seed, rank)
-
-    ev = lambda: torch.cuda.Event(enable_timing=True)
-    upd_ms, walk_ms, tot_steps, tot_upd = [], [], 0, 0
-    launches0 = None
-    sampler = ClockSampler(local)
-    for i in range(nsteps):
-        timed = i >= args.warmup
-        if timed and launches0 is None:
-            if ws > 1:
-                dist.barrier()
-            torch.cuda.synchronize()
-            launches0 = g.kernel_launches()
-            sampler.start()
-            t_wall0 = time.perf_counter()
-        flush.fill_(i)  # L2 flush between steps (outside the events)
-        torch.cuda.synchronize()
-        e0, e1, e2 = ev(), ev(), ev()
-        e0.record(stream)
-        st = g.apply_updates(recs[i], stream=stream)
-        e1.record(stream)
-        g.walk(starts, pol, seed0 + i, stride, paths, plen, mode=mode, stream=stream)
-        e2.record(stream)
-        torch.cuda.synchronize()
-        if timed:
-            upd_ms.append(e0.elapsed_time(e1))
-            walk_ms.append(e1.elapsed_time(e2))
-            tot_steps += int((plen.to(torch.int64) - 1).sum().item())
-            tot_upd += len(wl.batches[i])
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    wall = time.perf_counter() - t_wall0
-    clocks = sampler.stop()
-    launches = g.kernel_launches() - launches0
-    g.check(stream)
-    step_ms = [a + b for a, b in zip(upd_ms, walk_ms)]
-    t_total = max_over_ranks(sum(step_ms) / 1e3, dev)
-    all_steps = sum_over_ranks(float(tot_steps), dev)
-    value = all_steps / t_total
-    walk_rate = tot_steps / (sum(walk_ms) / 1e3)
-    upd_rate = tot_upd / (sum(upd_ms) / 1e3)
-
-    # roofline of the walk kernel from the current state and the last timed walk's paths
-    ex = g.export_state()
-    per_v = expected_bytes_per_vertex(ex)
-    p_np = paths.cpu().numpy().view(np.uint32)
-    l_np = plen.cpu().numpy().view(np.uint32)
-    abytes = walk_bytes(per_v, p_np, l_np)
-    pk, pk_src = peaks()
-    achieved = abytes / (walk_ms[-1] / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"],
-            "traffic": args.traffic if args.traffic is not None else measured_traffic(args.workload),
-            "kernel": "k_walk_persistent", "peak_source": f"{pk_src} hbm_gbs (copy bandwidth)",
-            "bytes_per_step": abytes / max(1, int((l_np.astype(np.int64) - 1).sum()))}
-
-    # the update roofline: the byte model over one further batch of the same stream (state exported before
-    # and after it, outside the timed region) divided by the mean time of the timed batches
-    g.apply_updates(recs[nsteps], stream=stream)
-    ub = update_bytes(ex, g.export_state(), wl.batches[nsteps].records())
-    upd_achieved = ub / (float(np.mean(upd_ms)) / 1e3) / 1e9
-    upd_roof = {"bound": "hbm", "achieved": upd_achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": upd_achieved / pk["hbm_gbs"], "kernel": "update pipeline (one captured graph per batch)",
-                "bytes_per_update": ub / len(wl.batches[nsteps]),
-                "model": "per record, sort, locate, adjacency slot, list-group entries, count lines"}
-
-    # end to end through the public API with host buffers (pinned), copies inside the timed region
-    h_starts = torch.from_numpy(W.walk_starts(G.n, nw, wl.walk_seed)).pin_memory()
-    h_paths = torch.empty((nw, stride), dtype=torch.int32).pin_memory()
-    h_plen = torch.empty(nw, dtype=torch.int32).pin_memory()
-    h_recs = [torch.from_numpy(np.ascontiguousarray(b.records())).pin_memory() for b in wl.batches]
-    e2e_steps, e2e_t = 0, 0.0
-    n_e2e = 0 if args.no_e2e else min(args.steps, 3)
-    for i in range(n_e2e + (1 if n_e2e else 0)):  # the first pass is an untimed warm-up (staging buffers)
-        flush.fill_(i)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        g.apply_updates(h_recs[i % len(h_recs)], stream=stream)  # host records: H2D inside the call
-        # padded form: the call writes every entry of the host rows, so nothing is uploaded first
-        g.walk(h_starts, pol, seed0 + 1000 + i, stride, h_paths, h_plen, mode=B.WALK_PERSISTENT, stream=stream)
-        if i == 0:
-            continue
-        e2e_t += time.perf_counter() - t0
-        e2e_steps += int((h_plen.numpy().astype(np.int64) - 1).sum())
-    e2e_t = max_over_ranks(e2e_t, dev)
-    e2e = {"value": sum_over_ranks(float(e2e_steps), dev) / e2e_t if e2e_t > 0 else None, "unit": "steps/s",
-           "h2d_bytes_per_step": int(h_starts.numel() * 4 + h_recs[0].numel() * 4),
-           "d2h_bytes_per_step": int(h_paths.numel() * 4 + h_plen.numel() * 4)}
-    if n_e2e:
-        # context for the end-to-end number: one plain device-to-pinned-host copy of the path buffer
-        c0, c1 = ev(), ev()
-        with torch.cuda.stream(stream):
-            c0.record(stream)
-            h_paths.copy_(paths, non_blocking=True)
-            c1.record(stream)
-        torch.cuda.synchronize()
-        e2e["d2h_copy_gbs"] = h_paths.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
-        # the same copy split into four parts on four streams (several copy engines)
-        cs = [torch.cuda.Stream(device=dev) for _ in range(4)]
-        parts = np.linspace(0, nw, 5).astype(int)
-        c0, ends = ev(), [ev() for _ in cs]
-        c0.record(stream)
-        for k, sk in enumerate(cs):
-            sk.wait_event(c0)
-            with torch.cuda.stream(sk):
-                h_paths[parts[k]:parts[k + 1]].copy_(paths[parts[k]:parts[k + 1]], non_blocking=True)
-                ends[k].record(sk)
-        torch.cuda.synchronize()
-        e2e["d2h_copy_gbs_4streams"] = h_paths.numel() * 4 / (max(c0.elapsed_time(x) for x in ends) / 1e3) / 1e9
-
-    # streaming: the same kind of records applied as batches of one (Section 4.2), device buffers
-    streaming = None
-    if not args.no_e2e:
-        srec = t(wl.batches[-1].records()[: args.stream_records])
-        torch.cuda.synchronize()
-        e0, e1 = ev(), ev()
-        e0.record(stream)
-        g.stream_updates(srec, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        one_ms = []
-        for j in range(30):  # single-record calls: the latency of one streamed update through the API
-            r1 = srec[j: j + 1]
-            t0 = time.perf_counter()
-            g.stream_updates(r1, stream=stream)
-            one_ms.append(1e3 * (time.perf_counter() - t0))
-        streaming = {"records": int(srec.shape[0]), "updates_per_s": int(srec.shape[0]) / (e0.elapsed_time(e1) / 1e3),
-                     "single_record_call_ms_median": float(np.median(one_ms)),
-                     "batched_over_streaming": upd_rate / (int(srec.shape[0]) / (e0.elapsed_time(e1) / 1e3))}
-
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(G, wl.batches[0], wl.length, 77, args.cpu_seconds)
+    main = run_main(args, args.workload, dev, rank, ws, local)
+    sec = None
+    if args.secondary and args.secondary != args.workload and args.secondary != "none":
+        sec = run_main(args, args.secondary, dev, rank, ws, local, secondary=True)
     if rank == 0:
         line = {"metric": METRIC_MAIN,
-                "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
-                "config": {**main_config(args, wl),
-                           "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write); state > L2",
-                           "walk_config": {"lanes_per_walker": g.config().lanes_per_walker,
-                                           "warps_per_block": g.config().warps_per_block,
-                                           "reg_variant": g.config().reg_variant}},
-                "updated_edges_per_s": upd_rate, "update_roofline": upd_roof, "walk_steps_per_s": walk_rate,
-                "update_ms_per_step": float(np.mean(upd_ms)), "walk_ms_per_step": float(np.mean(walk_ms)),
-                "wall_s_timed": wall, "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
-                "roofline": roof, "cpu_baseline": cpu, "streaming": streaming}
+                "value": main["value"], "unit": "steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic", "config": main["config"],
+                **{k: v for k, v in main.items() if k not in ("value", "ms_per_step", "config")}}
+        if sec is not None:
+            line["secondary"] = {"workload": args.secondary, **sec}
         print(json.dumps(line), flush=True)
-    g.close()
     if ws > 1:
         dist.destroy_process_group()
 
@@ -991,7 +1156,8 @@ def main():
     ap.add_argument("--steps", type=int, default=7)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--workload", default="c5")
+    ap.add_argument("--secondary", default="c2", help="a second main workload reported beside the headline (none: off)")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass (profiling runs)")
@@ -1010,12 +1176,14 @@ def main():
         run_mixed(args)
     elif args.workload == "c4":
         run_serving(args)
-    elif args.workload == "c5":
+    elif args.workload == "c5-sweep":
         run_sweep(args)
     elif args.workload in ("f1", "f2", "f3"):
         run_ablation(args)
-    else:
+    elif args.workload in MAIN:
         run_ours(args)
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
 
 
 if __name__ == "__main__":

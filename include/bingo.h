@@ -88,11 +88,11 @@ typedef struct {
     uint32_t beta_pct;         /* Eq. group beta, percent (paper: 10) */
     uint32_t max_bits;         /* K: bias bits, 1..32; biases must be < 2^max_bits */
     uint32_t lanes_per_walker; /* group-selection team width: 1, 4 or 32; 0 = tuned default */
-    uint32_t warps_per_block;  /* walker kernel block size in warps; 0 = tuned default */
+    uint32_t warps_per_block;  /* walker kernel block size in warps, 1..24 (1..8 with reg_variant 1); 0 = tuned default */
     uint32_t blocks_per_sm;    /* walker kernel persistent blocks per SM; 0 = tuned default */
     uint32_t update_chunk;     /* vertex segments above this many adjacency slots (or above 256 records) are applied
                                   by a whole 512-thread block instead of one warp; 0 = 4096 */
-    uint32_t reg_variant;      /* walker register budget: 0 = 64 registers, 1 = 40 registers (more resident warps) */
+    uint32_t reg_variant;      /* walker register budget: 0 = up to 80 registers, 1 = 40 registers (more resident warps) */
     uint64_t pool_words;       /* device pool for adjacency and group blocks, in 4-byte words; 0 = auto */
     uint32_t bias_format;      /* BINGO_BIAS_U32 (default) or BINGO_BIAS_F32 */
     uint32_t all_regular;      /* 1: no group adaption, every nonempty group in regular format (the paper's
@@ -103,6 +103,8 @@ typedef struct {
     uint32_t vertex_order;     /* internal vertex numbering: BINGO_ORDER_AUTO (0; by degree when n <= 2^23),
                                   BINGO_ORDER_CALLER (the caller's ids) or BINGO_ORDER_DEGREE; every call still
                                   takes and returns the caller's ids (see BINGO_ORDER_*) */
+    uint32_t vertex_base;      /* partition graphs (bingo_part_*): global id of local vertex 0; 0 otherwise */
+    uint32_t dst_space;        /* partition graphs: destinations are global ids < dst_space; 0 = n (a whole graph) */
 } bingo_config;
 
 /* One update record, 16 bytes. */
@@ -253,6 +255,28 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
 bingo_status bingo_walk(bingo_graph* g, uint64_t nwalkers, const uint32_t* starts, const uint32_t* lengths,
                         const uint8_t* policy_ids, const bingo_policy* policies, uint32_t npolicies, uint64_t seed,
                         uint32_t stride, uint32_t* paths, uint32_t* path_len, uint32_t mode, void* stream);
+
+/*
+ * bingo_walk with packed output: each walker's path without padding, walkers
+ * concatenated in id order, so that only visited vertices cross to a host
+ * buffer (short PPR walks in long rows are mostly padding).
+ *   max_steps  every walker's step limit (its policy's max_len, or lengths[i])
+ *              must be <= max_steps (BINGO_E_INVALID otherwise)
+ *   path_len   uint32[nwalkers]: vertices of walker i's path (steps + 1)
+ *   vertices   uint32[capacity]: the paths; walker i's starts at the exclusive
+ *              prefix sum of path_len
+ *   total      nullable host uint64: sum of path_len
+ * The result equals bingo_walk's with stride = max_steps + 1 (same lengths; the
+ * packed vertices are each row's first path_len entries).  If the total
+ * exceeds capacity the call returns BINGO_E_INVALID after writing path_len and
+ * *total, and vertices is not written.  Arrays may be host or device pointers
+ * (host inputs staged, host outputs copied back).  Synchronises `stream` (the
+ * total sizes the copy).  Other arguments and errors as bingo_walk.
+ */
+bingo_status bingo_walk_packed(bingo_graph* g, uint64_t nwalkers, const uint32_t* starts, const uint32_t* lengths,
+                               const uint8_t* policy_ids, const bingo_policy* policies, uint32_t npolicies,
+                               uint64_t seed, uint32_t max_steps, uint32_t* path_len, uint32_t* vertices,
+                               uint64_t capacity, uint64_t* total, void* stream);
 
 /*
  * Allocation-free variant of bingo_walk.  The paper has no counterpart: this
@@ -483,9 +507,70 @@ bingo_status bingo_server_submit_walk(bingo_server* s, const uint32_t* starts, u
  * buffers, and the epoch it ran at.  BINGO_E_TIMEOUT if not done in time (it stays queued). */
 bingo_status bingo_server_wait(bingo_server* s, uint64_t ticket, uint32_t timeout_ms, uint32_t* paths,
                                uint32_t* path_len, uint64_t* epoch);
+/* Admission control.  While paused (paused != 0) no request is admitted; queued requests keep their
+ * place and updates are still applied at epoch boundaries.  Resuming (paused = 0) admits as usual. */
+bingo_status bingo_server_pause(bingo_server* s, uint32_t paused);
+
+/* One request's progress, for callers that track admission and latency: state 0 queued, 1 running,
+ * 2 done (status then holds its bingo_status); the epoch it was admitted at; the times it was
+ * submitted, admitted and completed, in ms since the server was created (-1 = not yet).  Valid
+ * until bingo_server_wait returns the request.  Admission: a request is admitted while the walker
+ * slots in flight plus its walkers stay within max_inflight_walkers (a lone request is always
+ * admitted) and its launch buffers leave hbm_reserve_bytes of device memory free; otherwise it
+ * waits in the queue, in order, until launches complete or memory frees. */
+typedef struct {
+    uint32_t state, status;
+    uint64_t walkers;
+    uint64_t epoch;
+    double submit_ms, admit_ms, done_ms;
+} bingo_server_request_info;
+bingo_status bingo_server_request_get(bingo_server* s, uint64_t ticket, bingo_server_request_info* out);
+
 /* Block until every queued update and request has been processed (bounded by timeout_ms). */
 bingo_status bingo_server_drain(bingo_server* s, uint32_t timeout_ms);
 bingo_status bingo_server_stats_get(bingo_server* s, bingo_server_stats* out);
+
+/* ---------------------------------------------------------------------------------------------- partitions
+ * 1-D partitioned graphs and walks with walker migration (Supplement, dynamic graph support and
+ * partitioning).  The vertices are split into contiguous ranges; each range's out-edges, groups and
+ * vertex records form one partition graph (created like a whole graph: rows are the range's
+ * vertices, destinations global ids).  A walk runs in supersteps: each partition resumes the
+ * walkers standing on its vertices and runs each until it ends or steps onto another partition's
+ * vertex, leaving a 24-byte record {walker, vertex, previous vertex, step}; the records are routed
+ * to their owners for the next superstep until no walker is left.  node2vec's distance probe reads
+ * the edge index of the previous vertex's owner.  Walker w draws from Philox counters (w, step, j)
+ * wherever it runs, so paths equal those of the same walk on the whole graph (created with
+ * BINGO_ORDER_CALLER and given the same updates).  Updates go to the owner of their source.  All
+ * partitions live on the device current at creation.  Edge ids are assigned per partition (each
+ * partition numbers its own edges in its CSR order, then its insertions in batch order).
+ */
+typedef struct bingo_partset bingo_partset;
+
+/* Build the partitions of a CSR graph (arguments as bingo_create; row_ptr host or device).  bounds:
+ * nullable host uint32[nparts + 1], 0 = bounds[0] < bounds[1] < ... < bounds[nparts] = n; NULL =
+ * contiguous ranges with nearly equal edge counts.  Integer biases, radix base 2.  Errors as
+ * bingo_create, BINGO_E_INVALID for bad bounds.  Synchronises `stream`. */
+bingo_status bingo_part_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const uint32_t* col,
+                               const uint32_t* bias, const bingo_config* cfg, uint32_t nparts, const uint32_t* bounds,
+                               void* stream, bingo_partset** out);
+bingo_status bingo_part_destroy(bingo_partset* ps);
+/* Partition p's graph (for bingo_export_vertices with local ids 0 .. hi-lo-1) and its range [lo, hi). */
+bingo_status bingo_part_info(bingo_partset* ps, uint32_t p, bingo_graph** graph, uint32_t* lo, uint32_t* hi);
+/* One batch (host or device records, global ids), validated as a whole, then each record applied by
+ * the owner of its source in batch order (Section 5.2 semantics per source).  stats: sums over the
+ * partitions.  BINGO_E_OOM in a partition leaves the earlier partitions' records applied. */
+bingo_status bingo_part_apply_updates(bingo_partset* ps, const bingo_update* ups, uint64_t count, void* stream,
+                                      bingo_update_stats* stats);
+/* bingo_walk over the partitions (persistent form; device buffers only; arguments and results as
+ * bingo_walk).  Synchronises `stream` once per superstep; device-side errors are latched in the
+ * partitions and reported by bingo_part_check. */
+bingo_status bingo_part_walk(bingo_partset* ps, uint64_t nwalkers, const uint32_t* starts, const uint32_t* lengths,
+                             const uint8_t* policy_ids, const bingo_policy* policies, uint32_t npolicies, uint64_t seed,
+                             uint32_t stride, uint32_t* paths, uint32_t* path_len, uint32_t mode, void* stream);
+/* bingo_check over every partition (the first non-OK status). */
+bingo_status bingo_part_check(bingo_partset* ps, void* stream);
+/* Supersteps the last bingo_part_walk took. */
+uint64_t bingo_part_supersteps(bingo_partset* ps);
 
 #ifdef __cplusplus
 }

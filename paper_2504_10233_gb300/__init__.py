@@ -44,7 +44,8 @@ class bingo_config(c.Structure):
                 ("lanes_per_walker", c.c_uint32), ("warps_per_block", c.c_uint32), ("blocks_per_sm", c.c_uint32),
                 ("update_chunk", c.c_uint32), ("reg_variant", c.c_uint32), ("pool_words", c.c_uint64),
                 ("bias_format", c.c_uint32), ("all_regular", c.c_uint32), ("lambda_", c.c_double),
-                ("radix_base", c.c_uint32), ("vertex_order", c.c_uint32)]
+                ("radix_base", c.c_uint32), ("vertex_order", c.c_uint32), ("vertex_base", c.c_uint32),
+                ("dst_space", c.c_uint32)]
 
 
 class bingo_update_stats(c.Structure):
@@ -74,6 +75,11 @@ class bingo_server_config(c.Structure):
                 ("flags", c.c_uint32), ("update_delay_us", c.c_uint32), ("reserved", c.c_uint32)]
 
 
+class bingo_server_request_info(c.Structure):
+    _fields_ = [("state", c.c_uint32), ("status", c.c_uint32), ("walkers", c.c_uint64), ("epoch", c.c_uint64),
+                ("submit_ms", c.c_double), ("admit_ms", c.c_double), ("done_ms", c.c_double)]
+
+
 class bingo_server_stats(c.Structure):
     _fields_ = [("requests_done", c.c_uint64), ("walkers_done", c.c_uint64), ("steps_done", c.c_uint64),
                 ("updates_applied", c.c_uint64), ("epochs", c.c_uint64), ("p50_ms", c.c_double),
@@ -91,6 +97,8 @@ SIGNATURES = {
     "bingo_stream_updates": (c.c_int, [VP, VP, c.c_uint64, VP, c.POINTER(bingo_update_stats)]),
     "bingo_walk": (c.c_int, [VP, c.c_uint64, VP, VP, VP, c.POINTER(bingo_policy), c.c_uint32, c.c_uint64,
                              c.c_uint32, VP, VP, c.c_uint32, VP]),
+    "bingo_walk_packed": (c.c_int, [VP, c.c_uint64, VP, VP, VP, c.POINTER(bingo_policy), c.c_uint32, c.c_uint64,
+                                    c.c_uint32, VP, VP, c.c_uint64, c.POINTER(c.c_uint64), VP]),
     "bingo_walk_noalloc": (c.c_int, [VP, c.c_uint64, VP, VP, VP, c.POINTER(bingo_policy), c.c_uint32, c.c_uint64,
                                      c.c_uint32, VP, VP, c.c_uint32, VP]),
     "bingo_check": (c.c_int, [VP, VP]),
@@ -113,8 +121,19 @@ SIGNATURES = {
     "bingo_server_wait": (c.c_int, [VP, c.c_uint64, c.c_uint32, VP, VP, c.POINTER(c.c_uint64)]),
     "bingo_server_drain": (c.c_int, [VP, c.c_uint32]),
     "bingo_server_stats_get": (c.c_int, [VP, c.POINTER(bingo_server_stats)]),
+    "bingo_server_pause": (c.c_int, [VP, c.c_uint32]),
+    "bingo_server_request_get": (c.c_int, [VP, c.c_uint64, c.POINTER(bingo_server_request_info)]),
     "bingo_export_vertices_sizes": (c.c_int, [VP, VP, c.c_uint64, c.POINTER(c.c_uint64)]),
     "bingo_export_vertices": (c.c_int, [VP, VP, c.c_uint64] + [VP] * 13),
+    "bingo_part_create": (c.c_int, [c.c_uint32, c.c_uint64, VP, VP, VP, c.POINTER(bingo_config), c.c_uint32, VP, VP,
+                                    c.POINTER(VP)]),
+    "bingo_part_destroy": (c.c_int, [VP]),
+    "bingo_part_info": (c.c_int, [VP, c.c_uint32, c.POINTER(VP), c.POINTER(c.c_uint32), c.POINTER(c.c_uint32)]),
+    "bingo_part_apply_updates": (c.c_int, [VP, VP, c.c_uint64, VP, c.POINTER(bingo_update_stats)]),
+    "bingo_part_walk": (c.c_int, [VP, c.c_uint64, VP, VP, VP, c.POINTER(bingo_policy), c.c_uint32, c.c_uint64,
+                                  c.c_uint32, VP, VP, c.c_uint32, VP]),
+    "bingo_part_check": (c.c_int, [VP, VP]),
+    "bingo_part_supersteps": (c.c_uint64, [VP]),
     "bingo_policy_make": (c.c_int, [c.c_uint32, c.c_uint32, c.c_double, c.c_double, c.c_double,
                                     c.POINTER(bingo_policy)]),
     "bingo_philox4x32_10": (c.c_int, [c.c_uint64, VP, VP, VP]),
@@ -246,6 +265,17 @@ def bingo_walk(h, nwalkers, starts, policies, seed, stride, paths, path_len, len
     arr = (bingo_policy * len(policies))(*policies)
     _err(load().bingo_walk(h, nwalkers, _ptr(starts), _ptr(lengths), _ptr(policy_ids), arr, len(policies), seed,
                            stride, _ptr(paths), _ptr(path_len), mode, _stream(stream)))
+
+
+def bingo_walk_packed(h, nwalkers, starts, policies, seed, max_steps, path_len, vertices, lengths=None,
+                      policy_ids=None, stream=None) -> int:
+    """Packed walk (no padding): returns the number of vertices written to `vertices`."""
+    arr = (bingo_policy * len(policies))(*policies)
+    tot = c.c_uint64()
+    cap = int(vertices.numel() if hasattr(vertices, "numel") else vertices.size)
+    _err(load().bingo_walk_packed(h, nwalkers, _ptr(starts), _ptr(lengths), _ptr(policy_ids), arr, len(policies),
+                                  seed, max_steps, _ptr(path_len), _ptr(vertices), cap, c.byref(tot), _stream(stream)))
+    return int(tot.value)
 
 
 def bingo_walk_noalloc(h, nwalkers, starts, policies, seed, stride, paths, path_len, lengths=None, policy_ids=None,
@@ -470,6 +500,11 @@ class Graph:
         bingo_walk(self.h, len(starts), starts, policies, seed, stride, paths, path_len, lengths, policy_ids, mode,
                    stream)
 
+    def walk_packed(self, starts, policies, seed, max_steps, path_len, vertices, lengths=None, policy_ids=None,
+                    stream=None) -> int:
+        return bingo_walk_packed(self.h, len(starts), starts, policies, seed, max_steps, path_len, vertices, lengths,
+                                 policy_ids, stream)
+
     def check(self, stream=None):
         bingo_check(self.h, stream)
 
@@ -505,3 +540,55 @@ class Graph:
 
     def kernel_launches(self) -> int:
         return bingo_kernel_launches(self.h)
+
+
+class PartitionedGraph:
+    """Owns a bingo_partset: the graph split into vertex ranges, walked with walker migration."""
+
+    def __init__(self, n, row_ptr, col, bias, nparts, bounds=None, max_bits=32, stream=None, **cfg):
+        self.n = int(n)
+        self.cfg = default_config(max_bits=max_bits, **cfg)
+        h = VP()
+        b = None if bounds is None else np.ascontiguousarray(np.asarray(bounds, dtype=np.uint32))
+        _err(load().bingo_part_create(self.n, int(len(col)), _ptr(row_ptr), _ptr(col), _ptr(bias), c.byref(self.cfg),
+                                      int(nparts), _ptr(b), _stream(stream), c.byref(h)))
+        self.h = h
+        self.nparts = int(nparts)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().bingo_part_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def part(self, p):
+        """(partition graph handle, lo, hi) of partition p."""
+        g, lo, hi = VP(), c.c_uint32(), c.c_uint32()
+        _err(load().bingo_part_info(self.h, p, c.byref(g), c.byref(lo), c.byref(hi)))
+        return g, int(lo.value), int(hi.value)
+
+    def export_vertices(self, p, local_ids):
+        return bingo_export_vertices(self.part(p)[0], local_ids)
+
+    def apply_updates(self, records, stream=None):
+        stats = bingo_update_stats()
+        _err(load().bingo_part_apply_updates(self.h, _ptr(records), int(records.shape[0]), _stream(stream),
+                                             c.byref(stats)))
+        return stats.as_dict()
+
+    def walk(self, starts, policies, seed, stride, paths, path_len, lengths=None, policy_ids=None,
+             mode=WALK_PERSISTENT, stream=None):
+        arr = (bingo_policy * len(policies))(*policies)
+        _err(load().bingo_part_walk(self.h, len(starts), _ptr(starts), _ptr(lengths), _ptr(policy_ids), arr,
+                                    len(policies), seed, stride, _ptr(paths), _ptr(path_len), mode, _stream(stream)))
+
+    def check(self, stream=None):
+        _err(load().bingo_part_check(self.h, _stream(stream)))
+
+    def supersteps(self) -> int:
+        return int(load().bingo_part_supersteps(self.h))

@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(HERE, "_obj")
 LIB = os.path.join(HERE, "libbingo.so")
 
-SOURCES = ["util.cu", "graph.cu", "walk.cu", "update.cu", "api.cu", "server.cu", "walk_noalloc.cu"]
+SOURCES = ["util.cu", "graph.cu", "walk.cu", "update.cu", "api.cu", "server.cu", "walk_noalloc.cu", "part.cu"]
 HEADERS = ["bingo_internal.cuh", "bingo_host.h", "groups.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

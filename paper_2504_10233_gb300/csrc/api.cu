@@ -162,6 +162,22 @@ __global__ void k_walker_draws(uint2 key, uint64_t walker, uint32_t step, uint64
     for (uint32_t i = 0; i < count; i++) out[i] = range ? below64(R, range, status) : (uint64_t)R.next();
 }
 
+// Packed walk output: lengths widened for the scan, then every walker's row prefix copied to its
+// offset (one thread per walker; each row is contiguous, and so is each packed path).
+__global__ void k_len64(const uint32_t* __restrict__ plen, uint64_t n, uint64_t* __restrict__ out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = plen[i];
+}
+__global__ void k_pack_rows(const uint32_t* __restrict__ rows, uint32_t stride, const uint32_t* __restrict__ plen,
+                            const uint64_t* __restrict__ off, uint64_t n, uint32_t* __restrict__ out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t L = plen[i] <= stride ? plen[i] : stride;
+        const uint32_t* src = rows + i * (uint64_t)stride;
+        uint32_t* dst = out + off[i];
+        for (uint32_t j = 0; j < L; j++) dst[j] = src[j];
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -173,6 +189,7 @@ bingo_status bingo_walk(bingo_graph* g, uint64_t nwalkers, const uint32_t* start
     if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
     bingo_status st = check_device(g, "walk");
     if (st != BINGO_OK) return st;
+    if (g->part) { set_error("walk: a partition graph walks only through bingo_part_walk"); return BINGO_E_STATE; }
     const uint32_t base_mode = mode & 0xFF;
     const bool pad = !(mode & 0x100);
     if (base_mode > BINGO_WALK_STEPWISE) { set_error("unknown walk mode %u", mode); return BINGO_E_INVALID; }
@@ -254,6 +271,104 @@ bingo_status bingo_walk(bingo_graph* g, uint64_t nwalkers, const uint32_t* start
     return BINGO_OK;
 }
 
+bingo_status bingo_walk_packed(bingo_graph* g, uint64_t nwalkers, const uint32_t* starts, const uint32_t* lengths,
+                               const uint8_t* policy_ids, const bingo_policy* policies, uint32_t npolicies,
+                               uint64_t seed, uint32_t max_steps, uint32_t* path_len, uint32_t* vertices,
+                               uint64_t capacity, uint64_t* total, void* stream) {
+    if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
+    if (g->broken) { set_error("graph state is unusable after an earlier device failure"); return BINGO_E_STATE; }
+    bingo_status st = check_device(g, "walk_packed");
+    if (st != BINGO_OK) return st;
+    if (g->part) { set_error("walk_packed: a partition graph walks only through bingo_part_walk"); return BINGO_E_STATE; }
+    if (nwalkers && (!starts || !path_len || (!vertices && capacity))) { set_error("walk_packed: NULL buffer"); return BINGO_E_INVALID; }
+    if (max_steps >= 0xFFFFFFFFu) { set_error("walk_packed: max_steps too large"); return BINGO_E_INVALID; }
+    const uint32_t stride = max_steps + 1;
+    bool need_n2v = false;
+    uint32_t max_len = 0;
+    st = check_policies(policies, npolicies, stride, lengths != nullptr, &need_n2v, &max_len);
+    if (st != BINGO_OK) return st;
+    if (total) *total = 0;
+    if (nwalkers == 0) return BINGO_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (need_n2v && g->G.eh_mask == 0) {
+        st = edge_index_build(g, s);
+        if (st != BINGO_OK) return st;
+    }
+    auto in = [&](const void* src, size_t bytes, Buf& b, const void** out) -> bingo_status {
+        if (!src || is_device_ptr(src)) { *out = src; return BINGO_OK; }
+        CK(ensure(b, bytes), "walk staging");
+        CK(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, s), "walk upload");
+        *out = b.p;
+        return BINGO_OK;
+    };
+    const uint32_t *ds, *dl;
+    const uint8_t* dp;
+    if ((st = in(starts, 4 * nwalkers, g->w_starts, (const void**)&ds)) != BINGO_OK) return st;
+    if ((st = in(lengths, 4 * nwalkers, g->w_len, (const void**)&dl)) != BINGO_OK) return st;
+    if ((st = in(policy_ids, nwalkers, g->w_pid, (const void**)&dp)) != BINGO_OK) return st;
+    const bool host_len = !is_device_ptr(path_len), host_vert = vertices && !is_device_ptr(vertices);
+    CK(ensure(g->w_paths, 4ull * nwalkers * stride), "walk rows");
+    uint32_t* dplen = path_len;
+    if (host_len) {
+        CK(ensure(g->w_plen, 4ull * nwalkers), "walk lengths");
+        dplen = (uint32_t*)g->w_plen.p;
+    }
+    CK(ensure(g->w_pols, sizeof(bingo_policy) * npolicies), "policy staging");
+    CK(cudaMemcpyAsync(g->w_pols.p, policies, sizeof(bingo_policy) * npolicies, cudaMemcpyHostToDevice, s),
+       "policy upload");
+    WalkReq q;
+    q.nwalkers = nwalkers;
+    q.starts = ds;
+    q.lengths = dl;
+    q.pids = dp;
+    q.dev_pols = (const bingo_policy*)g->w_pols.p;
+    q.npol = npolicies;
+    q.seed = seed;
+    q.stride = stride;
+    q.paths = (uint32_t*)g->w_paths.p;
+    q.plen = dplen;
+    q.mode = BINGO_WALK_PERSISTENT;
+    q.pad = false;
+    q.max_steps = lengths ? max_steps : max_len;
+    q.queue = (unsigned long long*)((uint64_t*)g->d_ctl + CTL_QUEUE);
+    if ((st = walk_launch(g, q, s)) != BINGO_OK) return st;
+    if (host_len) CK(cudaMemcpyAsync(path_len, dplen, 4ull * nwalkers, cudaMemcpyDeviceToHost, s), "lengths download");
+    // offsets: exclusive scan of the lengths; off[nwalkers] = total
+    CK(ensure(g->w_len64, 8ull * nwalkers), "walk offsets");
+    CK(ensure(g->w_off, 8ull * (nwalkers + 1)), "walk offsets");
+    uint64_t* off = (uint64_t*)g->w_off.p;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((nwalkers + 255) / 256, (uint64_t)g->num_sms * 16);
+    k_len64<<<blocks, 256, 0, s>>>(dplen, nwalkers, (uint64_t*)g->w_len64.p);
+    g->launches++;
+    CK(scan_excl_u64((const uint64_t*)g->w_len64.p, off, nwalkers, off + nwalkers, g->s_tmp, s, &g->launches),
+       "walk offsets");
+    uint64_t tot = 0;
+    CK(cudaMemcpyAsync(&tot, off + nwalkers, 8, cudaMemcpyDeviceToHost, s), "walk total");
+    CK(cudaStreamSynchronize(s), "walk");
+    uint32_t status = 0;
+    CK(cudaMemcpy(&status, (uint64_t*)g->d_ctl + CTL_STATUS, 4, cudaMemcpyDeviceToHost), "status read");
+    if (status & ST_STATE) { set_error("walk: inconsistent group structure"); return BINGO_E_STATE; }
+    if (status & ST_INVALID) { set_error("walk: a start vertex >= n, a policy id >= npolicies or a length > max_steps"); return BINGO_E_INVALID; }
+    if (status & ST_TIMEOUT) { set_error("walk: a bounded rejection loop gave up"); return BINGO_E_TIMEOUT; }
+    if (total) *total = tot;
+    if (tot > capacity) {
+        set_error("walk_packed: the paths hold %llu vertices, more than the capacity %llu", (unsigned long long)tot,
+                  (unsigned long long)capacity);
+        return BINGO_E_INVALID;
+    }
+    uint32_t* dvert = vertices;
+    if (host_vert) {
+        CK(ensure(g->w_packed, 4ull * (tot ? tot : 1)), "packed paths");
+        dvert = (uint32_t*)g->w_packed.p;
+    }
+    k_pack_rows<<<blocks, 256, 0, s>>>((const uint32_t*)g->w_paths.p, stride, dplen, off, nwalkers, dvert);
+    g->launches++;
+    CK(cudaGetLastError(), "pack paths");
+    if (host_vert && tot) CK(cudaMemcpyAsync(vertices, dvert, 4ull * tot, cudaMemcpyDeviceToHost, s), "paths download");
+    if (host_vert) CK(cudaStreamSynchronize(s), "paths download");
+    return BINGO_OK;
+}
+
 // Synchronise `stream` and return (and clear) the device status latched by asynchronous calls.
 bingo_status bingo_check(bingo_graph* g, void* stream) {
     if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
@@ -272,6 +387,7 @@ bingo_status bingo_check(bingo_graph* g, void* stream) {
 bingo_status bingo_autotune(bingo_graph* g, uint64_t nwalkers, const uint32_t* starts, uint32_t length, void* stream,
                             bingo_config* out_cfg) {
     if (!g || !starts || nwalkers == 0 || length == 0) { set_error("autotune: bad arguments"); return BINGO_E_INVALID; }
+    if (g->part) { set_error("autotune: a partition graph walks only through bingo_part_walk"); return BINGO_E_STATE; }
     cudaStream_t s = (cudaStream_t)stream;
     Buf dstarts, dpaths, dplen;
     const uint32_t* ds = starts;

@@ -61,6 +61,13 @@ struct WalkReq {
     uint32_t* host_flags = nullptr;      // device view of host-mapped pinned memory
     uint32_t chunk_shift = 0;
     uint32_t io_seq = 0;
+    // partitioned walks (see WalkParams in walk.cu); resume null = start mode
+    const PartRec* resume = nullptr;
+    PartRec* outbox = nullptr;
+    unsigned long long* nout = nullptr;
+    const PartEH* peh = nullptr;
+    const uint32_t* bounds = nullptr;
+    uint32_t npart = 0;
 };
 
 bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s);
@@ -127,6 +134,7 @@ struct bingo_graph {
     bingo::Buf s_rec, s_seginfo;  // sorted insertion records, per-segment {v, first key, ni, nd}
     bingo::Buf s_gcand, s_gcand_cnt;  // deletion candidates of big segments from the pre-pass
     bingo::Buf w_starts, w_len, w_pid, w_paths, w_plen, w_pols, w_chunk_done;
+    bingo::Buf w_len64, w_off, w_packed;  // packed walks: lengths as u64, their exclusive scan, packed rows
     // host-buffer walks: download streams, events, host-mapped chunk flags (see walk_host_io_overlap)
     cudaStream_t io_copy[bingo::WALK_IO_STREAMS] = {};
     cudaEvent_t io_kernel = nullptr, io_done[bingo::WALK_IO_STREAMS] = {};
@@ -143,6 +151,7 @@ struct bingo_graph {
     cudaStream_t cap_stream = nullptr; // capture stream (the caller's may be the legacy stream)
     uint64_t launches = 0;
     bool broken = false;        // a device-side failure left the state unusable
+    bool part = false;          // a partition graph (vertex range of a larger graph): walks only through bingo_part_walk
 };
 
 // control-word layout inside d_ctl (u64 words)

@@ -66,7 +66,7 @@ struct __align__(64) VHot {
     uint32_t adj;   // adjacency block, 32-byte units
     uint32_t deg;
     uint32_t mask;
-    uint32_t word;  // the caller's id of this vertex (path entries of walks)
+    uint32_t word;  // the caller's id of this vertex (path entries of walks); top bit: cold_desc below
     uint2 g[HOT_GROUPS];
 };
 struct __align__(32) VCold {
@@ -193,6 +193,10 @@ struct DevGraph {
     // internal vertex i, perm[v] = internal id of the caller's vertex v; both null = identity.
     const uint32_t* order;
     const uint32_t* perm;
+    // A partition graph holds the rows of the global vertices [base, base + n) as local vertices
+    // 0 .. n-1; its destinations are global ids below dst_n.  A whole graph has base 0, dst_n = n.
+    uint32_t base;
+    uint32_t dst_n;
 
     VHot* vh;
     VCold* vc;
@@ -203,6 +207,21 @@ struct DevGraph {
     uint64_t eh_mask;            // capacity - 1, 0 = absent
 };
 constexpr unsigned long long EH_EMPTY = 0xFFFFFFFFFFFFFFFFull;
+
+// Partitioned walks (graphs split into vertex ranges, walkers moving between them): a walker between
+// two partitions' launches is a record {walker id, current vertex, previous vertex (global ids), the
+// step it is at}; the next launch of the current vertex's owner resumes it.
+struct PartRec {
+    uint64_t wid;
+    uint32_t cur, prev, step, pad;
+};
+static_assert(sizeof(PartRec) == 24, "walker records are 24 bytes");
+// One partition's node2vec edge index (keys: local source << 32 | global destination).
+struct PartEH {
+    const unsigned long long* key;
+    const uint32_t* cnt;
+    uint64_t mask;  // 0 = absent
+};
 
 #ifdef __CUDACC__
 __device__ __forceinline__ VHdr load_hdr(const DevGraph& G, uint64_t v) {
@@ -236,7 +255,9 @@ __device__ __forceinline__ void store_hdr(const DevGraph& G, uint64_t v, const V
 __device__ __forceinline__ uint32_t to_internal(const DevGraph& G, uint32_t v) {
     return (G.perm && v < G.n) ? __ldg(G.perm + v) : v;
 }
-__device__ __forceinline__ uint32_t to_caller(const DevGraph& G, uint32_t v) { return G.order ? __ldg(G.order + v) : v; }
+__device__ __forceinline__ uint32_t to_caller(const DevGraph& G, uint32_t v) {
+    return G.order ? __ldg(G.order + v) : v + G.base;
+}
 
 // {|G_k|, ref} of group k of vertex v
 __device__ __forceinline__ uint2& grp(const DevGraph& G, uint64_t v, uint32_t k) {
@@ -294,6 +315,46 @@ __device__ __forceinline__ uint64_t cold_total(const DevGraph& G, const uint32_t
     for (uint32_t k = HOT_GROUPS; k < 32; k++) w += graph_slot_weight(G, cnt[k], k);
     return w;
 }
+
+// Order in which a draw that falls beyond the hot groups scans the cold groups.  The walker reads
+// the cold pairs (pairs 3..15, groups 2i and 2i+1) in batches whose loads are issued together, and
+// reads a batch only when the draw lies beyond the earlier ones: upwards, the aligned batches
+// [3, 7), [7, 11), [11, 15), [15]; downwards, windows of four consecutive pairs from the highest
+// nonempty cold pair; batches without a nonempty pair are skipped.  Any fixed order gives the same
+// law (Eq. group_prob).  Upwards suits biases whose weight is in the low bits (floor Pareto);
+// uniform biases put half their weight on the top bit, where upwards reads every batch.  The order
+// is a pure function of the counts: downwards iff it reads fewer batches in expectation (each
+// pair's weight times the number of batches read to reach it), ties upwards.  It is kept in the
+// top bit of the hot record's caller-id word (vertex ids are below 2^31).
+constexpr uint32_t WORD_DESC = 0x80000000u;
+constexpr uint32_t WORD_ID = 0x7FFFFFFFu;
+__device__ __forceinline__ bool cold_desc(const DevGraph& G, const uint32_t* cnt) {
+    uint64_t wp[16];
+    int hi = -1;
+    for (int i = HOT_GROUPS / 2; i < 16; i++) {
+        wp[i] = graph_slot_weight(G, cnt[2 * i], 2 * i) + graph_slot_weight(G, cnt[2 * i + 1], 2 * i + 1);
+        if (cnt[2 * i] || cnt[2 * i + 1]) hi = i;
+    }
+    if (hi < 0) return false;
+    // 128-bit sums: at most 13 pairs x 4 batches x 2^64
+    unsigned __int128 ea = 0, ed = 0;
+    int rank = 0, prev = -1;
+    for (int i = HOT_GROUPS / 2; i < 16; i++) {
+        if (!(cnt[2 * i] || cnt[2 * i + 1])) continue;
+        const int b = (i - HOT_GROUPS / 2) / 4;
+        if (b != prev) { rank++; prev = b; }
+        ea += (unsigned __int128)wp[i] * (unsigned)rank;
+    }
+    rank = 0;
+    prev = -1;
+    for (int i = hi; i >= HOT_GROUPS / 2; i--) {
+        if (!(cnt[2 * i] || cnt[2 * i + 1])) continue;
+        const int w = (hi - i) / 4;
+        if (w != prev) { rank++; prev = w; }
+        ed += (unsigned __int128)wp[i] * (unsigned)rank;
+    }
+    return ed < ea;
+}
 // ---- radix base 4 (Appendix): sub-group (digit position i, value v) is slot 3 i + v - 1.
 constexpr uint32_t B4_POSITIONS = 10;  // biases below 4^10 = 2^20: slots 0..29
 // Sub-group mask of a bias: bit 3 i + v - 1 for every nonzero base-4 digit v at position i.  Stored
@@ -335,17 +396,21 @@ __device__ __forceinline__ uint64_t eh_hash(uint64_t key) {
     key ^= key >> 33;
     return key;
 }
-// live copies of (u, x) in the edge index; bounded probe
-__device__ __forceinline__ uint32_t eh_lookup(const DevGraph& G, uint32_t u, uint32_t x) {
+// live copies of (u, x) in an edge index; bounded probe
+__device__ __forceinline__ uint32_t eh_lookup_in(const unsigned long long* keys, const uint32_t* cnts, uint64_t mask,
+                                                 uint32_t u, uint32_t x) {
     const unsigned long long key = ((unsigned long long)u << 32) | x;
-    uint64_t h = eh_hash(key) & G.eh_mask;
-    for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
-        unsigned long long k = __ldg(G.eh_key + h);
-        if (k == key) return __ldg(G.eh_cnt + h);
+    uint64_t h = eh_hash(key) & mask;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+        unsigned long long k = __ldg(keys + h);
+        if (k == key) return __ldg(cnts + h);
         if (k == EH_EMPTY) return 0;
-        h = (h + 1) & G.eh_mask;
+        h = (h + 1) & mask;
     }
     return 0;
+}
+__device__ __forceinline__ uint32_t eh_lookup(const DevGraph& G, uint32_t u, uint32_t x) {
+    return eh_lookup_in(G.eh_key, G.eh_cnt, G.eh_mask, u, x);
 }
 
 // ---------------------------------------------------------------------------------------------- Philox4x32-10

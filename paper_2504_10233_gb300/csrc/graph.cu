@@ -25,13 +25,14 @@ const char* last_error_cstr();
 
 // Integer biases: 1 <= w < 2^max_bits.  Real biases (real = true) were checked by k_split_biases;
 // their degree must stay below REAL_MAX_DEG.
-__global__ void k_validate_csr(uint32_t n, uint64_t m, const uint64_t* __restrict__ rp, const uint32_t* __restrict__ col,
-                               const uint32_t* __restrict__ bias, uint32_t max_bits, bool real, uint32_t* status) {
+__global__ void k_validate_csr(uint32_t n, uint32_t dst_n, uint64_t m, const uint64_t* __restrict__ rp,
+                               const uint32_t* __restrict__ col, const uint32_t* __restrict__ bias, uint32_t max_bits,
+                               bool real, uint32_t* status) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     bool bad = false;
     for (uint64_t j = tid; j < m; j += nt) {
         const uint32_t w = bias[j];
-        bad |= col[j] >= n || (!real && (w == 0 || (max_bits < 32 && (w >> max_bits) != 0)));
+        bad |= col[j] >= dst_n || (!real && (w == 0 || (max_bits < 32 && (w >> max_bits) != 0)));
     }
     const uint64_t dlim = real ? REAL_MAX_DEG : 0xFFFFFFFFull;
     for (uint64_t v = tid; v < n; v += nt) {
@@ -112,7 +113,7 @@ __global__ void k_build_count(DevGraph G, const uint64_t* __restrict__ rp, const
             h.lcaps = caps ? (uint8_t)(log2_u32(caps) + 1) : 0;
             h.pad = 0;
             store_hdr(G, v, h);
-            G.vh[v].word = G.order ? G.order[v] : (uint32_t)v;  // read by the walker for path entries
+            G.vh[v].word = G.order ? G.order[v] : G.base + (uint32_t)v;  // read by the walker for path entries
         }
     }
 }
@@ -186,12 +187,17 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
         gref_ref(G, v, lane) = gref;
         __syncwarp();
         // total weight of the cold groups (the decimal slot's count was written above)
-        uint64_t wc = lane >= HOT_GROUPS ? graph_slot_weight(G, cnt_ref(G, v, lane), lane) : 0ull;
+        const uint32_t myc = cnt_ref(G, v, lane);
+        uint64_t wc = lane >= HOT_GROUPS ? graph_slot_weight(G, myc, lane) : 0ull;
 #pragma unroll
         for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(FULL, wc, o);
+        uint32_t call[32];
+#pragma unroll
+        for (int k = 0; k < 32; k++) call[k] = __shfl_sync(FULL, myc, k);
         if (lane == 0) {
             store_hdr(G, v, h);
             G.vc[v].wcold = wc;
+            G.vh[v].word = (G.vh[v].word & WORD_ID) | (cold_desc(G, call) ? WORD_DESC : 0u);
         }
     }
 }
@@ -275,7 +281,13 @@ __global__ void k_export_fill(DevGraph G, const uint32_t* __restrict__ ids, uint
         uint64_t wc = lane >= HOT_GROUPS ? graph_slot_weight(G, c, lane) : 0ull;
 #pragma unroll
         for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(FULL, wc, o);
-        if (lane == 0 && (wc != G.vc[v].wcold || G.vh[v].word != (uint32_t)ve)) atomicAdd(bad, 1ull);
+        uint32_t call[32];
+#pragma unroll
+        for (int k = 0; k < 32; k++) call[k] = __shfl_sync(FULL, c, k);
+        const uint32_t hw = G.vh[v].word;
+        if (lane == 0 && (wc != G.vc[v].wcold || (hw & WORD_ID) != G.base + (uint32_t)ve ||
+                          ((hw & WORD_DESC) != 0) != cold_desc(G, call)))
+            atomicAdd(bad, 1ull);
         okind[i * 32 + lane] = (uint8_t)kd;
         ocnt[i * 32 + lane] = c;
         uint32_t one_slot = NONE32;
@@ -394,7 +406,8 @@ static void free_graph(bingo_graph* g) {
         if (p) cudaFree(p);
     Buf* bufs[] = {&g->s_in, &g->s_keys, &g->s_keys2, &g->s_vals, &g->s_vals2, &g->s_tmp, &g->s_seg,
                    &g->s_rank, &g->s_best, &g->s_aux, &g->s_walk, &g->s_stage, &g->s_rec, &g->s_seginfo, &g->s_gcand, &g->s_gcand_cnt,
-                   &g->w_starts, &g->w_len, &g->w_pid, &g->w_paths, &g->w_plen, &g->w_pols, &g->w_chunk_done};
+                   &g->w_starts, &g->w_len, &g->w_pid, &g->w_paths, &g->w_plen, &g->w_pols, &g->w_chunk_done,
+                   &g->w_len64, &g->w_off, &g->w_packed};
     for (Buf* b : bufs) release(*b);
     delete g;
 }
@@ -449,6 +462,14 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
         set_error("invalid vertex order %u", c.vertex_order);
         return BINGO_E_INVALID;
     }
+    const bool part = c.vertex_base != 0 || c.dst_space != 0;
+    const uint32_t dst_n = c.dst_space ? c.dst_space : n;
+    if (part && (dst_n >= 0x80000000u || (uint64_t)c.vertex_base + n > dst_n || c.vertex_order == BINGO_ORDER_DEGREE)) {
+        set_error("invalid partition (base %u, %u rows, destination space %u; caller vertex order only)",
+                  c.vertex_base, n, dst_n);
+        return BINGO_E_INVALID;
+    }
+    if (part) c.vertex_order = BINGO_ORDER_CALLER;
     if (c.radix_base == 0) c.radix_base = 2;
     const bool base4 = c.radix_base == 4;
     if ((c.radix_base != 2 && !base4) || (base4 && real)) {
@@ -490,7 +511,7 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
         bs = (const uint32_t*)bint.p;
         dq = (const uint8_t*)bdec.p;
     }
-    k_validate_csr<<<grid_for(g, (m > n ? m : n), 256), 256, 0, s>>>(n, m, rp, cl, bs, c.max_bits, real, status);
+    k_validate_csr<<<grid_for(g, (m > n ? m : n), 256), 256, 0, s>>>(n, dst_n, m, rp, cl, bs, c.max_bits, real, status);
     g->launches++;
     if (base4 && m) {  // factorise the sub-group masks from here on (validation saw the biases)
         if (!cu(ensure(bint, sizeof(uint32_t) * m), "sub-group masks")) { release_stage(); return fail(st); }
@@ -512,6 +533,9 @@ bingo_status bingo_create(uint32_t n, uint64_t m, const uint64_t* row_ptr, const
         !cu(cudaMalloc(&g->d_cold, sizeof(VCold) * (size_t)n), "vertex records (cold)")) { release_stage(); return fail(st); }
     DevGraph& G = g->G;
     G.n = n;
+    G.base = c.vertex_base;
+    G.dst_n = dst_n;
+    g->part = part;
     G.max_bits = c.max_bits;
     G.alpha = c.all_regular ? ALL_REGULAR : c.alpha_pct;
     G.beta = c.all_regular ? 0u : c.beta_pct;
@@ -642,7 +666,7 @@ bingo_status bingo_get_config(bingo_graph* g, bingo_config* out) {
 
 bingo_status bingo_set_walk_config(bingo_graph* g, uint32_t lanes, uint32_t wpb, uint32_t bps, uint32_t regv) {
     if (!g) { set_error("NULL graph"); return BINGO_E_INVALID; }
-    if (!(lanes == 1 || lanes == 4 || lanes == 32) || wpb == 0 || wpb > 32 || regv > 1 || (regv && wpb > 8)) {
+    if (!(lanes == 1 || lanes == 4 || lanes == 32) || wpb == 0 || wpb > 24 || regv > 1 || (regv && wpb > 8)) {
         set_error("invalid walk config (lanes %u, warps/block %u, register variant %u)", lanes, wpb, regv);
         return BINGO_E_INVALID;
     }

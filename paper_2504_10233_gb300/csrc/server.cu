@@ -37,7 +37,7 @@ struct Request {
     std::vector<uint32_t> starts;
     bingo_policy pol{};
     uint64_t seed = 0;
-    double t_arrival = 0, t_done = 0;
+    double t_arrival = 0, t_admit = -1, t_done = -1;
     uint64_t epoch = 0;
     std::vector<uint32_t> paths, plen;
     int state = 0;  // 0 queued, 1 running, 2 done
@@ -66,6 +66,8 @@ struct bingo_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     bool stop = false;
+    bool paused = false;       // bingo_server_pause: no admissions while set
+    double t_created = 0;
     std::deque<bingo_update> updates;
     std::deque<Request*> queue;
     std::map<uint64_t, Request*> reqs;
@@ -161,9 +163,11 @@ bool launch_slot(bingo_server* S, Slot& sl, std::vector<Request*>& batch, uint64
     sl.walkers = total;
     sl.reqs = batch;
     sl.busy = true;
+    const double ta = now_s();
     for (Request* r : batch) {
         r->state = 1;
         r->epoch = epoch;
+        r->t_admit = ta;
     }
     return true;
 }
@@ -202,7 +206,7 @@ void worker_main(bingo_server* S) {
                 continue;
             }
         }
-        if (!S->queue.empty() && !updates_due) {
+        if (!S->queue.empty() && !updates_due && !S->paused) {
             // 3. admission into a free slot
             Slot* free_slot = nullptr;
             for (Slot& sl : S->slots)
@@ -217,8 +221,11 @@ void worker_main(bingo_server* S) {
                     const uint64_t n = r->starts.size();
                     const uint64_t need = n * 4ull * (r->pol.max_len + 3);
                     if (!batch.empty() && (!merge || S->inflight + w + n > max_walkers || batch.size() >= 4096)) break;
+                    // walker slots: a request waits for in-flight launches to free enough of them
                     if (batch.empty() && S->inflight + n > max_walkers && S->inflight > 0) break;
-                    if (bytes + need + S->cfg.hbm_reserve_bytes > fr && !batch.empty()) break;
+                    // device memory: a request is admitted only if its launch buffers leave hbm_reserve_bytes free;
+                    // otherwise it waits (for launches or other users of the device to free memory)
+                    if (bytes + need + S->cfg.hbm_reserve_bytes > fr) break;
                     batch.push_back(r);
                     S->queue.pop_front();
                     w += n;
@@ -253,6 +260,7 @@ extern "C" {
 
 bingo_status bingo_server_create(bingo_graph* g, const bingo_server_config* cfg, bingo_server** out) {
     if (!g || !out) { set_error("NULL argument"); return BINGO_E_INVALID; }
+    if (g->part) { set_error("server: a partition graph walks only through bingo_part_walk"); return BINGO_E_STATE; }
     bingo_server* S = new bingo_server();
     S->g = g;
     if (cfg) S->cfg = *cfg;
@@ -262,6 +270,7 @@ bingo_status bingo_server_create(bingo_graph* g, const bingo_server_config* cfg,
     if (!S->cfg.concurrent_launches) S->cfg.concurrent_launches = 4;
     if (!S->cfg.max_len_cap) S->cfg.max_len_cap = 128;
     if (!S->cfg.update_delay_us) S->cfg.update_delay_us = 1000;
+    S->t_created = now_s();
     S->slots.resize(S->cfg.concurrent_launches);
     for (Slot& sl : S->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -375,6 +384,34 @@ bingo_status bingo_server_drain(bingo_server* S, uint32_t timeout_ms) {
         set_error("an update batch failed inside the server");
         return S->worker_error;
     }
+    return BINGO_OK;
+}
+
+bingo_status bingo_server_pause(bingo_server* S, uint32_t paused) {
+    if (!S) { set_error("NULL server"); return BINGO_E_INVALID; }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->paused = paused != 0;
+    }
+    S->cv_work.notify_all();
+    return BINGO_OK;
+}
+
+bingo_status bingo_server_request_get(bingo_server* S, uint64_t ticket, bingo_server_request_info* out) {
+    if (!S || !out) { set_error("NULL argument"); return BINGO_E_INVALID; }
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) { set_error("unknown ticket %llu", (unsigned long long)ticket); return BINGO_E_INVALID; }
+    const Request* r = it->second;
+    memset(out, 0, sizeof(*out));
+    out->state = (uint32_t)r->state;
+    out->status = (uint32_t)r->status;
+    out->walkers = r->starts.size();
+    out->epoch = r->epoch;
+    const auto ms = [&](double t) { return t < 0 ? -1.0 : (t - S->t_created) * 1e3; };
+    out->submit_ms = ms(r->t_arrival);
+    out->admit_ms = ms(r->t_admit);
+    out->done_ms = ms(r->t_done);
     return BINGO_OK;
 }
 

@@ -755,6 +755,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     }
     if (rank == 0) {
         G.vc[v].wcold = cold_total(G, sh.cnt_new);
+        G.vh[v].word = (G.vh[v].word & WORD_ID) | (cold_desc(G, sh.cnt_new) ? WORD_DESC : 0u);
         VHdr h;
         h.adj = adj;
         h.deg = d1;
@@ -788,6 +789,7 @@ struct BatchArgs {
     uint64_t count;                // record capacity (grid size); the live count is *count_dev when set
     const uint64_t* count_dev;
     uint32_t n, max_bits, bn;
+    uint32_t dst_n;  // destinations are ids below dst_n (n for a whole graph; the global count for a partition)
     uint32_t fbits;       // real biases (Section 4.3) when nonzero
     double lambda;
     uint64_t* keys;
@@ -814,7 +816,7 @@ __global__ void k_expand(BatchArgs A) {
         const uint4 u = A.ups[i];
         const bool ins = u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS;
         const bool del = u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS;
-        bad |= u.x >= A.n || u.y >= A.n || u.w > 2;
+        bad |= u.x >= A.n || u.y >= A.dst_n || u.w > 2;
         if (ins && A.fbits) {
             uint32_t I, q;
             bad |= !split_real_bias(u.z, A.lambda, I, q);
@@ -831,7 +833,7 @@ __global__ void k_make_keys(BatchArgs A) {
     const uint64_t cnt = live_count(A);
     for (uint64_t i = tid; i < cnt; i += nt) {
         const uint4 u = A.ups[i];
-        if (u.x >= A.n || u.y >= A.n || u.w > 2) continue;
+        if (u.x >= A.n || u.y >= A.dst_n || u.w > 2) continue;
         uint64_t pos = A.pscan[i] & 0xFFFFFFFFull;
         const uint64_t sk = (uint64_t)batch_id(A, u.x) << (A.bn + 1);
         if (u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS) {
@@ -1448,10 +1450,11 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     A.count = cap;
     A.count_dev = ctl + CTL_SCR + 8;
     A.n = g->n;
+    A.dst_n = g->G.dst_n;
     A.max_bits = g->G.base4 ? std::min<uint32_t>(g->cfg.max_bits, 2 * B4_POSITIONS) : g->cfg.max_bits;
     A.fbits = g->G.fbits;
     A.lambda = g->G.lambda;
-    A.bn = bits_for(g->n);
+    A.bn = bits_for(std::max(g->n, g->G.dst_n));  // one key width for the source and the destination
     A.keys = (uint64_t*)g->s_keys.p;
     A.vals = (uint32_t*)g->s_vals.p;
     A.packed = (uint64_t*)g->s_rank.p;
@@ -1630,10 +1633,11 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     A.count = count;
     A.count_dev = nullptr;
     A.n = g->n;
+    A.dst_n = g->G.dst_n;
     A.max_bits = g->G.base4 ? std::min<uint32_t>(g->cfg.max_bits, 2 * B4_POSITIONS) : g->cfg.max_bits;
     A.fbits = g->G.fbits;
     A.lambda = g->G.lambda;
-    A.bn = bits_for(g->n);
+    A.bn = bits_for(std::max(g->n, g->G.dst_n));  // one key width for the source and the destination
     A.keys = (uint64_t*)g->s_keys.p;
     A.vals = (uint32_t*)g->s_vals.p;
     A.packed = (uint64_t*)g->s_rank.p;

@@ -25,6 +25,10 @@ using namespace bingo;
 namespace {
 
 constexpr int MAX_DENSE_TRIES = 1 << 14;
+// Thread bound of the 64+-register walker instances: 768 threads a block leave each thread up to 80
+// registers, which the cold-group scan needs without spilling (measured faster than 64 registers
+// with spills at 1,024 threads).
+constexpr int WALK_MAX_THREADS = 768;
 constexpr int MAX_N2V_TRIES = 1 << 14;
 constexpr uint32_t WF_PAD = 1u;  // pad path rows with 0xFFFFFFFF
 
@@ -54,7 +58,27 @@ struct WalkParams {
     // stepwise state
     uint32_t* s_cur;
     uint32_t* s_prev;
+    // partitioned walks: this launch serves the graph's vertex range [G.base, G.base + G.n); walkers
+    // come from `resume` records (global ids) and leave through `outbox` when their next vertex is
+    // another partition's; node2vec probes the previous vertex's owner's edge index
+    const PartRec* resume;
+    PartRec* outbox;
+    unsigned long long* nout;
+    const PartEH* peh;
+    const uint32_t* bounds;  // npart + 1 boundaries of the partitions (global ids)
+    uint32_t npart;
 };
+
+// Live copies of (prev, x), global ids, in the edge index of prev's partition.
+__device__ __forceinline__ uint32_t part_probe(const WalkParams& A, uint32_t prev, uint32_t x) {
+    uint32_t lo = 0, hi = A.npart;  // last p with bounds[p] <= prev
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(A.bounds + mid) <= prev) lo = mid; else hi = mid;
+    }
+    const PartEH e = A.peh[lo];
+    return e.mask ? eh_lookup_in(e.key, e.cnt, e.mask, prev - __ldg(A.bounds + lo), x) : 0u;
+}
 
 // Policy index of walker `wid`: its request in request mode, else policy_ids[wid] (default 0).
 __device__ __forceinline__ uint32_t walker_pid(const WalkParams& A, uint64_t wid) {
@@ -96,7 +120,7 @@ __device__ __forceinline__ uint4 ld_hot(const uint4* q) {
 // Hot part of a vertex record: the header and groups 0-5 (pairs 0-2), one 64-byte line.
 struct Sec0 {
     uint32_t adj, deg, mask;
-    uint32_t word;  // the caller's id of the vertex
+    uint32_t word;  // the caller's id of the vertex, and the cold scan order (WORD_DESC)
     uint4 p0, p1, p2;
 };
 __device__ __forceinline__ Sec0 ld_sec0(const DevGraph& G, uint32_t v) {
@@ -127,9 +151,10 @@ __device__ __forceinline__ uint64_t pair_w(uint4 x, uint32_t i) {
 __device__ __forceinline__ uint32_t pair_bits(uint32_t mask) { return (mask | (mask >> 1)) & 0x55555555u; }
 
 // --------------------------------------------------------------------------------- group selection
-// All variants pick k* = min{k : sum_{j<=k} 2^j |G_j| > r} with r uniform in [0, sum_j 2^j |G_j|),
-// i.e. group k with probability W(p_k) / sum W (Eq. group_prob); they differ only in how a team
-// of T lanes shares the vertex record.  Outputs k*, |G_k*| and the group's ref.
+// All variants pick the first group k* in the vertex's scan order whose running sum of
+// W(p_k) = 2^k |G_k| exceeds r, r uniform in [0, sum_j W(p_j)): group k with probability
+// W(p_k) / sum W (Eq. group_prob).  They differ only in how a team of T lanes shares the vertex
+// record.  Outputs k*, |G_k*| and the group's ref.
 
 template <int WM>
 __device__ __forceinline__ bool scan_pair(uint4 x, uint32_t i, uint64_t r, uint64_t& acc, uint32_t& ks, uint32_t& cs,
@@ -140,11 +165,29 @@ __device__ __forceinline__ bool scan_pair(uint4 x, uint32_t i, uint64_t r, uint6
     if (r < acc) { ks = 2 * i + 1; cs = x.z; ref = x.w; return true; }
     return false;
 }
+// The same with the pair's two groups in descending order (cold groups of a vertex scanned downwards).
+template <int WM>
+__device__ __forceinline__ bool scan_pair_desc(uint4 x, uint32_t i, uint64_t r, uint64_t& acc, uint32_t& ks,
+                                               uint32_t& cs, uint32_t& ref) {
+    const uint64_t hi = acc + slot_weight<WM>(x.z, 2 * i + 1);
+    if (r < hi) { ks = 2 * i + 1; cs = x.z; ref = x.w; return true; }
+    acc = hi + slot_weight<WM>(x.x, 2 * i);
+    if (r < acc) { ks = 2 * i; cs = x.x; ref = x.y; return true; }
+    return false;
+}
+
+// Scan order of the groups of a vertex: the hot groups 0-5 ascending, then the cold groups 6-31
+// ascending, or descending when the hot word's WORD_DESC bit is set (cold_desc).  Any fixed order
+// of the inverse CDF draws group k with probability W(p_k) / sum W; every team width uses this one,
+// so all give the same k* for the same r.
+constexpr uint32_t COLD_PAIRS = 0x55555540u;  // pair bits 2i of the cold pairs i = 3..15
 
 // T = 1: one lane per walker.  Pairs 0-2 came with the header and the total weight of groups
 // 6-31 comes from the cold record's first sector (VCold.wcold, read when the mask shows a cold
-// group), so r is drawn without reading the cold groups.  They are read, in batches of four pairs whose loads are issued together
-// (predicated on the mask), only when r falls beyond the hot groups.
+// group), so r is drawn without reading the cold groups.  They are read only when r falls beyond
+// the hot groups, in the vertex's scan order (cold_desc): upwards in the aligned batches of pairs
+// [3, 7), [7, 11), [11, 15), [15], or downwards in windows of four pairs from the highest nonempty
+// cold pair; the loads of a batch are issued together and empty batches are skipped.
 template <int WM>
 __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status) {
@@ -157,18 +200,31 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
     if (scan_pair<WM>(h.p0, 0, r, acc, ks, cs, ref)) return;
     if (scan_pair<WM>(h.p1, 1, r, acc, ks, cs, ref)) return;
     if (scan_pair<WM>(h.p2, 2, r, acc, ks, cs, ref)) return;
+    // one loop for both directions: batch starts i0 = 3, 7, 11, 15 upwards, or top, top - 4, ...
+    // downwards; a downward pair is scanned odd group first (its halves swapped)
+    const bool desc = (h.word & WORD_DESC) != 0;
+    const uint32_t cm = pb & COLD_PAIRS;
+    const int dir = desc ? -1 : 1;
 #pragma unroll 1
-    for (uint32_t i0 = 3; i0 < 16; i0 += 4) {
-        if (!((pb >> (2 * i0)) & 0x55u)) continue;
+    for (int i0 = desc ? (int)((31 - __clz(cm)) >> 1) : 3; desc ? i0 >= 3 : i0 < 16; i0 += 4 * dir) {
+        const int low = desc ? i0 - 3 : i0;  // lowest pair of the batch (>= 0: i0 >= 3 downwards)
+        if (!((cm >> (2 * low)) & 0xFFu)) continue;
         uint4 x[4];
 #pragma unroll
-        for (uint32_t j = 0; j < 4; j++) {
-            const uint32_t i = i0 + j;
-            x[j] = (i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair(G, v, i) : make_uint4(0, 0, 0, 0);
+        for (int j = 0; j < 4; j++) {
+            const int i = i0 + dir * j;
+            x[j] = (i >= 3 && i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair(G, v, (uint32_t)i) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
-        for (uint32_t j = 0; j < 4; j++)
-            if (scan_pair<WM>(x[j], i0 + j, r, acc, ks, cs, ref)) return;
+        for (int j = 0; j < 4; j++) {
+            const uint32_t i = (uint32_t)(i0 + dir * j);
+            const uint4 y = desc ? make_uint4(x[j].z, x[j].w, x[j].x, x[j].y) : x[j];
+            const uint32_t k0 = desc ? 2 * i + 1 : 2 * i, k1 = desc ? 2 * i : 2 * i + 1;
+            const uint64_t lo = acc + slot_weight<WM>(y.x, k0);
+            if (r < lo) { ks = k0; cs = y.x; ref = y.y; return; }
+            acc = lo + slot_weight<WM>(y.z, k1);
+            if (r < acc) { ks = k1; cs = y.z; ref = y.w; return; }
+        }
     }
     ks = 31;
     cs = 0;
@@ -176,17 +232,22 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
     atomicOr(status, ST_STATE);  // r beyond every group: the cached total disagrees with the counts
 }
 
-// T = 4: lane t of the team owns pairs [4t, 4t+4) (groups 8t..8t+7); a two-level shuffle prefix
+// Pair at scan position p (0..15) of a vertex: hot pairs 0-2, then the cold pairs up or down.
+__device__ __forceinline__ uint32_t pair_at(uint32_t p, bool desc) { return (p < 3 || !desc) ? p : 18 - p; }
+
+// T = 4: lane t of the team owns scan positions [4t, 4t+4) (pair_at); a two-level shuffle prefix
 // over the team and a ballot find the lane holding k*, which searches its pairs again.
 template <int WM>
 __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status,
                                                uint32_t tl, uint32_t team_mask, uint32_t team_base) {
-    const uint32_t mine = (pair_bits(h.mask) >> (8 * tl)) & 0x55u;
+    const uint32_t pb = pair_bits(h.mask);
+    const bool desc = (h.word & WORD_DESC) != 0;
     uint64_t s = 0;
-    for (uint32_t m = mine; m; m &= m - 1) {
-        const uint32_t i = 4 * tl + ((__ffs(m) - 1) >> 1);
-        s += pair_w<WM>(ld_pair(G, v, i), i);
+#pragma unroll
+    for (uint32_t j = 0; j < 4; j++) {
+        const uint32_t i = pair_at(4 * tl + j, desc);
+        if ((pb >> (2 * i)) & 1u) s += pair_w<WM>(ld_pair(G, v, i), i);
     }
     uint64_t incl = s;
 #pragma unroll
@@ -209,14 +270,13 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
     uint32_t k_l = 0, c_l = 0, r_l = 0;
     if (lane_id() == owner) {
         uint64_t acc = excl;
-        bool found = false;
-        for (uint32_t m = mine; m && !found; m &= m - 1) {
-            const uint32_t i = 4 * tl + ((__ffs(m) - 1) >> 1);
+        for (uint32_t j = 0; j < 4; j++) {
+            const uint32_t p = 4 * tl + j, i = pair_at(p, desc);
+            if (!((pb >> (2 * i)) & 1u)) continue;
             const uint4 x = ld_pair(G, v, i);
-            acc += slot_weight<WM>(x.x, 2 * i);
-            if (r < acc) { k_l = 2 * i; c_l = x.x; r_l = x.y; found = true; break; }
-            acc += slot_weight<WM>(x.z, 2 * i + 1);
-            if (r < acc) { k_l = 2 * i + 1; c_l = x.z; r_l = x.w; found = true; }
+            if ((p >= 3 && desc) ? scan_pair_desc<WM>(x, i, r, acc, k_l, c_l, r_l)
+                                 : scan_pair<WM>(x, i, r, acc, k_l, c_l, r_l))
+                break;
         }
     }
     ks = __shfl_sync(team_mask, k_l, owner);
@@ -224,16 +284,19 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
     ref = __shfl_sync(team_mask, r_l, owner);
 }
 
-// T = 32: lane k owns group k; a warp-wide shuffle prefix of W_k = 2^k |G_k| and a ballot of
-// (prefix > r) give k* as the first set bit.
+// T = 32: lane l owns the group at scan position l (slot l, or 37 - l for cold positions scanned
+// downwards); a warp-wide shuffle prefix of W_k = 2^k |G_k| and a ballot of (prefix > r) give k*
+// at the first set bit.
 template <int WM>
 __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                 uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status,
                                                 uint32_t lane) {
+    const bool desc = (h.word & WORD_DESC) != 0;
+    const uint32_t k = (lane < HOT_GROUPS || !desc) ? lane : 37 - lane;
     uint2 gk = make_uint2(0, 0);
-    if ((h.mask >> lane) & 1u)
-        gk = __ldg(lane < HOT_GROUPS ? &G.vh[v].g[lane] : &G.vc[v].g[lane - HOT_GROUPS]);
-    uint64_t incl = slot_weight<WM>(gk.x, lane);
+    if ((h.mask >> k) & 1u)
+        gk = __ldg(k < HOT_GROUPS ? &G.vh[v].g[k] : &G.vc[v].g[k - HOT_GROUPS]);
+    uint64_t incl = slot_weight<WM>(gk.x, k);
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const uint64_t y = __shfl_up_sync(FULL, incl, d);
@@ -249,9 +312,10 @@ __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, c
         if (lane == 0) atomicOr(status, ST_STATE);
         return;
     }
-    ks = __ffs(b) - 1;
-    cs = __shfl_sync(FULL, gk.x, ks);
-    ref = __shfl_sync(FULL, gk.y, ks);
+    const uint32_t owner = __ffs(b) - 1;
+    ks = __shfl_sync(FULL, k, owner);
+    cs = __shfl_sync(FULL, gk.x, owner);
+    ref = __shfl_sync(FULL, gk.y, owner);
 }
 
 // --------------------------------------------------------------------------------- intra-group pick
@@ -323,7 +387,8 @@ __device__ __forceinline__ uint32_t pick_member(const DevGraph& G, const Sec0& h
 }
 
 // One step of a walker at `cur`.  Returns false if the walk ends here (PPR stop, no out-edge, error).
-template <int T, int WM>
+// PART: a partition graph's walker (previous vertex and the sampled vertex are global ids).
+template <int T, int WM, bool PART>
 __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A, uint64_t wid, uint32_t pid,
                                           uint32_t step, uint32_t& cur, uint32_t& prev, uint32_t tl,
                                           uint32_t team_mask, uint32_t team_base, uint32_t lane, uint32_t& hword) {
@@ -339,7 +404,7 @@ __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A
     hword = NONE32;
     if (kind == BINGO_PPR && R.next() < __ldg(&P->ppr_stop_u32)) return false;
     const Sec0 h = ld_sec0(G, cur);
-    hword = h.word;
+    hword = h.word & WORD_ID;
     if (h.deg == 0) return false;
     for (int attempt = 0; attempt < MAX_N2V_TRIES; attempt++) {
         uint32_t ks, cs, ref;
@@ -347,7 +412,7 @@ __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A
         else if constexpr (T == 4) select_group_4<WM>(G, cur, h, R, ks, cs, ref, A.status, tl, team_mask, team_base);
         else select_group_32<WM>(G, cur, h, R, ks, cs, ref, A.status, lane);
         const uint32_t x = pick_member<WM>(G, h, ks, cs, ref, R, A.status);
-        if (x >= G.n) {
+        if (x >= G.dst_n) {
             if (x != NONE32) atomicOr(A.status, ST_STATE);
             return false;
         }
@@ -362,12 +427,12 @@ __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A
                 const uint64_t lo = a1 < a2 ? a1 : a2, hi = a1 < a2 ? a2 : a1;
                 if (u < lo) acc = true;        // accepted at either distance: no probe needed
                 else if (u >= hi) acc = false; // rejected at either distance
-                else acc = u < (eh_lookup(G, prev, x) ? a1 : a2);
+                else acc = u < ((PART ? part_probe(A, prev, x) : eh_lookup(G, prev, x)) ? a1 : a2);
             }
             if (!acc) continue;
         }
-        prev = cur;
-        cur = x;
+        prev = PART ? cur + G.base : cur;  // partitioned walks keep the previous vertex's global id
+        cur = x;                           // partitioned walks: a global id (the caller localises it)
         return true;
     }
     atomicOr(A.status, ST_TIMEOUT);
@@ -403,8 +468,8 @@ __device__ __forceinline__ void finish_walker(const WalkParams& A, uint64_t wid,
 // (256-thread blocks, six per SM), trading spills to L1 for 50% more resident warps.
 // WM: the graph's weight mode; each mode runs its own instance (integer graphs carry no code for the
 // decimal group or the base-4 weights).
-template <int T, int OCC, int WM>
-__global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persistent(DevGraph G, WalkParams A) {
+template <int T, int OCC, int WM, bool PART = false>
+__global__ void __launch_bounds__(OCC ? 256 : WALK_MAX_THREADS, OCC ? 6 : 1) k_walk_persistent(DevGraph G, WalkParams A) {
     const uint32_t lane = threadIdx.x & 31, tl = lane % T, team = lane / T;
     const uint32_t team_base = team * T;
     const uint32_t team_mask = (T == 32) ? FULL : (((1u << T) - 1u) << team_base);
@@ -423,7 +488,24 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
                 uint64_t mine = base + __popc(nm & lanemask_lt());
                 mine = __shfl_sync(FULL, mine, team_base);
                 if (base + __popc(nm) >= A.nwalkers) drained = true;
-                if (!have && mine < A.nwalkers) {
+                if (PART && !have && mine < A.nwalkers) {  // a walker arriving in this partition
+                    const PartRec rc = A.resume[mine];
+                    wid = rc.wid;
+                    pid = walker_pid(A, wid);
+                    if (pid >= A.npol) { pid = 0; atomicOr(A.status, ST_INVALID); }
+                    L = A.lengths ? __ldg(A.lengths + wid) : __ldg(&A.pols[pid].max_len);
+                    if (L + 1 > A.stride) { L = A.stride - 1; atomicOr(A.status, ST_INVALID); }
+                    cur = rc.cur - G.base;
+                    prev = rc.prev;
+                    step = rc.step;
+                    if (cur >= G.n) { L = step; atomicOr(A.status, ST_STATE); }  // routed to a wrong partition
+                    have = true;
+                    if (step == 0 && tl == 0) A.paths[wid * (uint64_t)A.stride] = rc.cur;
+                    if (step >= L) {
+                        finish_walker(A, wid, step, tl, T, team_mask);
+                        have = false;
+                    }
+                } else if (!PART && !have && mine < A.nwalkers) {
                     wid = mine;
                     pid = walker_pid(A, wid);
                     if (pid >= A.npol) { pid = 0; atomicOr(A.status, ST_INVALID); }
@@ -449,18 +531,35 @@ __global__ void __launch_bounds__(OCC ? 256 : 1024, OCC ? 6 : 1) k_walk_persiste
         }
         if (have) {
             uint32_t hword;
-            const bool took = walk_step<T, WM>(G, A, wid, pid, step, cur, prev, tl, team_mask, team_base, lane, hword);
+            const bool took = walk_step<T, WM, PART>(G, A, wid, pid, step, cur, prev, tl, team_mask, team_base, lane, hword);
             uint32_t* row = A.paths + wid * (uint64_t)A.stride;
             // Path entry `step` is the vertex this step started from, whose hot line carries the
             // caller's id; it is read there (no extra load) except when the walk stopped before
             // reading it, and for the last vertex of a walk.
             if (step && tl == 0) row[step] = hword != NONE32 ? hword : to_caller(G, cur);
+            bool remote = false;
             if (took) {
                 step++;
-                if (step == L && tl == 0) row[step] = to_caller(G, cur);
+                if (PART) {  // partitioned: the sampled vertex is a global id
+                    remote = cur - G.base >= G.n;
+                    if (!remote) cur -= G.base;
+                }
+                if (step == L && tl == 0) row[step] = remote ? cur : to_caller(G, cur);
             }
             if (!took || step == L) {
                 finish_walker(A, wid, step, tl, T, team_mask);
+                have = false;
+            } else if (PART && remote) {  // continue in the owner's next launch
+                if (tl == 0) {
+                    row[step] = cur;
+                    PartRec rc;
+                    rc.wid = wid;
+                    rc.cur = cur;
+                    rc.prev = prev;
+                    rc.step = step;
+                    rc.pad = 0;
+                    A.outbox[atomicAdd(A.nout, 1ull)] = rc;
+                }
                 have = false;
             }
         }
@@ -494,7 +593,7 @@ __global__ void k_walk_step(DevGraph G, WalkParams A, uint32_t s) {
             prev = A.s_prev[wid];
         }
         uint32_t hword;
-        const bool took = walk_step<1, WM>(G, A, wid, pid, s, cur, prev, 0, 0, 0, 0, hword);
+        const bool took = walk_step<1, WM, false>(G, A, wid, pid, s, cur, prev, 0, 0, 0, 0, hword);
         if (took) A.paths[wid * (uint64_t)A.stride + s + 1] = to_caller(G, cur);
         if (!took || s + 1 == L) {
             finish_walker(A, wid, took ? s + 1 : s, 0, 1, 1u << (threadIdx.x & 31));
@@ -638,6 +737,12 @@ bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
     A.host_flags = q.host_flags;
     A.chunk_shift = q.chunk_shift;
     A.io_seq = q.io_seq;
+    A.resume = q.resume;
+    A.outbox = q.outbox;
+    A.nout = q.nout;
+    A.peh = q.peh;
+    A.bounds = q.bounds;
+    A.npart = q.npart;
     if (nwalkers == 0) return BINGO_OK;
     if (mode == BINGO_WALK_STEPWISE) {
         CK(ensure(g->s_walk, 8 * nwalkers), "walk state");
@@ -659,6 +764,8 @@ bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
     const int lanes = (int)g->tune.lanes, occ_mode = (int)g->tune.occ;
     int wpb = (int)g->tune.warps_per_block;
     if (occ_mode && wpb > 8) wpb = 8;  // the 40-register variant is bounded to 256-thread blocks
+    if (wpb > WALK_MAX_THREADS / 32) wpb = WALK_MAX_THREADS / 32;
+    if (wpb < 1) wpb = 1;
     int bps = (int)g->tune.blocks_per_sm;
     const int wm = weight_mode(g);
     const int occ = walk_blocks_per_sm(lanes, wpb, occ_mode, wm);
@@ -669,8 +776,17 @@ bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
     if (blocks > useful) blocks = useful;
     if (blocks == 0) blocks = 1;
     void* args[] = {(void*)&g->G, (void*)&A};
-    CK(cudaLaunchKernel(walk_kernel(lanes, occ_mode, wm), dim3((unsigned)blocks), dim3(wpb * 32), args, 0, s),
-       "walk launch");
+    void* fn = walk_kernel(lanes, occ_mode, wm);
+    if (q.resume) {  // partitioned walks: one lane per walker, the 80-register build
+        fn = wm == WM_REAL ? (void*)k_walk_persistent<1, 0, WM_REAL, true>
+             : wm == WM_B4 ? (void*)k_walk_persistent<1, 0, WM_B4, true>
+                           : (void*)k_walk_persistent<1, 0, WM_INT, true>;
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 8 * 32, 0);
+        blocks = std::min<uint64_t>((uint64_t)g->num_sms * (nb < 1 ? 1 : nb), (nwalkers + 31) / 32);
+        wpb = 8;
+    }
+    CK(cudaLaunchKernel(fn, dim3((unsigned)(blocks ? blocks : 1)), dim3(wpb * 32), args, 0, s), "walk launch");
     g->launches++;
     CK(cudaGetLastError(), "walk launch");
     return BINGO_OK;

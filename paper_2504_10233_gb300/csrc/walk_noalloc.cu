@@ -77,6 +77,7 @@ extern "C" bingo_status bingo_walk_noalloc(bingo_graph* g, uint64_t nwalkers, co
     if (g->broken) { set_error("walk_noalloc: graph state is unusable"); return BINGO_E_STATE; }
     bingo_status st = check_device(g, "walk_noalloc");
     if (st != BINGO_OK) return st;
+    if (g->part) { set_error("walk_noalloc: a partition graph walks only through bingo_part_walk"); return BINGO_E_STATE; }
     if ((mode & 0xFF) != BINGO_WALK_PERSISTENT) {
         set_error("walk_noalloc: only the persistent form runs without allocating (mode %u)", mode);
         return BINGO_E_INVALID;

@@ -33,9 +33,11 @@ def b4_slots(w):
     return out
 
 
-def gpu_canonical(ex, memb=None):
+def gpu_canonical(ex, memb=None, skip_dense=False):
     """Edges sorted by (vertex, eid) and group memberships sorted by (vertex, k, eid).  memb: per
-    edge slot mask when it is not the bias itself (radix base 4)."""
+    edge slot mask when it is not the bias itself (radix base 4).  skip_dense: leave out dense groups,
+    whose members are by definition the adjacency filtered by bit k (compared through the adjacency
+    and the kinds)."""
     deg = ex["deg"].astype(np.int64)
     n = len(deg)
     eoff = _segments(deg)
@@ -48,7 +50,7 @@ def gpu_canonical(ex, memb=None):
     w = (ex["bias"] if memb is None else memb).astype(np.uint64)
     vs, ks, es = [], [], []
     # dense groups: filter the adjacency by bit k
-    for k in range(32):
+    for k in (range(32) if not skip_dense else ()):
         bit = ((w >> np.uint64(k)) & np.uint64(1)).astype(bool)
         dense_v = kind[:, k] == O.DENSE
         sel = bit & dense_v[vslot]
@@ -171,3 +173,61 @@ def assert_steps_live(og: O.Graph, paths: np.ndarray, plen: np.ndarray, keys=Non
     if padded:
         pad = np.arange(L)[None, :] >= plen.astype(np.int64)[:, None]
         assert (paths[pad] == 0xFFFFFFFF).all(), "padding is not 0xFFFFFFFF"
+
+
+def assert_vertices_match(exv, og: O.Graph, ids, alpha=40, beta=10):
+    """Bit-exact state of listed vertices (bingo_export_vertices rows) against an oracle graph holding
+    at least those vertices' rows: adjacency (destination, bias, edge id), |G_k| and kinds, and the
+    member sets of every one-element, sparse and regular group; layout invariants of the rows.  Dense
+    groups are the adjacency filtered by bit k on both sides, so the adjacency and kind comparisons
+    cover them."""
+    ids = np.asarray(ids, dtype=np.uint32)
+    k = len(ids)
+    (gv, gd, gw, ge), (Gv, Gk, Ge) = gpu_canonical(exv, skip_dense=True)
+    offs, od, ow, oe = og.edges_of(ids)
+    odeg = np.diff(offs.astype(np.int64))
+    ov = np.repeat(np.arange(k, dtype=np.int64), odeg)
+    assert (exv["deg"].astype(np.int64) == odeg).all(), "degrees differ"
+    assert len(ge) == len(oe), f"edge count {len(ge)} != oracle {len(oe)}"
+    assert (gv == ov).all() and (gd == od).all() and (gw == ow).all() and (ge == oe).all(), "adjacency differs"
+    cnt = np.zeros((k, 32), dtype=np.uint32)
+    kd = np.zeros((k, 32), dtype=np.uint8)
+    for i, v in enumerate(ids):
+        cnt[i], kd[i], _ = og.factor(int(v), alpha, beta)
+    assert (exv["cnt"] == cnt).all(), "group counts differ"
+    assert (exv["kind"] == kd).all(), "group kinds differ"
+    # members of the non-dense groups by definition: the edges whose bias has bit k (Eq. dwi)
+    vs, ks, es = [], [], []
+    listlike = (kd == O.ONE) | (kd == O.SPARSE) | (kd == O.REGULAR)
+    keep = listlike.any(axis=1)[ov]  # only rows with a non-dense group have members to compare
+    ov_, w64, oe_ = ov[keep], ow[keep].astype(np.uint64), oe[keep]
+    for b in range(32):
+        sel = (((w64 >> np.uint64(b)) & np.uint64(1)) == 1) & listlike[ov_, b]
+        vs.append(ov_[sel]); ks.append(np.full(int(sel.sum()), b, np.int64)); es.append(oe_[sel])
+    V, K, E = np.concatenate(vs), np.concatenate(ks), np.concatenate(es).astype(np.uint64)
+    o = np.lexsort((E, K, V))
+    assert len(Ge) == len(E), f"membership count {len(Ge)} != oracle {len(E)}"
+    assert (Gv == V[o]).all() and (Gk == K[o]).all() and (Ge == E[o]).all(), "group memberships differ"
+    check_layout_invariants(exv)
+
+
+def sampled_oracle(G, ids, next_eid=None):
+    """Oracle graph holding only the rows of the listed sources of CSR graph G, each edge with its id
+    in G (its CSR position); other vertices have no edges."""
+    ids = np.unique(np.asarray(ids, dtype=np.int64))
+    rp = G.row_ptr.astype(np.int64)
+    deg = rp[ids + 1] - rp[ids]
+    sub_rp = np.zeros(G.n + 1, dtype=np.int64)
+    sub_rp[ids + 1] = deg
+    sub_rp = np.cumsum(sub_rp).astype(np.uint64)
+    tot = int(deg.sum())
+    rows = np.repeat(rp[ids], deg) + (np.arange(tot, dtype=np.int64) - np.repeat(np.cumsum(deg) - deg, deg))
+    return O.Graph.from_csr_ids(G.n, sub_rp, G.col[rows], G.w[rows], rows.astype(np.uint64),
+                                int(rp[-1]) if next_eid is None else next_eid)
+
+
+def insertion_ids(records, next_eid):
+    """Edge id of every insertion record of a batch: the count continues in batch order (Section 5.2)."""
+    op = np.asarray(records)[:, 3]
+    ins = (op == 0) | (op == 2)
+    return (next_eid + np.cumsum(ins) - 1).astype(np.uint64), next_eid + int(ins.sum())

@@ -72,3 +72,36 @@ def test_cpu_baseline_leg_reports_a_bounded_sample():
     cb = bench.cpu_baseline(wl.graph, wl.batches[0], wl.length, 77, target_s=0.2)
     assert cb["kind"] == "oracle" and cb["unit"] == "steps/s" and cb["value"] > 0 and cb["cores"] >= 1
     assert "DeepWalk walkers x 80" in cb["sample"]
+
+
+def test_update_bytes_on_exported_rows_equals_whole_export():
+    """The same batch counted from exports of only the touched vertices (rows in id order) gives the
+    bytes of the whole export."""
+    ex0 = _export([2, 1, 0], [1, 2, 0], [5, 3, 1], [0, 1, 2], 3)
+    ex0["kind"][0, 0], ex0["kind"][0, 2] = REGULAR, ONE
+    ex1 = _export([2, 1, 0], [2, 2, 0], [3, 6, 1], [1, 3, 2], 3)
+    ex1["kind"][0, 0], ex1["kind"][0, 1], ex1["kind"][0, 2] = REGULAR, ONE, DENSE
+    ex1["cnt"][0, 0], ex1["cnt"][0, 1], ex1["cnt"][0, 2] = 1, 1, 1
+    rec = np.array([[0, 2, 6, 0], [0, 1, 0, 1], [2, 0, 0, 1], [1, 0, 9, 2]], np.uint32)
+    whole = bench.update_bytes(ex0, ex1, rec)
+
+    def rows(ex, ids):
+        deg = ex["deg"].astype(np.int64)
+        off = np.concatenate([[0], np.cumsum(deg)])
+        sel = np.concatenate([np.arange(off[v], off[v + 1]) for v in ids]).astype(np.int64)
+        return {"deg": ex["deg"][ids], "dst": ex["dst"][sel], "bias": ex["bias"][sel], "eid": ex["eid"][sel],
+                "kind": ex["kind"][ids], "cnt": ex["cnt"][ids]}
+
+    ids = np.array([0, 1, 2])
+    assert bench.update_bytes(rows(ex0, ids), rows(ex1, ids), rec, ids=ids) == whole
+
+
+def test_sampled_steps_are_uniform_over_the_launch_steps():
+    plen = np.array([1, 3, 2, 0, 5], np.uint32)  # steps per walker: 0, 2, 1, 0, 4 (7 in all)
+    w, t, tot = bench.sample_steps(plen, 70000, 3)
+    assert tot == 7
+    assert ((t >= 0) & (t < plen[w].astype(np.int64) - 1)).all()
+    freq = np.bincount(w * 8 + t, minlength=64) / 70000
+    for walker, steps in enumerate([0, 2, 1, 0, 4]):
+        for step in range(steps):
+            assert abs(freq[walker * 8 + step] - 1 / 7) < 0.01
