@@ -304,15 +304,18 @@ POLICY_NAME = {"deepwalk": "DeepWalk", "ppr": "PPR (stop 0.15; x = cap)"}
 METRIC_MAIN = "sampled walk steps/s (update batch + walk per step); updated edges/s; p50/p99 latency in the serving bench"
 
 
-def main_workload(name, nsteps):
+def main_workload(name, nsteps, scale=None):
     """The workload and its per-step batches (plus, for c5, the records of the batch-size sweep): one
-    stream of hold-out-protocol records cut into consecutive batches."""
+    stream of hold-out-protocol records cut into consecutive batches.  scale: a smaller RMAT scale of
+    the same recipe (edge factor 16; hubs keep their degree up to a sixteenth of the edges), for
+    profiling captures that must stay small."""
     spec = MAIN[name]
     extra = SWEEP_REPS * sum(SWEEP_SIZES) if spec["sweep"] else 0
+    shrink = {} if scale is None else {"scale": scale, "m": 16 << scale}
     if name in ("c1", "c2"):
-        wl = W.make_workload(name, nbatch=nsteps)
+        wl = W.make_workload(name, nbatch=nsteps, **shrink)
         return wl, [b.records() for b in wl.batches], None
-    wl = W.make_workload(name, nbatch=1, batch=nsteps * spec["batch"] + extra)
+    wl = W.make_workload(name, nbatch=1, batch=nsteps * spec["batch"] + extra, **shrink)
     rec = wl.batches[0].records()
     b = spec["batch"]
     return wl, [rec[i * b:(i + 1) * b] for i in range(nsteps)], rec[nsteps * b:]
@@ -322,7 +325,10 @@ def main_config(args, wl, name=None):
     """The workload part of the main line's config, shared by both arms."""
     name = name or args.workload
     spec = MAIN[name]
-    return {"workload": spec["text"], "walkers": wl.nwalkers, "length": spec["length"], "policy": spec["policy"],
+    text = spec["text"]
+    if getattr(args, "scale", None) is not None and name == args.workload:
+        text = f"scaled to RMAT-{args.scale} (2^{args.scale} vertices, edge factor 16), otherwise: " + text
+    return {"workload": text, "walkers": wl.nwalkers, "length": spec["length"], "policy": spec["policy"],
             "updates_per_step": spec["batch"]}
 
 
@@ -356,9 +362,13 @@ def cpu_baseline(G, batch, length, seed, target_s=15.0, name="c2", one_thread_s=
         return float((plen.astype(np.int64) - 1).sum()), time.perf_counter() - t0
 
     def sized(budget_s, seed_):
-        steps, dt = timed(4096, seed_)
-        rate = max(steps / max(dt, 1e-9), 1.0)
-        nw = int(min(1 << 24, max(4096, budget_s * rate / max(length * 0.5, 1))))
+        # every walk call first rebuilds the prefix sums of the whole graph: fit that fixed cost and
+        # the cost per walker from two calibration calls, then size the sample to the budget
+        _, t1 = timed(4096, seed_)
+        _, t2 = timed(32768, seed_ + 2)
+        per = max((t2 - t1) / (32768 - 4096), 1e-9)
+        fixed = max(t1 - 4096 * per, 0.0)
+        nw = int(min(1 << 24, max(4096, (budget_s - fixed) / per)))
         steps, dt = timed(nw, seed_ + 1)
         return nw, steps, dt
 
@@ -389,7 +399,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    wl, batches, _ = main_workload(args.workload, args.steps + args.warmup)
+    wl, batches, _ = main_workload(args.workload, args.steps + args.warmup, args.scale)
     G = wl.graph
     og = O.Graph(G.n, G.row_ptr, G.col, G.w)
     pol = _oracle_policy(O, args.workload)
@@ -478,7 +488,7 @@ def run_main(args, name, dev, rank, ws, local, secondary=False):
     nsteps = args.warmup + args.steps
     t_setup = time.perf_counter()
     # after the timed steps: one more batch for the update byte model and one for the end-to-end warm-up
-    wl, batches, sweep_rec = main_workload(name, nsteps + 2 + min(args.steps, 3))
+    wl, batches, sweep_rec = main_workload(name, nsteps + 2 + min(args.steps, 3), None if secondary else args.scale)
     t_gen = time.perf_counter() - t_setup
     G = wl.graph
     stream = torch.cuda.Stream(device=dev)
@@ -603,7 +613,7 @@ def run_main(args, name, dev, rank, ws, local, secondary=False):
         out["streaming"] = {"records": int(srec.shape[0]), "updates_per_s": sps,
                             "single_record_call_ms_median": float(np.median(one_ms)),
                             "batched_over_streaming": upd_rate / sps}
-    if not secondary and sweep_rec is not None:
+    if not secondary and sweep_rec is not None and not args.no_sweep:
         out["batch_sweep"] = update_sweep(g, torch, t, sweep_rec, stream)
     if not secondary:
         out["memory_bytes"] = g.memory_report()
@@ -1158,6 +1168,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c5")
     ap.add_argument("--secondary", default="c2", help="a second main workload reported beside the headline (none: off)")
+    ap.add_argument("--scale", type=int, default=None, help="smaller RMAT scale of the main workload (profiling)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the update batch-size sweep (profiling)")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass (profiling runs)")

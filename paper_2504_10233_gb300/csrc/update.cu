@@ -208,8 +208,8 @@ struct SegScratch {
 };
 
 constexpr uint32_t PRE_MULT = 4;             // candidate region per deletion key
-constexpr uint32_t PRE_CHUNK = 256 * 8;
-constexpr uint32_t PRE_MIN_DEG = 1u << 16;   // vertices this large are scanned by the whole grid
+constexpr uint32_t PRE_CHUNK = 256 * 8;      // slots of one pre-pass work item
+constexpr uint32_t PRE_MIN_DEG = 1024;       // segments with deletions at vertices this large are pre-scanned
 constexpr uint32_t NO_PRE = 0xFFFFFFFFu;
 
 // Deletion candidates among the pre-existing slots [0, d0), collected for a big segment by the
@@ -965,6 +965,7 @@ struct SegArgs {
                                   // NO_PRE for segments the pre-pass does not scan
     uint32_t* huge_list;          // segments scanned by the pre-pass
     unsigned long long* nhuge;
+    uint32_t* huge_coff;          // [nhuge + 1] first pre-pass chunk of each listed segment (k_cand_plan)
     uint64_t eid_base;
     const unsigned long long* eid_base_dev;  // when set, the edge-id base is read on the device
     uint32_t* holes;
@@ -998,7 +999,7 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
         for (uint32_t i = a; i < lo; i++) insbits |= S.rec[i].z;
         bound += pool_bound(G, v, h, ni, b - lo, insbits);
         const bool big = dtot > S.big_slots || (b - a) > 256;
-        const bool huge = h.deg >= PRE_MIN_DEG && b > lo;  // hub with deletions: grid-wide candidate scan
+        const bool huge = h.deg >= PRE_MIN_DEG && b > lo;  // deletions at a large vertex: grid-wide candidate scan
         S.gcand_cnt[sidx] = huge ? 0u : NO_PRE;
         if (huge) S.huge_list[atomicAdd(S.nhuge, 1ull)] = (uint32_t)sidx;
         if (big) S.big_list[atomicAdd(&S.counts[1], 1ull)] = (uint32_t)sidx;
@@ -1014,53 +1015,72 @@ __global__ void k_oom_check(DevGraph G, const unsigned long long* counts, unsign
     queue[1] = 0;
 }
 
-// Grid-wide pre-pass for the big segments (hubs): the pre-existing slots [0, d0) whose destination
-// is deleted in the segment, found by every block at once instead of by the segment's single team
-// (an O(d) scan per touched hub).  Candidate order is irrelevant: resolution takes minima of edge ids.
-constexpr uint32_t PRE_SMEM_KEYS = 4096;  // deletion destinations staged per block
+// Grid-wide pre-pass: for every segment with deletions at a vertex of at least PRE_MIN_DEG edges, the
+// pre-existing slots [0, d0) whose destination is deleted in the segment, found by the whole grid at
+// once instead of by the segment's single team (an O(d) scan per touched large vertex).  The work is
+// flattened into chunks of PRE_CHUNK slots over all listed segments (k_cand_plan numbers them), so
+// every block takes chunks of any segment and no segment is a serial step.  Candidate order is
+// irrelevant: resolution takes minima of edge ids.
+__global__ void __launch_bounds__(1024) k_cand_plan(DevGraph G, SegArgs S) {
+    __shared__ uint32_t sm[64];
+    if (*(volatile uint32_t*)G.pool.status & ST_STOP) return;
+    const uint64_t nhuge = *S.nhuge;
+    uint32_t base = 0;
+    for (uint64_t t0 = 0; t0 < nhuge; t0 += blockDim.x) {
+        const uint64_t i = t0 + threadIdx.x;
+        uint32_t c = 0;
+        if (i < nhuge) {
+            const uint4 info = S.seginfo[S.huge_list[i]];
+            const uint32_t d0 = load_hdr(G, info.x).deg;
+            c = (d0 + PRE_CHUNK - 1) / PRE_CHUNK;
+        }
+        const uint2 r = block_scan_excl(sm, c);
+        if (i < nhuge) S.huge_coff[i] = base + r.x;
+        base += r.y;
+    }
+    if (threadIdx.x == 0) S.huge_coff[nhuge] = base;
+}
+
 __global__ void __launch_bounds__(256) k_cand_scan(DevGraph G, SegArgs S) {
-    __shared__ uint32_t sk[PRE_SMEM_KEYS];
-    if (*(volatile uint32_t*)G.pool.status & ST_STOP) return;  // block-uniform: read once below
+    if (*(volatile uint32_t*)G.pool.status & ST_STOP) return;  // block-uniform
     const unsigned long long nhuge = *S.nhuge;
+    if (nhuge == 0) return;
+    const uint32_t total = S.huge_coff[nhuge];
     const uint64_t dmask = (1ull << S.B.bn) - 1;
-    for (unsigned long long i = 0; i < nhuge; i++) {
-        const uint32_t sidx = S.huge_list[i];
+    for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
+        uint32_t lo = 0, hi = (uint32_t)nhuge;  // last listed segment whose first chunk is <= c
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (S.huge_coff[mid] <= c) lo = mid; else hi = mid;
+        }
+        const uint32_t sidx = S.huge_list[lo];
         const uint4 info = S.seginfo[sidx];
-        const uint32_t nd = info.w;
-        const uint32_t v = info.x, first = info.y + info.z;
+        const uint32_t nd = info.w, v = info.x, first = info.y + info.z;
         const VHdr h = load_hdr(G, v);
         const uint32_t d0 = h.deg;
-        if (nd == 0 || blockIdx.x * PRE_CHUNK >= d0) continue;  // block-uniform
         const uint2* pairs = adj_pairs(G, h.adj);
-        const uint64_t* dk = S.sorted_keys + first;
-        const bool staged = nd <= PRE_SMEM_KEYS;
-        __syncthreads();  // the previous segment's keys are no longer read
-        if (staged)
-            for (uint32_t k = threadIdx.x; k < nd; k += blockDim.x) sk[k] = (uint32_t)(dk[k] & dmask);
-        __syncthreads();
+        const uint64_t* dk = S.sorted_keys + first;  // the segment's deletion keys, ascending destination
         uint32_t* out = S.gcand + (uint64_t)PRE_MULT * first;
         const uint32_t cap = PRE_MULT * nd;
-        for (uint32_t c0 = blockIdx.x * PRE_CHUNK; c0 < d0; c0 += gridDim.x * PRE_CHUNK) {
-            uint32_t x[8];
+        const uint32_t c0 = (c - S.huge_coff[lo]) * PRE_CHUNK;
+        uint32_t x[8];
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const uint32_t j = c0 + q * 256 + threadIdx.x;
-                x[q] = j < d0 ? pairs[j].x : NONE32;
+        for (int q = 0; q < 8; q++) {
+            const uint32_t j = c0 + q * 256 + threadIdx.x;
+            x[q] = j < d0 ? pairs[j].x : NONE32;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint32_t j = c0 + q * 256 + threadIdx.x;
+            if (j >= d0) continue;
+            uint32_t a = 0, b = nd;
+            while (a < b) {
+                const uint32_t mid = (a + b) >> 1;
+                if ((uint32_t)(__ldg(dk + mid) & dmask) < x[q]) a = mid + 1; else b = mid;
             }
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const uint32_t j = c0 + q * 256 + threadIdx.x;
-                if (j >= d0) continue;
-                uint32_t lo = 0, hi = nd;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    const uint32_t kv = staged ? sk[mid] : (uint32_t)(dk[mid] & dmask);
-                    if (kv < x[q]) lo = mid + 1; else hi = mid;
-                }
-                if (lo < nd && (staged ? sk[lo] : (uint32_t)(dk[lo] & dmask)) == x[q]) {
-                    const uint32_t pos = atomicAdd(S.gcand_cnt + sidx, 1u);
-                    if (pos < cap) out[pos] = j;
-                }
+            if (a < nd && (uint32_t)(__ldg(dk + a) & dmask) == x[q]) {
+                const uint32_t pos = atomicAdd(S.gcand_cnt + sidx, 1u);
+                if (pos < cap) out[pos] = j;
             }
         }
     }
@@ -1171,7 +1191,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) k_apply(DevGraph G, SegArgs 
         i = __shfl_sync(FULL, i, 0);
         if (i >= nsmall) break;
         run_segment<REAL>(t, G, S, smem.small.sh[w], S.small_list[i], smem.small.sdel[w], SMALL_SDEL, smem.small.cand[w],
-                    SMALL_CAND, &smem.small.x[w], bstats);
+                    SMALL_CAND, &smem.small.x[w], bstats, true);
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < S_CONV + 25; i += blockDim.x)
@@ -1425,7 +1445,7 @@ static bingo_status update_capacity(bingo_graph* g, uint64_t count) {
     CK(ensure(g->s_rec, 16 * kc), "update scratch");
     CK(ensure(g->s_seginfo, 16 * kc + 16), "update scratch");
     CK(ensure(g->s_gcand, 4ull * PRE_MULT * kc), "update scratch");
-    CK(ensure(g->s_gcand_cnt, 8 * kc + 32), "update scratch");
+    CK(ensure(g->s_gcand_cnt, 12 * kc + 64), "update scratch");  // counts, segment list, chunk offsets
     CK(ensure(g->s_tmp, std::max(radix_sort_tmp_bytes(kc), scan_tmp_bytes(kc))), "update scratch");
     if (!g->apply_blocks) {
         int per_sm = 0;
@@ -1507,6 +1527,7 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     S.gcand = (uint32_t*)g->s_gcand.p;
     S.gcand_cnt = (uint32_t*)g->s_gcand_cnt.p;
     S.huge_list = S.gcand_cnt + kc + 4;
+    S.huge_coff = S.huge_list + kc + 4;
     S.nhuge = (unsigned long long*)(ctl + CTL_SCR + 13);
     CK(cudaMemsetAsync(S.nhuge, 0, 8, s), "pre-pass count reset");
     S.holes = (uint32_t*)g->s_aux.p;
@@ -1517,10 +1538,11 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     k_seg_classify<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S);
     S.queue = (unsigned long long*)(ctl + CTL_SCR + 11);
     k_oom_check<<<1, 1, 0, s>>>(g->G, counts, S.queue);
-    k_cand_scan<<<(unsigned)g->num_sms * 4, 256, 0, s>>>(g->G, S);
+    k_cand_plan<<<1, 1024, 0, s>>>(g->G, S);
+    k_cand_scan<<<(unsigned)g->num_sms * 8, 256, 0, s>>>(g->G, S);
     if (g->G.fbits) k_apply<true><<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
     else k_apply<false><<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
-    g->launches += 4;
+    g->launches += 5;
     if (g->G.eh_mask) {
         k_eh_apply<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S, kc, nkeys_dev);
         g->launches++;
