@@ -169,6 +169,25 @@ def expected_bytes_per_vertex(ex, alpha=40, beta=10):
     return np.where(deg > 0, per, 0.0)
 
 
+def expected_bytes_parts(ex):
+    """The per-vertex model split into what a step reads once (header sector, count line) and what
+    every draw of a candidate reads again (the group's pick), for walks that retry candidates."""
+    deg = ex["deg"].astype(np.float64)
+    cnt = ex["cnt"].astype(np.float64)
+    mask = cnt > 0
+    kv = np.where(mask.any(axis=1), 32 - np.argmax(mask[:, ::-1], axis=1), 0)
+    fixed = np.where(deg > 0, 32.0 + 32.0 * np.ceil(4.0 * kv / 32.0), 0.0)
+    pick = np.where(deg > 0, expected_bytes_per_vertex(ex) - fixed - 4.0, 0.0)
+    return fixed, pick
+
+
+def node2vec_step_bytes(fixed, pick, p_accept, p_probe, probe_bytes=64.0):
+    """Model bytes of one node2vec step by rejection (Eq. node2vec): the step's fixed part once, then
+    E[candidates] = 1 / P(accept) picks, each followed with probability p_probe by an edge-index probe
+    (the key's sector and its count's), and the 4-byte path entry."""
+    return fixed + (pick + p_probe * probe_bytes) / p_accept + 4.0
+
+
 def walk_bytes(per_vertex, paths, plen):
     """Sum of per-step bytes over the recorded walks (steps leave from paths[:, t], t < plen-1)."""
     L = paths.shape[1]
@@ -752,11 +771,12 @@ def run_mixed(args):
         a, b = timed_walk(200, t(W.walk_starts(G.n, nw, wl.walk_seed)[sel]), t(pids_np[sel]), mode, len(sel))
         per_ms += a
         per_steps += b
-    # first-order roofline model over the last launch (node2vec retries and probes not counted)
-    ex = g.export_state()
-    per_v = expected_bytes_per_vertex(ex)
+    # roofline model over the last launch, on a uniform sample of its steps: PPR steps and node2vec's
+    # first step by the first-order model; later node2vec steps with their rejected candidates and
+    # edge-index probes (Eq. node2vec: accept with f(dist)/max f = 1/4, 1/2, 1 at distance 0, 1, 2;
+    # the probe is needed when the acceptance draw falls between the distance-1 and -2 thresholds)
     a, b = timed_walk(300, starts, pids, mode, nw)
-    abytes = walk_bytes(per_v, paths.cpu().numpy().view(np.uint32), plen.cpu().numpy().view(np.uint32))
+    abytes, model_note = mixed_walk_bytes(g, torch, paths, plen, pols)
     pk, pk_src = peaks()
     achieved = abytes / (a / 1e3) / 1e9
     cpu = None
@@ -788,10 +808,48 @@ def run_mixed(args):
             "clocks": clocks, "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": "k_walk_persistent",
-                         "peak_source": f"{pk_src} hbm_gbs", "model": "first-order bytes per accepted step"},
+                         "peak_source": f"{pk_src} hbm_gbs", "model": model_note},
             "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     g.close()
+
+
+def mixed_walk_bytes(g, torch, paths, plen, pols, nsample=20000):
+    """Model bytes of a launch mixing node2vec (even walker ids) and PPR (odd): the mean model bytes of
+    a uniform sample of its steps times its steps."""
+    plen_h = plen.cpu().numpy().view(np.uint32)
+    w, t, tot = sample_steps(plen_h, nsample, 99)
+    P = paths.cpu().numpy().view(np.uint32)
+    cur = P[w, t]
+    n2v = (w % 2 == 0) & (t >= 1)
+    prev = np.where(n2v, P[w, np.maximum(t - 1, 0)], 0)
+    ids = np.unique(np.concatenate([cur, prev[n2v]]))
+    ex = g.export_vertices(ids)
+    fixed, pick = expected_bytes_parts(ex)
+    row = np.searchsorted(ids, cur)
+    off = np.concatenate([[0], np.cumsum(ex["deg"].astype(np.int64))])
+    acc = [int(x) / 2 ** 32 for x in pols[0].n2v_accept]  # accept probability at distance 0, 1, 2
+    lo, hi = sorted(acc[1:])
+    total = 0.0
+    for i in range(len(w)):
+        r = row[i]
+        if not n2v[i]:
+            total += fixed[r] + pick[r] + 4.0
+            continue
+        rp = np.searchsorted(ids, prev[i])
+        dst = ex["dst"][off[r]:off[r + 1]]
+        wt = ex["bias"][off[r]:off[r + 1]].astype(np.float64)
+        wt /= wt.sum()
+        nbr_prev = ex["dst"][off[rp]:off[rp + 1]]
+        d1 = np.isin(dst, nbr_prev)
+        is_prev = dst == prev[i]
+        a = np.where(is_prev, acc[0], np.where(d1, acc[1], acc[2]))
+        p_acc = float((wt * a).sum())
+        p_probe = float((wt * ~is_prev).sum()) * (hi - lo)
+        total += node2vec_step_bytes(fixed[r], pick[r], p_acc, p_probe)
+    bps = total / max(len(w), 1)
+    return bps * tot, (f"per-step model bytes averaged over {len(w)} sampled steps (node2vec with E[candidates] "
+                       f"and edge-index probes): {bps:.1f} B/step")
 
 
 def run_sweep(args):

@@ -66,7 +66,7 @@ struct __align__(64) VHot {
     uint32_t adj;   // adjacency block, 32-byte units
     uint32_t deg;
     uint32_t mask;
-    uint32_t word;  // the caller's id of this vertex (path entries of walks); top bit: cold_desc below
+    uint32_t word;  // the caller's id of this vertex (path entries of walks); top bit: the cold scan order (cold_summary)
     uint2 g[HOT_GROUPS];
 };
 struct __align__(32) VCold {
@@ -309,13 +309,6 @@ __device__ __forceinline__ uint64_t slot_weight(uint32_t c, uint32_t k) {
 __device__ __forceinline__ uint64_t graph_slot_weight(const DevGraph& G, uint32_t c, uint32_t k) {
     return G.base4 ? slot_weight<WM_B4>(c, k) : slot_w(c, k, G.fbits);
 }
-// VCold.wcold of a vertex from its 32 slot counts.
-__device__ __forceinline__ uint64_t cold_total(const DevGraph& G, const uint32_t* cnt) {
-    uint64_t w = 0;
-    for (uint32_t k = HOT_GROUPS; k < 32; k++) w += graph_slot_weight(G, cnt[k], k);
-    return w;
-}
-
 // Order in which a draw that falls beyond the hot groups scans the cold groups.  The walker reads
 // the cold pairs (pairs 3..15, groups 2i and 2i+1) in batches whose loads are issued together, and
 // reads a batch only when the draw lies beyond the earlier ones: upwards, the aligned batches
@@ -328,33 +321,37 @@ __device__ __forceinline__ uint64_t cold_total(const DevGraph& G, const uint32_t
 // top bit of the hot record's caller-id word (vertex ids are below 2^31).
 constexpr uint32_t WORD_DESC = 0x80000000u;
 constexpr uint32_t WORD_ID = 0x7FFFFFFFu;
-__device__ __forceinline__ bool cold_desc(const DevGraph& G, const uint32_t* cnt) {
-    uint64_t wp[16];
-    int hi = -1;
-    for (int i = HOT_GROUPS / 2; i < 16; i++) {
-        wp[i] = graph_slot_weight(G, cnt[2 * i], 2 * i) + graph_slot_weight(G, cnt[2 * i + 1], 2 * i + 1);
-        if (cnt[2 * i] || cnt[2 * i + 1]) hi = i;
-    }
-    if (hi < 0) return false;
-    // 128-bit sums: at most 13 pairs x 4 batches x 2^64
-    unsigned __int128 ea = 0, ed = 0;
-    int rank = 0, prev = -1;
-    for (int i = HOT_GROUPS / 2; i < 16; i++) {
-        if (!(cnt[2 * i] || cnt[2 * i + 1])) continue;
-        const int b = (i - HOT_GROUPS / 2) / 4;
-        if (b != prev) { rank++; prev = b; }
-        ea += (unsigned __int128)wp[i] * (unsigned)rank;
-    }
-    rank = 0;
-    prev = -1;
-    for (int i = hi; i >= HOT_GROUPS / 2; i--) {
-        if (!(cnt[2 * i] || cnt[2 * i + 1])) continue;
-        const int w = (hi - i) / 4;
-        if (w != prev) { rank++; prev = w; }
-        ed += (unsigned __int128)wp[i] * (unsigned)rank;
-    }
-    return ed < ea;
+#ifdef __CUDACC__
+// The cold total (VCold.wcold, exact) and the cold scan order of a vertex from its 32 slot counts,
+// computed by one whole warp (every lane calls it with its lane id and the count of slot `lane`):
+// lane k weighs slot k,
+// lane i < 16 pair i; batch and window ranks come from ballots; the expected-batch comparison is a
+// sum of weight x (upward rank - downward rank) in binary64, reduced in a fixed shuffle order, so
+// the same counts always give the same order (build, update and the export's check all call this).
+__device__ __forceinline__ void cold_summary(const DevGraph& G, uint32_t c, uint32_t lane, uint64_t& wcold,
+                                             bool& desc) {
+    const uint64_t wk = graph_slot_weight(G, c, lane);
+    uint64_t wc = lane >= HOT_GROUPS ? wk : 0ull;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(0xFFFFFFFFu, wc, o);
+    wcold = wc;
+    const uint32_t i = lane & 15;
+    const uint64_t wp = __shfl_sync(0xFFFFFFFFu, wk, 2 * i) + __shfl_sync(0xFFFFFFFFu, wk, 2 * i + 1);
+    const uint32_t cp = __shfl_sync(0xFFFFFFFFu, c, 2 * i) | __shfl_sync(0xFFFFFFFFu, c, 2 * i + 1);
+    const bool ne = lane < 16 && lane >= HOT_GROUPS / 2 && cp != 0;
+    const uint32_t M = __ballot_sync(0xFFFFFFFFu, ne);
+    if (!M) { desc = false; return; }
+    const uint32_t hi = 31 - __clz(M);
+    const uint32_t b = (i - HOT_GROUPS / 2) / 4, w = (hi - i) / 4;  // meaningful where ne
+    const uint32_t BM = __reduce_or_sync(0xFFFFFFFFu, ne ? 1u << b : 0u);
+    const uint32_t WMk = __reduce_or_sync(0xFFFFFFFFu, ne ? 1u << w : 0u);
+    const int ra = __popc(BM & ((2u << b) - 1u)), rd = __popc(WMk & ((2u << w) - 1u));
+    double x = ne ? (double)wp * (double)(ra - rd) : 0.0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    desc = x > 0.0;
 }
+#endif
 // ---- radix base 4 (Appendix): sub-group (digit position i, value v) is slot 3 i + v - 1.
 constexpr uint32_t B4_POSITIONS = 10;  // biases below 4^10 = 2^20: slots 0..29
 // Sub-group mask of a bias: bit 3 i + v - 1 for every nonzero base-4 digit v at position i.  Stored

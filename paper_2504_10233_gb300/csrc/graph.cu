@@ -187,17 +187,13 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
         gref_ref(G, v, lane) = gref;
         __syncwarp();
         // total weight of the cold groups (the decimal slot's count was written above)
-        const uint32_t myc = cnt_ref(G, v, lane);
-        uint64_t wc = lane >= HOT_GROUPS ? graph_slot_weight(G, myc, lane) : 0ull;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(FULL, wc, o);
-        uint32_t call[32];
-#pragma unroll
-        for (int k = 0; k < 32; k++) call[k] = __shfl_sync(FULL, myc, k);
+        uint64_t wc;
+        bool desc;
+        cold_summary(G, cnt_ref(G, v, lane), lane, wc, desc);
         if (lane == 0) {
             store_hdr(G, v, h);
             G.vc[v].wcold = wc;
-            G.vh[v].word = (G.vh[v].word & WORD_ID) | (cold_desc(G, call) ? WORD_DESC : 0u);
+            G.vh[v].word = (G.vh[v].word & WORD_ID) | (desc ? WORD_DESC : 0u);
         }
     }
 }
@@ -277,16 +273,13 @@ __global__ void k_export_fill(DevGraph G, const uint32_t* __restrict__ ids, uint
         const uint32_t c = cnt_ref(G, v, lane);
         const uint32_t kd = slot_kind(G, c, d, lane);
         const uint32_t gr = gref_ref(G, v, lane);
-        // the walker's cached cold total and the caller's id in the hot line
-        uint64_t wc = lane >= HOT_GROUPS ? graph_slot_weight(G, c, lane) : 0ull;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(FULL, wc, o);
-        uint32_t call[32];
-#pragma unroll
-        for (int k = 0; k < 32; k++) call[k] = __shfl_sync(FULL, c, k);
+        // the walker's cached cold total, scan order and the caller's id in the hot line
+        uint64_t wc;
+        bool desc;
+        cold_summary(G, c, lane, wc, desc);
         const uint32_t hw = G.vh[v].word;
         if (lane == 0 && (wc != G.vc[v].wcold || (hw & WORD_ID) != G.base + (uint32_t)ve ||
-                          ((hw & WORD_DESC) != 0) != cold_desc(G, call)))
+                          ((hw & WORD_DESC) != 0) != desc))
             atomicAdd(bad, 1ull);
         okind[i * 32 + lane] = (uint8_t)kd;
         ocnt[i * 32 + lane] = c;

@@ -753,9 +753,16 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     for (uint32_t k = rank; k < 32; k += T) {
         grp(G, v, k) = make_uint2(sh.cnt_new[k], (uint32_t)sh.gref_new[k]);
     }
+    if (rank < 32) {  // the team's first warp (the whole team for a warp team)
+        uint64_t wc;
+        bool desc;
+        cold_summary(G, sh.cnt_new[rank], rank, wc, desc);
+        if (rank == 0) {
+            G.vc[v].wcold = wc;
+            G.vh[v].word = (G.vh[v].word & WORD_ID) | (desc ? WORD_DESC : 0u);
+        }
+    }
     if (rank == 0) {
-        G.vc[v].wcold = cold_total(G, sh.cnt_new);
-        G.vh[v].word = (G.vh[v].word & WORD_ID) | (cold_desc(G, sh.cnt_new) ? WORD_DESC : 0u);
         VHdr h;
         h.adj = adj;
         h.deg = d1;

@@ -177,7 +177,7 @@ __device__ __forceinline__ bool scan_pair_desc(uint4 x, uint32_t i, uint64_t r, 
 }
 
 // Scan order of the groups of a vertex: the hot groups 0-5 ascending, then the cold groups 6-31
-// ascending, or descending when the hot word's WORD_DESC bit is set (cold_desc).  Any fixed order
+// ascending, or descending when the hot word's WORD_DESC bit is set (cold_summary).  Any fixed order
 // of the inverse CDF draws group k with probability W(p_k) / sum W; every team width uses this one,
 // so all give the same k* for the same r.
 constexpr uint32_t COLD_PAIRS = 0x55555540u;  // pair bits 2i of the cold pairs i = 3..15
@@ -185,7 +185,7 @@ constexpr uint32_t COLD_PAIRS = 0x55555540u;  // pair bits 2i of the cold pairs 
 // T = 1: one lane per walker.  Pairs 0-2 came with the header and the total weight of groups
 // 6-31 comes from the cold record's first sector (VCold.wcold, read when the mask shows a cold
 // group), so r is drawn without reading the cold groups.  They are read only when r falls beyond
-// the hot groups, in the vertex's scan order (cold_desc): upwards in the aligned batches of pairs
+// the hot groups, in the vertex's scan order (cold_summary): upwards in the aligned batches of pairs
 // [3, 7), [7, 11), [11, 15), [15], or downwards in windows of four pairs from the highest nonempty
 // cold pair; the loads of a batch are issued together and empty batches are skipped.
 template <int WM>

@@ -105,3 +105,17 @@ def test_sampled_steps_are_uniform_over_the_launch_steps():
     for walker, steps in enumerate([0, 2, 1, 0, 4]):
         for step in range(steps):
             assert abs(freq[walker * 8 + step] - 1 / 7) < 0.01
+
+
+def test_bytes_parts_and_node2vec_step():
+    ex = _export([4, 0], [1, 1, 1, 1], [1, 1, 4, 8], [0, 1, 2, 3], 2)
+    ex["cnt"][0, 0], ex["cnt"][0, 2], ex["cnt"][0, 3] = 2, 1, 1
+    ex["kind"][0, 0], ex["kind"][0, 2], ex["kind"][0, 3] = DENSE, REGULAR, SPARSE
+    per = bench.expected_bytes_per_vertex(ex)
+    fixed, pick = bench.expected_bytes_parts(ex)
+    assert np.allclose(fixed + pick + 4.0, per[:1].tolist() + [4.0]) and fixed[1] == 0 and pick[1] == 0
+    assert fixed[0] == 32 + 32
+    # always accepted, never probed: the first-order model
+    assert np.isclose(bench.node2vec_step_bytes(fixed[0], pick[0], 1.0, 0.0), per[0])
+    # half the candidates rejected, a probe on every second candidate
+    assert np.isclose(bench.node2vec_step_bytes(64.0, 100.0, 0.5, 0.5), 64 + (100 + 32) * 2 + 4)
