@@ -1,12 +1,13 @@
 // Internal device structures and primitives of the radix-factorised sampler.
 //
 // Device state of a graph (all in HBM):
-//   vh[v]   VHot, 64 bytes: header {adjacency block, degree d, nonempty-group mask, the caller's id
-//           of v (path entries)} and groups 0-5 as {|G_k|, ref} (Eq. wpk: W(p_k) = 2^k |G_k|); ref =
-//           destination of the member of a one-element group, or the group block of a regular/sparse
-//           group, else 0.  The hot array is n x 64 B, small enough to stay largely in L2.
-//   vc[v]   VCold, 256 bytes: one sector {the total weight of groups 6-31, the update-only fields
-//           (|S|, log2 capacities, sparse-list block)}, then groups 6-31.
+//   vh[v]   VHot, 64 bytes: one sector {adjacency block, degree d, nonempty-group mask, the
+//           caller's id of v (path entries), the total weight of groups 4-31}, then groups 0-3 as
+//           {|G_k|, ref} (Eq. wpk: W(p_k) = 2^k |G_k|); ref = destination of the member of a
+//           one-element group, or the group block of a regular/sparse group, else 0.  A walker
+//           step draws its group from this one line whenever the draw falls in groups 0-3.
+//   vc[v]   VCold, 256 bytes: one sector of update-only fields (|S|, log2 capacities, sparse-list
+//           block), then groups 4-31.
 //   pool    u32 words holding every variable-size block, in power-of-two sizes (offsets stored in
 //           32-byte units):
 //             adjacency   4*capA words: capA x {dst, bias} (8 B, AoS) then capA x u64 edge id
@@ -61,25 +62,26 @@ struct VHdr {
     uint16_t pad;
 };
 
-constexpr uint32_t HOT_GROUPS = 6;
+constexpr uint32_t HOT_GROUPS = 4;
 struct __align__(64) VHot {
     uint32_t adj;   // adjacency block, 32-byte units
     uint32_t deg;
     uint32_t mask;
     uint32_t word;  // the caller's id of this vertex (path entries of walks); top bit: the cold scan order (cold_summary)
+    uint64_t wcold; // sum of the weights of groups 4-31: with the hot groups, the vertex total
+    uint32_t spare[2];
     uint2 g[HOT_GROUPS];
 };
 struct __align__(32) VCold {
-    uint64_t wcold;      // sum of the weights of groups 6-31: with the hot groups, the vertex total
     uint32_t nsp;
     uint8_t lcapa, lcaps;
     uint16_t pad;
     uint32_t sref;       // sparse-list block, 32-byte units
-    uint32_t spare[3];
+    uint32_t spare[5];
     uint2 g[32 - HOT_GROUPS];
-    uint32_t tail[4];
 };
 static_assert(sizeof(VHot) == 64, "VHot must be two sectors");
+static_assert(offsetof(VHot, g) == 32, "hot groups fill the second sector");
 static_assert(sizeof(VCold) == 256, "VCold must be eight sectors");
 static_assert(offsetof(VCold, g) == 32, "cold groups start at the second sector");
 
@@ -310,9 +312,9 @@ __device__ __forceinline__ uint64_t graph_slot_weight(const DevGraph& G, uint32_
     return G.base4 ? slot_weight<WM_B4>(c, k) : slot_w(c, k, G.fbits);
 }
 // Order in which a draw that falls beyond the hot groups scans the cold groups.  The walker reads
-// the cold pairs (pairs 3..15, groups 2i and 2i+1) in batches whose loads are issued together, and
+// the cold pairs (pairs 2..15, groups 2i and 2i+1) in batches whose loads are issued together, and
 // reads a batch only when the draw lies beyond the earlier ones: upwards, the aligned batches
-// [3, 7), [7, 11), [11, 15), [15]; downwards, windows of four consecutive pairs from the highest
+// [2, 6), [6, 10), [10, 14), [14, 16); downwards, windows of four consecutive pairs from the highest
 // nonempty cold pair; batches without a nonempty pair are skipped.  Any fixed order gives the same
 // law (Eq. group_prob).  Upwards suits biases whose weight is in the low bits (floor Pareto);
 // uniform biases put half their weight on the top bit, where upwards reads every batch.  The order
@@ -322,7 +324,7 @@ __device__ __forceinline__ uint64_t graph_slot_weight(const DevGraph& G, uint32_
 constexpr uint32_t WORD_DESC = 0x80000000u;
 constexpr uint32_t WORD_ID = 0x7FFFFFFFu;
 #ifdef __CUDACC__
-// The cold total (VCold.wcold, exact) and the cold scan order of a vertex from its 32 slot counts,
+// The cold total (VHot.wcold, exact) and the cold scan order of a vertex from its 32 slot counts,
 // computed by one whole warp (every lane calls it with its lane id and the count of slot `lane`):
 // lane k weighs slot k,
 // lane i < 16 pair i; batch and window ranks come from ballots; the expected-batch comparison is a

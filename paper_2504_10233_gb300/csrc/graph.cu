@@ -192,7 +192,7 @@ __global__ void k_build_fill(DevGraph G, const uint64_t* __restrict__ rp, const 
         cold_summary(G, cnt_ref(G, v, lane), lane, wc, desc);
         if (lane == 0) {
             store_hdr(G, v, h);
-            G.vc[v].wcold = wc;
+            G.vh[v].wcold = wc;
             G.vh[v].word = (G.vh[v].word & WORD_ID) | (desc ? WORD_DESC : 0u);
         }
     }
@@ -278,7 +278,7 @@ __global__ void k_export_fill(DevGraph G, const uint32_t* __restrict__ ids, uint
         bool desc;
         cold_summary(G, c, lane, wc, desc);
         const uint32_t hw = G.vh[v].word;
-        if (lane == 0 && (wc != G.vc[v].wcold || (hw & WORD_ID) != G.base + (uint32_t)ve ||
+        if (lane == 0 && (wc != G.vh[v].wcold || (hw & WORD_ID) != G.base + (uint32_t)ve ||
                           ((hw & WORD_DESC) != 0) != desc))
             atomicAdd(bad, 1ull);
         okind[i * 32 + lane] = (uint8_t)kd;

@@ -758,7 +758,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
         bool desc;
         cold_summary(G, sh.cnt_new[rank], rank, wc, desc);
         if (rank == 0) {
-            G.vc[v].wcold = wc;
+            G.vh[v].wcold = wc;
             G.vh[v].word = (G.vh[v].word & WORD_ID) | (desc ? WORD_DESC : 0u);
         }
     }
@@ -900,7 +900,7 @@ __global__ void k_seg_write(const uint64_t* __restrict__ flag, const uint64_t* _
 // rebuilt together), and a sparse list.
 // The 32 group counts of vertex v, read as whole 16-byte pairs with every load in flight at once.
 __device__ __forceinline__ void load_counts(const DevGraph& G, uint32_t v, uint32_t* cnt) {
-    const uint4* hot = reinterpret_cast<const uint4*>(G.vh + v) + 1;
+    const uint4* hot = reinterpret_cast<const uint4*>(G.vh[v].g);
     const uint4* cold = reinterpret_cast<const uint4*>(G.vc[v].g);
     uint4 x[16];
 #pragma unroll

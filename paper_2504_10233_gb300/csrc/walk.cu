@@ -117,28 +117,30 @@ __device__ __forceinline__ uint4 ld_hot(const uint4* q) {
     return r;
 }
 
-// Hot part of a vertex record: the header and groups 0-5 (pairs 0-2), one 64-byte line.
+// Hot part of a vertex record: the header, the cold total and groups 0-3 (pairs 0-1), one 64-byte line.
 struct Sec0 {
     uint32_t adj, deg, mask;
-    uint32_t word;  // the caller's id of the vertex, and the cold scan order (WORD_DESC)
-    uint4 p0, p1, p2;
+    uint32_t word;   // the caller's id of the vertex, and the cold scan order (WORD_DESC)
+    uint64_t wcold;  // total weight of the cold groups
+    uint4 p0, p1;
 };
 __device__ __forceinline__ Sec0 ld_sec0(const DevGraph& G, uint32_t v) {
     const uint4* q = reinterpret_cast<const uint4*>(G.vh + v);
     const uint4 a = ld_hot(q);
+    const uint4 b = ld_hot(q + 1);
     Sec0 s;
     s.adj = a.x;
     s.deg = a.y;
     s.mask = a.z;
     s.word = a.w;
-    s.p0 = ld_hot(q + 1);
-    s.p1 = ld_hot(q + 2);
-    s.p2 = ld_hot(q + 3);
+    s.wcold = (uint64_t)b.x | ((uint64_t)b.y << 32);
+    s.p0 = ld_hot(q + 2);
+    s.p1 = ld_hot(q + 3);
     return s;
 }
 // Groups 2i and 2i+1 of vertex v as {c_2i, ref_2i, c_2i+1, ref_2i+1} (16-byte aligned).
 __device__ __forceinline__ uint4 ld_pair(const DevGraph& G, uint32_t v, uint32_t i) {
-    if (i < HOT_GROUPS / 2) return ld_hot(reinterpret_cast<const uint4*>(G.vh + v) + 1 + i);
+    if (i < HOT_GROUPS / 2) return ld_hot(reinterpret_cast<const uint4*>(G.vh + v) + 2 + i);
     return __ldg(reinterpret_cast<const uint4*>(G.vc[v].g) + (i - HOT_GROUPS / 2));
 }
 // WM: the weight mode (slot_weight): integer base 2, real biases (every integer group counts 2^8
@@ -176,44 +178,42 @@ __device__ __forceinline__ bool scan_pair_desc(uint4 x, uint32_t i, uint64_t r, 
     return false;
 }
 
-// Scan order of the groups of a vertex: the hot groups 0-5 ascending, then the cold groups 6-31
+// Scan order of the groups of a vertex: the hot groups 0-3 ascending, then the cold groups 4-31
 // ascending, or descending when the hot word's WORD_DESC bit is set (cold_summary).  Any fixed order
 // of the inverse CDF draws group k with probability W(p_k) / sum W; every team width uses this one,
 // so all give the same k* for the same r.
-constexpr uint32_t COLD_PAIRS = 0x55555540u;  // pair bits 2i of the cold pairs i = 3..15
+constexpr uint32_t COLD_PAIRS = 0x55555550u;  // pair bits 2i of the cold pairs i = 2..15
 
-// T = 1: one lane per walker.  Pairs 0-2 came with the header and the total weight of groups
-// 6-31 comes from the cold record's first sector (VCold.wcold, read when the mask shows a cold
-// group), so r is drawn without reading the cold groups.  They are read only when r falls beyond
+// T = 1: one lane per walker.  Pairs 0-1 and the total weight of groups 4-31 came with the
+// header, so r is drawn from one 64-byte line.  The cold groups are read only when r falls beyond
 // the hot groups, in the vertex's scan order (cold_summary): upwards in the aligned batches of pairs
-// [3, 7), [7, 11), [11, 15), [15], or downwards in windows of four pairs from the highest nonempty
+// [2, 6), [6, 10), [10, 14), [14, 16), or downwards in windows of four pairs from the highest nonempty
 // cold pair; the loads of a batch are issued together and empty batches are skipped.
 template <int WM>
 __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status) {
     const uint32_t pb = pair_bits(h.mask);  // pairs holding a nonempty slot
-    const uint64_t whot = pair_w<WM>(h.p0, 0) + pair_w<WM>(h.p1, 1) + pair_w<WM>(h.p2, 2);
-    uint64_t wcold = 0;
-    if (h.mask >> HOT_GROUPS) wcold = __ldg(&G.vc[v].wcold);
-    const uint64_t r = below64(R, whot + wcold, status);
+    const uint64_t whot = pair_w<WM>(h.p0, 0) + pair_w<WM>(h.p1, 1);
+    const uint64_t r = below64(R, whot + h.wcold, status);
     uint64_t acc = 0;
     if (scan_pair<WM>(h.p0, 0, r, acc, ks, cs, ref)) return;
     if (scan_pair<WM>(h.p1, 1, r, acc, ks, cs, ref)) return;
-    if (scan_pair<WM>(h.p2, 2, r, acc, ks, cs, ref)) return;
     // one loop for both directions: batch starts i0 = 3, 7, 11, 15 upwards, or top, top - 4, ...
     // downwards; a downward pair is scanned odd group first (its halves swapped)
     const bool desc = (h.word & WORD_DESC) != 0;
     const uint32_t cm = pb & COLD_PAIRS;
     const int dir = desc ? -1 : 1;
+    constexpr int HP = HOT_GROUPS / 2;  // first cold pair
 #pragma unroll 1
-    for (int i0 = desc ? (int)((31 - __clz(cm)) >> 1) : 3; desc ? i0 >= 3 : i0 < 16; i0 += 4 * dir) {
-        const int low = desc ? i0 - 3 : i0;  // lowest pair of the batch (>= 0: i0 >= 3 downwards)
-        if (!((cm >> (2 * low)) & 0xFFu)) continue;
+    for (int i0 = desc ? (int)((31 - __clz(cm)) >> 1) : HP; desc ? i0 >= HP : i0 < 16; i0 += 4 * dir) {
+        const int low = desc ? i0 - 3 : i0;  // lowest pair of the batch (may be below 0 downwards)
+        const uint32_t wbits = low >= 0 ? (cm >> (2 * low)) & 0xFFu : (cm << (-2 * low)) & 0xFFu;
+        if (!wbits) continue;
         uint4 x[4];
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const int i = i0 + dir * j;
-            x[j] = (i >= 3 && i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair(G, v, (uint32_t)i) : make_uint4(0, 0, 0, 0);
+            x[j] = (i >= HP && i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair(G, v, (uint32_t)i) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int j = 0; j < 4; j++) {
@@ -232,8 +232,10 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
     atomicOr(status, ST_STATE);  // r beyond every group: the cached total disagrees with the counts
 }
 
-// Pair at scan position p (0..15) of a vertex: hot pairs 0-2, then the cold pairs up or down.
-__device__ __forceinline__ uint32_t pair_at(uint32_t p, bool desc) { return (p < 3 || !desc) ? p : 18 - p; }
+// Pair at scan position p (0..15) of a vertex: hot pairs 0-1, then the cold pairs up or down.
+__device__ __forceinline__ uint32_t pair_at(uint32_t p, bool desc) {
+    return (p < HOT_GROUPS / 2 || !desc) ? p : 15 + HOT_GROUPS / 2 - p;
+}
 
 // T = 4: lane t of the team owns scan positions [4t, 4t+4) (pair_at); a two-level shuffle prefix
 // over the team and a ballot find the lane holding k*, which searches its pairs again.
@@ -274,7 +276,7 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
             const uint32_t p = 4 * tl + j, i = pair_at(p, desc);
             if (!((pb >> (2 * i)) & 1u)) continue;
             const uint4 x = ld_pair(G, v, i);
-            if ((p >= 3 && desc) ? scan_pair_desc<WM>(x, i, r, acc, k_l, c_l, r_l)
+            if ((p >= HOT_GROUPS / 2 && desc) ? scan_pair_desc<WM>(x, i, r, acc, k_l, c_l, r_l)
                                  : scan_pair<WM>(x, i, r, acc, k_l, c_l, r_l))
                 break;
         }
@@ -284,7 +286,7 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
     ref = __shfl_sync(team_mask, r_l, owner);
 }
 
-// T = 32: lane l owns the group at scan position l (slot l, or 37 - l for cold positions scanned
+// T = 32: lane l owns the group at scan position l (slot l, or 35 - l for cold positions scanned
 // downwards); a warp-wide shuffle prefix of W_k = 2^k |G_k| and a ballot of (prefix > r) give k*
 // at the first set bit.
 template <int WM>
@@ -292,7 +294,7 @@ __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, c
                                                 uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status,
                                                 uint32_t lane) {
     const bool desc = (h.word & WORD_DESC) != 0;
-    const uint32_t k = (lane < HOT_GROUPS || !desc) ? lane : 37 - lane;
+    const uint32_t k = (lane < HOT_GROUPS || !desc) ? lane : 31 + HOT_GROUPS - lane;
     uint2 gk = make_uint2(0, 0);
     if ((h.mask >> k) & 1u)
         gk = __ldg(k < HOT_GROUPS ? &G.vh[v].g[k] : &G.vc[v].g[k - HOT_GROUPS]);
