@@ -323,7 +323,7 @@ POLICY_NAME = {"deepwalk": "DeepWalk", "ppr": "PPR (stop 0.15; x = cap)"}
 METRIC_MAIN = "sampled walk steps/s (update batch + walk per step); updated edges/s; p50/p99 latency in the serving bench"
 
 
-def main_workload(name, nsteps, scale=None):
+def main_workload(name, nsteps, scale=None, hubs=True, nwalkers=None):
     """The workload and its per-step batches (plus, for c5, the records of the batch-size sweep): one
     stream of hold-out-protocol records cut into consecutive batches.  scale: a smaller RMAT scale of
     the same recipe (edge factor 16; hubs keep their degree up to a sixteenth of the edges), for
@@ -331,6 +331,10 @@ def main_workload(name, nsteps, scale=None):
     spec = MAIN[name]
     extra = SWEEP_REPS * sum(SWEEP_SIZES) if spec["sweep"] else 0
     shrink = {} if scale is None else {"scale": scale, "m": 16 << scale}
+    if not hubs:
+        shrink["hubs"] = False
+    if nwalkers:
+        shrink["nwalkers"] = nwalkers
     if name in ("c1", "c2"):
         wl = W.make_workload(name, nbatch=nsteps, **shrink)
         return wl, [b.records() for b in wl.batches], None
@@ -347,6 +351,10 @@ def main_config(args, wl, name=None):
     text = spec["text"]
     if getattr(args, "scale", None) is not None and name == args.workload:
         text = f"scaled to RMAT-{args.scale} (2^{args.scale} vertices, edge factor 16), otherwise: " + text
+    if getattr(args, "no_hubs", False) and name == args.workload:
+        text = "without its hub edges (profiling), otherwise: " + text
+    if getattr(args, "walkers", None) and name == args.workload:
+        text = f"{args.walkers} walkers per step (profiling), otherwise: " + text
     return {"workload": text, "walkers": wl.nwalkers, "length": spec["length"], "policy": spec["policy"],
             "updates_per_step": spec["batch"]}
 
@@ -418,7 +426,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    wl, batches, _ = main_workload(args.workload, args.steps + args.warmup, args.scale)
+    wl, batches, _ = main_workload(args.workload, args.steps + args.warmup, args.scale, not args.no_hubs, args.walkers)
     G = wl.graph
     og = O.Graph(G.n, G.row_ptr, G.col, G.w)
     pol = _oracle_policy(O, args.workload)
@@ -507,7 +515,8 @@ def run_main(args, name, dev, rank, ws, local, secondary=False):
     nsteps = args.warmup + args.steps
     t_setup = time.perf_counter()
     # after the timed steps: one more batch for the update byte model and one for the end-to-end warm-up
-    wl, batches, sweep_rec = main_workload(name, nsteps + 2 + min(args.steps, 3), None if secondary else args.scale)
+    wl, batches, sweep_rec = main_workload(name, nsteps + 2 + min(args.steps, 3), None if secondary else args.scale,
+                                           secondary or not args.no_hubs, None if secondary else args.walkers)
     t_gen = time.perf_counter() - t_setup
     G = wl.graph
     stream = torch.cuda.Stream(device=dev)
@@ -1228,6 +1237,8 @@ def main():
     ap.add_argument("--secondary", default="c2", help="a second main workload reported beside the headline (none: off)")
     ap.add_argument("--scale", type=int, default=None, help="smaller RMAT scale of the main workload (profiling)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the update batch-size sweep (profiling)")
+    ap.add_argument("--no-hubs", action="store_true", help="leave out the main workload's hub edges (profiling)")
+    ap.add_argument("--walkers", type=int, default=None, help="fewer walkers per step than the workload's (profiling)")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass (profiling runs)")

@@ -133,6 +133,7 @@ struct bingo_graph {
     bingo::Buf s_in, s_keys, s_keys2, s_vals, s_vals2, s_tmp, s_seg, s_rank, s_best, s_aux, s_walk, s_stage;
     bingo::Buf s_rec, s_seginfo;  // sorted insertion records, per-segment {v, first key, ni, nd}
     bingo::Buf s_gcand, s_gcand_cnt;  // deletion candidates of big segments from the pre-pass
+    bingo::Buf s_chunkmap;            // pre-pass chunk -> listed segment
     bingo::Buf w_starts, w_len, w_pid, w_paths, w_plen, w_pols, w_chunk_done;
     bingo::Buf w_len64, w_off, w_packed;  // packed walks: lengths as u64, their exclusive scan, packed rows
     // host-buffer walks: download streams, events, host-mapped chunk flags (see walk_host_io_overlap)

@@ -398,7 +398,7 @@ static void free_graph(bingo_graph* g) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     Buf* bufs[] = {&g->s_in, &g->s_keys, &g->s_keys2, &g->s_vals, &g->s_vals2, &g->s_tmp, &g->s_seg,
-                   &g->s_rank, &g->s_best, &g->s_aux, &g->s_walk, &g->s_stage, &g->s_rec, &g->s_seginfo, &g->s_gcand, &g->s_gcand_cnt,
+                   &g->s_rank, &g->s_best, &g->s_aux, &g->s_walk, &g->s_stage, &g->s_rec, &g->s_seginfo, &g->s_gcand, &g->s_gcand_cnt, &g->s_chunkmap,
                    &g->w_starts, &g->w_len, &g->w_pid, &g->w_paths, &g->w_plen, &g->w_pols, &g->w_chunk_done,
                    &g->w_len64, &g->w_off, &g->w_packed};
     for (Buf* b : bufs) release(*b);

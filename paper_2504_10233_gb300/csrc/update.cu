@@ -219,104 +219,17 @@ struct PreCand {
     uint32_t count = 0, cap = 0;
 };
 
-// Apply one vertex's segment (ni insertions then nd deletions).  Returns false if the graph ran out of pool.
-// REAL: real-bias graphs (decimal parts follow their edges, slot 31 holds the decimal total).
-template <bool REAL, class Team, class Src>
-__device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint32_t v, uint32_t ni, uint32_t nd,
-                              Src B, const SegScratch& X, unsigned long long* stats, uint32_t* sdel_buf,
-                              uint32_t sdel_cap, uint32_t* cand_buf = nullptr, uint32_t cand_cap = 0,
-                              PreCand pre = PreCand()) {
+// S3 of a segment: resolve each deletion to the earliest live copy (smallest edge id) of (v, dst);
+// the r-th deletion of the same dst takes the r-th earliest copy (round r).  Marks the chosen slots
+// dead (DEAD_BIT in the edge id), records them in X.del_slot and returns how many deletions found a copy.
+template <class Team, class Src>
+__device__ __forceinline__ uint32_t resolve_deletions(const Team& t, Src& B, const SegScratch& X, uint2* pairs,
+                                                      uint64_t* eids, uint32_t d0, uint32_t ni, uint32_t nd,
+                                                      uint32_t* sdel_buf, uint32_t sdel_cap, uint32_t* cand_buf,
+                                                      uint32_t cand_cap, const PreCand& pre) {
     const uint32_t rank = t.rank(), T = t.size();
-    const VHdr h0 = load_hdr(G, v);
-    const uint32_t d0 = h0.deg, capa0 = capa_of(h0), caps0 = caps_of(h0);
     const uint32_t dtot = d0 + ni;
-    for (uint32_t k = rank; k < 32; k += T) {
-        const uint2 gk = grp(G, v, k);
-        sh.cnt_old[k] = gk.x;
-        sh.gref_old[k] = gk.y;
-        sh.gref_new[k] = sh.gref_old[k];
-        sh.delta[k] = 0;
-        sh.removed[k] = 0;
-    }
-    if (rank == 0) {
-        sh.adj = h0.adj;
-        sh.nsp_del = 0;
-        sh.nsp_add = 0;
-        sh.found = 0;
-        sh.rounds = 0;
-    }
-    t.sync();
-    // old kinds
-    const KindMasks kmo = kind_masks<REAL>(t, sh, sh.cnt_old, d0, G, 0);
-    const uint32_t SPo = kmo.sp, REGo = kmo.reg, ONEo = kmo.one;
-
-    // ---- S1: adjacency capacity for the insertions
-    uint32_t capa1 = capa0;
-    bool full = false;
-    if (dtot > capa0) {
-        capa1 = capa_for(dtot);
-        full = true;
-        if (rank == 0) sh.alloc_off = pool_alloc(G.pool, 4ull * capa1);
-        t.sync();
-        const uint64_t noff = sh.alloc_off;
-        if (noff == 0) return;  // pool exhausted (flagged); the pre-check makes this unreachable
-        if (d0) {
-            const uint2* op = adj_pairs(G, h0.adj);
-            const uint64_t* oe = adj_eids(G, h0.adj, capa0);
-            uint2* np = adj_pairs(G, noff);
-            uint64_t* ne = adj_eids(G, noff, capa1);
-            for (uint32_t j = rank; j < d0; j += T) {
-                np[j] = op[j];
-                ne[j] = oe[j];
-            }
-        }
-        if constexpr (REAL) {  // the decimal block follows the adjacency's capacity
-            if (rank == 0) sh.alloc_off = pool_alloc(G.pool, dec_words(capa1));
-            t.sync();
-            const uint64_t qoff = sh.alloc_off;
-            if (qoff == 0) return;
-            uint8_t* nq = reinterpret_cast<uint8_t*>(G.pool.base + qoff);
-            if (d0) {
-                const uint8_t* oq = dec_bytes(G, (uint32_t)sh.gref_old[DEC_SLOT]);
-                for (uint32_t j = rank; j < d0; j += T) nq[j] = oq[j];
-            }
-            t.sync();
-            if (rank == 0) {
-                if (capa0) pool_free(G.pool, words_of(sh.gref_old[DEC_SLOT]), dec_words(capa0));
-                sh.gref_new[DEC_SLOT] = ref_of(qoff);
-            }
-        }
-        t.sync();
-        if (rank == 0) {
-            if (capa0) pool_free(G.pool, h0.adj, 4ull * capa0);
-            sh.adj = noff;
-        }
-        t.sync();
-    }
-    const uint64_t adj = sh.adj;
-    uint2* pairs = adj_pairs(G, adj);
-    uint64_t* eids = adj_eids(G, adj, capa1);
-    // real biases: decimal part of each slot (moves with its edge)
-    uint8_t* qbytes = nullptr;
-    if constexpr (REAL)
-        if (sh.gref_new[DEC_SLOT]) qbytes = dec_bytes(G, (uint32_t)sh.gref_new[DEC_SLOT]);
-
-    // ---- S2: append insertions at slots d0 .. d0+ni-1
-    for (uint32_t i = rank; i < ni; i += T) {
-        const uint4 u = B.ins(i);
-        pairs[d0 + i] = make_uint2(u.y, u.z);
-        eids[d0 + i] = B.ins_eid(i);
-        if (qbytes) qbytes[d0 + i] = (uint8_t)B.ins_q(i);
-    }
-    for (uint32_t j = rank; j < nd; j += T) {
-        X.del_slot[j] = NONE32;
-        X.best[j] = INF64;
-    }
-    t.sync();
-
-    // ---- S3: resolve each deletion to the earliest live copy (smallest edge id) of (v, dst);
-    // the r-th deletion of the same dst takes the r-th earliest copy (round r).  The sorted
-    // deletion destinations are staged in shared memory when they fit, for the per-slot searches.
+    // The sorted deletion destinations are staged in shared memory when they fit, for the per-slot searches.
     if (nd && sdel_buf && nd <= sdel_cap) {
         for (uint32_t j = rank; j < nd; j += T) sdel_buf[j] = B.del_dst_global(j);
         t.sync();
@@ -442,6 +355,140 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
         const uint32_t j = b + rank;
         found += t.sum(j < nd && X.del_slot[j] != NONE32 ? 1u : 0u);
     }
+    return found;
+}
+
+// S11-S12 of a segment: the new groups (sh.cnt_new, sh.gref_new), the walker's hot-line summary and
+// the header h1; then the batch statistics, kind conversions included.
+template <bool REAL, class Team>
+__device__ __forceinline__ void write_back(const Team& t, const DevGraph& G, const SegSh& sh, uint32_t v, const VHdr& h1,
+                                           uint32_t d0, uint32_t ni, uint32_t nd, uint32_t found, uint32_t rebuilt,
+                                           unsigned long long* stats) {
+    const uint32_t rank = t.rank(), T = t.size();
+    for (uint32_t k = rank; k < 32; k += T) grp(G, v, k) = make_uint2(sh.cnt_new[k], (uint32_t)sh.gref_new[k]);
+    if (rank < 32) {  // the team's first warp (the whole team for a warp team)
+        uint64_t wc;
+        bool desc;
+        cold_summary(G, sh.cnt_new[rank], rank, wc, desc);
+        if (rank == 0) {
+            G.vh[v].wcold = wc;
+            G.vh[v].word = (G.vh[v].word & WORD_ID) | (desc ? WORD_DESC : 0u);
+        }
+    }
+    if (rank == 0) {
+        store_hdr(G, v, h1);
+        atomicAdd(stats + S_INS, (unsigned long long)ni);
+        atomicAdd(stats + S_DEL, (unsigned long long)found);
+        atomicAdd(stats + S_NF, (unsigned long long)(nd - found));
+        atomicAdd(stats + S_TOUCH, 1ull);
+        if (rebuilt) atomicAdd(stats + S_REBUILT, (unsigned long long)rebuilt);
+    }
+    for (uint32_t k = rank; k < 32; k += T) {
+        const bool dec = REAL && k == DEC_SLOT;
+        const uint32_t ko = dec ? (uint32_t)K_EMPTY : kind_of(sh.cnt_old[k], d0, G.alpha, G.beta);
+        const uint32_t kn = dec ? (uint32_t)K_EMPTY : kind_of(sh.cnt_new[k], h1.deg, G.alpha, G.beta);
+        if (ko != kn) atomicAdd(stats + S_CONV + ko * 5 + kn, 1ull);
+    }
+    t.sync();
+}
+
+// Apply one vertex's segment (ni insertions then nd deletions).  Returns false if the graph ran out of pool.
+// REAL: real-bias graphs (decimal parts follow their edges, slot 31 holds the decimal total).
+template <bool REAL, class Team, class Src>
+__device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint32_t v, uint32_t ni, uint32_t nd,
+                              Src B, const SegScratch& X, unsigned long long* stats, uint32_t* sdel_buf,
+                              uint32_t sdel_cap, uint32_t* cand_buf = nullptr, uint32_t cand_cap = 0,
+                              PreCand pre = PreCand()) {
+    const uint32_t rank = t.rank(), T = t.size();
+    const VHdr h0 = load_hdr(G, v);
+    const uint32_t d0 = h0.deg, capa0 = capa_of(h0), caps0 = caps_of(h0);
+    const uint32_t dtot = d0 + ni;
+    for (uint32_t k = rank; k < 32; k += T) {
+        const uint2 gk = grp(G, v, k);
+        sh.cnt_old[k] = gk.x;
+        sh.gref_old[k] = gk.y;
+        sh.gref_new[k] = sh.gref_old[k];
+        sh.delta[k] = 0;
+        sh.removed[k] = 0;
+    }
+    if (rank == 0) {
+        sh.adj = h0.adj;
+        sh.nsp_del = 0;
+        sh.nsp_add = 0;
+        sh.found = 0;
+        sh.rounds = 0;
+    }
+    t.sync();
+    // old kinds
+    const KindMasks kmo = kind_masks<REAL>(t, sh, sh.cnt_old, d0, G, 0);
+    const uint32_t SPo = kmo.sp, REGo = kmo.reg, ONEo = kmo.one;
+
+    // ---- S1: adjacency capacity for the insertions
+    uint32_t capa1 = capa0;
+    bool full = false;
+    if (dtot > capa0) {
+        capa1 = capa_for(dtot);
+        full = true;
+        if (rank == 0) sh.alloc_off = pool_alloc(G.pool, 4ull * capa1);
+        t.sync();
+        const uint64_t noff = sh.alloc_off;
+        if (noff == 0) return;  // pool exhausted (flagged); the pre-check makes this unreachable
+        if (d0) {
+            const uint2* op = adj_pairs(G, h0.adj);
+            const uint64_t* oe = adj_eids(G, h0.adj, capa0);
+            uint2* np = adj_pairs(G, noff);
+            uint64_t* ne = adj_eids(G, noff, capa1);
+            for (uint32_t j = rank; j < d0; j += T) {
+                np[j] = op[j];
+                ne[j] = oe[j];
+            }
+        }
+        if constexpr (REAL) {  // the decimal block follows the adjacency's capacity
+            if (rank == 0) sh.alloc_off = pool_alloc(G.pool, dec_words(capa1));
+            t.sync();
+            const uint64_t qoff = sh.alloc_off;
+            if (qoff == 0) return;
+            uint8_t* nq = reinterpret_cast<uint8_t*>(G.pool.base + qoff);
+            if (d0) {
+                const uint8_t* oq = dec_bytes(G, (uint32_t)sh.gref_old[DEC_SLOT]);
+                for (uint32_t j = rank; j < d0; j += T) nq[j] = oq[j];
+            }
+            t.sync();
+            if (rank == 0) {
+                if (capa0) pool_free(G.pool, words_of(sh.gref_old[DEC_SLOT]), dec_words(capa0));
+                sh.gref_new[DEC_SLOT] = ref_of(qoff);
+            }
+        }
+        t.sync();
+        if (rank == 0) {
+            if (capa0) pool_free(G.pool, h0.adj, 4ull * capa0);
+            sh.adj = noff;
+        }
+        t.sync();
+    }
+    const uint64_t adj = sh.adj;
+    uint2* pairs = adj_pairs(G, adj);
+    uint64_t* eids = adj_eids(G, adj, capa1);
+    // real biases: decimal part of each slot (moves with its edge)
+    uint8_t* qbytes = nullptr;
+    if constexpr (REAL)
+        if (sh.gref_new[DEC_SLOT]) qbytes = dec_bytes(G, (uint32_t)sh.gref_new[DEC_SLOT]);
+
+    // ---- S2: append insertions at slots d0 .. d0+ni-1
+    for (uint32_t i = rank; i < ni; i += T) {
+        const uint4 u = B.ins(i);
+        pairs[d0 + i] = make_uint2(u.y, u.z);
+        eids[d0 + i] = B.ins_eid(i);
+        if (qbytes) qbytes[d0 + i] = (uint8_t)B.ins_q(i);
+    }
+    for (uint32_t j = rank; j < nd; j += T) {
+        X.del_slot[j] = NONE32;
+        X.best[j] = INF64;
+    }
+    t.sync();
+
+    // ---- S3: resolve each deletion to the earliest live copy
+    const uint32_t found = resolve_deletions(t, B, X, pairs, eids, d0, ni, nd, sdel_buf, sdel_cap, cand_buf, cand_cap, pre);
     const uint32_t d1 = dtot - found;
 
     // ---- S4: count deltas from the bits of deleted pre-existing and surviving new edges
@@ -749,44 +796,133 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     }
     t.sync();
 
-    // ---- S11: write back
+    // ---- S11-S12: write back, stats
+    VHdr h1;
+    h1.adj = adj;
+    h1.deg = d1;
+    h1.mask = maskn;
+    h1.sref = SPn ? sref1 : 0;
+    h1.nsp = SPn ? nsp1 : 0;
+    h1.lcapa = capa1 ? (uint8_t)(log2_u32(capa1) + 1) : 0;
+    h1.lcaps = SPn ? (uint8_t)(log2_u32(caps1) + 1) : 0;
+    h1.pad = 0;
+    write_back<REAL>(t, G, sh, v, h1, d0, ni, nd, found, rebuilt, stats);
+}
+
+// A segment whose groups are all dense or empty before it and stay so whatever its deletions find
+// (k_seg_classify proves it from the counts, the degree range and the inserted bits; integer
+// graphs only): no member list, sparse list or one-element reference exists before or after, so
+// apply_segment reduces to the adjacency (capacity, append, resolution, compaction) and the counts.
+// The same steps in the same order as apply_segment takes for such a segment, so the same result,
+// in far less code: most segments of a batch on a graph with wide biases take this path.
+template <class Team, class Src>
+__device__ void apply_dense_segment(const Team& t, const DevGraph& G, SegSh& sh, uint32_t v, uint32_t ni, uint32_t nd,
+                                    Src B, const SegScratch& X, unsigned long long* stats, uint32_t* sdel_buf,
+                                    uint32_t sdel_cap, uint32_t* cand_buf, uint32_t cand_cap, PreCand pre) {
+    const uint32_t rank = t.rank(), T = t.size();
+    const VHdr h0 = load_hdr(G, v);
+    const uint32_t d0 = h0.deg, capa0 = capa_of(h0);
+    const uint32_t dtot = d0 + ni;
     for (uint32_t k = rank; k < 32; k += T) {
-        grp(G, v, k) = make_uint2(sh.cnt_new[k], (uint32_t)sh.gref_new[k]);
+        sh.cnt_old[k] = grp(G, v, k).x;  // dense and empty groups carry no reference
+        sh.gref_new[k] = 0;
+        sh.delta[k] = 0;
     }
-    if (rank < 32) {  // the team's first warp (the whole team for a warp team)
-        uint64_t wc;
-        bool desc;
-        cold_summary(G, sh.cnt_new[rank], rank, wc, desc);
-        if (rank == 0) {
-            G.vh[v].wcold = wc;
-            G.vh[v].word = (G.vh[v].word & WORD_ID) | (desc ? WORD_DESC : 0u);
+    // S1: adjacency capacity for the insertions
+    uint32_t capa1 = capa0;
+    uint64_t adj = h0.adj;
+    if (dtot > capa0) {
+        capa1 = capa_for(dtot);
+        if (rank == 0) sh.alloc_off = pool_alloc(G.pool, 4ull * capa1);
+        t.sync();
+        const uint64_t noff = sh.alloc_off;
+        if (noff == 0) return;  // pool exhausted (flagged); the pre-check makes this unreachable
+        if (d0) {
+            const uint2* op = adj_pairs(G, h0.adj);
+            const uint64_t* oe = adj_eids(G, h0.adj, capa0);
+            uint2* np = adj_pairs(G, noff);
+            uint64_t* ne = adj_eids(G, noff, capa1);
+            for (uint32_t j = rank; j < d0; j += T) {
+                np[j] = op[j];
+                ne[j] = oe[j];
+            }
         }
+        t.sync();
+        if (rank == 0 && capa0) pool_free(G.pool, h0.adj, 4ull * capa0);
+        adj = noff;
     }
-    if (rank == 0) {
-        VHdr h;
-        h.adj = adj;
-        h.deg = d1;
-        h.mask = maskn;
-        h.sref = SPn ? sref1 : 0;
-        h.nsp = SPn ? nsp1 : 0;
-        h.lcapa = capa1 ? (uint8_t)(log2_u32(capa1) + 1) : 0;
-        h.lcaps = SPn ? (uint8_t)(log2_u32(caps1) + 1) : 0;
-        h.pad = 0;
-        store_hdr(G, v, h);
-        // ---- S12: stats
-        atomicAdd(stats + S_INS, (unsigned long long)ni);
-        atomicAdd(stats + S_DEL, (unsigned long long)found);
-        atomicAdd(stats + S_NF, (unsigned long long)(nd - found));
-        atomicAdd(stats + S_TOUCH, 1ull);
-        if (rebuilt) atomicAdd(stats + S_REBUILT, (unsigned long long)rebuilt);
+    uint2* pairs = adj_pairs(G, adj);
+    uint64_t* eids = adj_eids(G, adj, capa1);
+    // S2: append insertions at slots d0 .. d0+ni-1
+    for (uint32_t i = rank; i < ni; i += T) {
+        const uint4 u = B.ins(i);
+        pairs[d0 + i] = make_uint2(u.y, u.z);
+        eids[d0 + i] = B.ins_eid(i);
     }
-    for (uint32_t k = rank; k < 32; k += T) {
-        const bool dec = REAL && k == DEC_SLOT;
-        const uint32_t ko = dec ? (uint32_t)K_EMPTY : kind_of(sh.cnt_old[k], d0, G.alpha, G.beta);
-        const uint32_t kn = dec ? (uint32_t)K_EMPTY : kind_of(sh.cnt_new[k], d1, G.alpha, G.beta);
-        if (ko != kn) atomicAdd(stats + S_CONV + ko * 5 + kn, 1ull);
+    for (uint32_t j = rank; j < nd; j += T) {
+        X.del_slot[j] = NONE32;
+        X.best[j] = INF64;
     }
     t.sync();
+    // S3: resolution
+    const uint32_t found = resolve_deletions(t, B, X, pairs, eids, d0, ni, nd, sdel_buf, sdel_cap, cand_buf, cand_cap, pre);
+    const uint32_t d1 = dtot - found;
+    // S4: count deltas from the bits of deleted pre-existing and surviving new edges
+    for (uint32_t j = rank; j < nd; j += T) {
+        const uint32_t s = X.del_slot[j];
+        if (s != NONE32 && s < d0)
+            for (uint32_t b = pairs[s].y; b; b &= b - 1) atomicAdd(&sh.delta[__ffs(b) - 1], -1);
+    }
+    for (uint32_t i = rank; i < ni; i += T)
+        if (!(eids[d0 + i] & DEAD_BIT))
+            for (uint32_t b = pairs[d0 + i].y; b; b &= b - 1) atomicAdd(&sh.delta[__ffs(b) - 1], 1);
+    t.sync();
+    for (uint32_t k = rank; k < 32; k += T) sh.cnt_new[k] = (uint32_t)((int32_t)sh.cnt_old[k] + sh.delta[k]);
+    t.sync();
+    const KindMasks kmn = kind_masks<false>(t, sh, sh.cnt_new, d1, G, 1);
+    if ((kmn.sp | kmn.reg | kmn.one) && rank == 0) atomicOr(G.pool.status, ST_STATE);  // the classification was wrong
+    // S8: compact the adjacency: surviving edges of the tail [d1, dtot) fill the holes below d1
+    if (found) {
+        uint32_t nh = 0, ns = 0;
+        for (uint32_t b = 0; b < nd; b += T) {
+            const uint32_t j = b + rank;
+            const uint32_t s = j < nd ? X.del_slot[j] : NONE32;
+            const bool pred = s != NONE32 && s < d1;
+            uint32_t tot;
+            const uint32_t r = t.scan_pred(pred, tot);
+            if (pred) X.holes[nh + r] = s;
+            nh += tot;
+        }
+        for (uint32_t b = d1; b < dtot; b += T) {
+            const uint32_t q = b + rank;
+            const bool pred = q < dtot && !(eids[q] & DEAD_BIT);
+            uint32_t tot;
+            const uint32_t r = t.scan_pred(pred, tot);
+            if (pred) X.surv[ns + r] = q;
+            ns += tot;
+        }
+        t.sync();
+        for (uint32_t b = 0; b < nh; b += T) {
+            const uint32_t r = b + rank;
+            if (r < nh) {
+                const uint32_t q = X.holes[r], p = X.surv[r];
+                pairs[q] = pairs[p];
+                eids[q] = eids[p];
+            }
+        }
+        t.sync();
+    }
+    // S11-S12
+    VHdr h1;
+    h1.adj = adj;
+    h1.deg = d1;
+    h1.mask = kmn.nonempty;
+    h1.sref = 0;
+    h1.nsp = 0;
+    h1.lcapa = capa1 ? (uint8_t)(log2_u32(capa1) + 1) : 0;
+    h1.lcaps = 0;
+    h1.pad = 0;
+    write_back<false>(t, G, sh, v, h1, d0, ni, nd, found, 0u, stats);
 }
 
 // ------------------------------------------------------------------------------------------- batch kernels
@@ -912,8 +1048,10 @@ __device__ __forceinline__ void load_counts(const DevGraph& G, uint32_t v, uint3
     }
 }
 
+// dense_only (nullable): set when every group is dense or empty now and can be nothing else after
+// (no list kind and no one-element group reachable), on integer graphs with group adaption.
 __device__ __forceinline__ unsigned long long pool_bound(const DevGraph& G, uint32_t v, const VHdr& h, uint32_t ni,
-                                                         uint32_t nd, uint32_t insbits) {
+                                                         uint32_t nd, uint32_t insbits, bool* dense_only = nullptr) {
     uint32_t cnts[32];
     load_counts(G, v, cnts);
     const uint32_t d0 = h.deg, dmin = d0 + ni >= nd ? d0 + ni - nd : 0, dmax = d0 + ni;
@@ -922,10 +1060,14 @@ __device__ __forceinline__ unsigned long long pool_bound(const DevGraph& G, uint
     uint32_t nblocks = 0, sp_possible = 0;
     bool sp_set_may_change = false, any_old_sp = false;
     const uint32_t nslots = G.fbits ? DEC_SLOT : 32u;  // the decimal slot is never a list
+    bool dense = G.fbits == 0 && G.alpha != ALL_REGULAR;
     for (uint32_t k = 0; k < nslots; k++) {
         const uint32_t c = cnts[k];
         const uint32_t cmax = c + (((insbits >> k) & 1u) ? ni : 0u), cmin = c > nd ? c - nd : 0u;
         const uint32_t old = kind_of(c, d0, G.alpha, G.beta);
+        if (old != K_EMPTY && old != K_DENSE) dense = false;
+        // one-element reachable: a count of 1 at a degree where it is not dense (100 <= alpha d)
+        if (cmin <= 1 && cmax >= 1 && 100ull <= (uint64_t)G.alpha * dmax) dense = false;
         const uint32_t min_list = G.alpha == ALL_REGULAR ? 1u : 2u;  // smallest count of a list kind
         if (cmax < min_list) continue;  // can never be a list kind (and is not one now)
         const uint32_t lo2 = cmin > min_list ? cmin : min_list;
@@ -935,6 +1077,7 @@ __device__ __forceinline__ unsigned long long pool_bound(const DevGraph& G, uint
         const uint64_t rlo = ((uint64_t)G.beta * dmin + 99) / 100, rhi = ((uint64_t)G.alpha * dmax) / 100;
         const bool can_reg = lo2 <= rhi && cmax >= rlo && rlo <= rhi;
         const bool can_dense = 100ull * cmax > (uint64_t)G.alpha * dmin;
+        if (can_reg || can_sp) dense = false;
         if ((can_reg && (old != K_REGULAR || grows)) || (can_sp && (old != K_SPARSE || grows))) nblocks++;
         if (can_sp) sp_possible++;
         if (old == K_SPARSE) {
@@ -950,6 +1093,7 @@ __device__ __forceinline__ unsigned long long pool_bound(const DevGraph& G, uint
     unsigned long long words = grows ? 4ull * capa1 + (G.fbits ? dec_words(capa1) : 0ull) : 0ull;
     words += 4ull * capa1 * nblocks;
     if (sp_possible && sp_rebuild) words += 2ull * capa1 + 4ull * capa1 * sp_possible;
+    if (dense_only) *dense_only = dense;
     return words;
 }
 
@@ -961,6 +1105,8 @@ struct SegArgs {
     const uint64_t* nseg_dev;
     uint32_t* small_list;
     uint32_t* big_list;
+    uint32_t* dense_list;         // small dense-only segments (k_apply_dense)
+    unsigned long long* ndense;   // [0] count, [1] k_apply_dense work queue
     unsigned long long* counts;   // [0] small, [1] big, [2] pool bound
     unsigned long long* queue;    // [0] next small segment, [1] next big segment (k_apply work queues)
     uint32_t big_slots;           // segments above this many adjacency slots run on a block team
@@ -973,6 +1119,9 @@ struct SegArgs {
     uint32_t* huge_list;          // segments scanned by the pre-pass
     unsigned long long* nhuge;
     uint32_t* huge_coff;          // [nhuge + 1] first pre-pass chunk of each listed segment (k_cand_plan)
+    uint32_t* huge_nch;           // [nhuge] pre-pass chunks of each listed segment (k_seg_classify)
+    uint32_t* chunk_seg;          // [chunk_cap] listed segment of each pre-pass chunk (k_cand_plan)
+    uint32_t chunk_cap;
     uint64_t eid_base;
     const unsigned long long* eid_base_dev;  // when set, the edge-id base is read on the device
     uint32_t* holes;
@@ -1004,12 +1153,18 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
         if (G.fbits && dtot >= REAL_MAX_DEG) { atomicOr(G.pool.status, ST_INVALID); continue; }
         uint32_t insbits = 0;
         for (uint32_t i = a; i < lo; i++) insbits |= S.rec[i].z;
-        bound += pool_bound(G, v, h, ni, b - lo, insbits);
+        bool dense_only = false;
+        bound += pool_bound(G, v, h, ni, b - lo, insbits, &dense_only);
         const bool big = dtot > S.big_slots || (b - a) > 256;
         const bool huge = h.deg >= PRE_MIN_DEG && b > lo;  // deletions at a large vertex: grid-wide candidate scan
         S.gcand_cnt[sidx] = huge ? 0u : NO_PRE;
-        if (huge) S.huge_list[atomicAdd(S.nhuge, 1ull)] = (uint32_t)sidx;
+        if (huge) {
+            const unsigned long long pos = atomicAdd(S.nhuge, 1ull);
+            S.huge_list[pos] = (uint32_t)sidx;
+            S.huge_nch[pos] = (h.deg + PRE_CHUNK - 1) / PRE_CHUNK;
+        }
         if (big) S.big_list[atomicAdd(&S.counts[1], 1ull)] = (uint32_t)sidx;
+        else if (dense_only) S.dense_list[atomicAdd(S.ndense, 1ull)] = (uint32_t)sidx;
         else S.small_list[atomicAdd(&S.counts[0], 1ull)] = (uint32_t)sidx;
     }
     if (bound) atomicAdd(&S.counts[2], bound);
@@ -1035,30 +1190,40 @@ __global__ void __launch_bounds__(1024) k_cand_plan(DevGraph G, SegArgs S) {
     uint32_t base = 0;
     for (uint64_t t0 = 0; t0 < nhuge; t0 += blockDim.x) {
         const uint64_t i = t0 + threadIdx.x;
-        uint32_t c = 0;
-        if (i < nhuge) {
-            const uint4 info = S.seginfo[S.huge_list[i]];
-            const uint32_t d0 = load_hdr(G, info.x).deg;
-            c = (d0 + PRE_CHUNK - 1) / PRE_CHUNK;
-        }
+        const uint32_t c = i < nhuge ? S.huge_nch[i] : 0u;
         const uint2 r = block_scan_excl(sm, c);
         if (i < nhuge) S.huge_coff[i] = base + r.x;
         base += r.y;
     }
     if (threadIdx.x == 0) S.huge_coff[nhuge] = base;
+    // chunk -> segment map (when it fits; k_cand_scan searches the offsets otherwise)
+    if (base > S.chunk_cap) return;
+    __syncthreads();
+    for (uint64_t i = threadIdx.x; i < nhuge; i += blockDim.x) {
+        const uint32_t c0 = S.huge_coff[i], c1 = c0 + S.huge_nch[i];
+        for (uint32_t c = c0; c < c1; c++) S.chunk_seg[c] = (uint32_t)i;
+    }
 }
 
+constexpr uint32_t PRE_SDEL = 2048;  // deletion destinations of a chunk's segment staged in shared memory
 __global__ void __launch_bounds__(256) k_cand_scan(DevGraph G, SegArgs S) {
+    __shared__ uint32_t sdk[PRE_SDEL];
     if (*(volatile uint32_t*)G.pool.status & ST_STOP) return;  // block-uniform
     const unsigned long long nhuge = *S.nhuge;
     if (nhuge == 0) return;
     const uint32_t total = S.huge_coff[nhuge];
+    const bool mapped = total <= S.chunk_cap;
     const uint64_t dmask = (1ull << S.B.bn) - 1;
     for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
-        uint32_t lo = 0, hi = (uint32_t)nhuge;  // last listed segment whose first chunk is <= c
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (S.huge_coff[mid] <= c) lo = mid; else hi = mid;
+        uint32_t lo = 0;  // the listed segment holding chunk c: the last whose first chunk is <= c
+        if (mapped) {
+            lo = S.chunk_seg[c];
+        } else {
+            uint32_t hi = (uint32_t)nhuge;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (S.huge_coff[mid] <= c) lo = mid; else hi = mid;
+            }
         }
         const uint32_t sidx = S.huge_list[lo];
         const uint4 info = S.seginfo[sidx];
@@ -1076,6 +1241,11 @@ __global__ void __launch_bounds__(256) k_cand_scan(DevGraph G, SegArgs S) {
             const uint32_t j = c0 + q * 256 + threadIdx.x;
             x[q] = j < d0 ? pairs[j].x : NONE32;
         }
+        const bool staged = nd <= PRE_SDEL;
+        __syncthreads();  // the previous chunk's searches are done with sdk
+        if (staged)
+            for (uint32_t j = threadIdx.x; j < nd; j += blockDim.x) sdk[j] = (uint32_t)(__ldg(dk + j) & dmask);
+        __syncthreads();
 #pragma unroll
         for (int q = 0; q < 8; q++) {
             const uint32_t j = c0 + q * 256 + threadIdx.x;
@@ -1083,9 +1253,10 @@ __global__ void __launch_bounds__(256) k_cand_scan(DevGraph G, SegArgs S) {
             uint32_t a = 0, b = nd;
             while (a < b) {
                 const uint32_t mid = (a + b) >> 1;
-                if ((uint32_t)(__ldg(dk + mid) & dmask) < x[q]) a = mid + 1; else b = mid;
+                const uint32_t y = staged ? sdk[mid] : (uint32_t)(__ldg(dk + mid) & dmask);
+                if (y < x[q]) a = mid + 1; else b = mid;
             }
-            if (a < nd && (uint32_t)(__ldg(dk + a) & dmask) == x[q]) {
+            if (a < nd && (staged ? sdk[a] : (uint32_t)(__ldg(dk + a) & dmask)) == x[q]) {
                 const uint32_t pos = atomicAdd(S.gcand_cnt + sidx, 1u);
                 if (pos < cap) out[pos] = j;
             }
@@ -1105,7 +1276,8 @@ template <bool REAL, class Team>
 __device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, const SegArgs& S, SegSh& sh, uint32_t sidx,
                                             uint32_t* sdel_buf, uint32_t sdel_cap, uint32_t* cand_buf,
                                             uint32_t cand_cap, SmallScratch* sx = nullptr,
-                                            unsigned long long* stats = nullptr, bool pre_scanned = false) {
+                                            unsigned long long* stats = nullptr, bool pre_scanned = false,
+                                            bool dense_only = false) {
     const uint4 info = S.seginfo[sidx];
     const uint32_t v = info.x, a = info.y, ni = info.z, nd = info.w;
     BatchSrc src;
@@ -1135,8 +1307,15 @@ __device__ __forceinline__ void run_segment(const Team& t, const DevGraph& G, co
         pre.count = S.gcand_cnt[sidx];
         pre.cap = PRE_MULT * nd;
     }
-    apply_segment<REAL>(t, G, sh, v, ni, nd, src, X, stats ? stats : S.stats, sdel_buf, sdel_cap, cand_buf, cand_cap,
-                        pre);
+    if (!REAL && dense_only)
+        apply_dense_segment(t, G, sh, v, ni, nd, src, X, stats ? stats : S.stats, sdel_buf, sdel_cap, cand_buf, cand_cap,
+                            pre);
+    else
+        apply_segment<REAL>(t, G, sh, v, ni, nd, src, X, stats ? stats : S.stats, sdel_buf, sdel_cap, cand_buf,
+                            cand_cap, pre);
+    // the edge-index pass (k_eh_apply) reads from the batch scratch which deletions found an edge
+    if (G.eh_mask && X.del_slot != S.slot_scratch + a + ni)
+        for (uint32_t j = t.rank(); j < nd; j += t.size()) S.slot_scratch[a + ni + j] = X.del_slot[j];
 }
 
 constexpr uint32_t DEFAULT_UPDATE_CHUNK = 4096;  // best of 1,024 .. 16,384 on RMAT-20 with 10^5-update batches
@@ -1198,7 +1377,32 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) k_apply(DevGraph G, SegArgs 
         i = __shfl_sync(FULL, i, 0);
         if (i >= nsmall) break;
         run_segment<REAL>(t, G, S, smem.small.sh[w], S.small_list[i], smem.small.sdel[w], SMALL_SDEL, smem.small.cand[w],
-                    SMALL_CAND, &smem.small.x[w], bstats, true);
+                          SMALL_CAND, &smem.small.x[w], bstats, true);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < S_CONV + 25; i += blockDim.x)
+        if (bstats[i]) atomicAdd(S.stats + i, bstats[i]);
+}
+
+// The small dense-only segments (integer graphs), after k_apply: the same warp teams and queue,
+// on apply_dense_segment alone.  k_apply is bound by instruction fetch, and a launch that runs one
+// short procedure on every SM keeps it in the instruction cache, where sharing k_apply's warps with
+// the general procedure slowed both.
+__global__ void __launch_bounds__(APPLY_THREADS, 2) k_apply_dense(DevGraph G, SegArgs S) {
+    __shared__ SmallShared smem;
+    __shared__ unsigned long long bstats[S_CONV + 25];
+    for (uint32_t i = threadIdx.x; i < S_CONV + 25; i += blockDim.x) bstats[i] = 0;
+    __syncthreads();
+    const unsigned long long n = S.ndense[0];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpTeam t;
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = (*(volatile uint32_t*)G.pool.status & ST_STOP) ? n : atomicAdd(S.ndense + 1, 1ull);
+        i = __shfl_sync(FULL, i, 0);
+        if (i >= n) break;
+        run_segment<false>(t, G, S, smem.sh[w], S.dense_list[i], smem.sdel[w], SMALL_SDEL, smem.cand[w], SMALL_CAND,
+                           &smem.x[w], bstats, true, true);
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < S_CONV + 25; i += blockDim.x)
@@ -1256,17 +1460,92 @@ __global__ void k_finalize_pool(DevGraph G) {
 
 // Streaming (Section 4.2): every record is applied as a batch of one, in record order.  Records of
 // different source vertices touch disjoint state and edge ids are fixed by record position, so the
-// records are grouped by source (stable sort) and one warp applies each vertex's records in order
-// while vertices proceed in parallel: the result equals strict one-at-a-time application.
+// records are grouped by source (stable sort) and one team applies each vertex's records in order
+// while vertices proceed in parallel: the result equals strict one-at-a-time application.  A warp
+// applies the records of a vertex with fewer than STREAM_BIG_DEG edges; larger vertices (whose
+// deletions scan the whole adjacency) are listed and applied afterwards by a 512-thread block each.
 constexpr uint32_t STREAM_TEAMS = 16;
+constexpr uint32_t STREAM_BIG_DEG = 4096;
+constexpr uint32_t STREAM_BIG_THREADS = 512;
+constexpr uint32_t STREAM_BIG_CAND = 4096;
 struct StreamScratch {
     uint32_t holes[2], surv[2], ins_final[2], del_slot[2];
     unsigned long long best[2];
 };
 
+// Apply record r of the sorted stream with team t.  Returns false when processing must stop (pool
+// exhausted or an invalid record; the status says which).
+template <bool REAL, class Team>
+__device__ bool stream_record(const Team& t, const DevGraph& G, const SegArgs& S, SegSh& sh, StreamScratch& xs,
+                              uint32_t r, unsigned long long* reserved, uint32_t* cand_buf, uint32_t cand_cap) {
+    const bool stop = t.rank() == 0 && (*(volatile uint32_t*)G.pool.status & ST_STOP);
+    if (t.any(stop)) return false;  // one reader, so the whole team leaves together
+    const uint32_t rec = S.sorted_vals[r];
+    uint4 u = S.B.ups[rec];
+    u.x = to_internal(G, u.x);
+    u.y = to_internal(G, u.y);
+    const uint32_t ni = (u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
+    const uint32_t nd = (u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
+    // reserve this record's worst-case pool growth so no allocation inside it can fail
+    uint32_t I = u.z, qd = 0;
+    if (REAL && ni) split_real_bias(u.z, G.lambda, I, qd);
+    if (G.base4 && ni) I = b4_mask(u.z);
+    const VHdr h = load_hdr(G, u.x);
+    if (REAL && h.deg + ni >= REAL_MAX_DEG) {
+        if (t.rank() == 0) atomicOr(G.pool.status, ST_INVALID);
+        return false;
+    }
+    const unsigned long long need = pool_bound(G, u.x, h, ni, nd, ni ? I : 0u);
+    bool fail = false;
+    if (t.rank() == 0) {
+        const unsigned long long prev = atomicAdd(reserved, need);
+        if (*G.pool.top + prev + need > G.pool.words) {
+            atomicAdd(reserved, 0ull - need);
+            atomicOr(G.pool.status, ST_OOM);
+            fail = true;
+        }
+    }
+    if (t.any(fail)) return false;
+    OneSrc src;
+    src.dst = u.y;
+    src.bias = I;
+    src.q = qd;
+    src.eid = S.eid_base + (S.B.pscan[rec] >> 32);
+    SegScratch X;
+    X.holes = xs.holes;
+    X.surv = xs.surv;
+    X.ins_final = xs.ins_final;
+    X.del_slot = xs.del_slot;
+    X.best = xs.best;
+    apply_segment<REAL>(t, G, sh, u.x, ni, nd, src, X, S.stats, nullptr, 0u, cand_buf, cand_cap);
+    if (G.eh_mask && t.rank() == 0) {  // edge index: +1 per insertion, -1 per deletion that found an edge
+        const unsigned long long k = ((unsigned long long)u.x << 32) | u.y;
+        if (ni) {
+            uint64_t p = eh_hash(k) & G.eh_mask;
+            for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
+                const unsigned long long old = atomicCAS(G.eh_key + p, EH_EMPTY, k);
+                if (old == EH_EMPTY || old == k) { atomicAdd(G.eh_cnt + p, 1u); break; }
+                p = (p + 1) & G.eh_mask;
+            }
+        }
+        if (nd && X.del_slot[0] != NONE32) {
+            uint64_t p = eh_hash(k) & G.eh_mask;
+            for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
+                const unsigned long long cur = G.eh_key[p];
+                if (cur == k) { atomicSub(G.eh_cnt + p, 1u); break; }
+                if (cur == EH_EMPTY) break;
+                p = (p + 1) & G.eh_mask;
+            }
+        }
+    }
+    if (t.rank() == 0) atomicAdd(reserved, 0ull - need);
+    t.sync();
+    return true;
+}
+
 template <bool REAL>
-__global__ void __launch_bounds__(STREAM_TEAMS * 32) k_stream_apply(DevGraph G, SegArgs S,
-                                                                    unsigned long long* reserved) {
+__global__ void __launch_bounds__(STREAM_TEAMS * 32) k_stream_apply(DevGraph G, SegArgs S, unsigned long long* reserved,
+                                                                    uint32_t* big_list, unsigned long long* nbig) {
     __shared__ SegSh sh[STREAM_TEAMS];
     __shared__ StreamScratch xs[STREAM_TEAMS];
     const uint32_t w = threadIdx.x >> 5;
@@ -1274,70 +1553,33 @@ __global__ void __launch_bounds__(STREAM_TEAMS * 32) k_stream_apply(DevGraph G, 
     const uint64_t nseg = *S.nseg_dev;
     for (uint64_t sidx = (uint64_t)blockIdx.x * STREAM_TEAMS + w; sidx < nseg; sidx += (uint64_t)gridDim.x * STREAM_TEAMS) {
         const uint32_t a = S.seg_start[sidx], b = S.seg_start[sidx + 1];
-        for (uint32_t r = a; r < b; r++) {
-            if (*G.pool.status & ST_STOP) return;
-            const uint32_t rec = S.sorted_vals[r];
-            uint4 u = S.B.ups[rec];
-            u.x = to_internal(G, u.x);
-            u.y = to_internal(G, u.y);
-            const uint32_t ni = (u.w == BINGO_OP_INSERT || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
-            const uint32_t nd = (u.w == BINGO_OP_DELETE || u.w == BINGO_OP_SET_BIAS) ? 1u : 0u;
-            // reserve this record's worst-case pool growth so no allocation inside it can fail
-            uint32_t I = u.z, qd = 0;
-            if (REAL && ni) split_real_bias(u.z, G.lambda, I, qd);
-            if (G.base4 && ni) I = b4_mask(u.z);
-            const VHdr h = load_hdr(G, u.x);
-            if (REAL && h.deg + ni >= REAL_MAX_DEG) {
-                if (t.rank() == 0) atomicOr(G.pool.status, ST_INVALID);
-                return;
-            }
-            const unsigned long long need = pool_bound(G, u.x, h, ni, nd, ni ? I : 0u);
-            int ok = 1;
-            if (t.rank() == 0) {
-                const unsigned long long prev = atomicAdd(reserved, need);
-                if (*G.pool.top + prev + need > G.pool.words) {
-                    atomicAdd(reserved, 0ull - need);
-                    atomicOr(G.pool.status, ST_OOM);
-                    ok = 0;
-                }
-            }
-            ok = __shfl_sync(FULL, ok, 0);
-            if (!ok) return;
-            OneSrc src;
-            src.dst = u.y;
-            src.bias = I;
-            src.q = qd;
-            src.eid = S.eid_base + (S.B.pscan[rec] >> 32);
-            SegScratch X;
-            X.holes = xs[w].holes;
-            X.surv = xs[w].surv;
-            X.ins_final = xs[w].ins_final;
-            X.del_slot = xs[w].del_slot;
-            X.best = xs[w].best;
-            apply_segment<REAL>(t, G, sh[w], u.x, ni, nd, src, X, S.stats, nullptr, 0u);
-            if (G.eh_mask && t.rank() == 0) {  // edge index: +1 per insertion, -1 per deletion that found an edge
-                const unsigned long long k = ((unsigned long long)u.x << 32) | u.y;
-                if (ni) {
-                    uint64_t p = eh_hash(k) & G.eh_mask;
-                    for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
-                        const unsigned long long old = atomicCAS(G.eh_key + p, EH_EMPTY, k);
-                        if (old == EH_EMPTY || old == k) { atomicAdd(G.eh_cnt + p, 1u); break; }
-                        p = (p + 1) & G.eh_mask;
-                    }
-                }
-                if (nd && X.del_slot[0] != NONE32) {
-                    uint64_t p = eh_hash(k) & G.eh_mask;
-                    for (uint64_t probe = 0; probe <= G.eh_mask; probe++) {
-                        const unsigned long long cur = G.eh_key[p];
-                        if (cur == k) { atomicSub(G.eh_cnt + p, 1u); break; }
-                        if (cur == EH_EMPTY) break;
-                        p = (p + 1) & G.eh_mask;
-                    }
-                }
-            }
-            if (t.rank() == 0) atomicAdd(reserved, 0ull - need);
-            __syncwarp();
+        // the vertex's degree before its first record decides the team (the block pass runs after)
+        const uint32_t v = to_internal(G, S.B.ups[S.sorted_vals[a]].x);
+        if (v < G.n && load_hdr(G, v).deg >= STREAM_BIG_DEG) {
+            if (t.rank() == 0) big_list[atomicAdd(nbig, 1ull)] = (uint32_t)sidx;
+            continue;
         }
+        for (uint32_t r = a; r < b; r++)
+            if (!stream_record<REAL>(t, G, S, sh[w], xs[w], r, reserved, nullptr, 0u)) return;
+    }
+}
+
+// The listed large vertices, one 512-thread block team each, their records in order.
+template <bool REAL>
+__global__ void __launch_bounds__(STREAM_BIG_THREADS) k_stream_apply_big(DevGraph G, SegArgs S, unsigned long long* reserved,
+                                                                         const uint32_t* big_list,
+                                                                         const unsigned long long* nbig) {
+    __shared__ SegSh sh;
+    __shared__ StreamScratch xs;
+    __shared__ uint32_t cand[STREAM_BIG_CAND];
+    BlockTeam t;
+    t.sm = sh.tscratch;
+    const unsigned long long nb = *nbig;
+    for (unsigned long long i = blockIdx.x; i < nb; i += gridDim.x) {
+        const uint32_t sidx = big_list[i];
+        const uint32_t a = S.seg_start[sidx], b = S.seg_start[sidx + 1];
+        for (uint32_t r = a; r < b; r++)
+            if (!stream_record<REAL>(t, G, S, sh, xs, r, reserved, cand, STREAM_BIG_CAND)) return;
     }
 }
 
@@ -1446,13 +1688,15 @@ static bingo_status update_capacity(bingo_graph* g, uint64_t count) {
     CK(ensure(g->s_keys2, 8 * kc), "update scratch");
     CK(ensure(g->s_vals, 4 * kc), "update scratch");
     CK(ensure(g->s_vals2, 4 * kc), "update scratch");
-    CK(ensure(g->s_seg, 8 * kc * 2 + 4 * (kc + 2) * 3 + 64), "update scratch");
+    CK(ensure(g->s_seg, 8 * kc * 2 + 4 * (kc + 2) * 4 + 64), "update scratch");
     CK(ensure(g->s_aux, 4 * kc * 3 + 64), "update scratch");
     CK(ensure(g->s_best, 8 * kc + 64), "update scratch");
     CK(ensure(g->s_rec, 16 * kc), "update scratch");
     CK(ensure(g->s_seginfo, 16 * kc + 16), "update scratch");
     CK(ensure(g->s_gcand, 4ull * PRE_MULT * kc), "update scratch");
-    CK(ensure(g->s_gcand_cnt, 12 * kc + 64), "update scratch");  // counts, segment list, chunk offsets
+    CK(ensure(g->s_gcand_cnt, 16 * kc + 128), "update scratch");  // counts, segment list, chunk offsets and counts
+    const uint64_t chunk_cap = std::min<uint64_t>((g->next_eid + kc) / PRE_CHUNK + kc + 64, 0xFFFFFFFFull);
+    CK(ensure(g->s_chunkmap, 4 * chunk_cap), "update scratch");
     CK(ensure(g->s_tmp, std::max(radix_sort_tmp_bytes(kc), scan_tmp_bytes(kc))), "update scratch");
     if (!g->apply_blocks) {
         int per_sm = 0;
@@ -1507,6 +1751,7 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     uint32_t* seg_start = (uint32_t*)(segid + kc);
     uint32_t* small_list = seg_start + kc + 2;
     uint32_t* big_list = small_list + kc + 2;
+    uint32_t* dense_list = big_list + kc + 2;
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
     k_seg_flags<<<grid_cap(g, kc, 256), 256, 0, s>>>(skeys, svals, kc, nkeys_dev, A.bn, A.ups, A.pscan,
                                                      (const unsigned long long*)(ctl + CTL_SCR + 9), A.fbits,
@@ -1525,6 +1770,9 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     S.nseg_dev = nseg_dev;
     S.small_list = small_list;
     S.big_list = big_list;
+    S.dense_list = dense_list;
+    S.ndense = (unsigned long long*)(ctl + CTL_SCR + 14);
+    CK(cudaMemsetAsync(S.ndense, 0, 16, s), "dense segment count reset");
     S.counts = counts;
     S.eid_base = 0;
     S.eid_base_dev = (const unsigned long long*)(ctl + CTL_SCR + 9);
@@ -1535,6 +1783,9 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     S.gcand_cnt = (uint32_t*)g->s_gcand_cnt.p;
     S.huge_list = S.gcand_cnt + kc + 4;
     S.huge_coff = S.huge_list + kc + 4;
+    S.huge_nch = S.huge_coff + kc + 4;
+    S.chunk_seg = (uint32_t*)g->s_chunkmap.p;
+    S.chunk_cap = (uint32_t)(g->s_chunkmap.bytes / 4);
     S.nhuge = (unsigned long long*)(ctl + CTL_SCR + 13);
     CK(cudaMemsetAsync(S.nhuge, 0, 8, s), "pre-pass count reset");
     S.holes = (uint32_t*)g->s_aux.p;
@@ -1547,8 +1798,13 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     k_oom_check<<<1, 1, 0, s>>>(g->G, counts, S.queue);
     k_cand_plan<<<1, 1024, 0, s>>>(g->G, S);
     k_cand_scan<<<(unsigned)g->num_sms * 8, 256, 0, s>>>(g->G, S);
-    if (g->G.fbits) k_apply<true><<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
-    else k_apply<false><<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
+    if (g->G.fbits) {
+        k_apply<true><<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
+    } else {
+        k_apply<false><<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);
+        k_apply_dense<<<g->apply_blocks, APPLY_THREADS, 0, s>>>(g->G, S);  // no dense-only segments on real biases
+        g->launches++;
+    }
     g->launches += 5;
     if (g->G.eh_mask) {
         k_eh_apply<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S, kc, nkeys_dev);
@@ -1645,6 +1901,19 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
         if (stats) memset(stats, 0, sizeof(*stats));
         return BINGO_OK;
     }
+    // The batch pipeline's captured graph holds pointers to these shared scratch buffers: if one must
+    // grow, wait for earlier work, drop the graph and let the next batch size and capture it again.
+    {
+        auto grows = [](const Buf& b, size_t bytes) { return !(b.p && bytes <= b.bytes); };
+        if ((!is_device_ptr(ups) && grows(g->s_in, count * 16)) || grows(g->s_rank, 16 * count + 64) ||
+            grows(g->s_keys, 8 * count) || grows(g->s_keys2, 8 * count) || grows(g->s_vals, 4 * count) ||
+            grows(g->s_vals2, 4 * count) || grows(g->s_seg, 8 * count * 2 + 4 * (count + 2) * 4 + 64)) {
+            if (g->upd_graph) cudaGraphExecDestroy(g->upd_graph);
+            g->upd_graph = nullptr;
+            g->upd_cap = 0;
+            cudaDeviceSynchronize();
+        }
+    }
     const uint4* dups = (const uint4*)ups;
     if (!is_device_ptr(ups)) {
         CK(ensure(g->s_in, count * 16), "update staging");
@@ -1656,7 +1925,7 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     CK(ensure(g->s_keys2, 8 * count), "stream scratch");
     CK(ensure(g->s_vals, 4 * count), "stream scratch");
     CK(ensure(g->s_vals2, 4 * count), "stream scratch");
-    CK(ensure(g->s_seg, 8 * count * 2 + 4 * (count + 2) * 3 + 64), "segment scratch");
+    CK(ensure(g->s_seg, 8 * count * 2 + 4 * (count + 2) * 4 + 64), "segment scratch");
     BatchArgs A;
     A.ups = dups;
     A.count = count;
@@ -1703,10 +1972,19 @@ bingo_status bingo_stream_updates(bingo_graph* g, const bingo_update* ups, uint6
     S.eid_base_dev = nullptr;
     S.stats = (unsigned long long*)(ctl + CTL_STATS);
     unsigned long long* reserved = (unsigned long long*)(ctl + CTL_SCR + 7);
+    unsigned long long* nbig = (unsigned long long*)(ctl + CTL_SCR + 13);
+    uint32_t* big_list = seg_start + count + 2;
+    CK(cudaMemsetAsync(nbig, 0, 8, s), "stream big-vertex count");
     const unsigned blocks = grid_cap(g, count, STREAM_TEAMS, 8);
-    if (g->G.fbits) k_stream_apply<true><<<blocks, STREAM_TEAMS * 32, 0, s>>>(g->G, S, reserved);
-    else k_stream_apply<false><<<blocks, STREAM_TEAMS * 32, 0, s>>>(g->G, S, reserved);
-    g->launches += 3;
+    const unsigned big_blocks = (unsigned)g->num_sms * 2;
+    if (g->G.fbits) {
+        k_stream_apply<true><<<blocks, STREAM_TEAMS * 32, 0, s>>>(g->G, S, reserved, big_list, nbig);
+        k_stream_apply_big<true><<<big_blocks, STREAM_BIG_THREADS, 0, s>>>(g->G, S, reserved, big_list, nbig);
+    } else {
+        k_stream_apply<false><<<blocks, STREAM_TEAMS * 32, 0, s>>>(g->G, S, reserved, big_list, nbig);
+        k_stream_apply_big<false><<<big_blocks, STREAM_BIG_THREADS, 0, s>>>(g->G, S, reserved, big_list, nbig);
+    }
+    g->launches += 4;
     CK(cudaGetLastError(), "stream launch");
     bingo_status st = finish_batch(g, s, stats, 0);
     if (st == BINGO_OK && g->G.eh_mask && g->eh_distinct + (stats ? stats->inserted : count) > (g->G.eh_mask + 1) * 7 / 10) {

@@ -223,6 +223,53 @@ def test_streaming_parity(B):
         assert_state_matches(g.export_state(), og)
 
 
+def test_batch_after_a_stream_larger_than_its_capacity(B):
+    """Streaming shares the batch pipeline's scratch buffers: a stream with more records than the
+    captured batch capacity grows them, and the next batch must re-size and re-capture its pipeline
+    instead of reusing the old buffers; batches, streams and batches again all match the oracle."""
+    og = _stress_graph(5)
+    offs, dst, w, eid = og.edges()
+    g = B.Graph(og.n, dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=12)
+    rng = np.random.default_rng(17)
+    apply_both(g, og, _stress_batch(rng, og, og.n, 300), 12)
+    apply_both(g, og, _stress_batch(rng, og, og.n, 6000), 12, stream=True)
+    apply_both(g, og, _stress_batch(rng, og, og.n, 300), 12)
+    assert_state_matches(g.export_state(), og)
+    g.check()
+
+
+def test_streaming_large_vertices_use_block_teams(B):
+    """Streamed records of vertices with at least 4,096 edges are applied by a whole block (after the
+    warp pass over the smaller ones); duplicated edges, deletions of missing edges, set_bias and a
+    vertex that crosses 4,096 edges inside the stream must all match the oracle, one record at a time."""
+    n = 1 << 12
+    rng = np.random.default_rng(21)
+    edges = [(v, int(rng.integers(0, 64)), int(rng.integers(1, 1 << 10))) for v in range(3) for _ in range(6000)]
+    edges += [(3, int(rng.integers(0, n)), int(rng.integers(1, 1 << 10))) for _ in range(4090)]
+    edges += [(v, int(rng.integers(0, n)), int(rng.integers(1, 1 << 10))) for v in range(4, n) for _ in range(3)]
+    og = O.Graph.from_edges(n, edges)
+    offs, dst, w, eid = og.edges()
+    g = B.Graph(n, dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=10)
+    for it in range(2):
+        o_offs, o_dst, _, _ = og.edges()
+        rec = []
+        for _ in range(900):
+            v = int(rng.integers(0, 4)) if rng.random() < 0.7 else int(rng.integers(4, n))
+            a, c = int(o_offs[v]), int(o_offs[v + 1])
+            op = rng.random()
+            if op < 0.4:
+                rec.append([v, int(rng.integers(0, 64 if v < 3 else n)), int(rng.integers(1, 1 << 10)), 0])
+            elif op < 0.85:
+                x = int(o_dst[int(rng.integers(a, c))]) if c > a and rng.random() < 0.9 else int(rng.integers(0, n))
+                rec.append([v, x, 0, 1])
+            else:
+                x = int(o_dst[int(rng.integers(a, c))]) if c > a else int(rng.integers(0, n))
+                rec.append([v, x, int(rng.integers(1, 1 << 10)), 2])
+        apply_both(g, og, np.array(rec, dtype=np.uint32), 10, stream=True)
+        assert_state_matches(g.export_state(), og)
+    g.check()
+
+
 def test_capacity_growth_and_emptying(B):
     # one vertex grows far past its capacity (every structure rebuilt), another loses every edge
     n = 4096

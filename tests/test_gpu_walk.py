@@ -320,6 +320,31 @@ def test_node2vec_edge_index_follows_updates(B):
     assert tv(counts, wts) < 0.01 and chisq_p(counts, wts) > 1e-3
 
 
+def test_node2vec_edge_index_after_repeated_and_missing_deletions(B):
+    """The edge index counts live copies: a batch that deletes the one copy of 0 -> 2 twice and deletes an
+    edge that does not exist must leave 0 -> 2 absent (count 0, not one below it) and the rest unchanged,
+    so from 1 after 0 the neighbour 2 is at distance 2, as the oracle's Eq. node2vec weights say."""
+    gd = golden("node2vec_tiny.json")
+    og = O.Graph.from_edges(gd["n"], [tuple(e) for e in gd["edges"]])
+    offs, dst, w, _ = og.edges()
+    g = B.Graph(gd["n"], dev(offs.astype(np.uint64)), dev(dst), dev(w), max_bits=8)
+    _n2v_two_step(B, g, gd["accept_u32"], 1)  # builds the edge index
+    assert (0, 2) in {(int(a), int(b)) for a, b, _ in gd["edges"]}
+    missing = next(x for x in range(gd["n"]) if x not in {int(b) for a, b, _ in gd["edges"] if int(a) == 1})
+    rec = np.array([[0, 2, 0, 1], [0, 2, 0, 1], [1, missing, 0, 1]], dtype=np.uint32)
+    st = g.apply_updates(dev(rec))
+    rc, ost = og.apply(rec, 8)
+    assert rc == 0 and (st["deleted"], st["not_found"]) == (ost[1], ost[2]) == (1, 2)
+    paths, plen = _n2v_two_step(B, g, gd["accept_u32"], 2)
+    sel = paths[:, 1] == 1
+    assert sel.sum() > 0
+    wts = og.n2v_weights(0, 1, gd["accept_u32"]).astype(np.float64)
+    o2, d2, _, _ = og.edges()
+    nb = d2[o2[1]:o2[2]].astype(np.int64)
+    counts = np.array([(paths[sel, 2] == x).sum() for x in nb], dtype=np.float64)
+    assert tv(counts, wts) < 0.01 and chisq_p(counts, wts) > 1e-3
+
+
 def test_padding_flag_and_host_buffers(B):
     wl = W.make_workload("c1")
     G = wl.graph

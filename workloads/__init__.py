@@ -236,8 +236,9 @@ CONFIGS = {
 
 
 def make_workload(name: str, scale: int | None = None, m: int | None = None, nbatch: int | None = None,
-                  batch: int | None = None, nwalkers: int | None = None) -> Workload:
-    """Build a workload.  `scale`/`m`/`nbatch`/`batch`/`nwalkers` shrink it for tests.
+                  batch: int | None = None, nwalkers: int | None = None, hubs: bool = True) -> Workload:
+    """Build a workload.  `scale`/`m`/`nbatch`/`batch`/`nwalkers` shrink it for tests; hubs=False leaves
+    out a recipe's hub edges (profiling cases of the plain RMAT part).
 
     For the "stream" update protocol the graph generator produces m + (#inserts)
     edges; the held-out ones become the inserts (Section 5.1, datasets), so the
@@ -269,8 +270,9 @@ def make_workload(name: str, scale: int | None = None, m: int | None = None, nba
         s, d = er_edges(n, total, gseed)
     else:
         s, d = rmat_edges(int(np.log2(n)), total, gseed)
+    want_hubs = hubs
     hubs = None
-    if "hubs" in cfg:
+    if "hubs" in cfg and want_hubs:
         nh, per = cfg["hubs"]
         if scale is not None:
             per = max(1, min(per, mm // 16))
