@@ -100,12 +100,15 @@ typedef struct {
     double lambda;             /* BINGO_BIAS_F32: amortisation factor lambda > 0 (Section 4.3) */
     uint32_t radix_base;       /* 2 (default; 0 means 2) or 4: one group per base-4 digit position, split into
                                   value sub-groups (Appendix, Fig. base4); base 4 needs integer biases < 2^20 */
-    uint32_t vertex_order;     /* internal vertex numbering: BINGO_ORDER_AUTO (0; by degree when n <= 2^23),
+    uint32_t vertex_order;     /* internal vertex numbering: BINGO_ORDER_AUTO (0; by degree),
                                   BINGO_ORDER_CALLER (the caller's ids) or BINGO_ORDER_DEGREE; every call still
                                   takes and returns the caller's ids (see BINGO_ORDER_*) */
     uint32_t vertex_base;      /* partition graphs (bingo_part_*): global id of local vertex 0; 0 otherwise */
     uint32_t dst_space;        /* partition graphs: destinations are global ids < dst_space; 0 = n (a whole graph) */
+    uint32_t hot_l2_hint;      /* walker loads of the hot vertex records: BINGO_HOT_AUTO (0) or BINGO_HOT_EVICT_LAST
+                                  (an L2 evict-last policy), BINGO_HOT_NORMAL (the default policy) */
 } bingo_config;
+enum { BINGO_HOT_AUTO = 0, BINGO_HOT_EVICT_LAST = 1, BINGO_HOT_NORMAL = 2 };
 
 /* One update record, 16 bytes. */
 typedef struct {

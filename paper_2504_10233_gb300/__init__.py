@@ -45,7 +45,7 @@ class bingo_config(c.Structure):
                 ("update_chunk", c.c_uint32), ("reg_variant", c.c_uint32), ("pool_words", c.c_uint64),
                 ("bias_format", c.c_uint32), ("all_regular", c.c_uint32), ("lambda_", c.c_double),
                 ("radix_base", c.c_uint32), ("vertex_order", c.c_uint32), ("vertex_base", c.c_uint32),
-                ("dst_space", c.c_uint32)]
+                ("dst_space", c.c_uint32), ("hot_l2_hint", c.c_uint32)]
 
 
 class bingo_update_stats(c.Structure):

@@ -119,7 +119,9 @@ struct bingo_graph {
     bingo::DevGraph G{};
     // owned device allocations
     void* d_hdr = nullptr;      // VHot[n]
+    int l2_bytes = 0;           // the device's L2 size (walker cache policy)
     void* d_cold = nullptr;     // VCold[n]
+    void* d_upd = nullptr;      // VUpd[n]
     void* d_order = nullptr;    // internal -> caller vertex id [n] (degree numbering), else null
     void* d_perm = nullptr;     // caller -> internal vertex id [n]
     void* d_pool = nullptr;

@@ -60,30 +60,37 @@ struct VHdr {
     uint8_t lcapa;  // log2(capA) + 1, 0 = no adjacency block
     uint8_t lcaps;  // log2(capS) + 1, 0 = no sparse groups
     uint16_t pad;
+    uint32_t word;  // the hot record's caller-id word as loaded (store_hdr leaves it alone)
 };
 
-constexpr uint32_t HOT_GROUPS = 4;
+// The hot line carries copies of the vertex's two heaviest group pairs (pairs a, b: groups 2a, 2a+1,
+// 2b, 2b+1) and the total weight of every other group, so a draw that falls in those pairs needs no
+// other access.  The cold record holds all 32 groups (the authoritative copy that updates read).
 struct __align__(64) VHot {
     uint32_t adj;   // adjacency block, 32-byte units
     uint32_t deg;
     uint32_t mask;
-    uint32_t word;  // the caller's id of this vertex (path entries of walks); top bit: the cold scan order (cold_summary)
-    uint64_t wcold; // sum of the weights of groups 4-31: with the hot groups, the vertex total
-    uint32_t spare[2];
-    uint2 g[HOT_GROUPS];
+    uint32_t word;  // the caller's id of this vertex (path entries of walks); top bit: the cold scan order (hot_summary)
+    uint64_t wcold; // sum of the weights of the groups outside the hot pairs: with them, the vertex total
+    uint32_t hp;    // the hot pairs: a = hp & 15 (scanned first), b = (hp >> 4) & 15
+    uint32_t spare;
+    uint2 g[4];     // copies of groups 2a, 2a+1, 2b, 2b+1
 };
-struct __align__(32) VCold {
+struct __align__(64) VCold {
+    uint2 g[32];         // every group {|G_k|, ref}
+};
+// Fields that only updates read, in an array of their own.
+struct __align__(16) VUpd {
     uint32_t nsp;
     uint8_t lcapa, lcaps;
     uint16_t pad;
     uint32_t sref;       // sparse-list block, 32-byte units
-    uint32_t spare[5];
-    uint2 g[32 - HOT_GROUPS];
+    uint32_t spare;
 };
 static_assert(sizeof(VHot) == 64, "VHot must be two sectors");
-static_assert(offsetof(VHot, g) == 32, "hot groups fill the second sector");
-static_assert(sizeof(VCold) == 256, "VCold must be eight sectors");
-static_assert(offsetof(VCold, g) == 32, "cold groups start at the second sector");
+static_assert(offsetof(VHot, g) == 32, "hot copies fill the second sector");
+static_assert(sizeof(VCold) == 256, "VCold must be four lines");
+static_assert(sizeof(VUpd) == 16, "VUpd is 16 bytes");
 
 constexpr uint64_t POOL_UNIT_WORDS = 8;  // offsets are stored in 32-byte units
 constexpr uint64_t MAX_POOL_WORDS = (1ull << 32) * POOL_UNIT_WORDS;
@@ -202,6 +209,7 @@ struct DevGraph {
 
     VHot* vh;
     VCold* vc;
+    VUpd* vu;
     Pool pool;
     // edge index (node2vec distance probe): open addressing over (src << 32 | dst) -> live copies
     unsigned long long* eh_key;  // EH_EMPTY = empty
@@ -228,7 +236,7 @@ struct PartEH {
 #ifdef __CUDACC__
 __device__ __forceinline__ VHdr load_hdr(const DevGraph& G, uint64_t v) {
     const VHot& a = G.vh[v];
-    const VCold& b = G.vc[v];
+    const VUpd& b = G.vu[v];
     VHdr h;
     h.adj = words_of(a.adj);
     h.deg = a.deg;
@@ -238,11 +246,12 @@ __device__ __forceinline__ VHdr load_hdr(const DevGraph& G, uint64_t v) {
     h.lcapa = b.lcapa;
     h.lcaps = b.lcaps;
     h.pad = 0;
+    h.word = a.word;
     return h;
 }
 __device__ __forceinline__ void store_hdr(const DevGraph& G, uint64_t v, const VHdr& h) {
     VHot& a = G.vh[v];
-    VCold& b = G.vc[v];
+    VUpd& b = G.vu[v];
     a.adj = ref_of(h.adj);
     a.deg = h.deg;
     a.mask = h.mask;
@@ -263,7 +272,7 @@ __device__ __forceinline__ uint32_t to_caller(const DevGraph& G, uint32_t v) {
 
 // {|G_k|, ref} of group k of vertex v
 __device__ __forceinline__ uint2& grp(const DevGraph& G, uint64_t v, uint32_t k) {
-    return k < HOT_GROUPS ? G.vh[v].g[k] : G.vc[v].g[k - HOT_GROUPS];
+    return G.vc[v].g[k];
 }
 __device__ __forceinline__ uint32_t& cnt_ref(const DevGraph& G, uint64_t v, uint32_t k) { return grp(G, v, k).x; }
 __device__ __forceinline__ uint32_t& gref_ref(const DevGraph& G, uint64_t v, uint32_t k) { return grp(G, v, k).y; }
@@ -311,47 +320,81 @@ __device__ __forceinline__ uint64_t slot_weight(uint32_t c, uint32_t k) {
 __device__ __forceinline__ uint64_t graph_slot_weight(const DevGraph& G, uint32_t c, uint32_t k) {
     return G.base4 ? slot_weight<WM_B4>(c, k) : slot_w(c, k, G.fbits);
 }
-// Order in which a draw that falls beyond the hot groups scans the cold groups.  The walker reads
-// the cold pairs (pairs 2..15, groups 2i and 2i+1) in batches whose loads are issued together, and
-// reads a batch only when the draw lies beyond the earlier ones: upwards, the aligned batches
-// [2, 6), [6, 10), [10, 14), [14, 16); downwards, windows of four consecutive pairs from the highest
-// nonempty cold pair; batches without a nonempty pair are skipped.  Any fixed order gives the same
-// law (Eq. group_prob).  Upwards suits biases whose weight is in the low bits (floor Pareto);
-// uniform biases put half their weight on the top bit, where upwards reads every batch.  The order
-// is a pure function of the counts: downwards iff it reads fewer batches in expectation (each
-// pair's weight times the number of batches read to reach it), ties upwards.  It is kept in the
-// top bit of the hot record's caller-id word (vertex ids are below 2^31).
+// The hot pairs and the order in which a draw that falls beyond them scans the other (cold) pairs.
+// The hot pairs a, b are the two pairs of largest weight W(p_2i) + W(p_2i+1), ranked by the weight's
+// leading 21 bits (equal ranks: the lower pair; a vertex with one nonempty pair takes the lowest other
+// pair as b).  The walker reads the cold pairs
+// in batches whose loads are issued together, and reads a batch only when the draw lies beyond the
+// earlier ones: upwards, the aligned batches [0, 4), [4, 8), [8, 12), [12, 16); downwards, windows
+// of four consecutive pairs from the highest nonempty cold pair; hot pairs and batches without a
+// nonempty pair are skipped.  Any fixed order gives the same law (Eq. group_prob).  The order is a
+// pure function of the counts: downwards iff it reads fewer batches in expectation (each cold
+// pair's weight times the number of batches read to reach it), ties upwards.  It is kept in the top
+// bit of the hot record's caller-id word (vertex ids are below 2^31).
 constexpr uint32_t WORD_DESC = 0x80000000u;
 constexpr uint32_t WORD_ID = 0x7FFFFFFFu;
 #ifdef __CUDACC__
-// The cold total (VHot.wcold, exact) and the cold scan order of a vertex from its 32 slot counts,
-// computed by one whole warp (every lane calls it with its lane id and the count of slot `lane`):
-// lane k weighs slot k,
-// lane i < 16 pair i; batch and window ranks come from ballots; the expected-batch comparison is a
-// sum of weight x (upward rank - downward rank) in binary64, reduced in a fixed shuffle order, so
-// the same counts always give the same order (build, update and the export's check all call this).
-__device__ __forceinline__ void cold_summary(const DevGraph& G, uint32_t c, uint32_t lane, uint64_t& wcold,
-                                             bool& desc) {
+// The hot pairs (hp), the total weight outside them (wcold, exact) and the cold scan order of a
+// vertex from its 32 slot counts, computed by one whole warp (every lane calls it with its lane id and
+// the count of slot `lane`): lane k weighs slot k, lane i < 16 pair i; the arg-maxima, batch and
+// window ranks come from shuffles and ballots; the expected-batch comparison is a sum of weight x
+// (upward rank - downward rank) in binary64, reduced in a fixed shuffle order, so the same counts
+// always give the same result (build, update and the export's check all call this).
+__device__ __forceinline__ void hot_summary(const DevGraph& G, uint32_t c, uint32_t lane, uint64_t& wcold,
+                                            bool& desc, uint32_t& hp) {
     const uint64_t wk = graph_slot_weight(G, c, lane);
-    uint64_t wc = lane >= HOT_GROUPS ? wk : 0ull;
+    uint64_t tot = wk;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) wc += __shfl_xor_sync(0xFFFFFFFFu, wc, o);
-    wcold = wc;
+    for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
     const uint32_t i = lane & 15;
     const uint64_t wp = __shfl_sync(0xFFFFFFFFu, wk, 2 * i) + __shfl_sync(0xFFFFFFFFu, wk, 2 * i + 1);
     const uint32_t cp = __shfl_sync(0xFFFFFFFFu, c, 2 * i) | __shfl_sync(0xFFFFFFFFu, c, 2 * i + 1);
-    const bool ne = lane < 16 && lane >= HOT_GROUPS / 2 && cp != 0;
+    // pair ranks by a 32-bit key: the weight's bit length (7 bits) and the 20 bits below its leading
+    // one, then 15 - i (so equal keys go to the lower pair); the heaviest, then the heaviest of the rest
+    uint32_t key = 0;
+    if (lane < 16) {
+        const uint32_t e = 64u - (uint32_t)__clzll((long long)wp);  // 0 for an empty pair
+        const uint32_t m = e > 21 ? (uint32_t)(wp >> (e - 21)) : (uint32_t)(wp << (21 - e));
+        key = (e << 25) | ((m & 0xFFFFFu) << 5) | (15u - i);
+    }
+    const uint32_t a = 15u - (__reduce_max_sync(0xFFFFFFFFu, key) & 15u);
+    const uint32_t b = 15u - (__reduce_max_sync(0xFFFFFFFFu, lane < 16 && i != a ? key : 0u) & 15u);
+    hp = a | (b << 4);
+    wcold = tot - __shfl_sync(0xFFFFFFFFu, wp, a) - __shfl_sync(0xFFFFFFFFu, wp, b);
+    const bool ne = lane < 16 && i != a && i != b && cp != 0;
     const uint32_t M = __ballot_sync(0xFFFFFFFFu, ne);
     if (!M) { desc = false; return; }
     const uint32_t hi = 31 - __clz(M);
-    const uint32_t b = (i - HOT_GROUPS / 2) / 4, w = (hi - i) / 4;  // meaningful where ne
-    const uint32_t BM = __reduce_or_sync(0xFFFFFFFFu, ne ? 1u << b : 0u);
+    const uint32_t bt = i / 4, w = (hi - i) / 4;  // meaningful where ne
+    const uint32_t BM = __reduce_or_sync(0xFFFFFFFFu, ne ? 1u << bt : 0u);
     const uint32_t WMk = __reduce_or_sync(0xFFFFFFFFu, ne ? 1u << w : 0u);
-    const int ra = __popc(BM & ((2u << b) - 1u)), rd = __popc(WMk & ((2u << w) - 1u));
+    const int ra = __popc(BM & ((2u << bt) - 1u)), rd = __popc(WMk & ((2u << w) - 1u));
     double x = ne ? (double)wp * (double)(ra - rd) : 0.0;
 #pragma unroll
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
     desc = x > 0.0;
+}
+// Slot of the hot line that copies group k (0..3), or 4 if k is not in a hot pair.
+__device__ __forceinline__ uint32_t hot_slot(uint32_t hp, uint32_t k) {
+    const uint32_t p = k >> 1;
+    return p == (hp & 15u) ? (k & 1u) : p == ((hp >> 4) & 15u) ? 2u + (k & 1u) : 4u;
+}
+// Write the hot line of v from the warp's slot counts and refs (lane k: group k), after the groups
+// themselves: the copies of the hot pairs, the cold total, the hot pairs and the scan-order bit
+// (word: the record's caller-id word as it stands).
+__device__ __forceinline__ void write_hot(const DevGraph& G, uint64_t v, uint32_t lane, uint32_t c, uint32_t gref,
+                                          uint32_t word) {
+    uint64_t wc;
+    bool desc;
+    uint32_t hp;
+    hot_summary(G, c, lane, wc, desc, hp);
+    const uint32_t hs = hot_slot(hp, lane);
+    if (hs < 4) G.vh[v].g[hs] = make_uint2(c, gref);
+    if (lane == 0) {
+        G.vh[v].wcold = wc;
+        G.vh[v].hp = hp;
+        G.vh[v].word = (word & WORD_ID) | (desc ? WORD_DESC : 0u);
+    }
 }
 #endif
 // ---- radix base 4 (Appendix): sub-group (digit position i, value v) is slot 3 i + v - 1.

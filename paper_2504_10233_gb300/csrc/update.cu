@@ -366,15 +366,8 @@ __device__ __forceinline__ void write_back(const Team& t, const DevGraph& G, con
                                            unsigned long long* stats) {
     const uint32_t rank = t.rank(), T = t.size();
     for (uint32_t k = rank; k < 32; k += T) grp(G, v, k) = make_uint2(sh.cnt_new[k], (uint32_t)sh.gref_new[k]);
-    if (rank < 32) {  // the team's first warp (the whole team for a warp team)
-        uint64_t wc;
-        bool desc;
-        cold_summary(G, sh.cnt_new[rank], rank, wc, desc);
-        if (rank == 0) {
-            G.vh[v].wcold = wc;
-            G.vh[v].word = (G.vh[v].word & WORD_ID) | (desc ? WORD_DESC : 0u);
-        }
-    }
+    if (rank < 32)  // the team's first warp (the whole team for a warp team): the hot line
+        write_hot(G, v, rank, sh.cnt_new[rank], (uint32_t)sh.gref_new[rank], h1.word);
     if (rank == 0) {
         store_hdr(G, v, h1);
         atomicAdd(stats + S_INS, (unsigned long long)ni);
@@ -806,6 +799,7 @@ __device__ void apply_segment(const Team& t, const DevGraph& G, SegSh& sh, uint3
     h1.lcapa = capa1 ? (uint8_t)(log2_u32(capa1) + 1) : 0;
     h1.lcaps = SPn ? (uint8_t)(log2_u32(caps1) + 1) : 0;
     h1.pad = 0;
+    h1.word = h0.word;
     write_back<REAL>(t, G, sh, v, h1, d0, ni, nd, found, rebuilt, stats);
 }
 
@@ -922,6 +916,7 @@ __device__ void apply_dense_segment(const Team& t, const DevGraph& G, SegSh& sh,
     h1.lcapa = capa1 ? (uint8_t)(log2_u32(capa1) + 1) : 0;
     h1.lcaps = 0;
     h1.pad = 0;
+    h1.word = h0.word;
     write_back<false>(t, G, sh, v, h1, d0, ni, nd, found, 0u, stats);
 }
 
@@ -1036,11 +1031,10 @@ __global__ void k_seg_write(const uint64_t* __restrict__ flag, const uint64_t* _
 // rebuilt together), and a sparse list.
 // The 32 group counts of vertex v, read as whole 16-byte pairs with every load in flight at once.
 __device__ __forceinline__ void load_counts(const DevGraph& G, uint32_t v, uint32_t* cnt) {
-    const uint4* hot = reinterpret_cast<const uint4*>(G.vh[v].g);
     const uint4* cold = reinterpret_cast<const uint4*>(G.vc[v].g);
     uint4 x[16];
 #pragma unroll
-    for (int i = 0; i < 16; i++) x[i] = i < (int)HOT_GROUPS / 2 ? hot[i] : cold[i - HOT_GROUPS / 2];
+    for (int i = 0; i < 16; i++) x[i] = cold[i];
 #pragma unroll
     for (int i = 0; i < 16; i++) {
         cnt[2 * i] = x[i].x;

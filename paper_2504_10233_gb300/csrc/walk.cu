@@ -34,6 +34,7 @@ constexpr uint32_t WF_PAD = 1u;  // pad path rows with 0xFFFFFFFF
 
 struct WalkParams {
     uint64_t nwalkers;
+    uint32_t hot_last;  // hot-line loads with an L2 evict-last policy (hot_policy)
     const uint32_t* starts;
     const uint32_t* lengths;
     const uint8_t* pids;
@@ -106,10 +107,15 @@ __device__ __forceinline__ void walker_stream(const WalkParams& A, uint64_t wid,
 }
 
 // Hot lines are re-read at every visit of their vertex, while member reads and path stores mostly
-// touch a line once: hot-line loads carry an L2 evict-last policy.
-__device__ __forceinline__ uint4 ld_hot(const uint4* q) {
+// touch a line once: hot-line loads carry an L2 evict-last policy (hot_policy), unless the graph's
+// configuration asks for the normal one.
+__device__ __forceinline__ uint64_t hot_policy(uint32_t evict_last) {
     uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    if (evict_last) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    else asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint4 ld_hot(const uint4* q, uint64_t pol) {
     uint4 r;
     asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
         : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
@@ -117,31 +123,33 @@ __device__ __forceinline__ uint4 ld_hot(const uint4* q) {
     return r;
 }
 
-// Hot part of a vertex record: the header, the cold total and groups 0-3 (pairs 0-1), one 64-byte line.
+// Hot part of a vertex record, one 64-byte line: the header, the total weight outside the hot pairs,
+// the hot pairs a, b and copies of their groups.
 struct Sec0 {
     uint32_t adj, deg, mask;
     uint32_t word;   // the caller's id of the vertex, and the cold scan order (WORD_DESC)
-    uint64_t wcold;  // total weight of the cold groups
-    uint4 p0, p1;
+    uint64_t wcold;  // total weight of the groups outside the hot pairs
+    uint32_t hp;     // a = hp & 15, b = (hp >> 4) & 15
+    uint4 p0, p1;    // groups 2a, 2a+1 and 2b, 2b+1
 };
-__device__ __forceinline__ Sec0 ld_sec0(const DevGraph& G, uint32_t v) {
+__device__ __forceinline__ Sec0 ld_sec0(const DevGraph& G, uint32_t v, uint64_t pol) {
     const uint4* q = reinterpret_cast<const uint4*>(G.vh + v);
-    const uint4 a = ld_hot(q);
-    const uint4 b = ld_hot(q + 1);
+    const uint4 a = ld_hot(q, pol);
+    const uint4 b = ld_hot(q + 1, pol);
     Sec0 s;
     s.adj = a.x;
     s.deg = a.y;
     s.mask = a.z;
     s.word = a.w;
     s.wcold = (uint64_t)b.x | ((uint64_t)b.y << 32);
-    s.p0 = ld_hot(q + 2);
-    s.p1 = ld_hot(q + 3);
+    s.hp = b.z;
+    s.p0 = ld_hot(q + 2, pol);
+    s.p1 = ld_hot(q + 3, pol);
     return s;
 }
-// Groups 2i and 2i+1 of vertex v as {c_2i, ref_2i, c_2i+1, ref_2i+1} (16-byte aligned).
+// Groups 2i and 2i+1 of vertex v from its cold record as {c_2i, ref_2i, c_2i+1, ref_2i+1} (16-byte aligned).
 __device__ __forceinline__ uint4 ld_pair(const DevGraph& G, uint32_t v, uint32_t i) {
-    if (i < HOT_GROUPS / 2) return ld_hot(reinterpret_cast<const uint4*>(G.vh + v) + 2 + i);
-    return __ldg(reinterpret_cast<const uint4*>(G.vc[v].g) + (i - HOT_GROUPS / 2));
+    return __ldg(reinterpret_cast<const uint4*>(G.vc[v].g) + i);
 }
 // WM: the weight mode (slot_weight): integer base 2, real biases (every integer group counts 2^8
 // times and slot 31, the second half of pair 15, carries the decimal total itself), or base 4.
@@ -178,34 +186,32 @@ __device__ __forceinline__ bool scan_pair_desc(uint4 x, uint32_t i, uint64_t r, 
     return false;
 }
 
-// Scan order of the groups of a vertex: the hot groups 0-3 ascending, then the cold groups 4-31
-// ascending, or descending when the hot word's WORD_DESC bit is set (cold_summary).  Any fixed order
-// of the inverse CDF draws group k with probability W(p_k) / sum W; every team width uses this one,
-// so all give the same k* for the same r.
-constexpr uint32_t COLD_PAIRS = 0x55555550u;  // pair bits 2i of the cold pairs i = 2..15
+// Scan order of the groups of a vertex: the hot pairs a then b (each pair's groups ascending), then
+// the other pairs ascending, or descending (each pair's groups descending) when the hot word's
+// WORD_DESC bit is set (hot_summary).  Any fixed order of the inverse CDF draws group k with
+// probability W(p_k) / sum W; every team width uses this one, so all give the same k* for the same r.
 
-// T = 1: one lane per walker.  Pairs 0-1 and the total weight of groups 4-31 came with the
-// header, so r is drawn from one 64-byte line.  The cold groups are read only when r falls beyond
-// the hot groups, in the vertex's scan order (cold_summary): upwards in the aligned batches of pairs
-// [2, 6), [6, 10), [10, 14), [14, 16), or downwards in windows of four pairs from the highest nonempty
-// cold pair; the loads of a batch are issued together and empty batches are skipped.
+// T = 1: one lane per walker.  The hot pairs and the total weight outside them came with the header,
+// so r is drawn from one 64-byte line.  The cold pairs are read only when r falls beyond the hot
+// pairs, in the vertex's scan order (hot_summary): upwards in the aligned batches of pairs [0, 4),
+// [4, 8), [8, 12), [12, 16), or downwards in windows of four pairs from the highest nonempty cold
+// pair; the loads of a batch are issued together and batches without a nonempty cold pair are skipped.
 template <int WM>
 __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status) {
-    const uint32_t pb = pair_bits(h.mask);  // pairs holding a nonempty slot
-    const uint64_t whot = pair_w<WM>(h.p0, 0) + pair_w<WM>(h.p1, 1);
+    const uint32_t a = h.hp & 15u, b = (h.hp >> 4) & 15u;
+    const uint64_t whot = pair_w<WM>(h.p0, a) + pair_w<WM>(h.p1, b);
     const uint64_t r = below64(R, whot + h.wcold, status);
     uint64_t acc = 0;
-    if (scan_pair<WM>(h.p0, 0, r, acc, ks, cs, ref)) return;
-    if (scan_pair<WM>(h.p1, 1, r, acc, ks, cs, ref)) return;
-    // one loop for both directions: batch starts i0 = 3, 7, 11, 15 upwards, or top, top - 4, ...
+    if (scan_pair<WM>(h.p0, a, r, acc, ks, cs, ref)) return;
+    if (scan_pair<WM>(h.p1, b, r, acc, ks, cs, ref)) return;
+    // one loop for both directions: batch starts i0 = 0, 4, 8, 12 upwards, or top, top - 4, ...
     // downwards; a downward pair is scanned odd group first (its halves swapped)
     const bool desc = (h.word & WORD_DESC) != 0;
-    const uint32_t cm = pb & COLD_PAIRS;
+    const uint32_t cm = pair_bits(h.mask) & ~((1u << (2 * a)) | (1u << (2 * b)));  // nonempty cold pairs, bits 2i
     const int dir = desc ? -1 : 1;
-    constexpr int HP = HOT_GROUPS / 2;  // first cold pair
 #pragma unroll 1
-    for (int i0 = desc ? (int)((31 - __clz(cm)) >> 1) : HP; desc ? i0 >= HP : i0 < 16; i0 += 4 * dir) {
+    for (int i0 = desc ? (int)((31 - __clz(cm)) >> 1) : 0; desc ? i0 >= 0 : i0 < 16; i0 += 4 * dir) {
         const int low = desc ? i0 - 3 : i0;  // lowest pair of the batch (may be below 0 downwards)
         const uint32_t wbits = low >= 0 ? (cm >> (2 * low)) & 0xFFu : (cm << (-2 * low)) & 0xFFu;
         if (!wbits) continue;
@@ -213,7 +219,7 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const int i = i0 + dir * j;
-            x[j] = (i >= HP && i < 16 && ((pb >> (2 * i)) & 1u)) ? ld_pair(G, v, (uint32_t)i) : make_uint4(0, 0, 0, 0);
+            x[j] = (i >= 0 && i < 16 && ((cm >> (2 * i)) & 1u)) ? ld_pair(G, v, (uint32_t)i) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int j = 0; j < 4; j++) {
@@ -232,9 +238,22 @@ __device__ __forceinline__ void select_group_1(const DevGraph& G, uint32_t v, co
     atomicOr(status, ST_STATE);  // r beyond every group: the cached total disagrees with the counts
 }
 
-// Pair at scan position p (0..15) of a vertex: hot pairs 0-1, then the cold pairs up or down.
-__device__ __forceinline__ uint32_t pair_at(uint32_t p, bool desc) {
-    return (p < HOT_GROUPS / 2 || !desc) ? p : 15 + HOT_GROUPS / 2 - p;
+// Pair at scan position p (0..15) of a vertex: the hot pairs a, b, then the q = p - 2-th of the other
+// pairs, upwards or downwards.
+__device__ __forceinline__ uint32_t pair_at(uint32_t p, uint32_t hp, bool desc) {
+    const uint32_t a = hp & 15u, b = (hp >> 4) & 15u;
+    if (p == 0) return a;
+    if (p == 1) return b;
+    uint32_t lo = min(a, b), hi = max(a, b);
+    if (desc) {
+        const uint32_t t = 15 - lo;
+        lo = 15 - hi;
+        hi = t;
+    }
+    uint32_t c = p - 2;  // rank among the 14 cold pairs in scan order; skip the two hot ones
+    if (c >= lo) c++;
+    if (c >= hi) c++;
+    return desc ? 15 - c : c;
 }
 
 // T = 4: lane t of the team owns scan positions [4t, 4t+4) (pair_at); a two-level shuffle prefix
@@ -248,8 +267,8 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
     uint64_t s = 0;
 #pragma unroll
     for (uint32_t j = 0; j < 4; j++) {
-        const uint32_t i = pair_at(4 * tl + j, desc);
-        if ((pb >> (2 * i)) & 1u) s += pair_w<WM>(ld_pair(G, v, i), i);
+        const uint32_t p = 4 * tl + j, i = pair_at(p, h.hp, desc);
+        if ((pb >> (2 * i)) & 1u) s += pair_w<WM>(p == 0 ? h.p0 : p == 1 ? h.p1 : ld_pair(G, v, i), i);
     }
     uint64_t incl = s;
 #pragma unroll
@@ -273,10 +292,10 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
     if (lane_id() == owner) {
         uint64_t acc = excl;
         for (uint32_t j = 0; j < 4; j++) {
-            const uint32_t p = 4 * tl + j, i = pair_at(p, desc);
+            const uint32_t p = 4 * tl + j, i = pair_at(p, h.hp, desc);
             if (!((pb >> (2 * i)) & 1u)) continue;
-            const uint4 x = ld_pair(G, v, i);
-            if ((p >= HOT_GROUPS / 2 && desc) ? scan_pair_desc<WM>(x, i, r, acc, k_l, c_l, r_l)
+            const uint4 x = p == 0 ? h.p0 : p == 1 ? h.p1 : ld_pair(G, v, i);
+            if ((p >= 2 && desc) ? scan_pair_desc<WM>(x, i, r, acc, k_l, c_l, r_l)
                                  : scan_pair<WM>(x, i, r, acc, k_l, c_l, r_l))
                 break;
         }
@@ -286,18 +305,24 @@ __device__ __forceinline__ void select_group_4(const DevGraph& G, uint32_t v, co
     ref = __shfl_sync(team_mask, r_l, owner);
 }
 
-// T = 32: lane l owns the group at scan position l (slot l, or 35 - l for cold positions scanned
-// downwards); a warp-wide shuffle prefix of W_k = 2^k |G_k| and a ballot of (prefix > r) give k*
+// T = 32: lane l owns the group at scan position l (pair_at(l / 2), its lower group first unless
+// the pair is a cold pair scanned downwards); a warp-wide shuffle prefix of W_k = 2^k |G_k| and a ballot of (prefix > r) give k*
 // at the first set bit.
 template <int WM>
 __device__ __forceinline__ void select_group_32(const DevGraph& G, uint32_t v, const Sec0& h, StepRng& R,
                                                 uint32_t& ks, uint32_t& cs, uint32_t& ref, uint32_t* status,
                                                 uint32_t lane) {
     const bool desc = (h.word & WORD_DESC) != 0;
-    const uint32_t k = (lane < HOT_GROUPS || !desc) ? lane : 31 + HOT_GROUPS - lane;
+    // scan position lane: positions 0-3 the hot pairs' groups, then two positions per cold pair
+    const uint32_t i = pair_at(lane >> 1, h.hp, desc);
+    const uint32_t k = 2 * i + ((lane >= 4 && desc) ? 1u - (lane & 1u) : (lane & 1u));
     uint2 gk = make_uint2(0, 0);
-    if ((h.mask >> k) & 1u)
-        gk = __ldg(k < HOT_GROUPS ? &G.vh[v].g[k] : &G.vc[v].g[k - HOT_GROUPS]);
+    if (lane < 4) {
+        const uint4 x = lane < 2 ? h.p0 : h.p1;
+        gk = (lane & 1u) ? make_uint2(x.z, x.w) : make_uint2(x.x, x.y);
+    } else if ((h.mask >> k) & 1u) {
+        gk = __ldg(&G.vc[v].g[k]);
+    }
     uint64_t incl = slot_weight<WM>(gk.x, k);
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -405,7 +430,7 @@ __device__ __forceinline__ bool walk_step(const DevGraph& G, const WalkParams& A
     }
     hword = NONE32;
     if (kind == BINGO_PPR && R.next() < __ldg(&P->ppr_stop_u32)) return false;
-    const Sec0 h = ld_sec0(G, cur);
+    const Sec0 h = ld_sec0(G, cur, hot_policy(A.hot_last));
     hword = h.word & WORD_ID;
     if (h.deg == 0) return false;
     for (int attempt = 0; attempt < MAX_N2V_TRIES; attempt++) {
@@ -717,6 +742,7 @@ cudaError_t walk_preload(bingo_graph* g, cudaStream_t s) {
 bingo_status walk_launch(bingo_graph* g, const WalkReq& q, cudaStream_t s) {
     WalkParams A;
     memset(&A, 0, sizeof(A));
+    A.hot_last = g->cfg.hot_l2_hint != BINGO_HOT_NORMAL;
     const uint64_t nwalkers = q.nwalkers;
     const uint32_t mode = q.mode, max_steps = q.max_steps;
     A.nwalkers = nwalkers;

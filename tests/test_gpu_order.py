@@ -64,7 +64,7 @@ def test_config_reports_the_numbering(B):
     og = _stress_graph(4)
     offs, dst, w, _ = og.edges()
     args = (og.n, dev(offs.astype(np.uint64)), dev(dst), dev(w))
-    assert B.Graph(*args, max_bits=12).config().vertex_order == B.ORDER_DEGREE  # auto, n <= 2^23
+    assert B.Graph(*args, max_bits=12).config().vertex_order == B.ORDER_DEGREE  # auto
     assert B.Graph(*args, max_bits=12, vertex_order=B.ORDER_CALLER).config().vertex_order == B.ORDER_CALLER
     assert B.Graph(*args, max_bits=12, vertex_order=B.ORDER_DEGREE).config().vertex_order == B.ORDER_DEGREE
     with pytest.raises(B.BingoError):
