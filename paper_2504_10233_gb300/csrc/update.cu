@@ -1099,7 +1099,7 @@ struct SegArgs {
     const uint64_t* nseg_dev;
     uint32_t* small_list;
     uint32_t* big_list;
-    uint32_t* dense_list;         // small dense-only segments (k_apply_dense)
+    uint32_t* dense_flag;         // [segment] 1: a small dense-only segment (k_apply_dense)
     unsigned long long* ndense;   // [0] count, [1] k_apply_dense work queue
     unsigned long long* counts;   // [0] small, [1] big, [2] pool bound
     unsigned long long* queue;    // [0] next small segment, [1] next big segment (k_apply work queues)
@@ -1132,6 +1132,7 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
     unsigned long long bound = 0;
     for (uint64_t sidx = tid; sidx < nseg; sidx += nt) {
+        S.dense_flag[sidx] = 0u;
         const uint32_t a = S.seg_start[sidx], b = S.seg_start[sidx + 1];
         const uint32_t v = (uint32_t)(S.sorted_keys[a] >> (S.B.bn + 1));
         if (v >= G.n) { atomicOr(G.pool.status, ST_INVALID); continue; }
@@ -1150,6 +1151,7 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
         bool dense_only = false;
         bound += pool_bound(G, v, h, ni, b - lo, insbits, &dense_only);
         const bool big = dtot > S.big_slots || (b - a) > 256;
+        if (!big && dense_only) S.dense_flag[sidx] = 1u;
         const bool huge = h.deg >= PRE_MIN_DEG && b > lo;  // deletions at a large vertex: grid-wide candidate scan
         S.gcand_cnt[sidx] = huge ? 0u : NO_PRE;
         if (huge) {
@@ -1158,7 +1160,7 @@ __global__ void k_seg_classify(DevGraph G, SegArgs S) {
             S.huge_nch[pos] = (h.deg + PRE_CHUNK - 1) / PRE_CHUNK;
         }
         if (big) S.big_list[atomicAdd(&S.counts[1], 1ull)] = (uint32_t)sidx;
-        else if (dense_only) S.dense_list[atomicAdd(S.ndense, 1ull)] = (uint32_t)sidx;
+        else if (dense_only) atomicAdd(S.ndense, 1ull);
         else S.small_list[atomicAdd(&S.counts[0], 1ull)] = (uint32_t)sidx;
     }
     if (bound) atomicAdd(&S.counts[2], bound);
@@ -1387,7 +1389,9 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) k_apply_dense(DevGraph G, Se
     __shared__ unsigned long long bstats[S_CONV + 25];
     for (uint32_t i = threadIdx.x; i < S_CONV + 25; i += blockDim.x) bstats[i] = 0;
     __syncthreads();
-    const unsigned long long n = S.ndense[0];
+    // segments in their sorted order, which under the degree numbering puts the largest vertices
+    // (the longest segments) first, so the launch does not end on a few long ones
+    const unsigned long long n = S.ndense[0] ? *S.nseg_dev : 0ull;
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpTeam t;
     for (;;) {
@@ -1395,7 +1399,8 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) k_apply_dense(DevGraph G, Se
         if (lane == 0) i = (*(volatile uint32_t*)G.pool.status & ST_STOP) ? n : atomicAdd(S.ndense + 1, 1ull);
         i = __shfl_sync(FULL, i, 0);
         if (i >= n) break;
-        run_segment<false>(t, G, S, smem.sh[w], S.dense_list[i], smem.sdel[w], SMALL_SDEL, smem.cand[w], SMALL_CAND,
+        if (!S.dense_flag[i]) continue;
+        run_segment<false>(t, G, S, smem.sh[w], (uint32_t)i, smem.sdel[w], SMALL_SDEL, smem.cand[w], SMALL_CAND,
                            &smem.x[w], bstats, true, true);
     }
     __syncthreads();
@@ -1430,23 +1435,41 @@ __global__ void k_eh_apply(DevGraph G, SegArgs S, uint64_t cap, const uint64_t* 
     }
 }
 
-// Make this batch's frees reusable (single block).
-__global__ void k_finalize_pool(DevGraph G) {
+// Make this batch's frees reusable: the free stacks' counts (a class's count goes negative while
+// pops outrun its stack) are reset to zero, every pending block is pushed, and the counts clamped.
+// The pushes run grid-wide with one atomic per size class and warp (warp-aggregated).
+__global__ void k_pool_open(DevGraph G) {
     Pool P = G.pool;
     for (int c = threadIdx.x; c < NCLASS; c += blockDim.x)
         if (P.fcount[c] < 0) P.fcount[c] = 0;
-    __syncthreads();
+}
+__global__ void __launch_bounds__(256) k_pool_push(DevGraph G) {
+    Pool P = G.pool;
     const unsigned long long np = *P.npending;
     const unsigned long long lim = np < P.pcap ? np : P.pcap;
-    for (unsigned long long i = threadIdx.x; i < lim; i += blockDim.x) {
-        const uint64_t x = P.pending[i];
-        const uint32_t c = (uint32_t)(x & 0xFF);
-        const uint64_t off = x >> 8;
-        const long long idx = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&P.fcount[c]), 1ull);
-        if ((uint64_t)idx < P.fcap) P.fstack[(uint64_t)c * P.fcap + (uint64_t)idx] = off;
-        else atomicAdd(P.leaked, (unsigned long long)(8ull << c));
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned long long nt = (unsigned long long)gridDim.x * blockDim.x;
+    // every lane of a warp runs the same trips, so the warp stays converged for match and shuffle
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < lim; b += nt) {
+        const unsigned long long i = b + lane;
+        const bool live = i < lim;
+        const uint64_t x = live ? P.pending[i] : 0ull;
+        const uint32_t c = live ? (uint32_t)(x & 0xFF) : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(FULL, c);
+        const uint32_t leader = __ffs(peers) - 1;
+        unsigned long long base = 0;
+        if (live && lane == leader)
+            base = atomicAdd(reinterpret_cast<unsigned long long*>(&P.fcount[c]), (unsigned long long)__popc(peers));
+        base = __shfl_sync(FULL, base, leader);
+        if (live) {
+            const uint64_t idx = base + __popc(peers & lanemask_lt());
+            if (idx < P.fcap) P.fstack[(uint64_t)c * P.fcap + idx] = x >> 8;
+            else atomicAdd(P.leaked, (unsigned long long)(8ull << c));
+        }
     }
-    __syncthreads();
+}
+__global__ void k_pool_close(DevGraph G) {
+    Pool P = G.pool;
     for (int c = threadIdx.x; c < NCLASS; c += blockDim.x)
         if ((uint64_t)P.fcount[c] > P.fcap) P.fcount[c] = (long long)P.fcap;
     if (threadIdx.x == 0) *P.npending = 0;
@@ -1624,12 +1647,16 @@ static unsigned grid_cap(const bingo_graph* g, uint64_t items, unsigned block, u
     return b ? (unsigned)b : 1u;
 }
 
+static void launch_pool_merge(bingo_graph* g, cudaStream_t s) {
+    k_pool_open<<<1, 64, 0, s>>>(g->G);
+    k_pool_push<<<(unsigned)g->num_sms * 4, 256, 0, s>>>(g->G);
+    k_pool_close<<<1, 64, 0, s>>>(g->G);
+    g->launches += 3;
+}
+
 static bingo_status finish_batch(bingo_graph* g, cudaStream_t s, bingo_update_stats* stats, uint64_t inserts_expected,
                                  bool finalize = true) {
-    if (finalize) {
-        k_finalize_pool<<<1, 1024, 0, s>>>(g->G);
-        g->launches++;
-    }
+    if (finalize) launch_pool_merge(g, s);
     uint32_t status = 0;
     bingo_update_stats tmp;
     bingo_status st = read_stats(g, s, &tmp, &status);
@@ -1745,7 +1772,7 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     uint32_t* seg_start = (uint32_t*)(segid + kc);
     uint32_t* small_list = seg_start + kc + 2;
     uint32_t* big_list = small_list + kc + 2;
-    uint32_t* dense_list = big_list + kc + 2;
+    uint32_t* dense_flag = big_list + kc + 2;
     uint64_t* nseg_dev = (uint64_t*)(ctl + CTL_SCR + 3);
     k_seg_flags<<<grid_cap(g, kc, 256), 256, 0, s>>>(skeys, svals, kc, nkeys_dev, A.bn, A.ups, A.pscan,
                                                      (const unsigned long long*)(ctl + CTL_SCR + 9), A.fbits,
@@ -1764,7 +1791,7 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
     S.nseg_dev = nseg_dev;
     S.small_list = small_list;
     S.big_list = big_list;
-    S.dense_list = dense_list;
+    S.dense_flag = dense_flag;
     S.ndense = (unsigned long long*)(ctl + CTL_SCR + 14);
     CK(cudaMemsetAsync(S.ndense, 0, 16, s), "dense segment count reset");
     S.counts = counts;
@@ -1804,8 +1831,7 @@ static bingo_status enqueue_updates(bingo_graph* g, uint64_t cap, cudaStream_t s
         k_eh_apply<<<grid_cap(g, kc, 256), 256, 0, s>>>(g->G, S, kc, nkeys_dev);
         g->launches++;
     }
-    k_finalize_pool<<<1, 1024, 0, s>>>(g->G);
-    g->launches++;
+    launch_pool_merge(g, s);
     CK(cudaGetLastError(), "update launch");
     return BINGO_OK;
 }
