@@ -2,12 +2,14 @@
 //
 // Device state of a graph (all in HBM):
 //   vh[v]   VHot, 64 bytes: one sector {adjacency block, degree d, nonempty-group mask, the
-//           caller's id of v (path entries), the total weight of groups 4-31}, then groups 0-3 as
-//           {|G_k|, ref} (Eq. wpk: W(p_k) = 2^k |G_k|); ref = destination of the member of a
-//           one-element group, or the group block of a regular/sparse group, else 0.  A walker
-//           step draws its group from this one line whenever the draw falls in groups 0-3.
-//   vc[v]   VCold, 256 bytes: one sector of update-only fields (|S|, log2 capacities, sparse-list
-//           block), then groups 4-31.
+//           caller's id of v (path entries), the total weight outside the hot pairs, the hot pairs
+//           a, b}, then copies of groups 2a, 2a+1, 2b, 2b+1 as {|G_k|, ref} (Eq. wpk: W(p_k) =
+//           2^k |G_k|); ref = destination of the member of a one-element group, or the group block
+//           of a regular/sparse group, else 0.  The hot pairs are the vertex's two heaviest pairs
+//           (hot_summary): a walker step draws its group from this one line whenever the draw
+//           falls in them.
+//   vc[v]   VCold, 256 bytes: all 32 groups (the copy that updates read and write).
+//   vu[v]   VUpd, 16 bytes: update-only fields (|S|, log2 capacities, sparse-list block).
 //   pool    u32 words holding every variable-size block, in power-of-two sizes (offsets stored in
 //           32-byte units):
 //             adjacency   4*capA words: capA x {dst, bias} (8 B, AoS) then capA x u64 edge id
