@@ -45,10 +45,14 @@ def peaks():
 # ------------------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms from before the warm-up (starting the
+    """nvidia-smi clocks and throttle reasons, sampled every PERIOD_MS from before the warm-up (starting the
     sampler costs seconds, which must not fall in the timed region); stop() keeps the samples read
     inside the timed window [mark_start(), mark_end()]."""
 
+    # While nvidia-smi runs, this process's host time over the timed steps grows by about 2.5 s
+    # (7 RMAT-20 steps of 2.3 ms: 2.46 s of wall at 200 ms polling, 2.52 s at 1,000 ms, 0.02 s
+    # without the sampler); the events, and so the value, do not see it
+    PERIOD_MS = 200
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -62,7 +66,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -72,6 +76,13 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append((time.perf_counter(), line.strip()))
+
+    def wait_first(self, timeout=15.0):
+        """Block until nvidia-smi has printed its first sample: its start-up (NVML initialisation) holds
+        driver locks that stall CUDA calls, and must not overlap the timed region."""
+        t_end = time.perf_counter() + timeout
+        while self.proc is not None and not self.lines and time.perf_counter() < t_end:
+            time.sleep(0.05)
 
     def mark_start(self):
         self.t0 = time.perf_counter()
@@ -83,7 +94,7 @@ class ClockSampler:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         if self.t1 is not None:  # one more sample period so the window's last sample is read
-            while time.perf_counter() < self.t1 + 0.25:
+            while time.perf_counter() < self.t1 + self.PERIOD_MS / 1e3 + 0.05:
                 time.sleep(0.05)
         self.proc.terminate()
         try:
@@ -93,7 +104,7 @@ class ClockSampler:
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         lo = self.t0 if self.t0 is not None else -1e300
-        hi = (self.t1 + 0.25) if self.t1 is not None else 1e300
+        hi = (self.t1 + self.PERIOD_MS / 1e3 + 0.05) if self.t1 is not None else 1e300
         inside = [ln for ts, ln in self.lines if lo <= ts <= hi]
         if not inside and self.lines:  # a window shorter than the sampling period: the nearest sample
             mid = 0.5 * (lo + hi) if self.t0 is not None and self.t1 is not None else self.lines[-1][0]
@@ -545,7 +556,7 @@ def run_main(args, name, dev, rank, ws, local, secondary=False):
     sampler = ClockSampler(local)
     if not secondary:
         sampler.start()
-        time.sleep(0.5)  # the sampler's start-up stays out of the timed region
+        sampler.wait_first()  # the sampler's start-up stays out of the timed region
     for i in range(nsteps):
         timed = i >= args.warmup
         if timed and launches0 is None:
@@ -762,6 +773,7 @@ def run_mixed(args):
         timed_walk(100 + i, starts, pids, mode, nw)
     sampler = ClockSampler(0)
     sampler.start()
+    sampler.wait_first()
     launches0 = g.kernel_launches()
     ms, steps = [], 0
     for i in range(args.steps):
@@ -905,6 +917,7 @@ def run_sweep(args):
         if i == args.warmup:
             sampler = ClockSampler(0)
             sampler.start()
+            sampler.wait_first()
             launches0 = g.kernel_launches()
         torch.cuda.synchronize()
         e0, e1, e2 = ev(), ev(), ev()
@@ -1106,6 +1119,7 @@ def run_ablation(args):
             recs_r.append(t(r))
             recs_i.append(t(ri))
         sampler.start()
+        sampler.wait_first()
         w_r, steps_r = _timed_walks(torch, B, real, starts, stride, args.steps, args.warmup, 7, flush, stream)
         w_i, steps_i = _timed_walks(torch, B, integer, starts, stride, args.steps, args.warmup, 7, flush, stream)
         u_r, _ = _timed_batches(torch, real, recs_r, args.warmup, flush, stream)
@@ -1142,6 +1156,7 @@ def run_ablation(args):
         g2 = B.Graph(G.n, t(G.row_ptr), t(G.col), t(w20), max_bits=20)
         g4 = B.Graph(G.n, t(G.row_ptr), t(G.col), t(w20), max_bits=20, radix_base=4)
         sampler.start()
+        sampler.wait_first()
         w_2, steps = _timed_walks(torch, B, g2, starts, stride, args.steps, args.warmup, 7, flush, stream)
         w_4, _ = _timed_walks(torch, B, g4, starts, stride, args.steps, args.warmup, 7, flush, stream)
         u_2, _ = _timed_batches(torch, g2, recs, args.warmup, flush, stream)
@@ -1174,6 +1189,7 @@ def run_ablation(args):
             bs_err = str(e)
         recs = [t(b.records()) for b in wl.batches]
         sampler.start()
+        sampler.wait_first()
         w_ga, steps = _timed_walks(torch, B, ga, starts, stride, args.steps, args.warmup, 7, flush, stream)
         u_ga, conv = _timed_batches(torch, ga, recs, args.warmup, flush, stream)
         mem_bs = w_bs = u_bs = None
