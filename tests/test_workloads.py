@@ -69,6 +69,24 @@ def test_hub_edges():
     assert d.max() < 1 << 12
 
 
+def test_c5_hub_edges_and_the_no_hub_option():
+    """c5 at a small scale: the 64 hubs add their out-edges (capped at m/16 each at reduced scales) on
+    top of the m RMAT edges; hubs=False (a profiling case) leaves them out and nothing else changes."""
+    kw = dict(scale=12, m=1 << 16, nbatch=1, batch=2000)
+    with_h = W.make_workload("c5", **kw)
+    without = W.make_workload("c5", hubs=False, **kw)
+    deg_h = np.diff(with_h.graph.row_ptr.astype(np.int64))
+    deg_n = np.diff(without.graph.row_ptr.astype(np.int64))
+    hubs = with_h.extra["hubs"]
+    assert without.extra["hubs"] is None and len(hubs) == 64
+    assert without.graph.m == 1 << 16 and with_h.graph.m == (1 << 16) + 64 * ((1 << 16) // 16)
+    # the hold-out protocol keeps some hub edges back as insertions, so a hub's initial degree is a
+    # little below its 4,096 generated edges, yet far above any vertex of the plain RMAT part
+    assert deg_h[hubs].min() > deg_n.max() and deg_h[hubs].sum() > 0.9 * 64 * ((1 << 16) // 16)
+    rec = without.batches[0].records()
+    assert (rec[:, 3] == 0).sum() == 1000 and (rec[:, 3] == 1).sum() == 1000
+
+
 def test_hold_out_protocol_batches():
     """c2's stream protocol: the created graph has exactly m edges, each batch holds the stated
     insert/delete counts, insertions are edges held out of the generated set, and every deletion
